@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Time-to-tolerance of the RBRP interpolative decomposition on GB300.
+
+Workload (the headline metric): 100000 x 1000 FP32 near-duplicate Zipf GMM
+(100 N(0, I) centres, Zipf(1.5) cluster sizes, within-cluster N(0, 1e-6 I),
+5% extra N(0, 0.01 I) rows), tol 1e-4 on the squared relative residual,
+b = 64, Philox seed 0.  One step = one full rbrp_id call: Alg. 2 to the
+tolerance, then Alg. 3 (W), with X already resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (Philox problem id =
+rank): the path has no exchange step, so scaling is weak and there is no
+collective on the data path; rank 0 prints max-over-ranks time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ID time-to-tol (ms) at 1e5×1e3, rel err ≤1e-4; % of HBM/TC roofline"
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--w-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--n", type=int, default=100000)
+    ap.add_argument("--d", type=int, default=1000)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU baseline run (0: all rows)")
+    ap.add_argument("--ref-rows", type=int, default=20000, help="row sample per step of the reference arm")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": "zipf_gmm_near_duplicates", "n": a.n, "d": a.d, "dtype_in": "fp32", "clusters": 100,
+            "zipf_s": 1.5, "within_var": 1e-6, "extra_rows": 0.05, "extra_var": 0.01, "tol_sq_rel": a.tol,
+            "block": a.block, "seed": 0, "update": a.precision, "w_solve": a.w_precision,
+            "l2": "inputs larger than L2 (X is %.0f MB, residual copy %.0f MB per step)" % (a.n * a.d * 4 / 1e6,
+                                                                                            a.n * a.d * 4 / 1e6)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j, "measured"
+    return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_leg(a, X, rows, reps=1):
+    """The FP64 oracle as it stands on the first `rows` rows of the workload; returns (ms_scaled, info)."""
+    import numpy as np
+    from oracle import rbrp as O
+    ns = X.shape[0] if rows <= 0 else min(rows, X.shape[0])
+    Xs = np.ascontiguousarray(X[:ns])
+    times = []
+    k = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = O.rbrp_id(Xs, tau=a.tol, b=a.block, seed=0)
+        times.append(time.perf_counter() - t0)
+        k = len(out["S"])
+    ms = 1e3 * min(times)
+    scale = X.shape[0] / ns
+    if ns == X.shape[0]:
+        desc = "the full %d x %d workload, one run of Alg. 2 + Alg. 3 in FP64 (numpy/LAPACK threads)" % X.shape
+    else:
+        desc = ("first %d of %d rows of the same workload (same recipe, tol, b, seed), full Alg. 2 + Alg. 3 in "
+                "FP64; time scaled x%.2f to all rows (the O(n d k) work is linear in n)" % (ns, X.shape[0], scale))
+    info = {"sample": desc,
+            "sample_ms": ms, "sample_k": k, "cores": os.cpu_count()}
+    return ms * scale, info
+
+
+def run_reference(a):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    from paper_2309_16002_gb300 import workloads as WL
+    X = WL.zipf_gmm(n=a.n, d=a.d)
+    for _ in range(a.warmup):
+        cpu_oracle_leg(a, X, a.ref_rows)
+    vals = []
+    info = None
+    for _ in range(a.steps):
+        v, info = cpu_oracle_leg(a, X, a.ref_rows)
+        vals.append(v)
+    ms = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ws_n, rank, local = dist_init()
+    if ws_n > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0 or ws_n == 1:
+        ge.build()
+    if ws_n > 1:
+        torch.distributed.barrier()
+    ge.build()
+    from paper_2309_16002_gb300 import rbrp as G
+    from paper_2309_16002_gb300 import workloads as WL
+
+    X = WL.zipf_gmm(n=a.n, d=a.d)
+    Xd = torch.from_numpy(X).to(dev)
+    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=rank)
+    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, rank, "random", a.w_precision)
+    wsp = G.Workspace(a.n, a.d, opts, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return G.rbrp_id(Xd, a.tol, workspace=wsp, stream=stream, **kw)
+
+    for _ in range(a.warmup):
+        out = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws_n > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    G.rbrp_profile_begin()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ks = []
+    for _ in range(a.steps):
+        out = step()
+        ks.append(out["k"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = G.rbrp_profile_end()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1)
+    if ws_n > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms = elapsed / a.steps
+
+    # roofline of the fused residual update (Alg. 2 lines 12/16), events on the launch stream
+    n, d = a.n, a.d
+    blocks = prof["blocks"]
+    k_tot = prof["skeletons"]
+    r_bytes = 4 if a.precision != "fp64" else 8
+    upd_bytes = blocks * (2 * n * d * r_bytes + 16 * n) + n * k_tot * r_bytes
+    upd_ms = prof["update_ms"]
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM))
+    upd_gbs = upd_bytes / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+    k_step = k_tot / max(1, a.steps)
+    w_flops = a.steps * n * k_step * k_step
+    w_ms = prof["wsolve_ms"]
+    kernels = {"update": {"ms_per_step": upd_ms / a.steps, "launches": prof["update_launches"],
+                          "real_blocks": blocks, "GB/s": upd_gbs},
+               "w_solve": {"ms_per_step": w_ms / a.steps, "TFLOP/s": (w_flops / (w_ms / 1e3) / 1e12) if w_ms else None},
+               "other_ms_per_step": ms - (upd_ms + w_ms) / a.steps}
+    roofline = {"bound": "hbm", "kernel": "k_update_tf32" if a.precision == "tf32" else "update_simt",
+                "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
+                "peak_kind": peak_kind, "traffic": None,
+                "bytes_per_launch": upd_bytes / max(1, blocks),
+                "note": "achieved = (2 n d s + 16 n) per block + n k s for Lhat, over CUDA-event time of all "
+                        "update launches in the timed region (including no-op launches queued after the stop)"}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws_n, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"tf32": "tf32+f64", "fp32": "f32+f64", "fp64": "f64"}[a.precision], "data": "synthetic",
+                "config": workload_config(a), "k": ks[-1], "blocks_per_step": blocks / max(1, a.steps),
+                "rel_err_sq": out["rel_err_sq"], "roofline": roofline, "kernels": kernels,
+                "gpu_launches": prof["launches"], "clocks": clk}
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    if not a.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        kc = min(a.n, a.d)
+        skel_h = torch.empty(kc, dtype=torch.int64).pin_memory()
+        W_h = torch.empty((a.n, kc), dtype=torch.float64).pin_memory()
+        hws = G.HostWorkspace(a.n, a.d, 0, opts, dev)
+        del wsp
+        torch.cuda.empty_cache()
+        o2 = G.rbrp_id_host(Xh, a.tol, workspace=hws, skel_out=skel_h, W_out=W_h, stream=stream, **kw)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.e2e_steps):
+            o2 = G.rbrp_id_host(Xh, a.tol, workspace=hws, skel_out=skel_h, W_out=W_h, stream=stream, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
+        if ws_n > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        if line is not None:
+            line["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": a.n * a.d * 4,
+                           "d2h_bytes_per_step": o2["k"] * 8 + a.n * o2["k"] * 8}
+
+    if line is not None and ws_n == 1 and not a.no_cpu_baseline:
+        v, info = cpu_oracle_leg(a, X, a.cpu_rows)
+        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": info["cores"], "kind": "oracle",
+                                "sample": info["sample"]}
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if ws_n > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * rbrp.h -- C ABI of the GB300 (sm_103a) implementation of Robust Blockwise
+ * Random Pivoting (RBRP) for the row interpolative decomposition X ~ W X_S.
+ *
+ * Method: Dong, Chen, Martinsson, Pearce, "Robust Blockwise Random Pivoting:
+ * Fast and Accurate Adaptive Interpolative Decomposition", arXiv 2309.16002.
+ *   - problem statement (row ID, skeleton indices S, interpolation matrix W):
+ *     Eq. (1.1); skeletonization error E_X(S): Eq. (1.2)
+ *   - skeleton selection: Alg. 2 (RBRP) with the robust blockwise filtering
+ *     remark of Sec. 4 (truncated local CPQR, tau_b = 1/b) and the blockwise
+ *     greedy remark (RBGP) for the greedy sampler
+ *   - interpolation matrix: Alg. 3, W(S,:) = I, W(rest,:) = L2 L1^{-1}
+ *
+ * All functions are plain C: pointers, sizes and a CUDA stream handle.  No
+ * function allocates device memory: the caller owns X, every output buffer
+ * and the workspace (size from rbrp_workspace_size).  The library keeps no
+ * state between calls.
+ *
+ * Errors: every function returns an rbrp_status.  On RBRP_EINVAL /
+ * RBRP_EWORKSPACE nothing was launched.  On RBRP_ECUDA the CUDA error is
+ * available from rbrp_last_cuda_error().  On RBRP_ENONFINITE (a NaN or Inf in
+ * X, or a non-finite residual) and RBRP_ETIMEOUT the outputs are unspecified.
+ * RBRP_ENOTCONVERGED means k reached k_max (or min(n, d)) before the
+ * tolerance: S and W are valid for that k.
+ */
+#ifndef RBRP_H
+#define RBRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st *rbrp_stream_t;
+
+typedef enum {
+  RBRP_OK = 0,
+  RBRP_EINVAL = 1,          /* bad argument (sizes, pointers, options)            */
+  RBRP_ENOMEM = 2,          /* reserved: the library never allocates              */
+  RBRP_ECUDA = 3,           /* a CUDA runtime call or launch failed               */
+  RBRP_ENONFINITE = 4,      /* NaN/Inf in X or in the residual                    */
+  RBRP_ENOTCONVERGED = 5,   /* |S| hit k_max or min(n, d) before the tolerance    */
+  RBRP_ETIMEOUT = 6,        /* a bounded device wait gave up                      */
+  RBRP_EWORKSPACE = 7       /* workspace pointer misaligned or too small          */
+} rbrp_status;
+
+/* Arithmetic of the residual-update contraction (the O(n d b') step). */
+typedef enum {
+  RBRP_FP64 = 0,   /* residual R and every step in FP64 (CUDA-core DFMA)          */
+  RBRP_TF32 = 1,   /* R in FP32, update on tcgen05 tensor cores (TF32 in, FP32    */
+                   /* accumulate); sampler keys, CGS2 Gram corrections, the b x b */
+                   /* filter and Q' stay FP64                                     */
+  RBRP_FP32 = 2    /* R in FP32, update on CUDA cores in FP32 (same FP64 parts)   */
+} rbrp_precision;
+
+typedef enum {
+  RBRP_SAMPLER_RANDOM = 0,  /* Alg. 2 line 5: sample ~ d/||d||_1 without replacement */
+  RBRP_SAMPLER_GREEDY = 1   /* blockwise greedy remark (Sec. 4): top-b of d          */
+} rbrp_sampler;
+
+typedef enum {
+  RBRP_W_FP64 = 0,          /* Alg. 3 triangular solve in FP64                      */
+  RBRP_W_FP32 = 1           /* same solve in FP32 (for the TF32 path)               */
+} rbrp_w_precision;
+
+typedef struct {
+  int32_t precision;    /* rbrp_precision                                        */
+  int32_t block;        /* b, 1 <= b <= 256 (Alg. 2 input (c))                    */
+  double tau_b;         /* < 0: 1/b_t (the paper's choice); 0: plain BRP; else
+                           a fixed filter tolerance in [0, 1] (Alg. 2 input (d))  */
+  int64_t k_max;        /* <= 0: min(n, d); else caps |S|.  With tol < 0 the call
+                           runs in fixed-rank mode and stops at |S| = k_max.      */
+  uint64_t seed;        /* Philox4x64-10 key word 0                               */
+  uint64_t problem;     /* Philox4x64-10 key word 1 (problem id)                  */
+  int32_t sampler;      /* rbrp_sampler                                           */
+  int32_t w_precision;  /* rbrp_w_precision                                       */
+} rbrp_opts;
+
+typedef struct {
+  int64_t k;            /* number of skeletons |S|                                */
+  int64_t blocks;       /* number of blocks t run by Alg. 2                       */
+  double d0;            /* ||d0||_1 = ||X||_F^2                                  */
+  double d_final;       /* ||d||_1 at exit = ||X - L Q^T||_F^2 (Sec. 5.1 proof)   */
+  double rel_err_sq;    /* d_final / d0, the quantity tested against tol          */
+} rbrp_result;
+
+/* Fill *o with the defaults: TF32, b = 64, tau_b = 1/b_t, k_max = min(n, d),
+ * seed 0, problem 0, random sampler, W in FP64. */
+void rbrp_default_opts(rbrp_opts *o);
+
+/* Bytes of device workspace rbrp_id needs for an n x d problem with options o
+ * (residual copy of X, L, Q, the norms d and the per-block buffers). */
+rbrp_status rbrp_workspace_size(int64_t n, int64_t d, const rbrp_opts *o, size_t *bytes);
+
+/*
+ * rbrp_id -- rank-adaptive row ID of X by Alg. 2 followed by Alg. 3.
+ *
+ * X          device, row-major n x d, leading dimension ldx >= d (elements),
+ *            FP64 if x_is_fp64 else FP32.  Read only.
+ * tol        tau of Alg. 2: stop once ||d||_1 <= tol * ||d0||_1, i.e. the
+ *            squared relative residual ||X - L Q^T||_F^2 / ||X||_F^2 <= tol.
+ *            tol < 0 selects fixed-rank mode (stop at |S| = k_max).
+ * workspace  device, >= rbrp_workspace_size bytes, 256-byte aligned; scratch
+ *            only, contents undefined on return.
+ * skel       device int64[k_cap] (k_cap = k_max or min(n, d)): S in
+ *            acceptance order (block order, pivot order within a block).
+ * W          device FP64, row-major n x k_cap with leading dimension ldw >=
+ *            k_cap; column j belongs to skel[j]; only columns < k are written.
+ * res        host; filled on return.
+ * stream     all device work is ordered on this stream; the call returns after
+ *            the stream has finished the work it queued (res is host data).
+ */
+rbrp_status rbrp_id(const void *X, int x_is_fp64, int64_t n, int64_t d, int64_t ldx,
+                    double tol, const rbrp_opts *o, void *workspace, size_t ws_bytes,
+                    int64_t *skel, double *W, int64_t ldw, rbrp_result *res,
+                    rbrp_stream_t stream);
+
+/* Bytes of device workspace rbrp_id_host needs: rbrp_workspace_size plus room
+ * for X and W on the device. */
+rbrp_status rbrp_host_workspace_size(int64_t n, int64_t d, int x_is_fp64, const rbrp_opts *o,
+                                     size_t *bytes);
+
+/*
+ * rbrp_id_host -- rbrp_id on HOST buffers: copies X (host, row-major n x d,
+ * leading dimension d) to the device, runs rbrp_id, copies S and W back.
+ * skel_host: int64[k_cap]; W_host: FP64 n x k_cap row-major (ldw = k_cap),
+ * columns >= k left untouched.  Pinned host memory makes the copies
+ * asynchronous; pageable memory works but is slower.
+ */
+rbrp_status rbrp_id_host(const void *X_host, int x_is_fp64, int64_t n, int64_t d, double tol,
+                         const rbrp_opts *o, void *workspace, size_t ws_bytes,
+                         int64_t *skel_host, double *W_host, rbrp_result *res,
+                         rbrp_stream_t stream);
+
+/*
+ * Profiling counters (instrumentation; no counterpart in the paper).  Between
+ * rbrp_profile_begin() and rbrp_profile_end() the library counts every kernel
+ * it launches and brackets each residual-update launch (Alg. 2 lines 12/16)
+ * and each W solve (Alg. 3) with CUDA events recorded on the caller's stream.
+ * rbrp_profile_end synchronises those events, fills *out and stops counting.
+ * Process-wide; not thread-safe; calls outside a begin/end pair cost nothing.
+ */
+typedef struct {
+  int64_t launches;         /* kernels launched by the library                   */
+  int64_t update_launches;  /* residual-update launches timed                    */
+  double update_ms;         /* summed event time of those launches               */
+  int64_t wsolve_calls;     /* W solves timed                                    */
+  double wsolve_ms;         /* summed event time of the W solves                 */
+  int64_t blocks;           /* Alg. 2 blocks run (sum over calls)                */
+  int64_t skeletons;        /* skeletons accepted (sum over calls)               */
+} rbrp_profile;
+
+void rbrp_profile_begin(void);
+rbrp_status rbrp_profile_end(rbrp_profile *out);
+
+/* Human-readable name of a status code (static string). */
+const char *rbrp_status_string(rbrp_status s);
+
+/* The cudaError_t value behind the last RBRP_ECUDA returned on this thread. */
+int rbrp_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBRP_H */

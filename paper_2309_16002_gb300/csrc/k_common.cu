@@ -1,0 +1,785 @@
+// SIMT kernels of the RBRP block loop (Alg. 2) and of the interpolation matrix
+// (Alg. 3): initial norms, the Philox exponential-race sampler, the gather of
+// candidate rows, a split-K GEMM used for CGS2 / Gram / FP64 update products,
+// the pivoted-Cholesky form of the robust blockwise filter, row triangular
+// solves that build Q', the norm pass and the block finalisation.
+//
+// All per-block kernels take their sizes from the device State and return at
+// once when State::done is set, so a block is a fixed launch sequence.
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "rbrp_internal.cuh"
+
+namespace rbrp {
+
+// ============================================================================
+// Alg. 2 line 2: d0(i) = ||x_i||^2, copy of X into the residual R.
+// One warp per row; per-CTA partial sums in a fixed order (deterministic).
+// ============================================================================
+template <typename TX, typename TR>
+__global__ void __launch_bounds__(256) k_init_norms(const TX* __restrict__ X, long long n, long long d,
+                                                    long long ldx, TR* __restrict__ R, long long ldr,
+                                                    double* __restrict__ dvec, int* __restrict__ mark,
+                                                    double* __restrict__ partials) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double wsum[8];
+  double mine = 0.0;
+  for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
+    const TX* x = X + i * ldx;
+    TR* r = R + i * ldr;
+    double s = 0.0;
+    for (long long j = lane; j < ldr; j += 32) {
+      TR v = (j < d) ? (TR)x[j] : (TR)0;
+      r[j] = v;
+      const double dv = (double)v;
+      s = fma(dv, dv, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      dvec[i] = s;
+      mark[i] = 0;
+    }
+    mine += s;
+  }
+  if (lane == 0) wsum[warp] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_init_norms(const void* X, int x_is_fp64, long long n, long long d, long long ldx,
+                              void* R, int r_is_fp64, long long ldr, double* dvec, int* mark,
+                              double* partials, int nparts, State* st, cudaStream_t s) {
+  (void)st;
+  dim3 grid(nparts), block(256);
+  if (x_is_fp64 && r_is_fp64)
+    k_init_norms<double, double><<<grid, block, 0, s>>>((const double*)X, n, d, ldx, (double*)R, ldr, dvec, mark, partials);
+  else if (x_is_fp64)
+    k_init_norms<double, float><<<grid, block, 0, s>>>((const double*)X, n, d, ldx, (float*)R, ldr, dvec, mark, partials);
+  else if (r_is_fp64)
+    k_init_norms<float, double><<<grid, block, 0, s>>>((const float*)X, n, d, ldx, (double*)R, ldr, dvec, mark, partials);
+  else
+    k_init_norms<float, float><<<grid, block, 0, s>>>((const float*)X, n, d, ldx, (float*)R, ldr, dvec, mark, partials);
+  return counted(cudaGetLastError());
+}
+
+// Deterministic warp sum of partials[0..np) (fixed lane assignment and tree).
+__device__ __forceinline__ double warp_fixed_sum(const double* partials, int np) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < np; i += 32) s += partials[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__device__ __forceinline__ void stop_test(State* st) {
+  const bool cap = st->k >= st->k_cap;
+  const bool tol_met = (st->tau >= 0.0) && !(st->D > st->tau * st->D0);
+  st->done = (cap || tol_met) ? 1 : 0;
+}
+
+__global__ void k_finish_init(const double* __restrict__ partials, int np, State* st, double tau, double tau_b,
+                              long long k_cap) {
+  const double D0 = warp_fixed_sum(partials, np);
+  if (threadIdx.x == 0) {
+    st->tau = tau;
+    st->tau_b = tau_b;
+    st->k_cap = k_cap;
+    st->D0 = D0;
+    st->D = D0;
+    st->k = 0;
+    st->t = 0;
+    st->b_t = 0;
+    st->bp = 0;
+    st->bp_pad = 0;
+    st->status = 0;
+    if (!isfinite(D0)) {
+      st->status = RBRP_ENONFINITE;
+      st->done = 1;
+    } else {
+      stop_test(st);
+    }
+  }
+}
+
+cudaError_t launch_finish_init(const double* partials, int nparts, State* st, double tau, double tau_b,
+                               long long k_cap, cudaStream_t s) {
+  k_finish_init<<<1, 32, 0, s>>>(partials, nparts, st, tau, tau_b, k_cap);
+  return counted(cudaGetLastError());
+}
+
+// ============================================================================
+// Alg. 2 line 5: S_t ~ d / ||d||_1 without replacement, as an exponential race:
+// key kappa_i = -log(u_i) / d_i over eligible rows (d_i > 0; accepted rows
+// have d_i = 0), the b_t smallest in ascending (kappa, i) order.  The greedy
+// sampler (blockwise greedy remark) uses key -d_i.  Selection is a tree of
+// CTA-wide bitonic sorts: every CTA sorts 2048 (key, row) pairs and keeps its
+// b smallest, until one CTA is left.
+// ============================================================================
+struct Pair {
+  unsigned long long key;
+  long long idx;
+};
+
+__device__ __forceinline__ bool pair_less(const Pair& a, const Pair& b) {
+  return (a.key < b.key) || (a.key == b.key && a.idx < b.idx);
+}
+
+__global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict__ dvec, long long n,
+                                                       const Pair* __restrict__ in, long long n_in,
+                                                       Pair* __restrict__ out, int b, int greedy,
+                                                       unsigned long long seed, unsigned long long problem,
+                                                       long long* __restrict__ S_t, State* st, int first,
+                                                       int last) {
+  if (st->done) return;
+  __shared__ Pair sh[kSortChunk];
+  const unsigned long long block_no = (unsigned long long)st->t + 1ULL;  // the paper's t
+  const long long base = (long long)blockIdx.x * kSortChunk;
+  for (int e = threadIdx.x; e < kSortChunk; e += blockDim.x) {
+    const long long gidx = base + e;
+    Pair p{kIneligible, LLONG_MAX};
+    if (first) {
+      if (gidx < n) {
+        const double di = dvec[gidx];
+        if (di > 0.0) {
+          double key;
+          if (greedy) {
+            key = -di;
+          } else {
+            const double u = philox_uniform((unsigned long long)gidx, block_no, seed, problem);
+            key = -log(u) / di;
+          }
+          p.key = orderable(key);
+        }
+        p.idx = gidx;
+      }
+    } else if (gidx < n_in) {
+      p = in[gidx];
+    }
+    sh[e] = p;
+  }
+  __syncthreads();
+  // bitonic sort, ascending by (key, idx); 1024 threads x 1 compare-exchange per stage
+  for (int k = 2; k <= kSortChunk; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int t = threadIdx.x;
+      const int i = (t / j) * 2 * j + (t % j);
+      const int l = i + j;
+      const bool up = ((i & k) == 0);
+      Pair a = sh[i], c = sh[l];
+      const bool swap = up ? pair_less(c, a) : pair_less(a, c);
+      if (swap) {
+        sh[i] = c;
+        sh[l] = a;
+      }
+      __syncthreads();
+    }
+  }
+  if (!last) {
+    for (int e = threadIdx.x; e < b; e += blockDim.x) out[(long long)blockIdx.x * b + e] = sh[e];
+    return;
+  }
+  __shared__ int nfin;
+  if (threadIdx.x == 0) nfin = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < b; e += blockDim.x)
+    if (sh[e].key != kIneligible) atomicAdd(&nfin, 1);
+  __syncthreads();
+  long long bt = nfin;
+  if (bt > b) bt = b;
+  const long long room = st->k_cap - st->k;
+  if (bt > room) bt = room;
+  if (bt < 0) bt = 0;
+  for (int e = threadIdx.x; e < bt; e += blockDim.x) S_t[e] = sh[e].idx;
+  if (threadIdx.x == 0) {
+    st->b_t = bt;
+    if (bt == 0) st->done = 1;
+  }
+}
+
+size_t sample_scratch_pairs(long long n, int b) {
+  const long long g0 = (n + kSortChunk - 1) / kSortChunk;
+  return (size_t)(g0 * b + 1);
+}
+
+cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
+                          unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
+                          State* st, cudaStream_t s) {
+  long long groups = (n + kSortChunk - 1) / kSortChunk;
+  Pair* bufs[2] = {(Pair*)cand_a, (Pair*)cand_b};
+  int cur = 0;
+  k_sample_level<<<(unsigned)groups, 1024, 0, s>>>(dvec, n, nullptr, 0, bufs[cur], b, greedy, seed, problem,
+                                                   S_t, st, 1, groups == 1 ? 1 : 0);
+  cudaError_t e = counted(cudaGetLastError());
+  if (e != cudaSuccess) return e;
+  while (groups > 1) {
+    const long long n_in = groups * b;
+    groups = (n_in + kSortChunk - 1) / kSortChunk;
+    k_sample_level<<<(unsigned)groups, 1024, 0, s>>>(dvec, n, bufs[cur], n_in, bufs[cur ^ 1], b, greedy, seed,
+                                                     problem, S_t, st, 0, groups == 1 ? 1 : 0);
+    e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+    cur ^= 1;
+  }
+  return cudaSuccess;
+}
+
+// ============================================================================
+// Alg. 2 line 6 (first half): V = R(S_t, :) in FP64.
+// ============================================================================
+template <typename TR>
+__global__ void k_gather(const TR* __restrict__ R, long long ldr, const long long* __restrict__ S_t,
+                         double* __restrict__ V, long long ldv, long long d, const State* st) {
+  if (st->done) return;
+  const long long i = blockIdx.y;
+  if (i >= st->b_t) return;
+  const TR* r = R + S_t[i] * ldr;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (long long)gridDim.x * blockDim.x)
+    V[i * ldv + j] = (double)r[j];
+}
+
+cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t, double* V,
+                          long long ldv, long long d, int b, const State* st, cudaStream_t s) {
+  dim3 grid((unsigned)((d + 255) / 256), (unsigned)b);
+  if (r_is_fp64)
+    k_gather<double><<<grid, 256, 0, s>>>((const double*)R, ldr, S_t, V, ldv, d, st);
+  else
+    k_gather<float><<<grid, 256, 0, s>>>((const float*)R, ldr, S_t, V, ldv, d, st);
+  return counted(cudaGetLastError());
+}
+
+// ============================================================================
+// Split-K SIMT GEMM: C = alpha A B + beta C on strided views, sizes from the
+// device.  64 x 64 tile, 256 threads, 4 x 4 outputs per thread, K step 16.
+// TACC is the product/accumulation type (the operands are converted to it
+// when staged); the epilogue combines in double.
+// ============================================================================
+template <typename TA, typename TB, typename TC, typename TACC>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int splits) {
+  if (g.st && g.st->done) return;
+  const long long M = dim_val(g.M), N = dim_val(g.N), K = dim_val(g.K);
+  const long long m0 = (long long)blockIdx.y * kGemmTile, n0 = (long long)blockIdx.x * kGemmTile;
+  if (m0 >= M || n0 >= N) return;
+  const TA* A = (const TA*)g.A.base + dim_val(g.A.off);
+  const TB* B = (const TB*)g.B.base + dim_val(g.B.off);
+  TC* C = (TC*)g.C.base + dim_val(g.C.off);
+  long long kc = (K + splits - 1) / splits;
+  kc = (kc + 15) / 16 * 16;
+  const long long kb = (long long)blockIdx.z * kc;
+  const long long ke = (kb + kc < K) ? kb + kc : K;
+
+  __shared__ TACC As[16][kGemmTile];
+  __shared__ TACC Bs[16][kGemmTile];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  TACC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (TACC)0;
+
+  const bool a_kmajor = (g.A.cs == 1);
+  const bool b_nmajor = (g.B.cs == 1);
+  for (long long k0 = kb; k0 < ke; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int r, c;
+      if (a_kmajor) { r = e >> 4; c = e & 15; } else { r = e & 63; c = e >> 6; }
+      const long long gm = m0 + r, gk = k0 + c;
+      As[c][r] = (gm < M && gk < ke) ? (TACC)A[gm * g.A.rs + gk * g.A.cs] : (TACC)0;
+      int rb, cb;
+      if (b_nmajor) { rb = e >> 6; cb = e & 63; } else { rb = e & 15; cb = e >> 4; }
+      const long long hk = k0 + rb, hn = n0 + cb;
+      Bs[rb][cb] = (hk < ke && hn < N) ? (TACC)B[hk * g.B.rs + hn * g.B.cs] : (TACC)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      TACC a[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (splits == 1) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long gm = m0 + ty + 16 * i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long gn = n0 + tx + 16 * j;
+        if (gn >= N) continue;
+        TC* cp = C + gm * g.C.rs + gn * g.C.cs;
+        double v = g.alpha * (double)acc[i][j];
+        if (g.beta != 0.0) v += g.beta * (double)(*cp);
+        *cp = (TC)v;
+      }
+    }
+  } else {
+    TACC* P = (TACC*)g.partial + (long long)blockIdx.z * g.pm * g.pn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long gm = m0 + ty + 16 * i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long gn = n0 + tx + 16 * j;
+        if (gn < N) P[gm * g.pn + gn] = acc[i][j];
+      }
+    }
+  }
+}
+
+template <typename TC, typename TACC>
+__global__ void k_gemm_reduce(GemmArgs g, int splits) {
+  if (g.st && g.st->done) return;
+  const long long M = dim_val(g.M), N = dim_val(g.N);
+  TC* C = (TC*)g.C.base + dim_val(g.C.off);
+  const TACC* P = (const TACC*)g.partial;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / N, j = e % N;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += (double)P[(long long)z * g.pm * g.pn + i * g.pn + j];
+    TC* cp = C + i * g.C.rs + j * g.C.cs;
+    double v = g.alpha * s;
+    if (g.beta != 0.0) v += g.beta * (double)(*cp);
+    *cp = (TC)v;
+  }
+}
+
+template <typename TA, typename TB, typename TC, typename TACC>
+cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, cudaStream_t s) {
+  if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
+  if (splits < 1) splits = 1;
+  dim3 grid((unsigned)((Nmax + kGemmTile - 1) / kGemmTile), (unsigned)((Mmax + kGemmTile - 1) / kGemmTile),
+            (unsigned)splits);
+  k_gemm<TA, TB, TC, TACC><<<grid, 256, 0, s>>>(g, splits);
+  cudaError_t e = counted(cudaGetLastError());
+  if (e != cudaSuccess || splits == 1) return e;
+  long long tot = Mmax * Nmax;
+  unsigned rb = (unsigned)((tot + 255) / 256);
+  if (rb > 4096) rb = 4096;
+  k_gemm_reduce<TC, TACC><<<rb, 256, 0, s>>>(g, splits);
+  return counted(cudaGetLastError());
+}
+
+template cudaError_t launch_gemm<double, double, double, double>(const GemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_gemm<float, float, float, float>(const GemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_gemm<double, double, double, float>(const GemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_gemm<float, double, float, float>(const GemmArgs&, long long, long long, int, cudaStream_t);
+
+// ============================================================================
+// Alg. 2 lines 7-9 and the robust blockwise filtering remark (Sec. 4):
+// pivoted QR of V^T with truncation at the first i where the trailing mass
+// ||R_V(i:, i:)||_F^2 falls below tau_b ||R_V||_F^2.  On the GPU this is the
+// pivoted Cholesky factorisation of the Gram matrix G = V V^T (the same
+// pivots and R_V diagonal in exact arithmetic): the Schur-complement diagonal
+// is each remaining candidate's residual norm^2 and its sum is the trailing
+// mass.  One CTA.  pivoted = 0 gives a plain Cholesky (for CholQR2).
+// ============================================================================
+__global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ G, long long ldg,
+                                               double* __restrict__ Lc, long long ldl, double* __restrict__ Lw,
+                                               int* __restrict__ perm, const long long* __restrict__ S_t,
+                                               long long* __restrict__ skel, int* __restrict__ mark, State* st,
+                                               int pivoted) {
+  if (st->done) return;
+  __shared__ double diag[kMaxBlock];
+  __shared__ int alive[kMaxBlock];
+  __shared__ int s_piv;
+  __shared__ double s_total, s_pv;
+  __shared__ int s_stop;
+  __shared__ int s_perm[kMaxBlock];
+  const int m = pivoted ? (int)st->b_t : (int)st->bp;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < m; j += blockDim.x) {
+    diag[j] = G[(long long)j * ldg + j];
+    alive[j] = 1;
+  }
+  __syncthreads();
+  // total = ||V||_F^2 (fixed-order sum)
+  if (tid < 32) {
+    double s = 0.0;
+    for (int j = tid; j < m; j += 32) s += diag[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) s_total = s;
+  }
+  __syncthreads();
+  double tau_b = st->tau_b;
+  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+  int bp = 0;
+  for (int i = 0; i < m; ++i) {
+    // trailing mass and argmax (ties to the smallest candidate position)
+    double v = -DBL_MAX;
+    int vi = INT_MAX;
+    double msum = 0.0;
+    if (tid < 32) {
+      for (int j = tid; j < m; j += 32) {
+        if (!alive[j]) continue;
+        msum += diag[j];
+        const bool better = pivoted ? (diag[j] > v || (diag[j] == v && j < vi)) : (j == i);
+        if (better) { v = diag[j]; vi = j; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        msum += __shfl_xor_sync(0xffffffffu, msum, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+        if (ov > v || (ov == v && oi < vi)) { v = ov; vi = oi; }
+      }
+      if (tid == 0) {
+        s_piv = vi;
+        s_pv = v;
+        int stop = 0;
+        if (pivoted && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
+        if (vi == INT_MAX || !(v > 0.0)) stop = 1;
+        s_stop = stop;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_piv;
+    const double pivval = sqrt(s_pv);
+    // column i of the factor for every remaining candidate j (Lw is candidate-indexed)
+    for (int j = tid; j < m; j += blockDim.x) {
+      if (!alive[j]) continue;
+      if (j == p) {
+        Lw[(long long)j * kMaxBlock + i] = pivval;
+        continue;
+      }
+      double sacc = G[(long long)j * ldg + p];
+      for (int l = 0; l < i; ++l) sacc -= Lw[(long long)j * kMaxBlock + l] * Lw[(long long)p * kMaxBlock + l];
+      const double lji = sacc / pivval;
+      Lw[(long long)j * kMaxBlock + i] = lji;
+      diag[j] -= lji * lji;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      alive[p] = 0;
+      s_perm[i] = p;
+      if (perm) perm[i] = p;
+    }
+    __syncthreads();
+    bp = i + 1;
+  }
+  __syncthreads();
+  // pivot-order factor Lc (bp x bp, lower triangular)
+  for (int e = tid; e < bp * bp; e += blockDim.x) {
+    const int i = e / bp, l = e % bp;
+    Lc[(long long)i * ldl + l] = (l <= i) ? Lw[(long long)s_perm[i] * kMaxBlock + l] : 0.0;
+  }
+  if (pivoted) {
+    const long long k = st->k;
+    const int tno = (int)(st->t + 1);
+    for (int i = tid; i < bp; i += blockDim.x) {
+      const long long row = S_t[s_perm[i]];
+      skel[k + i] = row;
+      mark[row] = tno;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (pivoted) {
+      st->bp = bp;
+      st->bp_pad = (bp + 15) / 16 * 16;
+      if (bp == 0) st->done = 1;
+    } else if (bp < m) {
+      st->status = RBRP_ENONFINITE;  // Gram of Q' lost positive definiteness
+      st->done = 1;
+    }
+  }
+}
+
+cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
+                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+  (void)b;
+  // Lw (candidate-indexed factor, kMaxBlock x kMaxBlock) lives right after Lc in the workspace
+  double* Lw = Lc + (long long)kMaxBlock * ldl;
+  k_pchol<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, 1);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b, State* st,
+                        cudaStream_t s) {
+  (void)b;
+  double* Lw = Lc + (long long)kMaxBlock * ldl;
+  k_pchol<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, nullptr, nullptr, nullptr, nullptr, st, 0);
+  return counted(cudaGetLastError());
+}
+
+// ============================================================================
+// Q' rows by forward substitution: Y(i,:) = (V(perm[i],:) - sum_{l<i} Lc(i,l) Y(l,:)) / Lc(i,i),
+// i < b'.  With V_perm = Lc Y and Lc lower triangular, Y has orthonormal rows
+// spanning the accepted candidates in pivot order (Y_i in span of the first i
+// pivots), which keeps L1 lower triangular.  One thread per column.
+// ============================================================================
+__global__ void k_trsm_rows(const double* __restrict__ Lc, long long ldl, const int* __restrict__ perm,
+                            const double* __restrict__ V, long long ldv, double* __restrict__ Ybase, DimRef y_off,
+                            long long ldy, long long d, const State* st) {
+  if (st->done) return;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const int bp = (int)st->bp;
+  double* Y = Ybase + dim_val(y_off);
+  for (int i = 0; i < bp; ++i) {
+    const int src = perm ? perm[i] : i;
+    double s = V[(long long)src * ldv + c];
+    for (int l = 0; l < i; ++l) s -= Lc[(long long)i * ldl + l] * Y[(long long)l * ldy + c];
+    Y[(long long)i * ldy + c] = s / Lc[(long long)i * ldl + i];
+  }
+}
+
+cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V, long long ldv,
+                             double* Y, DimRef y_off, long long ldy, long long d, int b, const State* st,
+                             cudaStream_t s) {
+  (void)b;
+  k_trsm_rows<<<(unsigned)((d + 31) / 32), 32, 0, s>>>(Lc, ldl, perm, V, ldv, Y, y_off, ldy, d, st);
+  return counted(cudaGetLastError());
+}
+
+// ============================================================================
+// FP32 copies of the new basis rows for the low-precision update:
+// Qp (b'_pad x ldp, rows = basis vectors) and QpT (d x ldpt, transposed).
+// Rows >= b' and columns >= d are zero so padded MMA tiles add nothing.
+// ============================================================================
+__global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* __restrict__ Qp, long long ldp,
+                          float* __restrict__ QpT, long long ldpt, long long d, int bmax, const State* st) {
+  if (st->done) return;
+  const long long k = st->k;
+  const int bp = (int)st->bp;
+  const long long tot = (long long)bmax * ldp;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ldp);
+    const long long j = e % ldp;
+    const float v = (i < bp && j < d) ? (float)Qt[(k + i) * ldq + j] : 0.0f;
+    Qp[(long long)i * ldp + j] = v;
+    if (j < d && QpT) QpT[j * ldpt + i] = v;
+  }
+}
+
+cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, long long ldp, float* QpT, long long ldpt,
+                           long long d, int b, const State* st, cudaStream_t s) {
+  long long tot = (long long)b * ldp;
+  unsigned g = (unsigned)((tot + 255) / 256);
+  if (g > 2048) g = 2048;
+  k_qp_lowp<<<g, 256, 0, s>>>(Qt, ldq, Qp, ldp, QpT, ldpt, d, b, st);
+  return counted(cudaGetLastError());
+}
+
+// ============================================================================
+// Alg. 2 line 16 (residual form): d_i = ||R_i||^2; rows accepted in this block
+// are zeroed (R_i = 0, d_i = 0).  One warp per row, fixed-order partials.
+// ============================================================================
+template <typename TR>
+__global__ void __launch_bounds__(256) k_norms_zero(TR* __restrict__ R, long long ldr, long long n, long long d,
+                                                    const int* __restrict__ mark, double* __restrict__ dvec,
+                                                    double* __restrict__ partials, const State* st) {
+  if (st->done) return;
+  const int tno = (int)(st->t + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double wsum[8];
+  double mine = 0.0;
+  for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
+    TR* r = R + i * ldr;
+    double s = 0.0;
+    if (mark[i] == tno) {
+      for (long long j = lane; j < d; j += 32) r[j] = (TR)0;
+    } else {
+      for (long long j = lane; j < d; j += 32) {
+        const double v = (double)r[j];
+        s = fma(v, v, s);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane == 0) dvec[i] = s;
+    mine += s;
+  }
+  if (lane == 0) wsum[warp] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d, const int* mark,
+                              double* dvec, double* partials, int nparts, const State* st, cudaStream_t s) {
+  if (r_is_fp64)
+    k_norms_zero<double><<<nparts, 256, 0, s>>>((double*)R, ldr, n, d, mark, dvec, partials, st);
+  else
+    k_norms_zero<float><<<nparts, 256, 0, s>>>((float*)R, ldr, n, d, mark, dvec, partials, st);
+  return counted(cudaGetLastError());
+}
+
+// Alg. 2 line 3 after a block: D = ||d||_1, k += b', t += 1, stopping test.
+__global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st) {
+  if (st->done) return;
+  const double D = warp_fixed_sum(partials, np);
+  if (threadIdx.x == 0) {
+    st->D = D;
+    st->k += st->bp;
+    st->t += 1;
+    if (!isfinite(D)) {
+      st->status = RBRP_ENONFINITE;
+      st->done = 1;
+    } else {
+      stop_test(st);
+    }
+  }
+}
+
+cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s) {
+  k_finalize_block<<<1, 32, 0, s>>>(partials, nparts, st);
+  return counted(cudaGetLastError());
+}
+
+// ============================================================================
+// Alg. 3 pieces: column copies, L1 = L(S, :), per-row triangular solve on a
+// column block, and W(S, :) = I.
+// ============================================================================
+template <typename TL, typename TW>
+__global__ void k_copy_cols(const TL* __restrict__ L, long long ldl, long long n, long long c0, long long c1,
+                            TW* __restrict__ W, long long ldw) {
+  const long long w = c1 - c0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * w; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / w, j = c0 + e % w;
+    W[i * ldw + j] = (TW)L[i * ldl + j];
+  }
+}
+
+static unsigned grid_for(long long tot) {
+  long long g = (tot + 255) / 256;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+cudaError_t launch_copy_cols_to_f64(const void* L, int l_is_fp64, long long ldl, long long n, long long c0,
+                                    long long c1, double* W, long long ldw, cudaStream_t s) {
+  if (c1 <= c0 || n <= 0) return cudaSuccess;
+  const unsigned g = grid_for(n * (c1 - c0));
+  if (l_is_fp64)
+    k_copy_cols<double, double><<<g, 256, 0, s>>>((const double*)L, ldl, n, c0, c1, W, ldw);
+  else
+    k_copy_cols<float, double><<<g, 256, 0, s>>>((const float*)L, ldl, n, c0, c1, W, ldw);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_copy_cols_to_f32(const void* L, int l_is_fp64, long long ldl, long long n, long long c0,
+                                    long long c1, float* W, long long ldw, cudaStream_t s) {
+  if (c1 <= c0 || n <= 0) return cudaSuccess;
+  const unsigned g = grid_for(n * (c1 - c0));
+  if (l_is_fp64)
+    k_copy_cols<double, float><<<g, 256, 0, s>>>((const double*)L, ldl, n, c0, c1, W, ldw);
+  else
+    k_copy_cols<float, float><<<g, 256, 0, s>>>((const float*)L, ldl, n, c0, c1, W, ldw);
+  return counted(cudaGetLastError());
+}
+
+template <typename TL>
+__global__ void k_gather_rows(const TL* __restrict__ L, long long ldl, const long long* __restrict__ rows, long long k,
+                              double* __restrict__ out, long long ldo) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / k, j = e % k;
+    out[i * ldo + j] = (double)L[rows[i] * ldl + j];
+  }
+}
+
+cudaError_t launch_gather_rows_f64(const void* L, int l_is_fp64, long long ldl, const long long* rows, long long k,
+                                   double* out, long long ldo, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const unsigned g = grid_for(k * k);
+  if (l_is_fp64)
+    k_gather_rows<double><<<g, 256, 0, s>>>((const double*)L, ldl, rows, k, out, ldo);
+  else
+    k_gather_rows<float><<<g, 256, 0, s>>>((const float*)L, ldl, rows, k, out, ldo);
+  return counted(cudaGetLastError());
+}
+
+// W(i, J) <- W(i, J) L1(J, J)^{-1} for a column block J = [j0, j0 + nb) (L1 lower
+// triangular): w_j = (rhs_j - sum_{m > j} w_m L1(m, j)) / L1(j, j), j descending.
+template <typename T>
+__global__ void __launch_bounds__(128) k_trsm_cols(T* __restrict__ W, long long ldw, long long n, long long j0, int nb,
+                                                   const double* __restrict__ L1, long long ld1) {
+  __shared__ T Ls[64][65];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int a = e / nb, c = e % nb;
+    Ls[a][c] = (T)L1[(j0 + a) * ld1 + j0 + c];
+  }
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T w[64];
+  T* row = W + i * ldw + j0;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) w[j] = (j < nb) ? row[j] : (T)0;
+#pragma unroll
+  for (int j = 63; j >= 0; --j) {
+    if (j >= nb) continue;
+    T s = w[j];
+#pragma unroll
+    for (int m = j + 1; m < 64; ++m)
+      if (m < nb) s -= w[m] * Ls[m][j];
+    w[j] = s / Ls[j][j];
+  }
+#pragma unroll
+  for (int j = 0; j < 64; ++j)
+    if (j < nb) row[j] = w[j];
+}
+
+template <typename T>
+cudaError_t launch_trsm_cols(T* W, long long ldw, long long n, long long j0, int nb, const double* L1, long long ld1,
+                             cudaStream_t s) {
+  if (n <= 0 || nb <= 0) return cudaSuccess;
+  k_trsm_cols<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(W, ldw, n, j0, nb, L1, ld1);
+  return counted(cudaGetLastError());
+}
+template cudaError_t launch_trsm_cols<double>(double*, long long, long long, long long, int, const double*, long long,
+                                              cudaStream_t);
+template cudaError_t launch_trsm_cols<float>(float*, long long, long long, long long, int, const double*, long long,
+                                             cudaStream_t);
+
+// W(S, :) = I_k exactly; with W32 set, the FP32 solve result is first widened into W.
+__global__ void k_w_finish(double* __restrict__ W, long long ldw, const float* __restrict__ W32, long long ldw32,
+                           long long n, long long k, const long long* __restrict__ skel) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / k, j = e % k;
+    if (W32) W[i * ldw + j] = (double)W32[i * ldw32 + j];
+  }
+}
+__global__ void k_w_identity(double* __restrict__ W, long long ldw, long long k, const long long* __restrict__ skel) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / k, j = e % k;
+    W[skel[i] * ldw + j] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long long ldw32, long long n, long long k,
+                            const long long* skel, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  if (W32) {
+    k_w_finish<<<grid_for(n * k), 256, 0, s>>>(W, ldw, W32, ldw32, n, k, skel);
+    cudaError_t e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+  }
+  k_w_identity<<<grid_for(k * k), 256, 0, s>>>(W, ldw, k, skel);
+  return counted(cudaGetLastError());
+}
+
+}  // namespace rbrp

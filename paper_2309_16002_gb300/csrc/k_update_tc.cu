@@ -1,0 +1,446 @@
+// Fused residual update of RBRP on Blackwell tensor cores (sm_103a).
+//
+// Alg. 2 lines 12 and 16 in the residual form: for every 128-row tile of R,
+//   Lhat = R_tile Q'^T            (GEMM 1, K = d, N = b'_pad)
+//   R_tile <- R_tile - Lhat Q'    (GEMM 2, K = b'_pad, N = d in chunks)
+//   d_i = ||R_i||^2, rows accepted in this block set to 0,
+//   Lhat written to L(:, k : k + b').
+// Operands are staged by TMA (128-byte swizzle) and multiplied by tcgen05.mma
+// kind::tf32 with FP32 accumulators in tensor memory.  Lhat goes TMEM ->
+// registers -> (global L, shared memory A operand of GEMM 2).  The R tile is
+// read twice (GEMM 1 and the subtraction); the second read is meant to hit L2.
+//
+// Roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 owns TMEM and
+// lane 0 issues the MMAs, warps 2-5 (128 threads, one row each) run the
+// epilogues and the TMA stores.  Every mbarrier wait is bounded: after the
+// limit the CTA records RBRP_ETIMEOUT in the State, stops issuing work, waits
+// briefly for copies in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "rbrp_internal.cuh"
+
+namespace rbrp {
+namespace tc {
+
+constexpr int BM = 128;           // rows per tile (MMA M)
+constexpr int BK1 = 32;           // FP32 elements per 128-byte swizzle row
+constexpr int NB2 = 64;           // d-columns per GEMM-2 chunk (MMA N)
+constexpr int S1 = 4;             // GEMM-1 pipeline stages
+constexpr int S3 = 2;             // GEMM-2 / epilogue stages
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kD2Col = 128;  // D2 double buffer at TMEM columns 128 and 192
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+template <int BMAX>
+struct Cfg {
+  static constexpr int A1 = BM * BK1 * 4;
+  static constexpr int B1 = BMAX * BK1 * 4;
+  static constexpr int ST1 = A1 + B1;
+  static constexpr int R3 = (NB2 / 32) * BM * 128;
+  static constexpr int B2A = NB2 * 128;  // one 32-wide K atom of the GEMM-2 B tile
+  static constexpr int B2 = (BMAX / 32) * B2A;
+  static constexpr int ST3 = R3 + B2;
+  static constexpr int P = (S1 * ST1 > S3 * ST3) ? S1 * ST1 : S3 * ST3;
+  static constexpr int A2A = BM * 128;   // one 32-wide K atom of Lhat
+  static constexpr int A2 = (BMAX / 32) * A2A;
+  static constexpr int BAR_OFF = P + A2;
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; on timeout raises the CTA-wide abort flag.  Returns false once aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ kernel
+template <int BMAX>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_update_tf32(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
+                  const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
+                  long long d, const int* __restrict__ mark, double* __restrict__ dvec,
+                  double* __restrict__ partials, State* st) {
+  using C = Cfg<BMAX>;
+  if (st->done) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sb = smem_u32(smem);
+  const uint32_t sA2 = sb + C::P;
+  const uint32_t sBar = sb + C::BAR_OFF;
+  auto full1 = [&](int s) { return sBar + 8u * s; };
+  auto empty1 = [&](int s) { return sBar + 8u * (S1 + s); };
+  auto full3 = [&](int s) { return sBar + 8u * (2 * S1 + s); };
+  auto empty3 = [&](int s) { return sBar + 8u * (2 * S1 + S3 + s); };
+  const uint32_t d1_full = sBar + 8u * (2 * S1 + 2 * S3);
+  const uint32_t a2_ready = d1_full + 8u;
+  auto d2_full = [&](int b) { return a2_ready + 8u + 8u * b; };
+  auto d2_empty = [&](int b) { return a2_ready + 24u + 8u * b; };
+  auto epi_done = [&](int s) { return a2_ready + 40u + 8u * s; };  // S3 barriers
+  const uint32_t red_bar = a2_ready + 40u + 8u * S3;
+  uint32_t* tmem_slot = (uint32_t*)(smem + C::BAR_OFF + 8 * (2 * S1 + 2 * S3 + 7 + S3));
+
+  __shared__ int s_abort;
+  __shared__ double s_red[4];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long row0 = (long long)blockIdx.x * BM;
+  const long long kcol = st->k;
+  const int bp = (int)st->bp;
+  const int N1 = (int)st->bp_pad;
+  const int tno = (int)(st->t + 1);
+  const int nK1 = (int)((d + BK1 - 1) / BK1);
+  const int nC = (int)((d + NB2 - 1) / NB2);
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < S1; ++s) {
+      mbar_init(full1(s), 1);
+      mbar_init(empty1(s), 1);
+    }
+    for (int s = 0; s < S3; ++s) {
+      mbar_init(full3(s), 1);
+      mbar_init(empty3(s), 2);
+    }
+    mbar_init(d1_full, 1);
+    mbar_init(a2_ready, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(d2_full(b), 1);
+      mbar_init(d2_empty(b), 128);
+    }
+    for (int s = 0; s < S3; ++s) mbar_init(epi_done(s), 128);
+    mbar_init(red_bar, 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+  volatile int* abort = &s_abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      const uint32_t bytes1 = (uint32_t)C::ST1;
+      for (int kc = 0; kc < nK1; ++kc) {
+        const int s = kc % S1;
+        const uint32_t ph = (uint32_t)(kc / S1) & 1u;
+        if (!mbar_wait(empty1(s), ph ^ 1u, abort)) break;
+        mbar_expect_tx(full1(s), bytes1);
+        tma_load_2d(sb + s * C::ST1, &tmR, full1(s), kc * BK1, (int)row0);
+        tma_load_2d(sb + s * C::ST1 + C::A1, &tmQ, full1(s), kc * BK1, 0);
+      }
+      // phase-3 buffers alias the phase-1 ring: reuse only after GEMM 1 has drained it
+      if (mbar_wait(d1_full, 0, abort)) {
+        for (int c = 0; c < nC; ++c) {
+          const int s = c % S3;
+          const uint32_t ph = (uint32_t)(c / S3) & 1u;
+          if (!mbar_wait(empty3(s), ph ^ 1u, abort)) break;
+          mbar_expect_tx(full3(s), (uint32_t)C::ST3);
+          const uint32_t base = sb + s * C::ST3;
+#pragma unroll
+          for (int q = 0; q < NB2 / 32; ++q) tma_load_2d(base + q * (BM * 128), &tmR, full3(s), c * NB2 + q * 32, (int)row0);
+#pragma unroll
+          for (int a = 0; a < BMAX / 32; ++a) tma_load_2d(base + C::R3 + a * C::B2A, &tmQT, full3(s), a * 32, c * NB2);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t id1 = idesc_tf32(BM, N1);
+      for (int kc = 0; kc < nK1; ++kc) {
+        const int s = kc % S1;
+        const uint32_t ph = (uint32_t)(kc / S1) & 1u;
+        if (!mbar_wait(full1(s), ph, abort)) break;
+        tc_after();
+        const uint32_t a = sb + s * C::ST1, b = a + C::A1;
+#pragma unroll
+        for (int kk = 0; kk < BK1 / 8; ++kk)
+          mma_tf32(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), id1, (kc | kk) != 0 ? 1u : 0u);
+        mma_commit(empty1(s));
+      }
+      mma_commit(d1_full);
+      if (mbar_wait(a2_ready, 0, abort)) {
+        tc_after();
+        const uint32_t id2 = idesc_tf32(BM, NB2);
+        const int nk2 = N1 / 8;
+        for (int c = 0; c < nC; ++c) {
+          const int s = c % S3;
+          const uint32_t ph = (uint32_t)(c / S3) & 1u;
+          const int buf = c & 1;
+          const uint32_t bph = (uint32_t)(c >> 1) & 1u;
+          if (!mbar_wait(full3(s), ph, abort)) break;
+          if (!mbar_wait(d2_empty(buf), bph ^ 1u, abort)) break;
+          tc_after();
+          const uint32_t dt = tmem + kD2Col + (uint32_t)(buf * NB2);
+          const uint32_t b2 = sb + s * C::ST3 + C::R3;
+          for (int q = 0; q < nk2; ++q) {
+            const int a = q >> 2, kk = q & 3;
+            mma_tf32(dt, sdesc(sA2 + a * C::A2A + kk * 32), sdesc(b2 + a * C::B2A + kk * 32), id2, q != 0 ? 1u : 0u);
+          }
+          mma_commit(empty3(s));
+          mma_commit(d2_full(buf));
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: 128 threads, thread <-> row
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const int et = threadIdx.x - 64;
+    const long long row = row0 + r;
+    const bool in = row < n;
+    const bool marked = in && (mark[row] == tno);
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    double nrm = 0.0;
+    if (mbar_wait(d1_full, 0, abort)) {
+      tc_after();
+      for (int cb = 0; cb * 32 < N1; ++cb) {
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(cb * 32), v);
+        tmem_wait_ld();
+        if (in) {
+          float* lrow = L + row * ldl + kcol + cb * 32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (cb * 32 + j < bp) lrow[j] = __uint_as_float(v[j]);
+        }
+        uint8_t* a2row = smem + C::P + cb * C::A2A + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch)
+          *(float4*)(a2row + ((ch ^ (r & 7)) << 4)) =
+              make_float4(__uint_as_float(v[4 * ch]), __uint_as_float(v[4 * ch + 1]), __uint_as_float(v[4 * ch + 2]),
+                          __uint_as_float(v[4 * ch + 3]));
+      }
+    }
+    fence_async_smem();
+    tc_before();
+    mbar_arrive(a2_ready);
+    for (int c = 0; c < nC; ++c) {
+      const int s = c % S3;
+      const uint32_t ph = (uint32_t)(c / S3) & 1u;
+      const int buf = c & 1;
+      const uint32_t bph = (uint32_t)(c >> 1) & 1u;
+      if (!mbar_wait(full3(s), ph, abort)) break;
+      if (!mbar_wait(d2_full(buf), bph, abort)) break;
+      tc_after();
+#pragma unroll
+      for (int q4 = 0; q4 < NB2 / 32; ++q4) {
+        uint32_t u[32];
+        tmem_ld32(tmem + lane_base + kD2Col + (uint32_t)(buf * NB2 + q4 * 32), u);
+        tmem_wait_ld();
+        uint8_t* rrow = smem + s * C::ST3 + q4 * (BM * 128) + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          float4* p = (float4*)(rrow + ((ch ^ (r & 7)) << 4));
+          float4 x = *p;
+          x.x -= __uint_as_float(u[4 * ch]);
+          x.y -= __uint_as_float(u[4 * ch + 1]);
+          x.z -= __uint_as_float(u[4 * ch + 2]);
+          x.w -= __uint_as_float(u[4 * ch + 3]);
+          if (marked) x = make_float4(0.f, 0.f, 0.f, 0.f);
+          nrm = fma((double)x.x, (double)x.x, nrm);
+          nrm = fma((double)x.y, (double)x.y, nrm);
+          nrm = fma((double)x.z, (double)x.z, nrm);
+          nrm = fma((double)x.w, (double)x.w, nrm);
+          *p = x;
+        }
+      }
+      tc_before();
+      mbar_arrive(d2_empty(buf));
+      fence_async_smem();
+      mbar_arrive(epi_done(s));
+      if (et == 0) {
+        // every epilogue thread has written its row of this chunk (bounded wait)
+        if (!mbar_wait(epi_done(s), ph, abort)) break;
+        const uint32_t base = sb + s * C::ST3;
+#pragma unroll
+        for (int q4 = 0; q4 < NB2 / 32; ++q4) tma_store_2d(&tmR, base + q4 * (BM * 128), c * NB2 + q4 * 32, (int)row0);
+        tma_commit();
+        tma_wait_read0();
+        mbar_arrive(empty3(s));
+      }
+    }
+    if (in) dvec[row] = marked ? 0.0 : nrm;
+    double t = in ? nrm : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_red[q] = t;
+    mbar_arrive(red_bar);
+    if (et == 0) {
+      if (mbar_wait(red_bar, 0, abort)) partials[blockIdx.x] = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
+      tma_wait_all0();
+    }
+  }
+
+  tc_before();
+  __syncthreads();
+  if (s_abort) {
+    // let copies already in flight land before the shared memory is released
+    for (int i = 0; i < 64; ++i) __nanosleep(1000);
+    if (threadIdx.x == 0) {
+      st->status = RBRP_ETIMEOUT;
+      st->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer, long long row_bytes, int box_inner,
+              int box_outer) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BMAX>
+cudaError_t launch_bmax(float* R, long long ldr, long long n, long long d, const float* Qp, long long ldp,
+                        const float* QpT, long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
+                        double* partials, const State* st, cudaStream_t s) {
+  using C = Cfg<BMAX>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_update_tf32<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap mR, mQ, mQT;
+  if (!make_map(&mR, R, d, n, ldr * 4, 32, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mQ, Qp, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+  if (!make_map(&mQT, QpT, ldpt, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((n + BM - 1) / BM);
+  k_update_tf32<BMAX><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQT, L, ldl, n, d, mark, dvec, partials,
+                                                      const_cast<State*>(st));
+  return counted(cudaGetLastError());
+}
+
+}  // namespace tc
+
+int update_tf32_parts(long long n) { return (int)((n + tc::BM - 1) / tc::BM); }
+
+cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp, long long ldp,
+                               const float* QpT, long long ldpt, float* L, long long ldl, const int* mark,
+                               double* dvec, double* partials, int nparts, const State* st, int bmax,
+                               cudaStream_t s) {
+  (void)nparts;
+  if (bmax <= 32)
+    return tc::launch_bmax<32>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+  if (bmax <= 64)
+    return tc::launch_bmax<64>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+  if (bmax <= 128)
+    return tc::launch_bmax<128>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace rbrp

@@ -1,0 +1,582 @@
+// Host orchestration of RBRP (Alg. 2) and the ID (Alg. 3) behind the C ABI of
+// include/rbrp.h.  No device memory is allocated here: the caller's workspace
+// is carved into the buffers below.  One block of Alg. 2 is a fixed sequence of
+// launches whose sizes live in the device State; the host reads the State back
+// once per group of blocks to see whether the stopping test has fired (blocks
+// queued after that return at once).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rbrp_internal.cuh"
+
+namespace rbrp {
+
+long long g_kernel_launches = 0;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+// ---------------------------------------------------------------- profiling (rbrp_profile_*)
+struct EventPool {
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  cudaError_t next_pair(cudaEvent_t* a, cudaEvent_t* b) {
+    while (ev.size() < used + 2) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev.push_back(e);
+    }
+    *a = ev[used];
+    *b = ev[used + 1];
+    used += 2;
+    return cudaSuccess;
+  }
+};
+
+struct Profile {
+  bool on = false;
+  long long launches0 = 0;
+  EventPool upd, wsv;
+  long long blocks = 0, skel = 0;
+};
+Profile g_prof;
+
+// Records an event pair around `body` on stream s when profiling is on.
+template <typename F>
+cudaError_t timed(EventPool& pool, cudaStream_t s, F&& body) {
+  if (!g_prof.on) return body();
+  cudaEvent_t a, b;
+  cudaError_t e = pool.next_pair(&a, &b);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventRecord(a, s)) != cudaSuccess) return e;
+  if ((e = body()) != cudaSuccess) return e;
+  return cudaEventRecord(b, s);
+}
+
+struct Plan {
+  long long n, d, k_cap;
+  int b, prec, r64, l64, w32, greedy;
+  long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32;
+  int nparts;
+  int s_coef, s_apply, s_gram, s_upd1, s_upd2;
+  size_t pm, pn;  // split-K partial buffer extents (elements per split)
+  size_t partial_elems;
+  size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
+      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_L1, off_W32, total;
+};
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+int splits_for(long long M, long long N, long long K) {
+  const long long tiles = ((M + kGemmTile - 1) / kGemmTile) * ((N + kGemmTile - 1) / kGemmTile);
+  long long s = (304 + tiles - 1) / std::max(1LL, tiles);
+  const long long kmax = std::max(1LL, (K + 63) / 64);
+  s = std::min(s, kmax);
+  s = std::max(1LL, std::min(s, 64LL));
+  return (int)s;
+}
+
+rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
+  if (!o || n <= 0 || d <= 0) return RBRP_EINVAL;
+  if (o->block < 1 || o->block > kMaxBlock) return RBRP_EINVAL;
+  if (o->precision < RBRP_FP64 || o->precision > RBRP_FP32) return RBRP_EINVAL;
+  if (o->sampler != RBRP_SAMPLER_RANDOM && o->sampler != RBRP_SAMPLER_GREEDY) return RBRP_EINVAL;
+  if (o->w_precision != RBRP_W_FP64 && o->w_precision != RBRP_W_FP32) return RBRP_EINVAL;
+  if (o->tau_b > 1.0) return RBRP_EINVAL;
+  if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
+  // the tensor-core update keeps Lhat (128 x b'_pad) in shared memory: b <= 128
+  if (o->precision == RBRP_TF32 && o->block > 128) return RBRP_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->d = d;
+  long long kc = std::min(n, d);
+  if (o->k_max > 0) kc = std::min(kc, (long long)o->k_max);
+  p->k_cap = kc;
+  p->b = o->block;
+  p->prec = o->precision;
+  p->r64 = (o->precision == RBRP_FP64);
+  p->l64 = p->r64;
+  p->w32 = (o->w_precision == RBRP_W_FP32);
+  p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY);
+  p->ldr = round_up(d, 32);
+  p->ldq = round_up(d, 32);
+  p->ldl = round_up(kc, 8);
+  p->ldp = p->ldq;
+  p->ldpt = round_up(p->b, 32);
+  p->ldc = round_up(kc, 8);
+  p->ldg = p->b;
+  p->ldlc = kMaxBlock;
+  p->ldw32 = p->ldl;
+  {
+    long long np = (n + 7) / 8;
+    p->nparts = (int)std::min(np, 4LL * 152);
+  }
+  const long long b = p->b;
+  p->s_coef = splits_for(b, kc, d);
+  p->s_apply = splits_for(b, d, kc);
+  p->s_gram = splits_for(b, b, d);
+  p->s_upd1 = splits_for(n, b, d);
+  p->s_upd2 = splits_for(n, d, b);
+  size_t need = 0;
+  need = std::max<size_t>(need, (size_t)p->s_coef * b * kc);
+  need = std::max<size_t>(need, (size_t)p->s_apply * b * d);
+  need = std::max<size_t>(need, (size_t)p->s_gram * b * b);
+  if (p->prec != RBRP_TF32) {
+    need = std::max<size_t>(need, (size_t)p->s_upd1 * n * b);
+    need = std::max<size_t>(need, (size_t)p->s_upd2 * n * d);
+  }
+  need = std::max<size_t>(need, (size_t)splits_for(n, 64, kc) * n * 64);
+  p->partial_elems = need;
+
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o2 = off;
+    off = (size_t)round_up((long long)(off + bytes), 256);
+    return o2;
+  };
+  const size_t sR = p->r64 ? 8 : 4, sL = p->l64 ? 8 : 4;
+  p->off_R = take((size_t)n * p->ldr * sR);
+  p->off_L = take((size_t)n * p->ldl * sL);
+  p->off_Q = take((size_t)kc * p->ldq * 8 + (size_t)kMaxBlock * p->ldq * 8);
+  p->off_d = take((size_t)n * 8);
+  p->off_mark = take((size_t)n * 4);
+  p->off_part = take((size_t)std::max<long long>(std::max(p->nparts, 1024), update_tf32_parts(n)) * 8);
+  p->off_state = take(sizeof(State));
+  p->off_St = take((size_t)kMaxBlock * 8);
+  p->off_ca = take(sample_scratch_pairs(n, p->b) * 16);
+  p->off_cb = take(sample_scratch_pairs(n, p->b) * 16);
+  p->off_V = take((size_t)b * p->ldq * 8);
+  p->off_Y = take((size_t)b * p->ldq * 8);
+  p->off_C = take((size_t)b * p->ldc * 8);
+  p->off_G = take((size_t)b * b * 8);
+  p->off_Lc = take((size_t)(kMaxBlock * p->ldlc + kMaxBlock * kMaxBlock) * 8);
+  p->off_perm = take((size_t)kMaxBlock * 4);
+  p->off_gp = take(p->partial_elems * 8);
+  p->off_Qp = take((size_t)p->ldpt * p->ldp * 4);
+  p->off_QpT = take((size_t)p->ldq * p->ldpt * 4);
+  p->off_L1 = take((size_t)kc * kc * 8);
+  p->off_W32 = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
+  p->total = off;
+  return RBRP_OK;
+}
+
+#define CK(call)                        \
+  do {                                  \
+    cudaError_t e_ = (call);            \
+    if (e_ != cudaSuccess) {            \
+      g_last_cuda = (int)e_;            \
+      return RBRP_ECUDA;                \
+    }                                   \
+  } while (0)
+
+struct Bufs {
+  void* R;
+  void* L;
+  double* Qt;
+  double* dvec;
+  int* mark;
+  double* part;
+  State* st;
+  long long* S_t;
+  void* ca;
+  void* cb;
+  double* V;
+  double* Y;
+  double* C;
+  double* G;
+  double* Lc;
+  int* perm;
+  void* gp;
+  float* Qp;
+  float* QpT;
+  double* L1;
+  float* W32;
+  long long* skel;
+};
+
+Bufs carve(const Plan& p, void* ws) {
+  char* b = (char*)ws;
+  Bufs u;
+  u.R = b + p.off_R;
+  u.L = b + p.off_L;
+  u.Qt = (double*)(b + p.off_Q);
+  u.dvec = (double*)(b + p.off_d);
+  u.mark = (int*)(b + p.off_mark);
+  u.part = (double*)(b + p.off_part);
+  u.st = (State*)(b + p.off_state);
+  u.S_t = (long long*)(b + p.off_St);
+  u.ca = b + p.off_ca;
+  u.cb = b + p.off_cb;
+  u.V = (double*)(b + p.off_V);
+  u.Y = (double*)(b + p.off_Y);
+  u.C = (double*)(b + p.off_C);
+  u.G = (double*)(b + p.off_G);
+  u.Lc = (double*)(b + p.off_Lc);
+  u.perm = (int*)(b + p.off_perm);
+  u.gp = b + p.off_gp;
+  u.Qp = (float*)(b + p.off_Qp);
+  u.QpT = (float*)(b + p.off_QpT);
+  u.L1 = (double*)(b + p.off_L1);
+  u.W32 = p.w32 ? (float*)(b + p.off_W32) : nullptr;
+  u.skel = nullptr;
+  return u;
+}
+
+MatRef mat(void* base, DimRef off, long long rs, long long cs) { return MatRef{base, off, rs, cs}; }
+
+template <typename TA, typename TB, typename TC, typename TACC>
+cudaError_t gemm(const Plan& p, const Bufs& u, MatRef A, MatRef B, MatRef C, DimRef M, DimRef N, DimRef K,
+                 double alpha, double beta, long long Mmax, long long Nmax, int splits, const State* st,
+                 cudaStream_t s) {
+  GemmArgs g;
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.partial = u.gp;
+  g.pm = Mmax;
+  g.pn = Nmax;
+  g.st = st;
+  if ((size_t)splits * Mmax * Nmax > p.partial_elems) splits = 1;
+  return launch_gemm<TA, TB, TC, TACC>(g, Mmax, Nmax, splits, s);
+}
+
+// V <- V - (V Qt^T) Qt on rows [0, rows) of V (rows from the device), in FP64.
+cudaError_t cgs_pass(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s) {
+  const State* st = u.st;
+  const long long kc = p.k_cap, b = p.b;
+  cudaError_t e = gemm<double, double, double, double>(
+      p, u, mat(V, dim_const(0), p.ldq, 1), mat(u.Qt, dim_const(0), 1, p.ldq), mat(u.C, dim_const(0), p.ldc, 1),
+      rows, dim_dev(&st->k), dim_const(p.d), 1.0, 0.0, b, kc, p.s_coef, st, s);
+  if (e != cudaSuccess) return e;
+  return gemm<double, double, double, double>(
+      p, u, mat(u.C, dim_const(0), p.ldc, 1), mat(u.Qt, dim_const(0), p.ldq, 1), mat(V, dim_const(0), p.ldq, 1),
+      rows, dim_const(p.d), dim_dev(&st->k), -1.0, 1.0, b, p.d, p.s_apply, st, s);
+}
+
+cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s);
+
+// One block of Alg. 2 (lines 4-16), all sizes on the device.
+cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cudaStream_t s) {
+  State* st = u.st;
+  const long long n = p.n, d = p.d, b = p.b;
+  cudaError_t e;
+#define LK(call)                     \
+  do {                               \
+    e = (call);                      \
+    if (e != cudaSuccess) return e;  \
+  } while (0)
+  // line 5: S_t
+  LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, s));
+  // line 6: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
+  LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, p.ldq, d, p.b, st, s));
+  LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
+  LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
+  // lines 7-9: G = V V^T, pivoted Cholesky with the tail-mass truncation
+  LK((gemm<double, double, double, double>(p, u, mat(u.V, dim_const(0), p.ldq, 1), mat(u.V, dim_const(0), 1, p.ldq),
+                                           mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->b_t), dim_dev(&st->b_t),
+                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s)));
+  LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+  // Q'_V: Y = Lc^{-1} V(perm), then CGS against Q and a second CholQR pass
+  LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
+  LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
+  LK((gemm<double, double, double, double>(p, u, mat(u.Y, dim_const(0), p.ldq, 1), mat(u.Y, dim_const(0), 1, p.ldq),
+                                           mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->bp), dim_dev(&st->bp),
+                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s)));
+  LK(launch_chol(u.G, p.ldg, u.Lc, p.ldlc, p.b, st, s));
+  LK(launch_trsm_rows(u.Lc, p.ldlc, nullptr, u.Y, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+  // lines 12 and 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
+  if (p.prec == RBRP_TF32) {
+    LK(launch_qp_lowp(u.Qt, p.ldq, u.Qp, p.ldp, u.QpT, p.ldpt, d, (int)p.ldpt, st, s));
+    LK(timed(g_prof.upd, s, [&] {
+      return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, p.ldp, u.QpT, p.ldpt, (float*)u.L, p.ldl, u.mark,
+                                u.dvec, u.part, update_tf32_parts(n), st, (int)p.ldpt, s);
+    }));
+    LK(launch_finalize_block(u.part, update_tf32_parts(n), st, s));
+    return cudaSuccess;
+  }
+  LK(timed(g_prof.upd, s, [&] { return enqueue_update_simt(p, u, s); }));
+  LK(launch_finalize_block(u.part, p.nparts, st, s));
+#undef LK
+  return cudaSuccess;
+}
+
+// Residual update on CUDA cores (FP64 or FP32): Lhat = R Q'^T, R -= Lhat Q', norms.
+cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s) {
+  State* st = u.st;
+  const long long n = p.n, d = p.d, b = p.b;
+  cudaError_t e;
+#define LK(call)                     \
+  do {                               \
+    e = (call);                      \
+    if (e != cudaSuccess) return e;  \
+  } while (0)
+  if (p.prec == RBRP_FP64) {
+    LK((gemm<double, double, double, double>(
+        p, u, mat(u.R, dim_const(0), p.ldr, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), 1, p.ldq),
+        mat(u.L, dim_dev(&st->k), p.ldl, 1), dim_const(n), dim_dev(&st->bp), dim_const(d), 1.0, 0.0, n, b, p.s_upd1,
+        st, s)));
+    LK((gemm<double, double, double, double>(
+        p, u, mat(u.L, dim_dev(&st->k), p.ldl, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), p.ldq, 1),
+        mat(u.R, dim_const(0), p.ldr, 1), dim_const(n), dim_const(d), dim_dev(&st->bp), -1.0, 1.0, n, d, p.s_upd2,
+        st, s)));
+  } else {
+    LK((gemm<float, double, float, float>(
+        p, u, mat(u.R, dim_const(0), p.ldr, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), 1, p.ldq),
+        mat(u.L, dim_dev(&st->k), p.ldl, 1), dim_const(n), dim_dev(&st->bp), dim_const(d), 1.0, 0.0, n, b, p.s_upd1,
+        st, s)));
+    LK((gemm<float, double, float, float>(
+        p, u, mat(u.L, dim_dev(&st->k), p.ldl, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), p.ldq, 1),
+        mat(u.R, dim_const(0), p.ldr, 1), dim_const(n), dim_const(d), dim_dev(&st->bp), -1.0, 1.0, n, d, p.s_upd2,
+        st, s)));
+  }
+  LK(launch_norms_zero(u.R, p.r64, p.ldr, n, d, u.mark, u.dvec, u.part, p.nparts, st, s));
+#undef LK
+  return cudaSuccess;
+}
+
+// Alg. 3: W(S,:) = I, W(rest,:) = L2 L1^{-1}, blocked right-to-left substitution.
+rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* skel, double* W, long long ldw,
+                    cudaStream_t s) {
+  if (k <= 0) return RBRP_OK;
+  const long long n = p.n;
+  CK(launch_gather_rows_f64(u.L, p.l64, p.ldl, skel, k, u.L1, k, s));
+  const long long nblk = (k + 63) / 64;
+  if (!p.w32) {
+    CK(launch_copy_cols_to_f64(u.L, p.l64, p.ldl, n, 0, k, W, ldw, s));
+    for (long long J = nblk - 1; J >= 0; --J) {
+      const long long j0 = J * 64, nb = std::min(64LL, k - j0), rest = k - j0 - nb;
+      if (rest > 0) {
+        CK((gemm<double, double, double, double>(
+            p, u, mat(W, dim_const(j0 + nb), ldw, 1), mat(u.L1, dim_const((j0 + nb) * k + j0), k, 1),
+            mat(W, dim_const(j0), ldw, 1), dim_const(n), dim_const(nb), dim_const(rest), -1.0, 1.0, n, 64,
+            splits_for(n, 64, rest), nullptr, s)));
+      }
+      CK(launch_trsm_cols<double>(W, ldw, n, j0, (int)nb, u.L1, k, s));
+    }
+    CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));
+  } else {
+    float* W32 = u.W32;
+    const long long l32 = p.ldw32;
+    CK(launch_copy_cols_to_f32(u.L, p.l64, p.ldl, n, 0, k, W32, l32, s));
+    for (long long J = nblk - 1; J >= 0; --J) {
+      const long long j0 = J * 64, nb = std::min(64LL, k - j0), rest = k - j0 - nb;
+      if (rest > 0) {
+        CK((gemm<float, double, float, float>(
+            p, u, mat(W32, dim_const(j0 + nb), l32, 1), mat(u.L1, dim_const((j0 + nb) * k + j0), k, 1),
+            mat(W32, dim_const(j0), l32, 1), dim_const(n), dim_const(nb), dim_const(rest), -1.0, 1.0, n, 64,
+            splits_for(n, 64, rest), nullptr, s)));
+      }
+      CK(launch_trsm_cols<float>(W32, l32, n, j0, (int)nb, u.L1, k, s));
+    }
+    CK(launch_w_finish(W, ldw, W32, l32, n, k, skel, s));
+  }
+  return RBRP_OK;
+}
+
+rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long long ldx, double tol,
+                const rbrp_opts* o, void* ws, size_t ws_bytes, long long* skel, double* W, long long ldw,
+                rbrp_result* res, cudaStream_t s) {
+  Plan p;
+  rbrp_status rs = make_plan(n, d, o, &p);
+  if (rs != RBRP_OK) return rs;
+  if (!X || !skel || !W || !res || !ws) return RBRP_EINVAL;
+  if (ldx < d || ldw < p.k_cap) return RBRP_EINVAL;
+  if (((uintptr_t)ws & 255) != 0 || ws_bytes < p.total) return RBRP_EWORKSPACE;
+  if (!(tol < 1.0)) return RBRP_EINVAL;
+  memset(res, 0, sizeof(*res));
+  Bufs u = carve(p, ws);
+  u.skel = skel;
+  State* st = u.st;
+  // Alg. 2 lines 1-2
+  CK(launch_init_norms(X, x_is_fp64, n, d, ldx, u.R, p.r64, p.ldr, u.dvec, u.mark, u.part, p.nparts, st, s));
+  CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
+  // Alg. 2 lines 3-16: blocks are queued in groups; queued blocks after the stop return at once
+  State h;
+  long long queued = 0;
+  long long group = 2;
+  for (;;) {
+    for (long long g = 0; g < group && queued < p.k_cap; ++g, ++queued) {
+      cudaError_t e = enqueue_block(p, u, o, s);
+      if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        return RBRP_ECUDA;
+      }
+    }
+    CK(cudaMemcpyAsync(&h, st, sizeof(State), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h.done || queued >= p.k_cap) break;
+    group = std::min<long long>(group * 2, 16);
+  }
+  if (h.status != 0) return (rbrp_status)h.status;
+  res->k = h.k;
+  res->blocks = h.t;
+  res->d0 = h.D0;
+  res->d_final = h.D;
+  res->rel_err_sq = (h.D0 > 0.0) ? h.D / h.D0 : 0.0;
+  // Alg. 3
+  {
+    rbrp_status wrs = RBRP_OK;
+    cudaError_t te = timed(g_prof.wsv, s, [&] {
+      wrs = solve_w(p, u, h.k, skel, W, ldw, s);
+      return cudaSuccess;
+    });
+    if (te != cudaSuccess) {
+      g_last_cuda = (int)te;
+      return RBRP_ECUDA;
+    }
+    if (wrs != RBRP_OK) return wrs;
+  }
+  if (g_prof.on) {
+    g_prof.blocks += h.t;
+    g_prof.skel += h.k;
+  }
+  CK(cudaStreamSynchronize(s));
+  if (tol >= 0.0 && h.D > tol * h.D0) return RBRP_ENOTCONVERGED;
+  return RBRP_OK;
+}
+
+}  // namespace
+}  // namespace rbrp
+
+using namespace rbrp;
+
+extern "C" {
+
+void rbrp_default_opts(rbrp_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = RBRP_TF32;
+  o->block = 64;
+  o->tau_b = -1.0;
+  o->k_max = 0;
+  o->seed = 0;
+  o->problem = 0;
+  o->sampler = RBRP_SAMPLER_RANDOM;
+  o->w_precision = RBRP_W_FP64;
+}
+
+rbrp_status rbrp_workspace_size(int64_t n, int64_t d, const rbrp_opts* o, size_t* bytes) {
+  if (!bytes) return RBRP_EINVAL;
+  Plan p;
+  rbrp_status rs = make_plan(n, d, o, &p);
+  if (rs != RBRP_OK) return rs;
+  *bytes = p.total;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_id(const void* X, int x_is_fp64, int64_t n, int64_t d, int64_t ldx, double tol, const rbrp_opts* o,
+                    void* workspace, size_t ws_bytes, int64_t* skel, double* W, int64_t ldw, rbrp_result* res,
+                    rbrp_stream_t stream) {
+  return run(X, x_is_fp64, n, d, ldx, tol, o, workspace, ws_bytes, (long long*)skel, W, ldw, res,
+             (cudaStream_t)stream);
+}
+
+rbrp_status rbrp_host_workspace_size(int64_t n, int64_t d, int x_is_fp64, const rbrp_opts* o, size_t* bytes) {
+  if (!bytes) return RBRP_EINVAL;
+  Plan p;
+  rbrp_status rs = make_plan(n, d, o, &p);
+  if (rs != RBRP_OK) return rs;
+  size_t off = (size_t)round_up((long long)p.total, 256);
+  off += (size_t)round_up((long long)n * d * (x_is_fp64 ? 8 : 4), 256);
+  off += (size_t)round_up((long long)n * p.k_cap * 8, 256);
+  off += (size_t)round_up((long long)p.k_cap * 8, 256);
+  *bytes = off;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_id_host(const void* X_host, int x_is_fp64, int64_t n, int64_t d, double tol, const rbrp_opts* o,
+                         void* workspace, size_t ws_bytes, int64_t* skel_host, double* W_host, rbrp_result* res,
+                         rbrp_stream_t stream) {
+  if (!X_host || !skel_host || !W_host || !res || !workspace) return RBRP_EINVAL;
+  Plan p;
+  rbrp_status rs = make_plan(n, d, o, &p);
+  if (rs != RBRP_OK) return rs;
+  size_t need = 0;
+  rs = rbrp_host_workspace_size(n, d, x_is_fp64, o, &need);
+  if (rs != RBRP_OK) return rs;
+  if (((uintptr_t)workspace & 255) != 0 || ws_bytes < need) return RBRP_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)workspace;
+  size_t off = (size_t)round_up((long long)p.total, 256);
+  void* Xd = base + off;
+  off += (size_t)round_up((long long)n * d * (x_is_fp64 ? 8 : 4), 256);
+  double* Wd = (double*)(base + off);
+  off += (size_t)round_up((long long)n * p.k_cap * 8, 256);
+  long long* Sd = (long long*)(base + off);
+  const size_t xb = (size_t)n * d * (x_is_fp64 ? 8 : 4);
+  CK(cudaMemcpyAsync(Xd, X_host, xb, cudaMemcpyHostToDevice, s));
+  rs = run(Xd, x_is_fp64, n, d, d, tol, o, workspace, p.total, Sd, Wd, p.k_cap, res, s);
+  if (rs != RBRP_OK && rs != RBRP_ENOTCONVERGED) return rs;
+  const long long k = res->k;
+  if (k > 0) {
+    CK(cudaMemcpyAsync(skel_host, Sd, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpy2DAsync(W_host, (size_t)p.k_cap * 8, Wd, (size_t)p.k_cap * 8, (size_t)k * 8, (size_t)n,
+                         cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return rs;
+}
+
+const char* rbrp_status_string(rbrp_status s) {
+  switch (s) {
+    case RBRP_OK: return "ok";
+    case RBRP_EINVAL: return "invalid argument";
+    case RBRP_ENOMEM: return "out of memory";
+    case RBRP_ECUDA: return "CUDA error";
+    case RBRP_ENONFINITE: return "non-finite value in X or in the residual";
+    case RBRP_ENOTCONVERGED: return "k_max reached before the tolerance";
+    case RBRP_ETIMEOUT: return "bounded device wait timed out";
+    case RBRP_EWORKSPACE: return "workspace misaligned or too small";
+  }
+  return "unknown status";
+}
+
+int rbrp_last_cuda_error(void) { return g_last_cuda; }
+
+void rbrp_profile_begin(void) {
+  g_prof.on = true;
+  g_prof.launches0 = g_kernel_launches;
+  g_prof.upd.used = 0;
+  g_prof.wsv.used = 0;
+  g_prof.blocks = 0;
+  g_prof.skel = 0;
+}
+
+rbrp_status rbrp_profile_end(rbrp_profile* out) {
+  if (!out) return RBRP_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->launches = g_kernel_launches - g_prof.launches0;
+  out->blocks = g_prof.blocks;
+  out->skeletons = g_prof.skel;
+  EventPool* pools[2] = {&g_prof.upd, &g_prof.wsv};
+  double* ms[2] = {&out->update_ms, &out->wsolve_ms};
+  int64_t* cnt[2] = {&out->update_launches, &out->wsolve_calls};
+  for (int q = 0; q < 2; ++q) {
+    for (size_t i = 0; i + 1 < pools[q]->used; i += 2) {
+      cudaError_t e = cudaEventSynchronize(pools[q]->ev[i + 1]);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pools[q]->ev[i], pools[q]->ev[i + 1]);
+      if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        g_prof.on = false;
+        return RBRP_ECUDA;
+      }
+      *ms[q] += t;
+      *cnt[q] += 1;
+    }
+  }
+  g_prof.on = false;
+  return RBRP_OK;
+}
+
+}  // extern "C"

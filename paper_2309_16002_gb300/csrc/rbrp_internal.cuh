@@ -1,0 +1,162 @@
+// Internal declarations shared by the CUDA translation units of the RBRP library.
+//
+// Every per-block kernel reads the sizes it works on (b_t, b', k) from a State
+// record in device memory, so that one block of Alg. 2 is a fixed sequence of
+// launches whose grids depend only on the problem's maxima (n, d, b, k_cap).
+// The host never needs to read a size back between blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbrp.h"
+
+namespace rbrp {
+
+// ---------------------------------------------------------------- device state
+struct State {
+  long long k;       // |S| accepted so far
+  long long t;       // blocks completed (the paper's t after the block ends)
+  long long b_t;     // rows drawn in the current block
+  long long bp;      // rows accepted in the current block (b')
+  long long k_cap;   // min(n, d, k_max)
+  long long done;    // 1 once the stopping test (Alg. 2 line 3) fails
+  long long status;  // rbrp_status raised on the device (0 = ok)
+  long long bp_pad;  // b' rounded up to a multiple of 16 (tensor-core N)
+  double D0;         // ||d0||_1
+  double D;          // ||d||_1 after the last block
+  double tau;        // tolerance (< 0: fixed-rank mode)
+  double tau_b;      // filter tolerance (< 0: 1/b_t)
+};
+
+// A size or offset resolved on the device: c + mul * (*p)  (p may be null).
+struct DimRef {
+  const long long* p;
+  long long c;
+  long long mul;
+};
+__host__ __device__ inline DimRef dim_const(long long c) { return DimRef{nullptr, c, 0}; }
+__host__ __device__ inline DimRef dim_dev(const long long* p, long long mul = 1, long long c = 0) {
+  return DimRef{p, c, mul};
+}
+__device__ __forceinline__ long long dim_val(const DimRef& r) { return r.c + (r.p ? r.mul * (*r.p) : 0); }
+
+// A strided matrix view: element (i, j) at base[off + i * rs + j * cs].
+struct MatRef {
+  void* base;
+  DimRef off;
+  long long rs, cs;
+};
+
+// C[M x N] = alpha * A[M x K] * B[K x N] + beta * C  (beta == 0 never reads C).
+struct GemmArgs {
+  MatRef A, B, C;
+  DimRef M, N, K;
+  double alpha, beta;
+  void* partial;        // split-K partial sums: splits x pm x pn (TACC)
+  long long pm, pn;     // partial buffer extents (maxima of M, N)
+  const State* st;      // kernels return at once when st->done (if non-null)
+};
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon et al. (SC'11): two 64x64->128 multiplies per round, Weyl key bump.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const unsigned long long n0 = hi1 ^ c[1] ^ k0;
+    const unsigned long long n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// Uniform in (0, 1) for (row, block): ((w0 >> 11) + 1/2) * 2^-53.
+__device__ __forceinline__ double philox_uniform(unsigned long long row, unsigned long long block,
+                                                 unsigned long long seed, unsigned long long problem) {
+  unsigned long long c[4] = {row, block, 0ULL, 0ULL};
+  philox4x64_10(c, seed, problem);
+  return ((double)(c[0] >> 11) + 0.5) * 0x1.0p-53;
+}
+
+// Order-preserving map of a double to an unsigned 64-bit key.
+__device__ __forceinline__ unsigned long long orderable(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+constexpr unsigned long long kIneligible = 0xFFFFFFFFFFFFFFFFULL;
+
+// ---------------------------------------------------------------- instrumentation
+// Number of kernels the library has launched (read by rbrp_profile_end).
+extern long long g_kernel_launches;
+inline cudaError_t counted(cudaError_t e) {
+  ++g_kernel_launches;
+  return e;
+}
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxBlock = 256;      // largest b
+constexpr int kSortChunk = 2048;    // sampler: elements sorted per CTA
+constexpr int kGemmTile = 64;       // SIMT GEMM tile (M and N)
+
+// ---------------------------------------------------------------- launch wrappers
+// (defined in k_common.cu / k_update_tc.cu; all enqueue on `s` and return the
+//  launch error, never synchronise)
+cudaError_t launch_init_norms(const void* X, int x_is_fp64, long long n, long long d, long long ldx,
+                              void* R, int r_is_fp64, long long ldr, double* dvec, int* mark,
+                              double* partials, int nparts, State* st, cudaStream_t s);
+cudaError_t launch_finish_init(const double* partials, int nparts, State* st, double tau, double tau_b,
+                               long long k_cap, cudaStream_t s);
+cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
+                          unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
+                          State* st, cudaStream_t s);
+size_t sample_scratch_pairs(long long n, int b);
+cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t,
+                          double* V, long long ldv, long long d, int b, const State* st, cudaStream_t s);
+template <typename TA, typename TB, typename TC, typename TACC>
+cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, cudaStream_t s);
+cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
+                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
+cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
+                        State* st, cudaStream_t s);
+cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V,
+                             long long ldv, double* Y, DimRef y_off, long long ldy, long long d, int b,
+                             const State* st, cudaStream_t s);
+cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, long long ldp, float* QpT,
+                           long long ldpt, long long d, int b, const State* st, cudaStream_t s);
+cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d,
+                              const int* mark, double* dvec, double* partials, int nparts,
+                              const State* st, cudaStream_t s);
+cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s);
+cudaError_t launch_copy_cols_to_f64(const void* L, int l_is_fp64, long long ldl, long long n,
+                                    long long c0, long long c1, double* W, long long ldw,
+                                    cudaStream_t s);
+cudaError_t launch_copy_cols_to_f32(const void* L, int l_is_fp64, long long ldl, long long n,
+                                    long long c0, long long c1, float* W, long long ldw,
+                                    cudaStream_t s);
+cudaError_t launch_gather_rows_f64(const void* L, int l_is_fp64, long long ldl, const long long* rows,
+                                   long long k, double* out, long long ldo, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trsm_cols(T* W, long long ldw, long long n, long long j0, int nb, const double* L1,
+                             long long ld1, cudaStream_t s);
+cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long long ldw32, long long n,
+                            long long k, const long long* skel, cudaStream_t s);
+
+// tcgen05 fused residual update (k_update_tc.cu): per 128-row tile,
+// Lhat = R Q'^T (TF32 in, FP32 accumulate in TMEM), R -= Lhat Q', d_i = ||R_i||^2,
+// rows accepted in this block zeroed; Lhat stored to L(:, k : k + b').
+cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp,
+                               long long ldp, const float* QpT, long long ldpt, float* L, long long ldl,
+                               const int* mark, double* dvec, double* partials, int nparts,
+                               const State* st, int bmax, cudaStream_t s);
+int update_tf32_parts(long long n);
+
+}  // namespace rbrp

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of librbrp.so (include/rbrp.h).
+
+Argument marshalling only: every step of RBRP runs in the CUDA library.  PyTorch
+supplies device memory (the workspace and the outputs) and the current stream.
+There is no CPU fallback: if the library is missing, loading it raises.
+
+Functions mirror the C ABI:
+  rbrp_id(X, tol, ...)          X a CUDA tensor (FP32 or FP64, row-major)
+  rbrp_id_host(X, tol, ...)     X a host tensor/array; copies inside the call
+  rbrp_workspace_size(n, d, opts), rbrp_host_workspace_size(n, d, x_is_fp64, opts)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "librbrp.so")
+_lib = None
+
+PRECISIONS = {"fp64": 0, "tf32": 1, "fp32": 2}
+SAMPLERS = {"random": 0, "greedy": 1}
+W_PRECISIONS = {"fp64": 0, "fp32": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "non-finite value",
+          5: "not converged", 6: "timeout", 7: "workspace"}
+RBRP_ENOTCONVERGED = 5
+
+EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_workspace_size", "rbrp_id_host",
+           "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("block", ctypes.c_int32), ("tau_b", ctypes.c_double),
+                ("k_max", ctypes.c_int64), ("seed", ctypes.c_uint64), ("problem", ctypes.c_uint64),
+                ("sampler", ctypes.c_int32), ("w_precision", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("blocks", ctypes.c_int64), ("d0", ctypes.c_double),
+                ("d_final", ctypes.c_double), ("rel_err_sq", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("update_launches", ctypes.c_int64), ("update_ms", ctypes.c_double),
+                ("wsolve_calls", ctypes.c_int64), ("wsolve_ms", ctypes.c_double), ("blocks", ctypes.c_int64),
+                ("skeletons", ctypes.c_int64)]
+
+
+class RBRPError(RuntimeError):
+    def __init__(self, status, where, cuda_err=0):
+        self.status = status
+        msg = "%s: %s" % (where, STATUS.get(status, str(status)))
+        if status == 3:
+            msg += " (cudaError %d)" % cuda_err
+        super().__init__(msg)
+
+
+def lib_path():
+    return _LIBPATH
+
+
+def load():
+    """Load librbrp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise RuntimeError("librbrp.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(_LIBPATH)
+    vp, sz, i64, dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_double
+    L.rbrp_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.rbrp_default_opts.restype = None
+    L.rbrp_workspace_size.argtypes = [i64, i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    L.rbrp_workspace_size.restype = ctypes.c_int
+    L.rbrp_host_workspace_size.argtypes = [i64, i64, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    L.rbrp_host_workspace_size.restype = ctypes.c_int
+    L.rbrp_id.argtypes = [vp, ctypes.c_int, i64, i64, i64, dbl, ctypes.POINTER(Opts), vp, sz, vp, vp, i64,
+                          ctypes.POINTER(Result), vp]
+    L.rbrp_id.restype = ctypes.c_int
+    L.rbrp_id_host.argtypes = [vp, ctypes.c_int, i64, i64, dbl, ctypes.POINTER(Opts), vp, sz, vp, vp,
+                               ctypes.POINTER(Result), vp]
+    L.rbrp_id_host.restype = ctypes.c_int
+    L.rbrp_status_string.argtypes = [ctypes.c_int]
+    L.rbrp_status_string.restype = ctypes.c_char_p
+    L.rbrp_last_cuda_error.argtypes = []
+    L.rbrp_last_cuda_error.restype = ctypes.c_int
+    L.rbrp_profile_begin.argtypes = []
+    L.rbrp_profile_begin.restype = None
+    L.rbrp_profile_end.argtypes = [ctypes.POINTER(Profile)]
+    L.rbrp_profile_end.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def rbrp_profile_begin():
+    load().rbrp_profile_begin()
+
+
+def rbrp_profile_end():
+    p = Profile()
+    st = load().rbrp_profile_end(ctypes.byref(p))
+    if st != 0:
+        raise RBRPError(st, "rbrp_profile_end", load().rbrp_last_cuda_error())
+    return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+
+def make_opts(block=64, precision="tf32", tau_b=-1.0, k_max=0, seed=0, problem=0, sampler="random",
+              w_precision="fp64"):
+    o = Opts()
+    load().rbrp_default_opts(ctypes.byref(o))
+    o.precision = PRECISIONS[precision]
+    o.block = int(block)
+    o.tau_b = float(tau_b)
+    o.k_max = int(k_max)
+    o.seed = int(seed)
+    o.problem = int(problem)
+    o.sampler = SAMPLERS[sampler]
+    o.w_precision = W_PRECISIONS[w_precision]
+    return o
+
+
+def k_cap(n, d, k_max=0):
+    kc = min(n, d)
+    return min(kc, k_max) if k_max and k_max > 0 else kc
+
+
+def rbrp_workspace_size(n, d, opts):
+    out = ctypes.c_size_t(0)
+    st = load().rbrp_workspace_size(int(n), int(d), ctypes.byref(opts), ctypes.byref(out))
+    if st != 0:
+        raise RBRPError(st, "rbrp_workspace_size")
+    return out.value
+
+
+def rbrp_host_workspace_size(n, d, x_is_fp64, opts):
+    out = ctypes.c_size_t(0)
+    st = load().rbrp_host_workspace_size(int(n), int(d), int(x_is_fp64), ctypes.byref(opts), ctypes.byref(out))
+    if st != 0:
+        raise RBRPError(st, "rbrp_host_workspace_size")
+    return out.value
+
+
+def _check(status, where, allow_notconverged=True):
+    if status == 0 or (allow_notconverged and status == RBRP_ENOTCONVERGED):
+        return
+    raise RBRPError(status, where, load().rbrp_last_cuda_error())
+
+
+def _result_dict(res, status):
+    return dict(k=int(res.k), blocks=int(res.blocks), d0=res.d0, d_final=res.d_final, rel_err_sq=res.rel_err_sq,
+                converged=(status == 0))
+
+
+class Workspace:
+    """Device buffers for repeated rbrp_id calls of one shape (allocated once by PyTorch)."""
+
+    def __init__(self, n, d, opts, device=None):
+        import torch
+        self.n, self.d = int(n), int(d)
+        self.opts = opts
+        self.kc = k_cap(n, d, opts.k_max)
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.ws = torch.empty(rbrp_workspace_size(n, d, opts) + 256, dtype=torch.uint8, device=dev)
+        self.skel = torch.empty(self.kc, dtype=torch.int64, device=dev)
+        self.W = torch.empty((self.n, self.kc), dtype=torch.float64, device=dev)
+
+    def ws_ptr(self):
+        p = self.ws.data_ptr()
+        return (p + 255) // 256 * 256
+
+    def ws_bytes(self):
+        return self.ws.numel() - (self.ws_ptr() - self.ws.data_ptr())
+
+
+def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0, sampler="random",
+            w_precision="fp64", workspace=None, stream=None):
+    """Row ID of a CUDA tensor X (n x d, FP32/FP64, row-major rows) by RBRP (Alg. 2) and Alg. 3.
+
+    Returns dict(S (int64 CUDA tensor, acceptance order), W (n x k FP64 CUDA tensor), k, blocks,
+    rel_err_sq (= ||d||_1 / ||d0||_1), d0, d_final, converged).
+    """
+    import torch
+    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
+    if X.dtype not in (torch.float32, torch.float64):
+        raise ValueError("X must be float32 or float64")
+    n, d = X.shape
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
+    ws = workspace if workspace is not None else Workspace(n, d, opts, X.device)
+    res = Result()
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    st = load().rbrp_id(ctypes.c_void_p(X.data_ptr()), int(X.dtype == torch.float64), n, d, X.stride(0), float(tol),
+                        ctypes.byref(opts), ctypes.c_void_p(ws.ws_ptr()), ws.ws_bytes(),
+                        ctypes.c_void_p(ws.skel.data_ptr()), ctypes.c_void_p(ws.W.data_ptr()), ws.kc,
+                        ctypes.byref(res), ctypes.c_void_p(s.cuda_stream))
+    _check(st, "rbrp_id")
+    out = _result_dict(res, st)
+    k = out["k"]
+    out["S"] = ws.skel[:k]
+    out["W"] = ws.W[:, :k]
+    return out
+
+
+class HostWorkspace:
+    """Device workspace for rbrp_id_host of one shape."""
+
+    def __init__(self, n, d, x_is_fp64, opts, device=None):
+        import torch
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.ws = torch.empty(rbrp_host_workspace_size(n, d, x_is_fp64, opts) + 256, dtype=torch.uint8, device=dev)
+
+    def ptr(self):
+        return (self.ws.data_ptr() + 255) // 256 * 256
+
+    def nbytes(self):
+        return self.ws.numel() - (self.ptr() - self.ws.data_ptr())
+
+
+def rbrp_id_host(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0, sampler="random",
+                 w_precision="fp64", workspace=None, skel_out=None, W_out=None, stream=None):
+    """rbrp_id on host buffers: X (numpy array or CPU tensor, C-contiguous FP32/FP64).
+
+    skel_out / W_out: optional preallocated host outputs (int64[k_cap], FP64 n x k_cap, pinned
+    tensors make the copies asynchronous).  Returns the same dict as rbrp_id with host S and W.
+    """
+    import torch
+    Xt = torch.as_tensor(X)
+    if Xt.is_cuda or Xt.dim() != 2 or not Xt.is_contiguous():
+        raise ValueError("X must be a C-contiguous 2-D host array")
+    n, d = Xt.shape
+    fp64 = int(Xt.dtype == torch.float64)
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
+    kc = k_cap(n, d, k_max)
+    ws = workspace if workspace is not None else HostWorkspace(n, d, fp64, opts)
+    skel = skel_out if skel_out is not None else torch.empty(kc, dtype=torch.int64)
+    W = W_out if W_out is not None else torch.empty((n, kc), dtype=torch.float64)
+    res = Result()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = load().rbrp_id_host(ctypes.c_void_p(Xt.data_ptr()), fp64, n, d, float(tol), ctypes.byref(opts),
+                             ctypes.c_void_p(ws.ptr()), ws.nbytes(), ctypes.c_void_p(skel.data_ptr()),
+                             ctypes.c_void_p(W.data_ptr()), ctypes.byref(res), ctypes.c_void_p(s.cuda_stream))
+    _check(st, "rbrp_id_host")
+    out = _result_dict(res, st)
+    k = out["k"]
+    out["S"] = skel[:k]
+    out["W"] = W[:, :k]
+    return out
+
+
+def exported_symbols():
+    """Names of the C ABI entry points the binding expects (declared in include/rbrp.h)."""
+    return list(EXPORTS)
+
+
+def as_numpy(t):
+    return t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)

@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every
+function declared in include/rbrp.h (no compute calls: there may be no GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(rbrp_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2309_16002_gb300 import rbrp
+    return rbrp.lib_path()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("rbrp_id", "rbrp_workspace_size", "rbrp_id_host", "rbrp_default_opts"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared_functions() - exported
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches(libpath):
+    from paper_2309_16002_gb300 import rbrp
+    L = rbrp.load()
+    for name in declared_functions():
+        assert hasattr(L, name)
+    assert set(rbrp.exported_symbols()) <= declared_functions()
+
+
+def test_workspace_size_and_validation_on_host(libpath):
+    """Pure host logic of the ABI (no GPU needed): sizing and argument validation."""
+    from paper_2309_16002_gb300 import rbrp
+    o = rbrp.make_opts(block=64, precision="tf32")
+    ws = rbrp.rbrp_workspace_size(100000, 1000, o)
+    # at least R (FP32) + L (FP32, n x k_cap) + Q (FP64, k_cap x d)
+    assert ws >= 100000 * 1024 * 4 + 100000 * 1000 * 4 + 1000 * 1024 * 8
+    with pytest.raises(rbrp.RBRPError):
+        rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=0))
+    with pytest.raises(rbrp.RBRPError):
+        rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=300, precision="fp64"))
+    with pytest.raises(rbrp.RBRPError):
+        rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=256, precision="tf32"))
+    with pytest.raises(rbrp.RBRPError):
+        rbrp.rbrp_workspace_size(0, 10, o)
+    assert rbrp.rbrp_host_workspace_size(1000, 50, 0, o) > rbrp.rbrp_workspace_size(1000, 50, o)
+
+
+def test_status_strings(libpath):
+    from paper_2309_16002_gb300 import rbrp
+    L = rbrp.load()
+    assert L.rbrp_status_string(0) == b"ok"
+    assert b"workspace" in L.rbrp_status_string(7)
