@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "tf32x3", "fp32", "fp64"])
     ap.add_argument("--w-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-4)
@@ -247,7 +247,7 @@ def run_ours(a):
                           "real_blocks": blocks, "GB/s": upd_gbs},
                "w_solve": {"ms_per_step": w_ms / a.steps, "TFLOP/s": (w_flops / (w_ms / 1e3) / 1e12) if w_ms else None},
                "other_ms_per_step": ms - (upd_ms + w_ms) / a.steps}
-    roofline = {"bound": "hbm", "kernel": "k_update_tf32" if a.precision == "tf32" else "update_simt",
+    roofline = {"bound": "hbm", "kernel": "k_update_tf32" if a.precision.startswith("tf32") else "update_simt",
                 "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
                 "peak_kind": peak_kind, "traffic": None,
                 "bytes_per_launch": upd_bytes / max(1, blocks),
@@ -258,7 +258,8 @@ def run_ours(a):
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws_n, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"tf32": "tf32+f64", "fp32": "f32+f64", "fp64": "f64"}[a.precision], "data": "synthetic",
+                "dtype": {"tf32": "tf32+f64", "tf32x3": "3xtf32+f64", "fp32": "f32+f64", "fp64": "f64"}[a.precision],
+                "data": "synthetic",
                 "config": workload_config(a), "k": ks[-1], "blocks_per_step": blocks / max(1, a.steps),
                 "rel_err_sq": out["rel_err_sq"], "roofline": roofline, "kernels": kernels,
                 "gpu_launches": prof["launches"], "clocks": clk}

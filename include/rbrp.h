@@ -53,7 +53,9 @@ typedef enum {
   RBRP_TF32 = 1,   /* R in FP32, update on tcgen05 tensor cores (TF32 in, FP32    */
                    /* accumulate); sampler keys, CGS2 Gram corrections, the b x b */
                    /* filter and Q' stay FP64                                     */
-  RBRP_FP32 = 2    /* R in FP32, update on CUDA cores in FP32 (same FP64 parts)   */
+  RBRP_FP32 = 2,   /* R in FP32, update on CUDA cores in FP32 (same FP64 parts)   */
+  RBRP_TF32X3 = 3  /* as RBRP_TF32 with every operand split into TF32 hi + lo and */
+                   /* three products per step (~FP32-accurate update); b <= 64    */
 } rbrp_precision;
 
 typedef enum {

@@ -257,15 +257,19 @@ cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const lon
 
 // ============================================================================
 // Split-K SIMT GEMM: C = alpha A B + beta C on strided views, sizes from the
-// device.  64 x 64 tile, 256 threads, 4 x 4 outputs per thread, K step 16.
-// TACC is the product/accumulation type (the operands are converted to it
-// when staged); the epilogue combines in double.
+// device.  TILE x TILE output tile (64 or 32), 256 threads, (TILE/16)^2 outputs
+// per thread, K step 16.  TACC is the product/accumulation type (the operands
+// are converted to it when staged); the epilogue combines in double.  Small
+// FP64 products use the 32-wide tile with a fine K split so that every SM gets
+// work (GB300 retires ~2 FP64 FMA per clock per SM).
 // ============================================================================
-template <typename TA, typename TB, typename TC, typename TACC>
+template <typename TA, typename TB, typename TC, typename TACC, int TILE>
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int splits) {
+  constexpr int R = TILE / 16;          // outputs per thread along each axis
+  constexpr int LOADS = TILE * 16 / 256;  // staged elements per thread per operand
   if (g.st && g.st->done) return;
   const long long M = dim_val(g.M), N = dim_val(g.N), K = dim_val(g.K);
-  const long long m0 = (long long)blockIdx.y * kGemmTile, n0 = (long long)blockIdx.x * kGemmTile;
+  const long long m0 = (long long)blockIdx.y * TILE, n0 = (long long)blockIdx.x * TILE;
   if (m0 >= M || n0 >= N) return;
   const TA* A = (const TA*)g.A.base + dim_val(g.A.off);
   const TB* B = (const TB*)g.B.base + dim_val(g.B.off);
@@ -275,52 +279,52 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int splits) {
   const long long kb = (long long)blockIdx.z * kc;
   const long long ke = (kb + kc < K) ? kb + kc : K;
 
-  __shared__ TACC As[16][kGemmTile];
-  __shared__ TACC Bs[16][kGemmTile];
+  __shared__ TACC As[16][TILE];
+  __shared__ TACC Bs[16][TILE];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  TACC acc[4][4];
+  TACC acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (TACC)0;
+    for (int j = 0; j < R; ++j) acc[i][j] = (TACC)0;
 
   const bool a_kmajor = (g.A.cs == 1);
   const bool b_nmajor = (g.B.cs == 1);
   for (long long k0 = kb; k0 < ke; k0 += 16) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < LOADS; ++q) {
       const int e = tid + 256 * q;
       int r, c;
-      if (a_kmajor) { r = e >> 4; c = e & 15; } else { r = e & 63; c = e >> 6; }
+      if (a_kmajor) { r = e >> 4; c = e & 15; } else { r = e % TILE; c = e / TILE; }
       const long long gm = m0 + r, gk = k0 + c;
       As[c][r] = (gm < M && gk < ke) ? (TACC)A[gm * g.A.rs + gk * g.A.cs] : (TACC)0;
       int rb, cb;
-      if (b_nmajor) { rb = e >> 6; cb = e & 63; } else { rb = e & 15; cb = e >> 4; }
+      if (b_nmajor) { rb = e / TILE; cb = e % TILE; } else { rb = e & 15; cb = e >> 4; }
       const long long hk = k0 + rb, hn = n0 + cb;
       Bs[rb][cb] = (hk < ke && hn < N) ? (TACC)B[hk * g.B.rs + hn * g.B.cs] : (TACC)0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      TACC a[4], bv[4];
+      TACC a[R], bv[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
   if (splits == 1) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
       const long long gm = m0 + ty + 16 * i;
       if (gm >= M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < R; ++j) {
         const long long gn = n0 + tx + 16 * j;
         if (gn >= N) continue;
         TC* cp = C + gm * g.C.rs + gn * g.C.cs;
@@ -332,11 +336,11 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int splits) {
   } else {
     TACC* P = (TACC*)g.partial + (long long)blockIdx.z * g.pm * g.pn;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
       const long long gm = m0 + ty + 16 * i;
       if (gm >= M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < R; ++j) {
         const long long gn = n0 + tx + 16 * j;
         if (gn < N) P[gm * g.pn + gn] = acc[i][j];
       }
@@ -362,12 +366,16 @@ __global__ void k_gemm_reduce(GemmArgs g, int splits) {
 }
 
 template <typename TA, typename TB, typename TC, typename TACC>
-cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, cudaStream_t s) {
+cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, int tile, cudaStream_t s) {
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
   if (splits < 1) splits = 1;
-  dim3 grid((unsigned)((Nmax + kGemmTile - 1) / kGemmTile), (unsigned)((Mmax + kGemmTile - 1) / kGemmTile),
-            (unsigned)splits);
-  k_gemm<TA, TB, TC, TACC><<<grid, 256, 0, s>>>(g, splits);
+  if (tile == 32) {
+    dim3 grid((unsigned)((Nmax + 31) / 32), (unsigned)((Mmax + 31) / 32), (unsigned)splits);
+    k_gemm<TA, TB, TC, TACC, 32><<<grid, 256, 0, s>>>(g, splits);
+  } else {
+    dim3 grid((unsigned)((Nmax + 63) / 64), (unsigned)((Mmax + 63) / 64), (unsigned)splits);
+    k_gemm<TA, TB, TC, TACC, 64><<<grid, 256, 0, s>>>(g, splits);
+  }
   cudaError_t e = counted(cudaGetLastError());
   if (e != cudaSuccess || splits == 1) return e;
   long long tot = Mmax * Nmax;
@@ -377,10 +385,10 @@ cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int s
   return counted(cudaGetLastError());
 }
 
-template cudaError_t launch_gemm<double, double, double, double>(const GemmArgs&, long long, long long, int, cudaStream_t);
-template cudaError_t launch_gemm<float, float, float, float>(const GemmArgs&, long long, long long, int, cudaStream_t);
-template cudaError_t launch_gemm<double, double, double, float>(const GemmArgs&, long long, long long, int, cudaStream_t);
-template cudaError_t launch_gemm<float, double, float, float>(const GemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_gemm<double, double, double, double>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
+template cudaError_t launch_gemm<float, float, float, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
+template cudaError_t launch_gemm<double, double, double, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
+template cudaError_t launch_gemm<float, double, float, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
 
 // ============================================================================
 // Alg. 2 lines 7-9 and the robust blockwise filtering remark (Sec. 4):
@@ -504,21 +512,159 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ G, lon
   }
 }
 
-cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
-                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
-  (void)b;
+// Right-looking form of the same factorisation for m <= 128 candidates: the
+// Schur complement (lower triangle) lives in shared memory and every step is a
+// parallel rank-1 downdate, so the O(m^3/6) FP64 work is spread over 512
+// threads instead of running as per-candidate dot products.
+constexpr int kSmemChol = 128;
+
+__global__ void __launch_bounds__(512) k_pchol_smem(const double* __restrict__ G, long long ldg,
+                                                    double* __restrict__ Lc, long long ldl, double* __restrict__ Lw,
+                                                    int* __restrict__ perm, const long long* __restrict__ S_t,
+                                                    long long* __restrict__ skel, int* __restrict__ mark, State* st,
+                                                    int pivoted) {
+  if (st->done) return;
+  extern __shared__ double Ssh[];  // m x m, row-major; entries (j, c) with c <= j are maintained
+  __shared__ double lcol[kSmemChol];
+  __shared__ int alive[kSmemChol];
+  __shared__ int s_perm[kSmemChol];
+  __shared__ int s_piv, s_stop;
+  __shared__ double s_pv, s_rinv, s_total;
+  const int m = pivoted ? (int)st->b_t : (int)st->bp;
+  const int tid = threadIdx.x;
+  for (int j = (tid >> 5); j < m; j += (blockDim.x >> 5))
+    for (int c = (tid & 31); c <= j; c += 32) Ssh[j * m + c] = G[(long long)j * ldg + c];
+  for (int j = tid; j < m; j += blockDim.x) alive[j] = 1;
+  __syncthreads();
+  if (tid < 32) {
+    double t = 0.0;
+    for (int j = tid; j < m; j += 32) t += Ssh[j * m + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (tid == 0) s_total = t;
+  }
+  __syncthreads();
+  double tau_b = st->tau_b;
+  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+  int bp = 0;
+  for (int i = 0; i < m; ++i) {
+    if (tid < 32) {
+      double v = -DBL_MAX, msum = 0.0;
+      int vi = INT_MAX;
+      for (int j = tid; j < m; j += 32) {
+        if (!alive[j]) continue;
+        const double dj = Ssh[j * m + j];
+        msum += dj;
+        const bool better = pivoted ? (dj > v || (dj == v && j < vi)) : (j == i);
+        if (better) {
+          v = dj;
+          vi = j;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        msum += __shfl_xor_sync(0xffffffffu, msum, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+        if (ov > v || (ov == v && oi < vi)) {
+          v = ov;
+          vi = oi;
+        }
+      }
+      if (tid == 0) {
+        int stop = 0;
+        if (pivoted && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
+        if (vi == INT_MAX || !(v > 0.0)) stop = 1;
+        s_stop = stop;
+        s_piv = vi;
+        // one FP64 square root and reciprocal per step (FP64 is ~2 FMA/clock/SM on GB300)
+        if (!stop) {
+          s_pv = sqrt(v);
+          s_rinv = 1.0 / s_pv;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_piv;
+    const double pivval = s_pv, rinv = s_rinv;
+    for (int j = tid; j < m; j += blockDim.x) {
+      double l = 0.0;
+      if (alive[j]) l = (j == p) ? pivval : ((j >= p) ? Ssh[j * m + p] : Ssh[p * m + j]) * rinv;
+      lcol[j] = (j == p) ? 0.0 : l;
+      if (alive[j]) Lw[(long long)j * kMaxBlock + i] = l;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      alive[p] = 0;
+      s_perm[i] = p;
+      if (perm) perm[i] = p;
+    }
+    __syncthreads();
+    // rank-1 downdate of the lower triangle: warp w takes rows j = w, w + 16, ...
+    for (int j = (tid >> 5); j < m; j += (blockDim.x >> 5)) {
+      if (!alive[j]) continue;
+      const double lj = lcol[j];
+      for (int c = (tid & 31); c <= j; c += 32)
+        if (alive[c]) Ssh[j * m + c] -= lj * lcol[c];
+    }
+    __syncthreads();
+    bp = i + 1;
+  }
+  for (int e = tid; e < bp * bp; e += blockDim.x) {
+    const int i = e / bp, l = e % bp;
+    Lc[(long long)i * ldl + l] = (l <= i) ? Lw[(long long)s_perm[i] * kMaxBlock + l] : 0.0;
+  }
+  if (pivoted) {
+    const long long k = st->k;
+    const int tno = (int)(st->t + 1);
+    for (int i = tid; i < bp; i += blockDim.x) {
+      const long long row = S_t[s_perm[i]];
+      skel[k + i] = row;
+      mark[row] = tno;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (pivoted) {
+      st->bp = bp;
+      st->bp_pad = (bp + 15) / 16 * 16;
+      if (bp == 0) st->done = 1;
+    } else if (bp < m) {
+      st->status = RBRP_ENONFINITE;
+      st->done = 1;
+    }
+  }
+}
+
+static cudaError_t launch_pchol_any(const double* G, long long ldg, double* Lc, long long ldl, int* perm,
+                                    const long long* S_t, long long* skel, int* mark, int b, State* st, int pivoted,
+                                    cudaStream_t s) {
   // Lw (candidate-indexed factor, kMaxBlock x kMaxBlock) lives right after Lc in the workspace
   double* Lw = Lc + (long long)kMaxBlock * ldl;
-  k_pchol<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, 1);
+  if (b <= kSmemChol) {
+    static bool attr = false;
+    const int smem = kSmemChol * kSmemChol * 8;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_pchol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_pchol_smem<<<1, 512, (size_t)b * b * 8, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+  } else {
+    k_pchol<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+  }
   return counted(cudaGetLastError());
+}
+
+cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
+                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+  return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 1, s);
 }
 
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b, State* st,
                         cudaStream_t s) {
-  (void)b;
-  double* Lw = Lc + (long long)kMaxBlock * ldl;
-  k_pchol<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, nullptr, nullptr, nullptr, nullptr, st, 0);
-  return counted(cudaGetLastError());
+  return launch_pchol_any(G, ldg, Lc, ldl, nullptr, nullptr, nullptr, nullptr, b, st, 0, s);
 }
 
 // ============================================================================
@@ -543,11 +689,45 @@ __global__ void k_trsm_rows(const double* __restrict__ Lc, long long ldl, const 
   }
 }
 
+// Same substitution with 16 columns per CTA: the right-hand sides sit in shared
+// memory and each dot product sum_{l<i} Lc(i,l) Y(l,c) is split over 16 threads
+// (a quarter-warp per column pair) and combined with shuffles.
+__global__ void __launch_bounds__(256) k_trsm_rows16(const double* __restrict__ Lc, long long ldl,
+                                                     const int* __restrict__ perm, const double* __restrict__ V,
+                                                     long long ldv, double* __restrict__ Ybase, DimRef y_off,
+                                                     long long ldy, long long d, const State* st) {
+  if (st->done) return;
+  __shared__ double Ys[kMaxBlock][16];
+  __shared__ double rdiag[kMaxBlock];
+  const int bp = (int)st->bp;
+  const int cl = threadIdx.x >> 4, part = threadIdx.x & 15;  // column within the chunk, summation lane
+  const long long c = (long long)blockIdx.x * 16 + cl;
+  for (int i = part; i < bp; i += 16) {
+    const int src = perm ? perm[i] : i;
+    Ys[i][cl] = (c < d) ? V[(long long)src * ldv + c] : 0.0;
+  }
+  // reciprocals of the diagonal once (FP64 division is costly on GB300)
+  for (int i = threadIdx.x; i < bp; i += blockDim.x) rdiag[i] = 1.0 / Lc[(long long)i * ldl + i];
+  __syncthreads();
+  for (int i = 0; i < bp; ++i) {
+    double acc = 0.0;
+    for (int l = part; l < i; l += 16) acc = fma(Lc[(long long)i * ldl + l], Ys[l][cl], acc);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (part == 0) Ys[i][cl] = (Ys[i][cl] - acc) * rdiag[i];
+    __syncthreads();
+  }
+  if (c < d) {
+    double* Y = Ybase + dim_val(y_off);
+    for (int i = part; i < bp; i += 16) Y[(long long)i * ldy + c] = Ys[i][cl];
+  }
+}
+
 cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V, long long ldv,
                              double* Y, DimRef y_off, long long ldy, long long d, int b, const State* st,
                              cudaStream_t s) {
   (void)b;
-  k_trsm_rows<<<(unsigned)((d + 31) / 32), 32, 0, s>>>(Lc, ldl, perm, V, ldv, Y, y_off, ldy, d, st);
+  k_trsm_rows16<<<(unsigned)((d + 15) / 16), 256, 0, s>>>(Lc, ldl, perm, V, ldv, Y, y_off, ldy, d, st);
   return counted(cudaGetLastError());
 }
 
@@ -556,8 +736,11 @@ cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, c
 // Qp (b'_pad x ldp, rows = basis vectors) and QpT (d x ldpt, transposed).
 // Rows >= b' and columns >= d are zero so padded MMA tiles add nothing.
 // ============================================================================
-__global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* __restrict__ Qp, long long ldp,
-                          float* __restrict__ QpT, long long ldpt, long long d, int bmax, const State* st) {
+// With the lo buffers set (3xTF32), hi is the FP32 value with the 13 low
+// mantissa bits cleared (exact in TF32) and lo = fp32(q - hi) is the rest.
+__global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* __restrict__ Qp,
+                          float* __restrict__ Qp_lo, long long ldp, float* __restrict__ QpT, float* __restrict__ QpT_lo,
+                          long long ldpt, long long d, int bmax, const State* st) {
   if (st->done) return;
   const long long k = st->k;
   const int bp = (int)st->bp;
@@ -565,18 +748,27 @@ __global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* _
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / ldp);
     const long long j = e % ldp;
-    const float v = (i < bp && j < d) ? (float)Qt[(k + i) * ldq + j] : 0.0f;
-    Qp[(long long)i * ldp + j] = v;
-    if (j < d && QpT) QpT[j * ldpt + i] = v;
+    const double q = (i < bp && j < d) ? Qt[(k + i) * ldq + j] : 0.0;
+    float hi = (float)q, lo = 0.0f;
+    if (Qp_lo) {
+      hi = __uint_as_float(__float_as_uint(hi) & 0xFFFFE000u);
+      lo = (float)(q - (double)hi);
+      Qp_lo[(long long)i * ldp + j] = lo;
+    }
+    Qp[(long long)i * ldp + j] = hi;
+    if (j < d && QpT) {
+      QpT[j * ldpt + i] = hi;
+      if (QpT_lo) QpT_lo[j * ldpt + i] = lo;
+    }
   }
 }
 
-cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, long long ldp, float* QpT, long long ldpt,
-                           long long d, int b, const State* st, cudaStream_t s) {
+cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, float* Qp_lo, long long ldp, float* QpT,
+                           float* QpT_lo, long long ldpt, long long d, int b, const State* st, cudaStream_t s) {
   long long tot = (long long)b * ldp;
   unsigned g = (unsigned)((tot + 255) / 256);
   if (g > 2048) g = 2048;
-  k_qp_lowp<<<g, 256, 0, s>>>(Qt, ldq, Qp, ldp, QpT, ldpt, d, b, st);
+  k_qp_lowp<<<g, 256, 0, s>>>(Qt, ldq, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, d, b, st);
   return counted(cudaGetLastError());
 }
 
@@ -718,10 +910,13 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_trsm_cols(T* __restrict__ W, long long ldw, long long n, long long j0, int nb,
                                                    const double* __restrict__ L1, long long ld1) {
   __shared__ T Ls[64][65];
+  __shared__ T rinv[64];
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     const int a = e / nb, c = e % nb;
     Ls[a][c] = (T)L1[(j0 + a) * ld1 + j0 + c];
   }
+  // reciprocals of the diagonal once per CTA instead of one division per element
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) rinv[j] = (T)(1.0 / L1[(j0 + j) * ld1 + j0 + j]);
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -736,7 +931,7 @@ __global__ void __launch_bounds__(128) k_trsm_cols(T* __restrict__ W, long long 
 #pragma unroll
     for (int m = j + 1; m < 64; ++m)
       if (m < nb) s -= w[m] * Ls[m][j];
-    w[j] = s / Ls[j][j];
+    w[j] = s * rinv[j];
   }
 #pragma unroll
   for (int j = 0; j < 64; ++j)

@@ -2,19 +2,28 @@
 //
 // Alg. 2 lines 12 and 16 in the residual form: for every 128-row tile of R,
 //   Lhat = R_tile Q'^T            (GEMM 1, K = d, N = b'_pad)
-//   R_tile <- R_tile - Lhat Q'    (GEMM 2, K = b'_pad, N = d in chunks)
+//   R_tile <- R_tile - Lhat Q'    (GEMM 2, K = b'_pad, N = d in 32-column chunks)
 //   d_i = ||R_i||^2, rows accepted in this block set to 0,
 //   Lhat written to L(:, k : k + b').
 // Operands are staged by TMA (128-byte swizzle) and multiplied by tcgen05.mma
 // kind::tf32 with FP32 accumulators in tensor memory.  Lhat goes TMEM ->
-// registers -> (global L, shared memory A operand of GEMM 2).  The R tile is
-// read twice (GEMM 1 and the subtraction); the second read is meant to hit L2.
+// registers -> (global L, shared-memory A operand of GEMM 2).  The R tile is
+// read twice (GEMM 1 and the subtraction); the second read is served by L2.
+//
+// SPLIT = true is the 3xTF32 form: every operand x is split into hi = x with
+// the low 13 mantissa bits cleared (exact in TF32) and lo = x - hi, and each
+// product is hi*hi + hi*lo + lo*hi.  That brings the contraction to ~FP32
+// accuracy, so the residual does not pick up the per-block floor that plain
+// TF32 leaves (relative energy ~u^2 with u = 2^-11).
 //
 // Roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 owns TMEM and
-// lane 0 issues the MMAs, warps 2-5 (128 threads, one row each) run the
-// epilogues and the TMA stores.  Every mbarrier wait is bounded: after the
-// limit the CTA records RBRP_ETIMEOUT in the State, stops issuing work, waits
-// briefly for copies in flight, frees its TMEM and returns.
+// lane 0 issues the MMAs, warps 2-5 (128 threads, one row each) split the
+// GEMM-1 A operand (SPLIT), run the epilogues and issue the TMA stores.  The
+// row norms are summed in FP32 over each 32-column chunk and the chunk sums in
+// FP64 (per-element FP64 arithmetic would cost ~2 FMA/clock/SM on GB300).
+// Every mbarrier wait is bounded: after the limit the CTA records
+// RBRP_ETIMEOUT in the State, stops issuing work, waits briefly for copies in
+// flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -25,29 +34,31 @@ namespace tc {
 
 constexpr int BM = 128;           // rows per tile (MMA M)
 constexpr int BK1 = 32;           // FP32 elements per 128-byte swizzle row
-constexpr int NB2 = 64;           // d-columns per GEMM-2 chunk (MMA N)
-constexpr int S1 = 4;             // GEMM-1 pipeline stages
-constexpr int S3 = 2;             // GEMM-2 / epilogue stages
+constexpr int NB2 = 32;           // d-columns per GEMM-2 chunk (MMA N)
+constexpr int S1 = 3;             // GEMM-1 pipeline stages
+constexpr int S3 = 3;             // GEMM-2 / epilogue stages
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kD2Col = 128;  // D2 double buffer at TMEM columns 128 and 192
 constexpr uint32_t kSpinLimit = 1u << 24;
 
-template <int BMAX>
+template <int BMAX, bool SPLIT>
 struct Cfg {
-  static constexpr int A1 = BM * BK1 * 4;
-  static constexpr int B1 = BMAX * BK1 * 4;
-  static constexpr int ST1 = A1 + B1;
-  static constexpr int R3 = (NB2 / 32) * BM * 128;
-  static constexpr int B2A = NB2 * 128;  // one 32-wide K atom of the GEMM-2 B tile
+  static constexpr int NOP = SPLIT ? 2 : 1;            // hi (and lo) copies of an operand
+  static constexpr int A1 = BM * BK1 * 4;              // one R chunk (16 KB)
+  static constexpr int B1 = BMAX * BK1 * 4;            // one Q' chunk
+  static constexpr int ST1 = NOP * (A1 + B1);          // [A hi][B hi]([A lo][B lo])
+  static constexpr int R3 = BM * NB2 * 4;              // one R chunk for the subtraction (16 KB)
+  static constexpr int B2A = NB2 * 128;                // one 32-wide K atom of the GEMM-2 B tile
   static constexpr int B2 = (BMAX / 32) * B2A;
-  static constexpr int ST3 = R3 + B2;
+  static constexpr int ST3 = R3 + NOP * B2;
   static constexpr int P = (S1 * ST1 > S3 * ST3) ? S1 * ST1 : S3 * ST3;
-  static constexpr int A2A = BM * 128;   // one 32-wide K atom of Lhat
+  static constexpr int A2A = BM * 128;                 // one 32-wide K atom of Lhat
   static constexpr int A2 = (BMAX / 32) * A2A;
-  static constexpr int BAR_OFF = P + A2;
+  static constexpr int BAR_OFF = P + NOP * A2;
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
+  static constexpr uint32_t D2COL = BMAX;              // D2 double buffer after D1
+  static constexpr uint32_t TMEM_COLS = (BMAX + 2 * NB2 <= 128) ? 128 : 256;
+  static constexpr int MIN_BLOCKS = (SMEM <= 110 * 1024) ? 2 : 1;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -97,8 +108,34 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t sr
                "r"(src), "r"(x), "r"(y)
                : "memory");
 }
+// Same copies with an L2 eviction-priority policy (createpolicy).
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                                 uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d_hint(const CUtensorMap* map, uint32_t src, int x, int y, uint64_t pol) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3}], [%1], %4;" ::"l"(
+                   (uint64_t)map),
+               "r"(src), "r"(x), "r"(y), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void tma_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void tma_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
@@ -133,31 +170,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// hi = x with the 13 low mantissa bits cleared (exactly representable in TF32).
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Offset of the 16-byte chunk `ch` of row `r` inside a 128-byte-swizzled tile.
+__device__ __forceinline__ uint32_t swz(int r, int ch) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4));
+}
+
 // ------------------------------------------------------------------ kernel
-template <int BMAX>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BMAX, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     k_update_tf32(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
-                  const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
+                  const __grid_constant__ CUtensorMap tmQlo, const __grid_constant__ CUtensorMap tmQT,
+                  const __grid_constant__ CUtensorMap tmQTlo, float* __restrict__ L, long long ldl, long long n,
                   long long d, const int* __restrict__ mark, double* __restrict__ dvec,
                   double* __restrict__ partials, State* st) {
-  using C = Cfg<BMAX>;
+  using C = Cfg<BMAX, SPLIT>;
   if (st->done) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
-  const uint32_t sA2 = sb + C::P;
+  const uint32_t sA2 = sb + C::P;             // Lhat hi; Lhat lo follows at + A2 (SPLIT)
   const uint32_t sBar = sb + C::BAR_OFF;
+  // barrier map (8 bytes each)
   auto full1 = [&](int s) { return sBar + 8u * s; };
   auto empty1 = [&](int s) { return sBar + 8u * (S1 + s); };
-  auto full3 = [&](int s) { return sBar + 8u * (2 * S1 + s); };
-  auto empty3 = [&](int s) { return sBar + 8u * (2 * S1 + S3 + s); };
-  const uint32_t d1_full = sBar + 8u * (2 * S1 + 2 * S3);
+  auto conv1 = [&](int s) { return sBar + 8u * (2 * S1 + s); };            // SPLIT: A lo written
+  auto full3 = [&](int s) { return sBar + 8u * (3 * S1 + s); };
+  auto empty3 = [&](int s) { return sBar + 8u * (3 * S1 + S3 + s); };
+  auto epi_done = [&](int s) { return sBar + 8u * (3 * S1 + 2 * S3 + s); };
+  const uint32_t d1_full = sBar + 8u * (3 * S1 + 3 * S3);
   const uint32_t a2_ready = d1_full + 8u;
   auto d2_full = [&](int b) { return a2_ready + 8u + 8u * b; };
   auto d2_empty = [&](int b) { return a2_ready + 24u + 8u * b; };
-  auto epi_done = [&](int s) { return a2_ready + 40u + 8u * s; };  // S3 barriers
-  const uint32_t red_bar = a2_ready + 40u + 8u * S3;
-  uint32_t* tmem_slot = (uint32_t*)(smem + C::BAR_OFF + 8 * (2 * S1 + 2 * S3 + 7 + S3));
+  const uint32_t red_bar = a2_ready + 40u;
+  uint32_t* tmem_slot = (uint32_t*)(smem + C::BAR_OFF + 8 * (3 * S1 + 3 * S3 + 7));
 
   __shared__ int s_abort;
   __shared__ double s_red[4];
@@ -176,10 +224,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < S1; ++s) {
       mbar_init(full1(s), 1);
       mbar_init(empty1(s), 1);
+      mbar_init(conv1(s), 128);
     }
     for (int s = 0; s < S3; ++s) {
       mbar_init(full3(s), 1);
       mbar_init(empty3(s), 2);
+      mbar_init(epi_done(s), 128);
     }
     mbar_init(d1_full, 1);
     mbar_init(a2_ready, 128);
@@ -187,13 +237,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(d2_full(b), 1);
       mbar_init(d2_empty(b), 128);
     }
-    for (int s = 0; s < S3; ++s) mbar_init(epi_done(s), 128);
     mbar_init(red_bar, 128);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -206,27 +255,35 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      const uint32_t bytes1 = (uint32_t)C::ST1;
+      // The first read of the R tile asks L2 to keep it (it is read again for the
+      // subtraction); the second read and the stores ask for early eviction.
+      const uint64_t keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
       for (int kc = 0; kc < nK1; ++kc) {
         const int s = kc % S1;
         const uint32_t ph = (uint32_t)(kc / S1) & 1u;
         if (!mbar_wait(empty1(s), ph ^ 1u, abort)) break;
-        mbar_expect_tx(full1(s), bytes1);
-        tma_load_2d(sb + s * C::ST1, &tmR, full1(s), kc * BK1, (int)row0);
-        tma_load_2d(sb + s * C::ST1 + C::A1, &tmQ, full1(s), kc * BK1, 0);
+        mbar_expect_tx(full1(s), (uint32_t)((C::A1 + C::B1) + (SPLIT ? C::B1 : 0)));
+        const uint32_t base = sb + s * C::ST1;
+        tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)row0, keep);
+        tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
+        if (SPLIT) tma_load_2d(base + 2 * C::A1 + C::B1, &tmQlo, full1(s), kc * BK1, 0);
       }
-      // phase-3 buffers alias the phase-1 ring: reuse only after GEMM 1 has drained it
+      // phase-3 buffers alias the phase-1 ring: reuse only after GEMM 1 has drained it.
+      // Chunks are taken last-to-first so the most recently loaded columns are re-read first.
       if (mbar_wait(d1_full, 0, abort)) {
         for (int c = 0; c < nC; ++c) {
           const int s = c % S3;
           const uint32_t ph = (uint32_t)(c / S3) & 1u;
+          const int col = (nC - 1 - c) * NB2;
           if (!mbar_wait(empty3(s), ph ^ 1u, abort)) break;
           mbar_expect_tx(full3(s), (uint32_t)C::ST3);
           const uint32_t base = sb + s * C::ST3;
+          tma_load_2d_hint(base, &tmR, full3(s), col, (int)row0, drop);
 #pragma unroll
-          for (int q = 0; q < NB2 / 32; ++q) tma_load_2d(base + q * (BM * 128), &tmR, full3(s), c * NB2 + q * 32, (int)row0);
-#pragma unroll
-          for (int a = 0; a < BMAX / 32; ++a) tma_load_2d(base + C::R3 + a * C::B2A, &tmQT, full3(s), a * 32, c * NB2);
+          for (int a = 0; a < BMAX / 32; ++a) {
+            tma_load_2d(base + C::R3 + a * C::B2A, &tmQT, full3(s), a * 32, col);
+            if (SPLIT) tma_load_2d(base + C::R3 + C::B2 + a * C::B2A, &tmQTlo, full3(s), a * 32, col);
+          }
         }
       }
     }
@@ -238,11 +295,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = kc % S1;
         const uint32_t ph = (uint32_t)(kc / S1) & 1u;
         if (!mbar_wait(full1(s), ph, abort)) break;
+        if (SPLIT && !mbar_wait(conv1(s), ph, abort)) break;
         tc_after();
         const uint32_t a = sb + s * C::ST1, b = a + C::A1;
+        const uint32_t alo = a + C::A1 + C::B1, blo = alo + C::A1;
 #pragma unroll
-        for (int kk = 0; kk < BK1 / 8; ++kk)
+        for (int kk = 0; kk < BK1 / 8; ++kk) {
           mma_tf32(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), id1, (kc | kk) != 0 ? 1u : 0u);
+          if (SPLIT) {
+            mma_tf32(tmem, sdesc(a + kk * 32), sdesc(blo + kk * 32), id1, 1u);
+            mma_tf32(tmem, sdesc(alo + kk * 32), sdesc(b + kk * 32), id1, 1u);
+          }
+        }
         mma_commit(empty1(s));
       }
       mma_commit(d1_full);
@@ -258,11 +322,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(full3(s), ph, abort)) break;
           if (!mbar_wait(d2_empty(buf), bph ^ 1u, abort)) break;
           tc_after();
-          const uint32_t dt = tmem + kD2Col + (uint32_t)(buf * NB2);
+          const uint32_t dt = tmem + C::D2COL + (uint32_t)(buf * NB2);
           const uint32_t b2 = sb + s * C::ST3 + C::R3;
           for (int q = 0; q < nk2; ++q) {
             const int a = q >> 2, kk = q & 3;
-            mma_tf32(dt, sdesc(sA2 + a * C::A2A + kk * 32), sdesc(b2 + a * C::B2A + kk * 32), id2, q != 0 ? 1u : 0u);
+            const uint32_t ao = a * C::A2A + kk * 32, bo = a * C::B2A + kk * 32;
+            mma_tf32(dt, sdesc(sA2 + ao), sdesc(b2 + bo), id2, q != 0 ? 1u : 0u);
+            if (SPLIT) {
+              mma_tf32(dt, sdesc(sA2 + ao), sdesc(b2 + C::B2 + bo), id2, 1u);
+              mma_tf32(dt, sdesc(sA2 + C::A2 + ao), sdesc(b2 + bo), id2, 1u);
+            }
           }
           mma_commit(empty3(s));
           mma_commit(d2_full(buf));
@@ -270,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: 128 threads, thread <-> row
+    // ---------------- warps 2-5: 128 threads, thread <-> row
     const int q = warp & 3;
     const int r = 32 * q + lane;
     const int et = threadIdx.x - 64;
@@ -278,6 +347,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool in = row < n;
     const bool marked = in && (mark[row] == tno);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const uint64_t drop = l2_policy_evict_first();
+    if (SPLIT) {
+      // split each GEMM-1 A chunk in place: hi stays, lo goes to its own buffer
+      for (int kc = 0; kc < nK1; ++kc) {
+        const int s = kc % S1;
+        const uint32_t ph = (uint32_t)(kc / S1) & 1u;
+        if (!mbar_wait(full1(s), ph, abort)) break;
+        uint8_t* a = smem + s * C::ST1 + (r >> 3) * 1024 + (r & 7) * 128;
+        uint8_t* alo = smem + s * C::ST1 + C::A1 + C::B1 + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          float4 x = *(float4*)(a + ch * 16);
+          float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+          *(float4*)(a + ch * 16) = h;
+          *(float4*)(alo + ch * 16) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        fence_async_smem();
+        mbar_arrive(conv1(s));
+      }
+    }
     double nrm = 0.0;
     if (mbar_wait(d1_full, 0, abort)) {
       tc_after();
@@ -291,12 +380,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 32; ++j)
             if (cb * 32 + j < bp) lrow[j] = __uint_as_float(v[j]);
         }
-        uint8_t* a2row = smem + C::P + cb * C::A2A + (r >> 3) * 1024 + (r & 7) * 128;
+        uint8_t* a2 = smem + C::P + cb * C::A2A;
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch)
-          *(float4*)(a2row + ((ch ^ (r & 7)) << 4)) =
-              make_float4(__uint_as_float(v[4 * ch]), __uint_as_float(v[4 * ch + 1]), __uint_as_float(v[4 * ch + 2]),
-                          __uint_as_float(v[4 * ch + 3]));
+        for (int ch = 0; ch < 8; ++ch) {
+          const float4 x = make_float4(__uint_as_float(v[4 * ch]), __uint_as_float(v[4 * ch + 1]),
+                                       __uint_as_float(v[4 * ch + 2]), __uint_as_float(v[4 * ch + 3]));
+          if (SPLIT) {
+            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            *(float4*)(a2 + swz(r, ch)) = h;
+            *(float4*)(a2 + C::A2 + swz(r, ch)) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          } else {
+            *(float4*)(a2 + swz(r, ch)) = x;
+          }
+        }
       }
     }
     fence_async_smem();
@@ -310,28 +406,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(full3(s), ph, abort)) break;
       if (!mbar_wait(d2_full(buf), bph, abort)) break;
       tc_after();
+      uint32_t u[32];
+      tmem_ld32(tmem + lane_base + C::D2COL + (uint32_t)(buf * NB2), u);
+      tmem_wait_ld();
+      uint8_t* rrow = smem + s * C::ST3;
+      float part = 0.f;
 #pragma unroll
-      for (int q4 = 0; q4 < NB2 / 32; ++q4) {
-        uint32_t u[32];
-        tmem_ld32(tmem + lane_base + kD2Col + (uint32_t)(buf * NB2 + q4 * 32), u);
-        tmem_wait_ld();
-        uint8_t* rrow = smem + s * C::ST3 + q4 * (BM * 128) + (r >> 3) * 1024 + (r & 7) * 128;
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-          float4* p = (float4*)(rrow + ((ch ^ (r & 7)) << 4));
-          float4 x = *p;
-          x.x -= __uint_as_float(u[4 * ch]);
-          x.y -= __uint_as_float(u[4 * ch + 1]);
-          x.z -= __uint_as_float(u[4 * ch + 2]);
-          x.w -= __uint_as_float(u[4 * ch + 3]);
-          if (marked) x = make_float4(0.f, 0.f, 0.f, 0.f);
-          nrm = fma((double)x.x, (double)x.x, nrm);
-          nrm = fma((double)x.y, (double)x.y, nrm);
-          nrm = fma((double)x.z, (double)x.z, nrm);
-          nrm = fma((double)x.w, (double)x.w, nrm);
-          *p = x;
-        }
+      for (int ch = 0; ch < 8; ++ch) {
+        float4* p = (float4*)(rrow + swz(r, ch));
+        float4 x = *p;
+        x.x -= __uint_as_float(u[4 * ch]);
+        x.y -= __uint_as_float(u[4 * ch + 1]);
+        x.z -= __uint_as_float(u[4 * ch + 2]);
+        x.w -= __uint_as_float(u[4 * ch + 3]);
+        if (marked) x = make_float4(0.f, 0.f, 0.f, 0.f);
+        part = fmaf(x.x, x.x, part);
+        part = fmaf(x.y, x.y, part);
+        part = fmaf(x.z, x.z, part);
+        part = fmaf(x.w, x.w, part);
+        *p = x;
       }
+      nrm += (double)part;
       tc_before();
       mbar_arrive(d2_empty(buf));
       fence_async_smem();
@@ -339,12 +434,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (et == 0) {
         // every epilogue thread has written its row of this chunk (bounded wait)
         if (!mbar_wait(epi_done(s), ph, abort)) break;
-        const uint32_t base = sb + s * C::ST3;
-#pragma unroll
-        for (int q4 = 0; q4 < NB2 / 32; ++q4) tma_store_2d(&tmR, base + q4 * (BM * 128), c * NB2 + q4 * 32, (int)row0);
+        tma_store_2d_hint(&tmR, sb + s * C::ST3, (nC - 1 - c) * NB2, (int)row0, drop);
         tma_commit();
-        tma_wait_read0();
-        mbar_arrive(empty3(s));
+        // with at most this store pending, the previous chunk's stage has been read out
+        if (c > 0) {
+          tma_wait_read1();
+          mbar_arrive(empty3((c - 1) % S3));
+        }
       }
     }
     if (in) dvec[row] = marked ? 0.0 : nrm;
@@ -371,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     tc_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
@@ -404,24 +500,32 @@ bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer,
   return r == CUDA_SUCCESS;
 }
 
-template <int BMAX>
-cudaError_t launch_bmax(float* R, long long ldr, long long n, long long d, const float* Qp, long long ldp,
-                        const float* QpT, long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
-                        double* partials, const State* st, cudaStream_t s) {
-  using C = Cfg<BMAX>;
+template <int BMAX, bool SPLIT>
+cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
+                       long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L, long long ldl,
+                       const int* mark, double* dvec, double* partials, const State* st, cudaStream_t s) {
+  using C = Cfg<BMAX, SPLIT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_update_tf32<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_update_tf32<BMAX, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  CUtensorMap mR, mQ, mQT;
+  CUtensorMap mR, mQ, mQlo, mQT, mQTlo;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, BM)) return cudaErrorInvalidValue;
   if (!make_map(&mQ, Qp, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, ldpt, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
+  if (SPLIT) {
+    if (!make_map(&mQlo, Qp_lo, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+    if (!make_map(&mQTlo, QpT_lo, ldpt, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
+  } else {
+    mQlo = mQ;
+    mQTlo = mQT;
+  }
   const unsigned grid = (unsigned)((n + BM - 1) / BM);
-  k_update_tf32<BMAX><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQT, L, ldl, n, d, mark, dvec, partials,
-                                                      const_cast<State*>(st));
+  k_update_tf32<BMAX, SPLIT><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark, dvec,
+                                                             partials, const_cast<State*>(st));
   return counted(cudaGetLastError());
 }
 
@@ -429,17 +533,22 @@ cudaError_t launch_bmax(float* R, long long ldr, long long n, long long d, const
 
 int update_tf32_parts(long long n) { return (int)((n + tc::BM - 1) / tc::BM); }
 
-cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp, long long ldp,
-                               const float* QpT, long long ldpt, float* L, long long ldl, const int* mark,
-                               double* dvec, double* partials, int nparts, const State* st, int bmax,
-                               cudaStream_t s) {
-  (void)nparts;
-  if (bmax <= 32)
-    return tc::launch_bmax<32>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
-  if (bmax <= 64)
-    return tc::launch_bmax<64>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
-  if (bmax <= 128)
-    return tc::launch_bmax<128>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+int update_tf32_max_block(int split) { return split ? 64 : 128; }
+
+cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
+                               long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L,
+                               long long ldl, const int* mark, double* dvec, double* partials, const State* st,
+                               int bmax, int split, cudaStream_t s) {
+#define RBRP_TC_ARGS R, ldr, n, d, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, L, ldl, mark, dvec, partials, st, s
+  if (split) {
+    if (bmax <= 32) return tc::launch_cfg<32, true>(RBRP_TC_ARGS);
+    if (bmax <= 64) return tc::launch_cfg<64, true>(RBRP_TC_ARGS);
+    return cudaErrorInvalidValue;
+  }
+  if (bmax <= 32) return tc::launch_cfg<32, false>(RBRP_TC_ARGS);
+  if (bmax <= 64) return tc::launch_cfg<64, false>(RBRP_TC_ARGS);
+  if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
+#undef RBRP_TC_ARGS
   return cudaErrorInvalidValue;
 }
 

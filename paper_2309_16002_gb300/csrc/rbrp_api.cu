@@ -5,6 +5,7 @@
 // once per group of blocks to see whether the stopping test has fired (blocks
 // queued after that return at once).
 #include <stdio.h>
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -67,30 +68,34 @@ struct Plan {
   size_t pm, pn;  // split-K partial buffer extents (elements per split)
   size_t partial_elems;
   size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
-      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_L1, off_W32, total;
+      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_W32, total;
 };
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
-int splits_for(long long M, long long N, long long K) {
-  const long long tiles = ((M + kGemmTile - 1) / kGemmTile) * ((N + kGemmTile - 1) / kGemmTile);
-  long long s = (304 + tiles - 1) / std::max(1LL, tiles);
-  const long long kmax = std::max(1LL, (K + 63) / 64);
+// K-splits so that about `target` CTAs get work, each at least one 16-deep K step.
+// FP64 products want every SM busy (~4 CTAs per SM); FP32 products are cheap
+// enough that fewer splits (less partial-sum traffic) win.
+int splits_for(long long M, long long N, long long K, int tile = kGemmTile, long long target = 608) {
+  const long long tiles = ((M + tile - 1) / tile) * ((N + tile - 1) / tile);
+  long long s = (target + tiles - 1) / std::max(1LL, tiles);
+  const long long kmax = std::max(1LL, (K + 15) / 16);
   s = std::min(s, kmax);
-  s = std::max(1LL, std::min(s, 64LL));
+  s = std::max(1LL, std::min(s, 256LL));
   return (int)s;
 }
 
 rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   if (!o || n <= 0 || d <= 0) return RBRP_EINVAL;
   if (o->block < 1 || o->block > kMaxBlock) return RBRP_EINVAL;
-  if (o->precision < RBRP_FP64 || o->precision > RBRP_FP32) return RBRP_EINVAL;
+  if (o->precision < RBRP_FP64 || o->precision > RBRP_TF32X3) return RBRP_EINVAL;
   if (o->sampler != RBRP_SAMPLER_RANDOM && o->sampler != RBRP_SAMPLER_GREEDY) return RBRP_EINVAL;
   if (o->w_precision != RBRP_W_FP64 && o->w_precision != RBRP_W_FP32) return RBRP_EINVAL;
   if (o->tau_b > 1.0) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
   // the tensor-core update keeps Lhat (128 x b'_pad) in shared memory: b <= 128
-  if (o->precision == RBRP_TF32 && o->block > 128) return RBRP_EINVAL;
+  if (o->precision == RBRP_TF32 && o->block > update_tf32_max_block(0)) return RBRP_EINVAL;
+  if (o->precision == RBRP_TF32X3 && o->block > update_tf32_max_block(1)) return RBRP_EINVAL;
   memset(p, 0, sizeof(*p));
   p->n = n;
   p->d = d;
@@ -117,16 +122,17 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
     p->nparts = (int)std::min(np, 4LL * 152);
   }
   const long long b = p->b;
-  p->s_coef = splits_for(b, kc, d);
-  p->s_apply = splits_for(b, d, kc);
-  p->s_gram = splits_for(b, b, d);
+  const long long cgs_target = (p->prec == RBRP_FP64) ? 608 : 160;
+  p->s_coef = splits_for(b, kc, d, kGemmTile, cgs_target);
+  p->s_apply = splits_for(b, d, kc, kGemmTile, cgs_target);
+  p->s_gram = splits_for(b, b, d, 32);
   p->s_upd1 = splits_for(n, b, d);
   p->s_upd2 = splits_for(n, d, b);
   size_t need = 0;
   need = std::max<size_t>(need, (size_t)p->s_coef * b * kc);
   need = std::max<size_t>(need, (size_t)p->s_apply * b * d);
   need = std::max<size_t>(need, (size_t)p->s_gram * b * b);
-  if (p->prec != RBRP_TF32) {
+  if (p->prec == RBRP_FP64 || p->prec == RBRP_FP32) {
     need = std::max<size_t>(need, (size_t)p->s_upd1 * n * b);
     need = std::max<size_t>(need, (size_t)p->s_upd2 * n * d);
   }
@@ -159,6 +165,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->off_gp = take(p->partial_elems * 8);
   p->off_Qp = take((size_t)p->ldpt * p->ldp * 4);
   p->off_QpT = take((size_t)p->ldq * p->ldpt * 4);
+  p->off_Qplo = take(p->prec == RBRP_TF32X3 ? (size_t)p->ldpt * p->ldp * 4 : 0);
+  p->off_QpTlo = take(p->prec == RBRP_TF32X3 ? (size_t)p->ldq * p->ldpt * 4 : 0);
   p->off_L1 = take((size_t)kc * kc * 8);
   p->off_W32 = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
   p->total = off;
@@ -194,6 +202,8 @@ struct Bufs {
   void* gp;
   float* Qp;
   float* QpT;
+  float* Qp_lo;
+  float* QpT_lo;
   double* L1;
   float* W32;
   long long* skel;
@@ -221,6 +231,8 @@ Bufs carve(const Plan& p, void* ws) {
   u.gp = b + p.off_gp;
   u.Qp = (float*)(b + p.off_Qp);
   u.QpT = (float*)(b + p.off_QpT);
+  u.Qp_lo = (p.prec == RBRP_TF32X3) ? (float*)(b + p.off_Qplo) : nullptr;
+  u.QpT_lo = (p.prec == RBRP_TF32X3) ? (float*)(b + p.off_QpTlo) : nullptr;
   u.L1 = (double*)(b + p.off_L1);
   u.W32 = p.w32 ? (float*)(b + p.off_W32) : nullptr;
   u.skel = nullptr;
@@ -232,7 +244,7 @@ MatRef mat(void* base, DimRef off, long long rs, long long cs) { return MatRef{b
 template <typename TA, typename TB, typename TC, typename TACC>
 cudaError_t gemm(const Plan& p, const Bufs& u, MatRef A, MatRef B, MatRef C, DimRef M, DimRef N, DimRef K,
                  double alpha, double beta, long long Mmax, long long Nmax, int splits, const State* st,
-                 cudaStream_t s) {
+                 cudaStream_t s, int tile = kGemmTile) {
   GemmArgs g;
   g.A = A;
   g.B = B;
@@ -247,20 +259,33 @@ cudaError_t gemm(const Plan& p, const Bufs& u, MatRef A, MatRef B, MatRef C, Dim
   g.pn = Nmax;
   g.st = st;
   if ((size_t)splits * Mmax * Nmax > p.partial_elems) splits = 1;
-  return launch_gemm<TA, TB, TC, TACC>(g, Mmax, Nmax, splits, s);
+  return launch_gemm<TA, TB, TC, TACC>(g, Mmax, Nmax, splits, tile, s);
 }
 
 // V <- V - (V Qt^T) Qt on rows [0, rows) of V (rows from the device), in FP64.
-cudaError_t cgs_pass(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s) {
+//
+// V and Q stay FP64 and the correction is subtracted in FP64.  On the mixed
+// paths (TF32 / FP32 residual) the correction products use FP32 (TACC = float):
+// the rows of V come from a residual that is already orthogonal to Q up to the
+// update's rounding, so the coefficients are small and each pass shrinks the
+// component in span(Q) by the FP32 product accuracy (~1e-7); two passes leave
+// it at FP64 level.  The FP64 path keeps FP64 products throughout.
+template <typename TACC>
+cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s) {
   const State* st = u.st;
   const long long kc = p.k_cap, b = p.b;
-  cudaError_t e = gemm<double, double, double, double>(
+  cudaError_t e = gemm<double, double, double, TACC>(
       p, u, mat(V, dim_const(0), p.ldq, 1), mat(u.Qt, dim_const(0), 1, p.ldq), mat(u.C, dim_const(0), p.ldc, 1),
       rows, dim_dev(&st->k), dim_const(p.d), 1.0, 0.0, b, kc, p.s_coef, st, s);
   if (e != cudaSuccess) return e;
-  return gemm<double, double, double, double>(
+  return gemm<double, double, double, TACC>(
       p, u, mat(u.C, dim_const(0), p.ldc, 1), mat(u.Qt, dim_const(0), p.ldq, 1), mat(V, dim_const(0), p.ldq, 1),
       rows, dim_const(p.d), dim_dev(&st->k), -1.0, 1.0, b, p.d, p.s_apply, st, s);
+}
+
+cudaError_t cgs_pass(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s) {
+  if (p.prec == RBRP_FP64) return cgs_pass_t<double>(p, u, V, rows, s);
+  return cgs_pass_t<float>(p, u, V, rows, s);
 }
 
 cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s);
@@ -284,22 +309,23 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   // lines 7-9: G = V V^T, pivoted Cholesky with the tail-mass truncation
   LK((gemm<double, double, double, double>(p, u, mat(u.V, dim_const(0), p.ldq, 1), mat(u.V, dim_const(0), 1, p.ldq),
                                            mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->b_t), dim_dev(&st->b_t),
-                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s)));
+                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
   LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
   // Q'_V: Y = Lc^{-1} V(perm), then CGS against Q and a second CholQR pass
   LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
   LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
   LK((gemm<double, double, double, double>(p, u, mat(u.Y, dim_const(0), p.ldq, 1), mat(u.Y, dim_const(0), 1, p.ldq),
                                            mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->bp), dim_dev(&st->bp),
-                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s)));
+                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
   LK(launch_chol(u.G, p.ldg, u.Lc, p.ldlc, p.b, st, s));
   LK(launch_trsm_rows(u.Lc, p.ldlc, nullptr, u.Y, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
   // lines 12 and 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
-  if (p.prec == RBRP_TF32) {
-    LK(launch_qp_lowp(u.Qt, p.ldq, u.Qp, p.ldp, u.QpT, p.ldpt, d, (int)p.ldpt, st, s));
+  if (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) {
+    const int split = (p.prec == RBRP_TF32X3);
+    LK(launch_qp_lowp(u.Qt, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
     LK(timed(g_prof.upd, s, [&] {
-      return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, p.ldp, u.QpT, p.ldpt, (float*)u.L, p.ldl, u.mark,
-                                u.dvec, u.part, update_tf32_parts(n), st, (int)p.ldpt, s);
+      return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, (float*)u.L,
+                                p.ldl, u.mark, u.dvec, u.part, st, (int)p.ldpt, split, s);
     }));
     LK(launch_finalize_block(u.part, update_tf32_parts(n), st, s));
     return cudaSuccess;
@@ -400,7 +426,11 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   // Alg. 2 lines 1-2
   CK(launch_init_norms(X, x_is_fp64, n, d, ldx, u.R, p.r64, p.ldr, u.dvec, u.mark, u.part, p.nparts, st, s));
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
-  // Alg. 2 lines 3-16: blocks are queued in groups; queued blocks after the stop return at once
+  // Alg. 2 lines 3-16: blocks are queued in groups and the State is read back
+  // after each group.  The group size is the number of blocks still expected,
+  // extrapolated from the observed per-block decay of ||d||_1 (or of the rank
+  // gap in fixed-rank mode), so that few blocks are queued past the stop
+  // (those return at once) and few host round trips are needed.
   State h;
   long long queued = 0;
   long long group = 2;
@@ -415,7 +445,17 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
     CK(cudaMemcpyAsync(&h, st, sizeof(State), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h.done || queued >= p.k_cap) break;
-    group = std::min<long long>(group * 2, 16);
+    double est = 2.0;
+    if (h.t > 0 && h.k > 0) {
+      const double per_block_k = (double)h.k / (double)h.t;
+      est = (double)(h.k_cap - h.k) / per_block_k;  // blocks to the rank cap
+      if (tol >= 0.0 && h.D > 0.0 && h.D0 > 0.0 && h.D < h.D0) {
+        const double rate = log(h.D0 / h.D) / (double)h.t;  // mean log-decay per block
+        const double need = log(h.D / (tol * h.D0)) / rate;
+        if (need < est) est = need;
+      }
+    }
+    group = std::max<long long>(1, std::min<long long>(16, (long long)ceil(est)));
   }
   if (h.status != 0) return (rbrp_status)h.status;
   res->k = h.k;

@@ -122,7 +122,7 @@ size_t sample_scratch_pairs(long long n, int b);
 cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t,
                           double* V, long long ldv, long long d, int b, const State* st, cudaStream_t s);
 template <typename TA, typename TB, typename TC, typename TACC>
-cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, cudaStream_t s);
+cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, int tile, cudaStream_t s);
 cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
                           int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
@@ -130,8 +130,9 @@ cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ld
 cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V,
                              long long ldv, double* Y, DimRef y_off, long long ldy, long long d, int b,
                              const State* st, cudaStream_t s);
-cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, long long ldp, float* QpT,
-                           long long ldpt, long long d, int b, const State* st, cudaStream_t s);
+// FP32 copies of the new basis rows Q' (and, when Qp_lo is set, the TF32 hi/lo split).
+cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, float* Qp_lo, long long ldp, float* QpT,
+                           float* QpT_lo, long long ldpt, long long d, int b, const State* st, cudaStream_t s);
 cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d,
                               const int* mark, double* dvec, double* partials, int nparts,
                               const State* st, cudaStream_t s);
@@ -153,10 +154,12 @@ cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long lon
 // tcgen05 fused residual update (k_update_tc.cu): per 128-row tile,
 // Lhat = R Q'^T (TF32 in, FP32 accumulate in TMEM), R -= Lhat Q', d_i = ||R_i||^2,
 // rows accepted in this block zeroed; Lhat stored to L(:, k : k + b').
+// split = 1: 3xTF32 (Qp_lo / QpT_lo hold the low parts of Q').
 cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp,
-                               long long ldp, const float* QpT, long long ldpt, float* L, long long ldl,
-                               const int* mark, double* dvec, double* partials, int nparts,
-                               const State* st, int bmax, cudaStream_t s);
+                               const float* Qp_lo, long long ldp, const float* QpT, const float* QpT_lo,
+                               long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
+                               double* partials, const State* st, int bmax, int split, cudaStream_t s);
 int update_tf32_parts(long long n);
+int update_tf32_max_block(int split);
 
 }  // namespace rbrp
