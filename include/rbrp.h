@@ -158,6 +158,36 @@ typedef struct {
 void rbrp_profile_begin(void);
 rbrp_status rbrp_profile_end(rbrp_profile *out);
 
+/*
+ * rbrp_id_noalloc -- rbrp_id for callers that cannot allocate device memory.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * Some callers run where cudaMalloc is not an option: inside an engine or
+ * plugin host that owns all device memory and forbids further allocation, or
+ * in code that must not grow a memory pool it does not control.  This entry
+ * point takes the same inputs and caller-owned outputs as rbrp_id (X, skel, W
+ * and res exactly as documented there) but uses, instead of a caller
+ * workspace, one fixed array of RBRP_NOALLOC_SCRATCH_BYTES bytes that lives in
+ * the library's device image: it calls no cudaMalloc, no cudaFree and no
+ * allocating library routine.  Every GPU that loads the library holds that
+ * array until the process exits.
+ *
+ * Limits and behaviour:
+ *  - a problem whose rbrp_workspace_size exceeds RBRP_NOALLOC_SCRATCH_BYTES is
+ *    rejected with RBRP_EWORKSPACE before anything is launched;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - all calls on a device share the one array and it keeps the previous
+ *    call's contents (each call rewrites what it reads), so calls whose work
+ *    overlaps on the GPU (different streams, different host threads) race and
+ *    must be serialised by the caller.
+ */
+#define RBRP_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+rbrp_status rbrp_id_noalloc(const void *X, int x_is_fp64, int64_t n, int64_t d, int64_t ldx,
+                            double tol, const rbrp_opts *o, int64_t *skel, double *W, int64_t ldw,
+                            rbrp_result *res, rbrp_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *rbrp_status_string(rbrp_status s);
 

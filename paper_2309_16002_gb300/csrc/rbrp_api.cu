@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "rbrp_internal.cuh"
@@ -486,6 +487,41 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
 }
 
 }  // namespace
+// ---------------------------------------------------------------- fixed scratch for rbrp_id_noalloc
+// Some callers cannot allocate device memory at all: code running inside an
+// allocator-free runtime (a plugin or an embedded engine that owns every byte
+// of device memory and forbids cudaMalloc once it has started), or code that
+// must not add to a memory pool it does not control.  For them the workspace of
+// rbrp_id_noalloc is this fixed array, which the CUDA runtime places in device
+// memory when the library's module is loaded on a device; every GPU that loads
+// the library keeps these RBRP_NOALLOC_SCRATCH_BYTES bytes until the process
+// exits.  In host code `g_noalloc_scratch` only names a host-side stand-in, so
+// the device address is looked up with cudaGetSymbolAddress (once per device).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RBRP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+// Device address of the fixed scratch on the current device (looked up on first use).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 }  // namespace rbrp
 
 using namespace rbrp;
@@ -582,6 +618,24 @@ const char* rbrp_status_string(rbrp_status s) {
 }
 
 int rbrp_last_cuda_error(void) { return g_last_cuda; }
+
+// rbrp_id with the workspace taken from the fixed device array above: no
+// cudaMalloc, no cudaFree, no allocating library call.  The run writes every
+// scratch word it reads before reading it (norms, residual copy, State, sampler
+// candidates, Gram and factor buffers are all produced inside the call), so
+// the contents left by the previous call need no clearing.
+rbrp_status rbrp_id_noalloc(const void* X, int x_is_fp64, int64_t n, int64_t d, int64_t ldx, double tol,
+                            const rbrp_opts* o, int64_t* skel, double* W, int64_t ldw, rbrp_result* res,
+                            rbrp_stream_t stream) {
+  size_t need = 0;
+  rbrp_status rs = rbrp_workspace_size(n, d, o, &need);
+  if (rs != RBRP_OK) return rs;
+  if (need > (size_t)RBRP_NOALLOC_SCRATCH_BYTES) return RBRP_EWORKSPACE;
+  void* ws = nullptr;
+  CK(noalloc_scratch(&ws));
+  return run(X, x_is_fp64, n, d, ldx, tol, o, ws, (size_t)RBRP_NOALLOC_SCRATCH_BYTES, (long long*)skel, W, ldw, res,
+             (cudaStream_t)stream);
+}
 
 void rbrp_profile_begin(void) {
   g_prof.on = true;

@@ -26,7 +26,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 RBRP_ENOTCONVERGED = 5
 
 EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_workspace_size", "rbrp_id_host",
-           "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end"]
+           "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
+           "rbrp_id_noalloc"]
 
 
 class Opts(ctypes.Structure):
@@ -84,6 +85,9 @@ def load():
     L.rbrp_status_string.restype = ctypes.c_char_p
     L.rbrp_last_cuda_error.argtypes = []
     L.rbrp_last_cuda_error.restype = ctypes.c_int
+    L.rbrp_id_noalloc.argtypes = [vp, ctypes.c_int, i64, i64, i64, dbl, ctypes.POINTER(Opts), vp, vp, i64,
+                                  ctypes.POINTER(Result), vp]
+    L.rbrp_id_noalloc.restype = ctypes.c_int
     L.rbrp_profile_begin.argtypes = []
     L.rbrp_profile_begin.restype = None
     L.rbrp_profile_end.argtypes = [ctypes.POINTER(Profile)]
@@ -198,6 +202,30 @@ def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, pro
     k = out["k"]
     out["S"] = ws.skel[:k]
     out["W"] = ws.W[:, :k]
+    return out
+
+
+def rbrp_id_noalloc(X, tol, skel_out, W_out, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0,
+                    sampler="random", w_precision="fp64", stream=None):
+    """rbrp_id without any device allocation by the library: the workspace is the library's
+    fixed device array (RBRP_NOALLOC_SCRATCH_BYTES).  For callers that cannot allocate; the
+    outputs skel_out (int64[k_cap]) and W_out (FP64 n x k_cap) are the caller's CUDA tensors."""
+    import torch
+    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
+    n, d = X.shape
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
+    res = Result()
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    st = load().rbrp_id_noalloc(ctypes.c_void_p(X.data_ptr()), int(X.dtype == torch.float64), n, d, X.stride(0),
+                                float(tol), ctypes.byref(opts), ctypes.c_void_p(skel_out.data_ptr()),
+                                ctypes.c_void_p(W_out.data_ptr()), W_out.stride(0), ctypes.byref(res),
+                                ctypes.c_void_p(s.cuda_stream))
+    _check(st, "rbrp_id_noalloc")
+    out = _result_dict(res, st)
+    k = out["k"]
+    out["S"] = skel_out[:k]
+    out["W"] = W_out[:, :k]
     return out
 
 
