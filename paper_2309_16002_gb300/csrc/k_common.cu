@@ -391,347 +391,6 @@ template cudaError_t launch_gemm<double, double, double, float>(const GemmArgs&,
 template cudaError_t launch_gemm<float, double, float, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
 
 // ============================================================================
-// Alg. 2 lines 7-9 and the robust blockwise filtering remark (Sec. 4):
-// pivoted QR of V^T with truncation at the first i where the trailing mass
-// ||R_V(i:, i:)||_F^2 falls below tau_b ||R_V||_F^2.  On the GPU this is the
-// pivoted Cholesky factorisation of the Gram matrix G = V V^T (the same
-// pivots and R_V diagonal in exact arithmetic): the Schur-complement diagonal
-// is each remaining candidate's residual norm^2 and its sum is the trailing
-// mass.  One CTA.  pivoted = 0 gives a plain Cholesky (for CholQR2).
-// ============================================================================
-__global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ G, long long ldg,
-                                               double* __restrict__ Lc, long long ldl, double* __restrict__ Lw,
-                                               int* __restrict__ perm, const long long* __restrict__ S_t,
-                                               long long* __restrict__ skel, int* __restrict__ mark, State* st,
-                                               int pivoted) {
-  if (st->done) return;
-  __shared__ double diag[kMaxBlock];
-  __shared__ int alive[kMaxBlock];
-  __shared__ int s_piv;
-  __shared__ double s_total, s_pv;
-  __shared__ int s_stop;
-  __shared__ int s_perm[kMaxBlock];
-  const int m = pivoted ? (int)st->b_t : (int)st->bp;
-  const int tid = threadIdx.x;
-  for (int j = tid; j < m; j += blockDim.x) {
-    diag[j] = G[(long long)j * ldg + j];
-    alive[j] = 1;
-  }
-  __syncthreads();
-  // total = ||V||_F^2 (fixed-order sum)
-  if (tid < 32) {
-    double s = 0.0;
-    for (int j = tid; j < m; j += 32) s += diag[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (tid == 0) s_total = s;
-  }
-  __syncthreads();
-  double tau_b = st->tau_b;
-  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
-  int bp = 0;
-  for (int i = 0; i < m; ++i) {
-    // trailing mass and argmax (ties to the smallest candidate position)
-    double v = -DBL_MAX;
-    int vi = INT_MAX;
-    double msum = 0.0;
-    if (tid < 32) {
-      for (int j = tid; j < m; j += 32) {
-        if (!alive[j]) continue;
-        msum += diag[j];
-        const bool better = pivoted ? (diag[j] > v || (diag[j] == v && j < vi)) : (j == i);
-        if (better) { v = diag[j]; vi = j; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        msum += __shfl_xor_sync(0xffffffffu, msum, o);
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
-        if (ov > v || (ov == v && oi < vi)) { v = ov; vi = oi; }
-      }
-      if (tid == 0) {
-        s_piv = vi;
-        s_pv = v;
-        int stop = 0;
-        if (pivoted && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
-        if (vi == INT_MAX || !(v > 0.0)) stop = 1;
-        s_stop = stop;
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const int p = s_piv;
-    const double pivval = sqrt(s_pv);
-    // column i of the factor for every remaining candidate j (Lw is candidate-indexed)
-    for (int j = tid; j < m; j += blockDim.x) {
-      if (!alive[j]) continue;
-      if (j == p) {
-        Lw[(long long)j * kMaxBlock + i] = pivval;
-        continue;
-      }
-      double sacc = G[(long long)j * ldg + p];
-      for (int l = 0; l < i; ++l) sacc -= Lw[(long long)j * kMaxBlock + l] * Lw[(long long)p * kMaxBlock + l];
-      const double lji = sacc / pivval;
-      Lw[(long long)j * kMaxBlock + i] = lji;
-      diag[j] -= lji * lji;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      alive[p] = 0;
-      s_perm[i] = p;
-      if (perm) perm[i] = p;
-    }
-    __syncthreads();
-    bp = i + 1;
-  }
-  __syncthreads();
-  // pivot-order factor Lc (bp x bp, lower triangular)
-  for (int e = tid; e < bp * bp; e += blockDim.x) {
-    const int i = e / bp, l = e % bp;
-    Lc[(long long)i * ldl + l] = (l <= i) ? Lw[(long long)s_perm[i] * kMaxBlock + l] : 0.0;
-  }
-  if (pivoted) {
-    const long long k = st->k;
-    const int tno = (int)(st->t + 1);
-    for (int i = tid; i < bp; i += blockDim.x) {
-      const long long row = S_t[s_perm[i]];
-      skel[k + i] = row;
-      mark[row] = tno;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (pivoted) {
-      st->bp = bp;
-      st->bp_pad = (bp + 15) / 16 * 16;
-      if (bp == 0) st->done = 1;
-    } else if (bp < m) {
-      st->status = RBRP_ENONFINITE;  // Gram of Q' lost positive definiteness
-      st->done = 1;
-    }
-  }
-}
-
-// Right-looking form of the same factorisation for m <= 128 candidates: the
-// Schur complement (lower triangle) lives in shared memory and every step is a
-// parallel rank-1 downdate, so the O(m^3/6) FP64 work is spread over 512
-// threads instead of running as per-candidate dot products.
-constexpr int kSmemChol = 128;
-
-__global__ void __launch_bounds__(512) k_pchol_smem(const double* __restrict__ G, long long ldg,
-                                                    double* __restrict__ Lc, long long ldl, double* __restrict__ Lw,
-                                                    int* __restrict__ perm, const long long* __restrict__ S_t,
-                                                    long long* __restrict__ skel, int* __restrict__ mark, State* st,
-                                                    int pivoted) {
-  if (st->done) return;
-  extern __shared__ double Ssh[];  // m x m, row-major; entries (j, c) with c <= j are maintained
-  __shared__ double lcol[kSmemChol];
-  __shared__ int alive[kSmemChol];
-  __shared__ int s_perm[kSmemChol];
-  __shared__ int s_piv, s_stop;
-  __shared__ double s_pv, s_rinv, s_total;
-  const int m = pivoted ? (int)st->b_t : (int)st->bp;
-  const int tid = threadIdx.x;
-  for (int j = (tid >> 5); j < m; j += (blockDim.x >> 5))
-    for (int c = (tid & 31); c <= j; c += 32) Ssh[j * m + c] = G[(long long)j * ldg + c];
-  for (int j = tid; j < m; j += blockDim.x) alive[j] = 1;
-  __syncthreads();
-  if (tid < 32) {
-    double t = 0.0;
-    for (int j = tid; j < m; j += 32) t += Ssh[j * m + j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (tid == 0) s_total = t;
-  }
-  __syncthreads();
-  double tau_b = st->tau_b;
-  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
-  int bp = 0;
-  for (int i = 0; i < m; ++i) {
-    if (tid < 32) {
-      double v = -DBL_MAX, msum = 0.0;
-      int vi = INT_MAX;
-      for (int j = tid; j < m; j += 32) {
-        if (!alive[j]) continue;
-        const double dj = Ssh[j * m + j];
-        msum += dj;
-        const bool better = pivoted ? (dj > v || (dj == v && j < vi)) : (j == i);
-        if (better) {
-          v = dj;
-          vi = j;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        msum += __shfl_xor_sync(0xffffffffu, msum, o);
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
-        if (ov > v || (ov == v && oi < vi)) {
-          v = ov;
-          vi = oi;
-        }
-      }
-      if (tid == 0) {
-        int stop = 0;
-        if (pivoted && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
-        if (vi == INT_MAX || !(v > 0.0)) stop = 1;
-        s_stop = stop;
-        s_piv = vi;
-        // one FP64 square root and reciprocal per step (FP64 is ~2 FMA/clock/SM on GB300)
-        if (!stop) {
-          s_pv = sqrt(v);
-          s_rinv = 1.0 / s_pv;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const int p = s_piv;
-    const double pivval = s_pv, rinv = s_rinv;
-    for (int j = tid; j < m; j += blockDim.x) {
-      double l = 0.0;
-      if (alive[j]) l = (j == p) ? pivval : ((j >= p) ? Ssh[j * m + p] : Ssh[p * m + j]) * rinv;
-      lcol[j] = (j == p) ? 0.0 : l;
-      if (alive[j]) Lw[(long long)j * kMaxBlock + i] = l;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      alive[p] = 0;
-      s_perm[i] = p;
-      if (perm) perm[i] = p;
-    }
-    __syncthreads();
-    // rank-1 downdate of the lower triangle: warp w takes rows j = w, w + 16, ...
-    for (int j = (tid >> 5); j < m; j += (blockDim.x >> 5)) {
-      if (!alive[j]) continue;
-      const double lj = lcol[j];
-      for (int c = (tid & 31); c <= j; c += 32)
-        if (alive[c]) Ssh[j * m + c] -= lj * lcol[c];
-    }
-    __syncthreads();
-    bp = i + 1;
-  }
-  for (int e = tid; e < bp * bp; e += blockDim.x) {
-    const int i = e / bp, l = e % bp;
-    Lc[(long long)i * ldl + l] = (l <= i) ? Lw[(long long)s_perm[i] * kMaxBlock + l] : 0.0;
-  }
-  if (pivoted) {
-    const long long k = st->k;
-    const int tno = (int)(st->t + 1);
-    for (int i = tid; i < bp; i += blockDim.x) {
-      const long long row = S_t[s_perm[i]];
-      skel[k + i] = row;
-      mark[row] = tno;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (pivoted) {
-      st->bp = bp;
-      st->bp_pad = (bp + 15) / 16 * 16;
-      if (bp == 0) st->done = 1;
-    } else if (bp < m) {
-      st->status = RBRP_ENONFINITE;
-      st->done = 1;
-    }
-  }
-}
-
-static cudaError_t launch_pchol_any(const double* G, long long ldg, double* Lc, long long ldl, int* perm,
-                                    const long long* S_t, long long* skel, int* mark, int b, State* st, int pivoted,
-                                    cudaStream_t s) {
-  // Lw (candidate-indexed factor, kMaxBlock x kMaxBlock) lives right after Lc in the workspace
-  double* Lw = Lc + (long long)kMaxBlock * ldl;
-  if (b <= kSmemChol) {
-    static bool attr = false;
-    const int smem = kSmemChol * kSmemChol * 8;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_pchol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_pchol_smem<<<1, 512, (size_t)b * b * 8, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
-  } else {
-    k_pchol<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
-  }
-  return counted(cudaGetLastError());
-}
-
-cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
-                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
-  return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 1, s);
-}
-
-cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b, State* st,
-                        cudaStream_t s) {
-  return launch_pchol_any(G, ldg, Lc, ldl, nullptr, nullptr, nullptr, nullptr, b, st, 0, s);
-}
-
-// ============================================================================
-// Q' rows by forward substitution: Y(i,:) = (V(perm[i],:) - sum_{l<i} Lc(i,l) Y(l,:)) / Lc(i,i),
-// i < b'.  With V_perm = Lc Y and Lc lower triangular, Y has orthonormal rows
-// spanning the accepted candidates in pivot order (Y_i in span of the first i
-// pivots), which keeps L1 lower triangular.  One thread per column.
-// ============================================================================
-__global__ void k_trsm_rows(const double* __restrict__ Lc, long long ldl, const int* __restrict__ perm,
-                            const double* __restrict__ V, long long ldv, double* __restrict__ Ybase, DimRef y_off,
-                            long long ldy, long long d, const State* st) {
-  if (st->done) return;
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d) return;
-  const int bp = (int)st->bp;
-  double* Y = Ybase + dim_val(y_off);
-  for (int i = 0; i < bp; ++i) {
-    const int src = perm ? perm[i] : i;
-    double s = V[(long long)src * ldv + c];
-    for (int l = 0; l < i; ++l) s -= Lc[(long long)i * ldl + l] * Y[(long long)l * ldy + c];
-    Y[(long long)i * ldy + c] = s / Lc[(long long)i * ldl + i];
-  }
-}
-
-// Same substitution with 16 columns per CTA: the right-hand sides sit in shared
-// memory and each dot product sum_{l<i} Lc(i,l) Y(l,c) is split over 16 threads
-// (a quarter-warp per column pair) and combined with shuffles.
-__global__ void __launch_bounds__(256) k_trsm_rows16(const double* __restrict__ Lc, long long ldl,
-                                                     const int* __restrict__ perm, const double* __restrict__ V,
-                                                     long long ldv, double* __restrict__ Ybase, DimRef y_off,
-                                                     long long ldy, long long d, const State* st) {
-  if (st->done) return;
-  __shared__ double Ys[kMaxBlock][16];
-  __shared__ double rdiag[kMaxBlock];
-  const int bp = (int)st->bp;
-  const int cl = threadIdx.x >> 4, part = threadIdx.x & 15;  // column within the chunk, summation lane
-  const long long c = (long long)blockIdx.x * 16 + cl;
-  for (int i = part; i < bp; i += 16) {
-    const int src = perm ? perm[i] : i;
-    Ys[i][cl] = (c < d) ? V[(long long)src * ldv + c] : 0.0;
-  }
-  // reciprocals of the diagonal once (FP64 division is costly on GB300)
-  for (int i = threadIdx.x; i < bp; i += blockDim.x) rdiag[i] = 1.0 / Lc[(long long)i * ldl + i];
-  __syncthreads();
-  for (int i = 0; i < bp; ++i) {
-    double acc = 0.0;
-    for (int l = part; l < i; l += 16) acc = fma(Lc[(long long)i * ldl + l], Ys[l][cl], acc);
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (part == 0) Ys[i][cl] = (Ys[i][cl] - acc) * rdiag[i];
-    __syncthreads();
-  }
-  if (c < d) {
-    double* Y = Ybase + dim_val(y_off);
-    for (int i = part; i < bp; i += 16) Y[(long long)i * ldy + c] = Ys[i][cl];
-  }
-}
-
-cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V, long long ldv,
-                             double* Y, DimRef y_off, long long ldy, long long d, int b, const State* st,
-                             cudaStream_t s) {
-  (void)b;
-  k_trsm_rows16<<<(unsigned)((d + 15) / 16), 256, 0, s>>>(Lc, ldl, perm, V, ldv, Y, y_off, ldy, d, st);
-  return counted(cudaGetLastError());
-}
-
-// ============================================================================
 // FP32 copies of the new basis rows for the low-precision update:
 // Qp (b'_pad x ldp, rows = basis vectors) and QpT (d x ldpt, transposed).
 // Rows >= b' and columns >= d are zero so padded MMA tiles add nothing.

@@ -1,0 +1,377 @@
+// The robust blockwise filter and the new basis Q' of one RBRP block.
+//
+// Alg. 2 lines 7-9 and the robust blockwise filtering remark (Sec. 4): the
+// candidates V (b_t rows) are pivoted like a column-pivoted QR of V^T and the
+// factorisation is truncated at the first step i where the trailing mass
+// ||R_V(i:, i:)||_F^2 drops below tau_b ||R_V||_F^2.  On the GPU this is the
+// pivoted Cholesky factorisation of the FP64 Gram matrix G = V V^T: the same
+// pivots and the same trailing masses in exact arithmetic (the Schur-complement
+// diagonal is each remaining candidate's residual norm^2 and its sum is the
+// trailing mass).  Q'_V then comes from V_perm = Lc Y by forward substitution
+// (CholQR), which keeps Y_i in the span of the first i pivots and therefore
+// L1 lower triangular (Sec. 5.1).
+//
+// GB300 retires about two FP64 FMAs per clock per SM, spread over its four
+// sub-partitions, so the b x b factorisation keeps the Schur complement in
+// registers of 256 threads (eight warps) and spends its per-step budget on
+// three barriers and independent register FMAs.
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "rbrp_internal.cuh"
+
+namespace rbrp {
+
+constexpr int kRegCholThreads = 256;
+constexpr int kRegCholMax = 128;
+
+// Packed lower-triangle index e -> (r, c), r >= c, row-major (e = r (r + 1) / 2 + c).
+__device__ __forceinline__ void tri_rc(int e, int& r, int& c) {
+  int rr = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+  while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+  while (rr * (rr + 1) / 2 > e) --rr;
+  r = rr;
+  c = e - rr * (rr + 1) / 2;
+}
+
+// Right-looking pivoted (or plain) Cholesky with the lower triangle of the
+// Schur complement in registers: thread t owns packed elements t, t + 256, ...
+// Candidates keep their original index; `alive` marks the unpivoted ones.
+template <int SLOTS>
+__global__ void __launch_bounds__(kRegCholThreads) k_pchol_reg(const double* __restrict__ G, long long ldg,
+                                                               double* __restrict__ Lc, long long ldl,
+                                                               double* __restrict__ Lw, int* __restrict__ perm,
+                                                               const long long* __restrict__ S_t,
+                                                               long long* __restrict__ skel, int* __restrict__ mark,
+                                                               State* st, int pivoted) {
+  if (st->done) return;
+  __shared__ double diag[kRegCholMax];
+  __shared__ double lcol[kRegCholMax];
+  __shared__ int alive[kRegCholMax];
+  __shared__ int s_perm[kRegCholMax];
+  __shared__ int s_piv, s_stop;
+  __shared__ double s_pv, s_rinv;
+  const int m = pivoted ? (int)st->b_t : (int)st->bp;
+  const int tid = threadIdx.x;
+  const int ne = m * (m + 1) / 2;
+  double a[SLOTS];
+  short rr[SLOTS], cc[SLOTS];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int e = tid + kRegCholThreads * s;
+    int r = -1, c = -1;
+    double v = 0.0;
+    if (e < ne) {
+      tri_rc(e, r, c);
+      v = G[(long long)r * ldg + c];
+      if (r == c) diag[r] = v;
+    }
+    a[s] = v;
+    rr[s] = (short)r;
+    cc[s] = (short)c;
+  }
+  for (int j = tid; j < m; j += kRegCholThreads) alive[j] = 1;
+  __syncthreads();
+  double total = 0.0;
+  if (tid < 32) {
+    for (int j = tid; j < m; j += 32) total += diag[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  }
+  double tau_b = st->tau_b;
+  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+  int bp = 0;
+  for (int i = 0; i < m; ++i) {
+    // (a) trailing mass and pivot (largest residual norm^2, ties to the smaller candidate index).
+    // The comparison runs on order-preserving integer keys (FP64 compares and
+    // shuffles sit on GB300's slow FP64 path); only the mass is summed in FP64.
+    if (tid < 32) {
+      double msum = 0.0;
+      unsigned long long key = 0ULL;  // below every orderable double
+      int vi = INT_MAX;
+      for (int j = tid; j < m; j += 32) {
+        if (!alive[j]) continue;
+        const double dj = diag[j];
+        msum += dj;
+        const unsigned long long kj = pivoted ? orderable(dj) : (j == i ? ~0ULL : 0ULL);
+        if (kj > key || (kj == key && j < vi)) {
+          key = kj;
+          vi = j;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        msum += __shfl_xor_sync(0xffffffffu, msum, o);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+        if (ok > key || (ok == key && oi < vi)) {
+          key = ok;
+          vi = oi;
+        }
+      }
+      if (tid == 0) {
+        const double v = (vi == INT_MAX) ? 0.0 : diag[vi];
+        int stop = 0;
+        if (pivoted && !(msum >= tau_b * total && msum > 0.0)) stop = 1;
+        if (vi == INT_MAX || !(v > 0.0)) stop = 1;
+        s_stop = stop;
+        s_piv = vi;
+        if (!stop) {
+          const double r = rsqrt(v);  // one FP64 reciprocal square root per step
+          s_rinv = r;
+          s_pv = v * r;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_piv;
+    const double rinv = s_rinv;
+    // (b) column p of the factor: owners of row/column p publish l_j = S(j, p) / sqrt(S(p, p))
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int r = rr[s], c = cc[s];
+      if (r < 0) continue;
+      int j = -1;
+      if (c == p && r != p) j = r;
+      else if (r == p && c != p) j = c;
+      if (j >= 0 && alive[j]) {
+        const double l = a[s] * rinv;
+        lcol[j] = l;
+        Lw[(long long)j * kMaxBlock + i] = l;
+      }
+    }
+    if (tid == 0) {
+      Lw[(long long)p * kMaxBlock + i] = s_pv;
+      alive[p] = 0;
+      s_perm[i] = p;
+      if (perm) perm[i] = p;
+    }
+    __syncthreads();
+    // (c) rank-1 downdate of the remaining lower triangle
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int r = rr[s], c = cc[s];
+      if (r < 0 || !alive[r] || !alive[c]) continue;
+      a[s] -= lcol[r] * lcol[c];
+      if (r == c) diag[r] = a[s];
+    }
+    __syncthreads();
+    bp = i + 1;
+  }
+  for (int e = tid; e < bp * bp; e += kRegCholThreads) {
+    const int i = e / bp, l = e % bp;
+    Lc[(long long)i * ldl + l] = (l <= i) ? Lw[(long long)s_perm[i] * kMaxBlock + l] : 0.0;
+  }
+  if (pivoted) {
+    const long long k = st->k;
+    const int tno = (int)(st->t + 1);
+    for (int i = tid; i < bp; i += kRegCholThreads) {
+      const long long row = S_t[s_perm[i]];
+      skel[k + i] = row;
+      mark[row] = tno;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (pivoted) {
+      st->bp = bp;
+      st->bp_pad = (bp + 15) / 16 * 16;
+      if (bp == 0) st->done = 1;
+    } else if (bp < m) {
+      st->status = RBRP_ENONFINITE;  // the Gram matrix of Q' lost positive definiteness
+      st->done = 1;
+    }
+  }
+}
+
+// Left-looking form for m > 128 candidates (FP64 / FP32 paths with b up to 256):
+// the factor is kept candidate-indexed in global memory.
+__global__ void __launch_bounds__(256) k_pchol_global(const double* __restrict__ G, long long ldg,
+                                               double* __restrict__ Lc, long long ldl, double* __restrict__ Lw,
+                                               int* __restrict__ perm, const long long* __restrict__ S_t,
+                                               long long* __restrict__ skel, int* __restrict__ mark, State* st,
+                                               int pivoted) {
+  if (st->done) return;
+  __shared__ double diag[kMaxBlock];
+  __shared__ int alive[kMaxBlock];
+  __shared__ int s_piv;
+  __shared__ double s_total, s_pv;
+  __shared__ int s_stop;
+  __shared__ int s_perm[kMaxBlock];
+  const int m = pivoted ? (int)st->b_t : (int)st->bp;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < m; j += blockDim.x) {
+    diag[j] = G[(long long)j * ldg + j];
+    alive[j] = 1;
+  }
+  __syncthreads();
+  // total = ||V||_F^2 (fixed-order sum)
+  if (tid < 32) {
+    double s = 0.0;
+    for (int j = tid; j < m; j += 32) s += diag[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) s_total = s;
+  }
+  __syncthreads();
+  double tau_b = st->tau_b;
+  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+  int bp = 0;
+  for (int i = 0; i < m; ++i) {
+    // trailing mass and argmax (ties to the smallest candidate position)
+    double v = -DBL_MAX;
+    int vi = INT_MAX;
+    double msum = 0.0;
+    if (tid < 32) {
+      for (int j = tid; j < m; j += 32) {
+        if (!alive[j]) continue;
+        msum += diag[j];
+        const bool better = pivoted ? (diag[j] > v || (diag[j] == v && j < vi)) : (j == i);
+        if (better) { v = diag[j]; vi = j; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        msum += __shfl_xor_sync(0xffffffffu, msum, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+        if (ov > v || (ov == v && oi < vi)) { v = ov; vi = oi; }
+      }
+      if (tid == 0) {
+        s_piv = vi;
+        s_pv = v;
+        int stop = 0;
+        if (pivoted && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
+        if (vi == INT_MAX || !(v > 0.0)) stop = 1;
+        s_stop = stop;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_piv;
+    const double pivval = sqrt(s_pv), rinv = 1.0 / pivval;
+    // column i of the factor for every remaining candidate j (Lw is candidate-indexed)
+    for (int j = tid; j < m; j += blockDim.x) {
+      if (!alive[j]) continue;
+      if (j == p) {
+        Lw[(long long)j * kMaxBlock + i] = pivval;
+        continue;
+      }
+      double sacc = G[(long long)j * ldg + p];
+      for (int l = 0; l < i; ++l) sacc -= Lw[(long long)j * kMaxBlock + l] * Lw[(long long)p * kMaxBlock + l];
+      const double lji = sacc * rinv;
+      Lw[(long long)j * kMaxBlock + i] = lji;
+      diag[j] -= lji * lji;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      alive[p] = 0;
+      s_perm[i] = p;
+      if (perm) perm[i] = p;
+    }
+    __syncthreads();
+    bp = i + 1;
+  }
+  __syncthreads();
+  // pivot-order factor Lc (bp x bp, lower triangular)
+  for (int e = tid; e < bp * bp; e += blockDim.x) {
+    const int i = e / bp, l = e % bp;
+    Lc[(long long)i * ldl + l] = (l <= i) ? Lw[(long long)s_perm[i] * kMaxBlock + l] : 0.0;
+  }
+  if (pivoted) {
+    const long long k = st->k;
+    const int tno = (int)(st->t + 1);
+    for (int i = tid; i < bp; i += blockDim.x) {
+      const long long row = S_t[s_perm[i]];
+      skel[k + i] = row;
+      mark[row] = tno;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (pivoted) {
+      st->bp = bp;
+      st->bp_pad = (bp + 15) / 16 * 16;
+      if (bp == 0) st->done = 1;
+    } else if (bp < m) {
+      st->status = RBRP_ENONFINITE;  // Gram of Q' lost positive definiteness
+      st->done = 1;
+    }
+  }
+}
+
+
+static cudaError_t launch_pchol_any(const double* G, long long ldg, double* Lc, long long ldl, int* perm,
+                                    const long long* S_t, long long* skel, int* mark, int b, State* st, int pivoted,
+                                    cudaStream_t s) {
+  // Lw (candidate-indexed factor, kMaxBlock x kMaxBlock) lives right after Lc in the workspace
+  double* Lw = Lc + (long long)kMaxBlock * ldl;
+  const int ne = b * (b + 1) / 2;
+  if (ne <= 9 * kRegCholThreads)
+    k_pchol_reg<9><<<1, kRegCholThreads, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+  else if (b <= kRegCholMax)
+    k_pchol_reg<33><<<1, kRegCholThreads, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+  else
+    k_pchol_global<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
+                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+  return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 1, s);
+}
+
+cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b, State* st,
+                        cudaStream_t s) {
+  return launch_pchol_any(G, ldg, Lc, ldl, nullptr, nullptr, nullptr, nullptr, b, st, 0, s);
+}
+
+// ============================================================================
+// Q' rows by forward substitution: Y(i,:) = (V(perm[i],:) - sum_{l<i} Lc(i,l) Y(l,:)) / Lc(i,i),
+// i < b'.  With V_perm = Lc Y and Lc lower triangular, Y has orthonormal rows
+// spanning the accepted candidates in pivot order.
+// ============================================================================
+// Same substitution with 16 columns per CTA: the right-hand sides sit in shared
+// memory and each dot product sum_{l<i} Lc(i,l) Y(l,c) is split over 16 threads
+// (a quarter-warp per column pair) and combined with shuffles.
+__global__ void __launch_bounds__(256) k_trsm_rows16(const double* __restrict__ Lc, long long ldl,
+                                                     const int* __restrict__ perm, const double* __restrict__ V,
+                                                     long long ldv, double* __restrict__ Ybase, DimRef y_off,
+                                                     long long ldy, long long d, const State* st) {
+  if (st->done) return;
+  __shared__ double Ys[kMaxBlock][16];
+  __shared__ double rdiag[kMaxBlock];
+  const int bp = (int)st->bp;
+  const int cl = threadIdx.x >> 4, part = threadIdx.x & 15;  // column within the chunk, summation lane
+  const long long c = (long long)blockIdx.x * 16 + cl;
+  for (int i = part; i < bp; i += 16) {
+    const int src = perm ? perm[i] : i;
+    Ys[i][cl] = (c < d) ? V[(long long)src * ldv + c] : 0.0;
+  }
+  // reciprocals of the diagonal once (FP64 division is costly on GB300)
+  for (int i = threadIdx.x; i < bp; i += blockDim.x) rdiag[i] = 1.0 / Lc[(long long)i * ldl + i];
+  __syncthreads();
+  for (int i = 0; i < bp; ++i) {
+    double acc = 0.0;
+    for (int l = part; l < i; l += 16) acc = fma(Lc[(long long)i * ldl + l], Ys[l][cl], acc);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (part == 0) Ys[i][cl] = (Ys[i][cl] - acc) * rdiag[i];
+    __syncthreads();
+  }
+  if (c < d) {
+    double* Y = Ybase + dim_val(y_off);
+    for (int i = part; i < bp; i += 16) Y[(long long)i * ldy + c] = Ys[i][cl];
+  }
+}
+
+cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V, long long ldv,
+                             double* Y, DimRef y_off, long long ldy, long long d, int b, const State* st,
+                             cudaStream_t s) {
+  (void)b;
+  k_trsm_rows16<<<(unsigned)((d + 15) / 16), 256, 0, s>>>(Lc, ldl, perm, V, ldv, Y, y_off, ldy, d, st);
+  return counted(cudaGetLastError());
+}
+
+}  // namespace rbrp

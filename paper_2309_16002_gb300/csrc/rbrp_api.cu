@@ -63,13 +63,14 @@ cudaError_t timed(EventPool& pool, cudaStream_t s, F&& body) {
 struct Plan {
   long long n, d, k_cap;
   int b, prec, r64, l64, w32, greedy;
-  long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32;
+  long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32, ldt;
   int nparts;
   int s_coef, s_apply, s_gram, s_upd1, s_upd2;
   size_t pm, pn;  // split-K partial buffer extents (elements per split)
   size_t partial_elems;
   size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
-      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_W32, total;
+      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_W32, off_L1Th, off_L1Tl,
+      total;
 };
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -118,6 +119,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->ldg = p->b;
   p->ldlc = kMaxBlock;
   p->ldw32 = p->ldl;
+  p->ldt = round_up(kc, 32);
   {
     long long np = (n + 7) / 8;
     p->nparts = (int)std::min(np, 4LL * 152);
@@ -170,6 +172,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->off_QpTlo = take(p->prec == RBRP_TF32X3 ? (size_t)p->ldq * p->ldpt * 4 : 0);
   p->off_L1 = take((size_t)kc * kc * 8);
   p->off_W32 = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
+  p->off_L1Th = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
+  p->off_L1Tl = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->total = off;
   return RBRP_OK;
 }
@@ -207,6 +211,8 @@ struct Bufs {
   float* QpT_lo;
   double* L1;
   float* W32;
+  float* L1Th;
+  float* L1Tl;
   long long* skel;
 };
 
@@ -236,6 +242,8 @@ Bufs carve(const Plan& p, void* ws) {
   u.QpT_lo = (p.prec == RBRP_TF32X3) ? (float*)(b + p.off_QpTlo) : nullptr;
   u.L1 = (double*)(b + p.off_L1);
   u.W32 = p.w32 ? (float*)(b + p.off_W32) : nullptr;
+  u.L1Th = p.w32 ? (float*)(b + p.off_L1Th) : nullptr;
+  u.L1Tl = p.w32 ? (float*)(b + p.off_L1Tl) : nullptr;
   u.skel = nullptr;
   return u;
 }
@@ -272,21 +280,23 @@ cudaError_t gemm(const Plan& p, const Bufs& u, MatRef A, MatRef B, MatRef C, Dim
 // component in span(Q) by the FP32 product accuracy (~1e-7); two passes leave
 // it at FP64 level.  The FP64 path keeps FP64 products throughout.
 template <typename TACC>
-cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s) {
+cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, double* V, DimRef voff, DimRef rows, cudaStream_t s) {
   const State* st = u.st;
   const long long kc = p.k_cap, b = p.b;
   cudaError_t e = gemm<double, double, double, TACC>(
-      p, u, mat(V, dim_const(0), p.ldq, 1), mat(u.Qt, dim_const(0), 1, p.ldq), mat(u.C, dim_const(0), p.ldc, 1),
-      rows, dim_dev(&st->k), dim_const(p.d), 1.0, 0.0, b, kc, p.s_coef, st, s);
+      p, u, mat(V, voff, p.ldq, 1), mat(u.Qt, dim_const(0), 1, p.ldq), mat(u.C, dim_const(0), p.ldc, 1), rows,
+      dim_dev(&st->k), dim_const(p.d), 1.0, 0.0, b, kc, p.s_coef, st, s);
   if (e != cudaSuccess) return e;
   return gemm<double, double, double, TACC>(
-      p, u, mat(u.C, dim_const(0), p.ldc, 1), mat(u.Qt, dim_const(0), p.ldq, 1), mat(V, dim_const(0), p.ldq, 1),
-      rows, dim_const(p.d), dim_dev(&st->k), -1.0, 1.0, b, p.d, p.s_apply, st, s);
+      p, u, mat(u.C, dim_const(0), p.ldc, 1), mat(u.Qt, dim_const(0), p.ldq, 1), mat(V, voff, p.ldq, 1), rows,
+      dim_const(p.d), dim_dev(&st->k), -1.0, 1.0, b, p.d, p.s_apply, st, s);
 }
 
-cudaError_t cgs_pass(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s) {
-  if (p.prec == RBRP_FP64) return cgs_pass_t<double>(p, u, V, rows, s);
-  return cgs_pass_t<float>(p, u, V, rows, s);
+// V (rows [0, rows) at V + voff, leading dimension ldq) <- V - (V Qt^T) Qt over Qt rows [0, k).
+cudaError_t cgs_pass(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s,
+                     DimRef voff = dim_const(0)) {
+  if (p.prec == RBRP_FP64) return cgs_pass_t<double>(p, u, V, voff, rows, s);
+  return cgs_pass_t<float>(p, u, V, voff, rows, s);
 }
 
 cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s);
@@ -312,14 +322,22 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
                                            mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->b_t), dim_dev(&st->b_t),
                                            dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
   LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
-  // Q'_V: Y = Lc^{-1} V(perm), then CGS against Q and a second CholQR pass
-  LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
-  LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
-  LK((gemm<double, double, double, double>(p, u, mat(u.Y, dim_const(0), p.ldq, 1), mat(u.Y, dim_const(0), 1, p.ldq),
-                                           mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->bp), dim_dev(&st->bp),
-                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
-  LK(launch_chol(u.G, p.ldg, u.Lc, p.ldlc, p.b, st, s));
-  LK(launch_trsm_rows(u.Lc, p.ldlc, nullptr, u.Y, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+  // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 path adds a
+  // second CholQR pass (orthogonality to FP64 rounding); on the mixed paths one
+  // FP64 CholQR already leaves ~u64 * cond^2 <= ~1e-8, far below the rounding of
+  // their residual update, so Q' is written in place and only re-projected.
+  if (p.prec == RBRP_FP64) {
+    LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
+    LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
+    LK((gemm<double, double, double, double>(
+        p, u, mat(u.Y, dim_const(0), p.ldq, 1), mat(u.Y, dim_const(0), 1, p.ldq), mat(u.G, dim_const(0), p.ldg, 1),
+        dim_dev(&st->bp), dim_dev(&st->bp), dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
+    LK(launch_chol(u.G, p.ldg, u.Lc, p.ldlc, p.b, st, s));
+    LK(launch_trsm_rows(u.Lc, p.ldlc, nullptr, u.Y, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+  } else {
+    LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+    LK(cgs_pass(p, u, u.Qt, dim_dev(&st->bp), s, dim_dev(&st->k, p.ldq)));
+  }
   // lines 12 and 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
   if (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) {
     const int split = (p.prec == RBRP_TF32X3);
@@ -392,19 +410,11 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
     }
     CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));
   } else {
+    // FP32 solve: blocked products on tensor cores (3xTF32) with the triangular
+    // solve fused into their epilogue, then widened into the FP64 output.
     float* W32 = u.W32;
     const long long l32 = p.ldw32;
-    CK(launch_copy_cols_to_f32(u.L, p.l64, p.ldl, n, 0, k, W32, l32, s));
-    for (long long J = nblk - 1; J >= 0; --J) {
-      const long long j0 = J * 64, nb = std::min(64LL, k - j0), rest = k - j0 - nb;
-      if (rest > 0) {
-        CK((gemm<float, double, float, float>(
-            p, u, mat(W32, dim_const(j0 + nb), l32, 1), mat(u.L1, dim_const((j0 + nb) * k + j0), k, 1),
-            mat(W32, dim_const(j0), l32, 1), dim_const(n), dim_const(nb), dim_const(rest), -1.0, 1.0, n, 64,
-            splits_for(n, 64, rest), nullptr, s)));
-      }
-      CK(launch_trsm_cols<float>(W32, l32, n, j0, (int)nb, u.L1, k, s));
-    }
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, W32, l32, u.L1, k, u.L1Th, u.L1Tl, p.ldt, n, k, u.st, s));
     CK(launch_w_finish(W, ldw, W32, l32, n, k, skel, s));
   }
   return RBRP_OK;

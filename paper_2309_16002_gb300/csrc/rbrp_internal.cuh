@@ -162,4 +162,11 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
 int update_tf32_parts(long long n);
 int update_tf32_max_block(int split);
 
+// Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k, FP32,
+// leading dimension ldw, 16-byte aligned rows) from L (FP32 or FP64) and
+// L1 = L(S, :) (FP64, k x k); L1T_hi/lo are k x ldt FP32 scratch.
+cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* W, long long ldw, const double* L1,
+                             long long ld1, float* L1T_hi, float* L1T_lo, long long ldt, long long n, long long k,
+                             State* st, cudaStream_t s);
+
 }  // namespace rbrp

@@ -158,6 +158,21 @@ def test_zero_and_nonfinite(G):
         _run(G, X.astype(np.float32), 1e-3, block=4, precision="tf32")
 
 
+@pytest.mark.parametrize("n,d,rate,tol,b", [(3001, 333, 0.97, 1e-8, 64), (777, 150, 0.9, 1e-8, 32),
+                                           (129, 100, 0.95, 1e-10, 16)])
+def test_w_fp32_tensor_core_solve_matches_fp64_solve(G, n, d, rate, tol, b):
+    """Alg. 3 in FP32 on tensor cores (3xTF32 products, fused triangular solve) against the FP64
+    solve on the same skeletons: k spans several 64-column blocks and n a ragged last tile."""
+    X, _ = WL.spectral(n=n, d=d, rate=rate, seed=n + d)
+    a = _run(G, X, tol, block=b, seed=5, precision="fp64", w_precision="fp64")
+    c = _run(G, X, tol, block=b, seed=5, precision="fp64", w_precision="fp32")
+    assert a["S"].tolist() == c["S"].tolist()
+    assert np.max(np.abs(c["W"] - a["W"])) <= 1e-4 * max(1.0, np.max(np.abs(a["W"])))
+    ea, ec = _e(X, a["S"], a["W"]), _e(X, c["S"], c["W"])
+    assert ec <= max(1.05 * ea, ea + 1e-5), (ec, ea)
+    assert np.array_equal(c["W"][c["S"]], np.eye(c["k"]))
+
+
 def test_fp64_w_fp32_solve(G):
     X, _ = WL.spectral(n=2000, d=200, rate=0.9, seed=1)
     ref = O.rbrp_id(X, tau=1e-6, b=16, seed=0)
