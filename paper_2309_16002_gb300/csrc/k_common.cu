@@ -30,11 +30,23 @@ __global__ void __launch_bounds__(256) k_init_norms(const TX* __restrict__ X, lo
     const TX* x = X + i * ldx;
     TR* r = R + i * ldr;
     double s = 0.0;
-    for (long long j = lane; j < ldr; j += 32) {
-      TR v = (j < d) ? (TR)x[j] : (TR)0;
-      r[j] = v;
-      const double dv = (double)v;
-      s = fma(dv, dv, s);
+    if (sizeof(TR) == 8) {
+      for (long long j = lane; j < ldr; j += 32) {
+        TR v = (j < d) ? (TR)x[j] : (TR)0;
+        r[j] = v;
+        const double dv = (double)v;
+        s = fma(dv, dv, s);
+      }
+    } else {
+      // FP32 residual: per-lane FP32 partial sums (FP64 FMAs run at ~2/clock/SM on GB300)
+      float sf = 0.f;
+      for (long long j = lane; j < ldr; j += 32) {
+        TR v = (j < d) ? (TR)x[j] : (TR)0;
+        r[j] = v;
+        const float fv = (float)v;
+        sf = fmaf(fv, fv, sf);
+      }
+      s = (double)sf;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -99,6 +111,7 @@ __global__ void k_finish_init(const double* __restrict__ partials, int np, State
     st->b_t = 0;
     st->bp = 0;
     st->bp_pad = 0;
+    st->sample_fallback = 0;
     st->status = 0;
     if (!isfinite(D0)) {
       st->status = RBRP_ENONFINITE;
@@ -138,7 +151,8 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
                                                        unsigned long long seed, unsigned long long problem,
                                                        long long* __restrict__ S_t, State* st, int first,
                                                        int last) {
-  if (st->done) return;
+  // exact FP64 sampler: runs only when the two-stage sampler asked for it
+  if (st->done || !st->sample_fallback) return;
   __shared__ Pair sh[kSortChunk];
   const unsigned long long block_no = (unsigned long long)st->t + 1ULL;  // the paper's t
   const long long base = (long long)blockIdx.x * kSortChunk;
@@ -198,8 +212,10 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
   if (bt > room) bt = room;
   if (bt < 0) bt = 0;
   for (int e = threadIdx.x; e < bt; e += blockDim.x) S_t[e] = sh[e].idx;
+  __syncthreads();
   if (threadIdx.x == 0) {
     st->b_t = bt;
+    st->sample_fallback = 0;
     if (bt == 0) st->done = 1;
   }
 }

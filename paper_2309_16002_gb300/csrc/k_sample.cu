@@ -1,0 +1,318 @@
+// Alg. 2 line 5 on the GPU: S_t ~ d / ||d||_1 without replacement (reading of
+// the sampling step as an exponential race: keys kappa_i = -log(u_i) / d_i over
+// eligible rows, the b_t smallest in ascending (kappa, i) order; the greedy
+// variant of the blockwise greedy remark uses -d_i).
+//
+// Two stages, exact:
+//  1. a log-domain FP32 key log(-log u_i) - log d_i per row (Philox and FP32
+//     logarithms only; FP64 arithmetic is slow on GB300) and an 11 + 11-bit
+//     radix histogram over those keys choose a cut that keeps at least
+//     b + kMargin candidates;
+//  2. one CTA recomputes the FP64 keys of the candidates exactly as the oracle
+//     does, ranks them, and checks that the cut lies more than the FP32 error
+//     bound above the b_t-th exact key, so no row outside the cut can belong
+//     to S_t.  If the check fails (or the candidate list overflows) it raises
+//     State::sample_fallback and the exact FP64 tree sampler in k_common.cu
+//     runs instead.
+// The histogram buffers are cleared by the final kernel for the next block.
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "rbrp_internal.cuh"
+
+namespace rbrp {
+
+constexpr int kMargin = 32;          // extra candidates kept by the FP32 cut
+constexpr int kBins = 2048;          // 11-bit digits
+constexpr int kSampThreads = 256;
+constexpr int kSampPerThread = 8;
+constexpr float kCutGuard = 2e-4f;   // absolute slack in log space (FP32 key error bound)
+
+// ln(d) from the FP64 bit pattern with FP32 arithmetic: exponent * ln2 + ln(mantissa).
+__device__ __forceinline__ float log_d_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return (float)log(d);  // subnormal d (rare): FP64 logarithm
+  const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL));
+  return (float)(e - 1023) * 0.69314718055994531f + logf((float)m);
+}
+
+// FP32 log-domain key of row i (smaller = drawn earlier); 0xFFFFFFFF for ineligible rows.
+__device__ __forceinline__ unsigned int approx_key(double di, long long i, unsigned long long block_no,
+                                                   unsigned long long seed, unsigned long long problem, int greedy) {
+  if (!(di > 0.0)) return 0xFFFFFFFFu;
+  float key;
+  if (greedy) {
+    key = -log_d_f32(di);
+  } else {
+    unsigned long long c[4] = {(unsigned long long)i, block_no, 0ULL, 0ULL};
+    philox4x64_10(c, seed, problem);
+    // E = -log(u) > 0 with u = ((w0 >> 11) + 1/2) 2^-53: logf(u) for u < 1/2, and
+    // -log1pf(-(1 - u)) above, where 1 - u is exact in FP64 (keeps E accurate near u = 1)
+    const double u = ((double)(c[0] >> 11) + 0.5) * 0x1.0p-53;
+    const float e = (u < 0.5) ? -logf((float)u) : -log1pf(-(float)(1.0 - u));
+    key = logf(e) - log_d_f32(di);
+  }
+  const unsigned int bits = __float_as_uint(key);
+  return (bits >> 31) ? ~bits : (bits | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_to_float(unsigned int k) {
+  return __uint_as_float((k >> 31) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// Pass 1: keys and the histogram of their top 11 bits (eligible rows only).
+__global__ void __launch_bounds__(kSampThreads) k_samp_keys(const double* __restrict__ dvec, long long n,
+                                                            unsigned int* __restrict__ K32,
+                                                            unsigned int* __restrict__ hist1, int greedy,
+                                                            unsigned long long seed, unsigned long long problem,
+                                                            const State* st) {
+  if (st->done) return;
+  __shared__ unsigned int h[kBins];
+  for (int j = threadIdx.x; j < kBins; j += kSampThreads) h[j] = 0;
+  __syncthreads();
+  const unsigned long long block_no = (unsigned long long)st->t + 1ULL;
+  const long long base = (long long)blockIdx.x * kSampThreads * kSampPerThread;
+#pragma unroll
+  for (int q = 0; q < kSampPerThread; ++q) {
+    const long long i = base + q * kSampThreads + threadIdx.x;
+    if (i >= n) break;
+    const unsigned int k = approx_key(dvec[i], i, block_no, seed, problem, greedy);
+    K32[i] = k;
+    if (k != 0xFFFFFFFFu) atomicAdd(&h[k >> 21], 1u);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kBins; j += kSampThreads)
+    if (h[j]) atomicAdd(&hist1[j], h[j]);
+}
+
+// Block-wide search over a 2048-bin histogram: the first bin where the running
+// count reaches `want`; returns the count below that bin in *below (or bin
+// kBins and the total when the histogram holds fewer than `want`).
+// Callable from any block size >= kSampThreads (threads beyond the first
+// kSampThreads only take part in the barriers).
+__device__ int find_bin(const unsigned int* __restrict__ hist, unsigned int want, unsigned int* below,
+                        unsigned int* total) {
+  __shared__ unsigned int part[kSampThreads];
+  __shared__ int s_bin;
+  __shared__ unsigned int s_below, s_total;
+  constexpr int per = kBins / kSampThreads;  // 8 bins per thread
+  if (threadIdx.x < kSampThreads) {
+    unsigned int sum = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) sum += hist[threadIdx.x * per + q];
+    part[threadIdx.x] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int run = 0;
+    int bin = kBins;
+    unsigned int bel = 0;
+    for (int t = 0; t < kSampThreads; ++t) {
+      if (bin == kBins && run + part[t] >= want) {
+        unsigned int r2 = run;
+        for (int q = 0; q < per; ++q) {
+          const unsigned int c = hist[t * per + q];
+          if (r2 + c >= want) {
+            bin = t * per + q;
+            bel = r2;
+            break;
+          }
+          r2 += c;
+        }
+      }
+      run += part[t];
+    }
+    s_bin = bin;
+    s_below = (bin == kBins) ? run : bel;
+    s_total = run;
+  }
+  __syncthreads();
+  *below = s_below;
+  *total = s_total;
+  const int bin = s_bin;
+  __syncthreads();  // the shared results may be overwritten by the next call
+  return bin;
+}
+
+// Pass 2: histogram of the next 11 bits inside the bin where the b + kMargin-th key falls.
+__global__ void __launch_bounds__(kSampThreads) k_samp_hist2(const unsigned int* __restrict__ K32, long long n,
+                                                             const unsigned int* __restrict__ hist1,
+                                                             unsigned int* __restrict__ hist2, int want,
+                                                             const State* st) {
+  if (st->done) return;
+  unsigned int below, total;
+  const int b1 = find_bin(hist1, (unsigned int)want, &below, &total);
+  if (b1 >= kBins) return;  // fewer eligible rows than wanted: every eligible row is a candidate
+  __shared__ unsigned int h[kBins];
+  for (int j = threadIdx.x; j < kBins; j += kSampThreads) h[j] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kSampThreads * kSampPerThread;
+#pragma unroll
+  for (int q = 0; q < kSampPerThread; ++q) {
+    const long long i = base + q * kSampThreads + threadIdx.x;
+    if (i >= n) break;
+    const unsigned int k = K32[i];
+    if ((int)(k >> 21) == b1 && k != 0xFFFFFFFFu) atomicAdd(&h[(k >> 10) & 0x7FF], 1u);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kBins; j += kSampThreads)
+    if (h[j]) atomicAdd(&hist2[j], h[j]);
+}
+
+// The 22-bit cut: rows whose key's top 22 bits are <= cut22 are candidates
+// (0x3FFFFF when every eligible row is).
+__device__ unsigned int cut22(const unsigned int* hist1, const unsigned int* hist2, int want) {
+  unsigned int below1, total1, below2, total2;
+  const int b1 = find_bin(hist1, (unsigned int)want, &below1, &total1);
+  if (b1 >= kBins) return 0x3FFFFFu;
+  const int b2 = find_bin(hist2, (unsigned int)(want - (int)below1), &below2, &total2);
+  return ((unsigned int)b1 << 11) | (unsigned int)(b2 >= kBins ? kBins - 1 : b2);
+}
+
+// Pass 3: compact the candidate rows.
+__global__ void __launch_bounds__(kSampThreads) k_samp_compact(const unsigned int* __restrict__ K32, long long n,
+                                                               const unsigned int* __restrict__ hist1,
+                                                               const unsigned int* __restrict__ hist2, int want,
+                                                               int* __restrict__ cand, unsigned int* __restrict__ ncand,
+                                                               int cap, const State* st) {
+  if (st->done) return;
+  const unsigned int c22 = cut22(hist1, hist2, want);
+  const long long base = (long long)blockIdx.x * kSampThreads * kSampPerThread;
+#pragma unroll
+  for (int q = 0; q < kSampPerThread; ++q) {
+    const long long i = base + q * kSampThreads + threadIdx.x;
+    if (i >= n) break;
+    const unsigned int k = K32[i];
+    if (k != 0xFFFFFFFFu && (k >> 10) <= c22) {
+      const unsigned int pos = atomicAdd(ncand, 1u);
+      if ((int)pos < cap) cand[pos] = (int)i;
+    }
+  }
+}
+
+// Pass 4 (one CTA): exact FP64 keys of the candidates, ranking, the margin
+// check, S_t and b_t; clears the histograms for the next block.
+__global__ void __launch_bounds__(1024) k_samp_final(const double* __restrict__ dvec, long long n,
+                                                     unsigned int* __restrict__ hist1, unsigned int* __restrict__ hist2,
+                                                     int want, const int* __restrict__ cand,
+                                                     unsigned int* __restrict__ ncand, int cap, int b, int greedy,
+                                                     unsigned long long seed, unsigned long long problem,
+                                                     long long* __restrict__ S_t, State* st) {
+  if (st->done) return;
+  __shared__ unsigned long long ek[kSampCap];
+  __shared__ long long eidx[kSampCap];
+  __shared__ double elog[kSampCap];
+  __shared__ long long sorted_idx[kMaxBlock];
+  __shared__ double sorted_log[kMaxBlock];
+  unsigned int below1, total1;
+  find_bin(hist1, (unsigned int)want, &below1, &total1);  // total1 = number of eligible rows
+  const unsigned int c22 = cut22(hist1, hist2, want);
+  const int nc = (int)*ncand;
+  const unsigned long long block_no = (unsigned long long)st->t + 1ULL;
+  const bool overflow = nc > cap;
+  const int m = overflow ? 0 : nc;
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    const long long i = cand[e];
+    const double di = dvec[i];
+    double key;
+    if (greedy) {
+      key = -di;
+      elog[e] = -log(di);
+    } else {
+      const double u = philox_uniform((unsigned long long)i, block_no, seed, problem);
+      key = -log(u) / di;
+      elog[e] = log(key);
+    }
+    ek[e] = orderable(key);
+    eidx[e] = i;
+  }
+  __syncthreads();
+  long long bt = (long long)total1;
+  if (bt > b) bt = b;
+  const long long room = st->k_cap - st->k;
+  if (bt > room) bt = room;
+  if (bt < 0) bt = 0;
+  // rank of each candidate among the candidates by (exact key, row); the b_t smallest are kept
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    int rank = 0;
+    const unsigned long long ke = ek[e];
+    const long long ie = eidx[e];
+    for (int f = 0; f < m; ++f) rank += (ek[f] < ke || (ek[f] == ke && eidx[f] < ie)) ? 1 : 0;
+    if (rank < bt) {
+      sorted_idx[rank] = ie;
+      sorted_log[rank] = elog[e];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool exact = !overflow && m >= bt;
+    if (exact && bt > 0 && (long long)m < (long long)total1 && c22 != 0x3FFFFFu) {
+      // every row outside the cut has an FP32 key >= the smallest key above the cut
+      const float outside = key_to_float(((c22 + 1u) << 10));
+      exact = sorted_log[bt - 1] < (double)outside - (double)kCutGuard - 1e-6 * fabs((double)outside);
+    }
+    if (!exact) {
+      st->sample_fallback = 1;
+    } else {
+      st->sample_fallback = 0;
+      st->b_t = bt;
+      if (bt == 0) st->done = 1;
+    }
+  }
+  __syncthreads();
+  if (!st->sample_fallback)
+    for (int e = threadIdx.x; e < bt; e += blockDim.x) S_t[e] = sorted_idx[e];
+  // clear the pass buffers for the next block
+  for (int j = threadIdx.x; j < kBins; j += blockDim.x) {
+    hist1[j] = 0;
+    hist2[j] = 0;
+  }
+  if (threadIdx.x == 0) *ncand = 0;
+}
+
+__global__ void k_samp_clear(unsigned int* __restrict__ hist1, unsigned int* __restrict__ hist2,
+                             unsigned int* __restrict__ ncand) {
+  for (int j = threadIdx.x; j < kBins; j += blockDim.x) {
+    hist1[j] = 0;
+    hist2[j] = 0;
+  }
+  if (threadIdx.x == 0) *ncand = 0;
+}
+
+size_t sample2_scratch_bytes(long long n) {
+  return (size_t)n * 4 + 2 * kBins * 4 + 64 + (size_t)kSampCap * 4;
+}
+
+cudaError_t launch_sample_clear(void* scratch, long long n, cudaStream_t s) {
+  unsigned int* K32 = (unsigned int*)scratch;
+  unsigned int* hist1 = K32 + n;
+  unsigned int* hist2 = hist1 + kBins;
+  unsigned int* ncand = hist2 + kBins;
+  k_samp_clear<<<1, 256, 0, s>>>(hist1, hist2, ncand);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
+                           unsigned long long problem, void* scratch, long long* S_t, State* st, cudaStream_t s) {
+  unsigned int* K32 = (unsigned int*)scratch;
+  unsigned int* hist1 = K32 + n;
+  unsigned int* hist2 = hist1 + kBins;
+  unsigned int* ncand = hist2 + kBins;
+  int* cand = (int*)(ncand + 16);
+  const int want = b + kMargin;
+  const unsigned grid = (unsigned)((n + kSampThreads * kSampPerThread - 1) / (kSampThreads * kSampPerThread));
+  k_samp_keys<<<grid, kSampThreads, 0, s>>>(dvec, n, K32, hist1, greedy, seed, problem, st);
+  cudaError_t e = counted(cudaGetLastError());
+  if (e != cudaSuccess) return e;
+  k_samp_hist2<<<grid, kSampThreads, 0, s>>>(K32, n, hist1, hist2, want, st);
+  if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
+  k_samp_compact<<<grid, kSampThreads, 0, s>>>(K32, n, hist1, hist2, want, cand, ncand, kSampCap, st);
+  if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
+  k_samp_final<<<1, 1024, 0, s>>>(dvec, n, hist1, hist2, want, cand, ncand, kSampCap, b, greedy, seed, problem, S_t,
+                                  st);
+  return counted(cudaGetLastError());
+}
+
+}  // namespace rbrp

@@ -70,7 +70,7 @@ struct Plan {
   size_t partial_elems;
   size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
       off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_W32, off_L1Th, off_L1Tl,
-      total;
+      off_Ldiag, off_samp2, total;
 };
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -174,6 +174,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->off_W32 = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
   p->off_L1Th = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->off_L1Tl = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
+  p->off_Ldiag = take(p->w32 ? wsolve_diag_floats(kc) * 4 : 0);
+  p->off_samp2 = take(sample2_scratch_bytes(n));
   p->total = off;
   return RBRP_OK;
 }
@@ -213,6 +215,8 @@ struct Bufs {
   float* W32;
   float* L1Th;
   float* L1Tl;
+  float* Ldiag;
+  void* samp2;
   long long* skel;
 };
 
@@ -244,6 +248,8 @@ Bufs carve(const Plan& p, void* ws) {
   u.W32 = p.w32 ? (float*)(b + p.off_W32) : nullptr;
   u.L1Th = p.w32 ? (float*)(b + p.off_L1Th) : nullptr;
   u.L1Tl = p.w32 ? (float*)(b + p.off_L1Tl) : nullptr;
+  u.Ldiag = p.w32 ? (float*)(b + p.off_Ldiag) : nullptr;
+  u.samp2 = b + p.off_samp2;
   u.skel = nullptr;
   return u;
 }
@@ -311,7 +317,8 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     e = (call);                      \
     if (e != cudaSuccess) return e;  \
   } while (0)
-  // line 5: S_t
+  // line 5: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it)
+  LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
   LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, s));
   // line 6: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
   LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, p.ldq, d, p.b, st, s));
@@ -414,8 +421,9 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
     // solve fused into their epilogue, then widened into the FP64 output.
     float* W32 = u.W32;
     const long long l32 = p.ldw32;
-    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, W32, l32, u.L1, k, u.L1Th, u.L1Tl, p.ldt, n, k, u.st, s));
-    CK(launch_w_finish(W, ldw, W32, l32, n, k, skel, s));
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, W32, l32, W, ldw, u.L1, k, u.L1Th, u.L1Tl, p.ldt, u.Ldiag, n, k, u.st,
+                        s));
+    CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));  // W(S, :) = I exactly
   }
   return RBRP_OK;
 }
@@ -437,6 +445,7 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   // Alg. 2 lines 1-2
   CK(launch_init_norms(X, x_is_fp64, n, d, ldx, u.R, p.r64, p.ldr, u.dvec, u.mark, u.part, p.nparts, st, s));
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
+  CK(launch_sample_clear(u.samp2, n, s));
   // Alg. 2 lines 3-16: blocks are queued in groups and the State is read back
   // after each group.  The group size is the number of blocks still expected,
   // extrapolated from the observed per-block decay of ||d||_1 (or of the rank

@@ -23,6 +23,8 @@ struct State {
   long long done;    // 1 once the stopping test (Alg. 2 line 3) fails
   long long status;  // rbrp_status raised on the device (0 = ok)
   long long bp_pad;  // b' rounded up to a multiple of 16 (tensor-core N)
+  long long sample_fallback;  // 1: the exact FP64 tree sampler must draw this block
+  long long pad_;
   double D0;         // ||d0||_1
   double D;          // ||d||_1 after the last block
   double tau;        // tolerance (< 0: fixed-rank mode)
@@ -106,6 +108,7 @@ inline cudaError_t counted(cudaError_t e) {
 constexpr int kMaxBlock = 256;      // largest b
 constexpr int kSortChunk = 2048;    // sampler: elements sorted per CTA
 constexpr int kGemmTile = 64;       // SIMT GEMM tile (M and N)
+constexpr int kSampCap = 1024;      // candidates the two-stage sampler can rank exactly
 
 // ---------------------------------------------------------------- launch wrappers
 // (defined in k_common.cu / k_update_tc.cu; all enqueue on `s` and return the
@@ -119,6 +122,13 @@ cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, un
                           unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
                           State* st, cudaStream_t s);
 size_t sample_scratch_pairs(long long n, int b);
+// Two-stage sampler (k_sample.cu): FP32 log-domain cut + exact FP64 ranking of
+// the candidates; sets State::sample_fallback when the exact tree sampler
+// (launch_sample, which then runs) must draw the block instead.
+cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
+                           unsigned long long problem, void* scratch, long long* S_t, State* st, cudaStream_t s);
+cudaError_t launch_sample_clear(void* scratch, long long n, cudaStream_t s);
+size_t sample2_scratch_bytes(long long n);
 cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t,
                           double* V, long long ldv, long long d, int b, const State* st, cudaStream_t s);
 template <typename TA, typename TB, typename TC, typename TACC>
@@ -165,8 +175,10 @@ int update_tf32_max_block(int split);
 // Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k, FP32,
 // leading dimension ldw, 16-byte aligned rows) from L (FP32 or FP64) and
 // L1 = L(S, :) (FP64, k x k); L1T_hi/lo are k x ldt FP32 scratch.
-cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* W, long long ldw, const double* L1,
-                             long long ld1, float* L1T_hi, float* L1T_lo, long long ldt, long long n, long long k,
-                             State* st, cudaStream_t s);
+// W64 (n x k FP64, leading dimension ldw64) receives the same values widened.
+cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* W, long long ldw, double* W64,
+                             long long ldw64, const double* L1, long long ld1, float* L1T_hi, float* L1T_lo,
+                             long long ldt, float* Ldiag, long long n, long long k, State* st, cudaStream_t s);
+size_t wsolve_diag_floats(long long k);  // size of the Ldiag scratch for k skeletons
 
 }  // namespace rbrp
