@@ -370,14 +370,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer, long long row_bytes, int box_inner,
-              int box_outer) {
+              int box_outer, bool f64) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
   cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
+  CUresult r = enc(m, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -388,12 +388,16 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
                        long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L, long long ldl,
                        const int* mark, double* dvec, double* partials, const State* st, cudaStream_t s) {
   using C = Cfg<BMAX, SPLIT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_update_tf32<BMAX, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  static unsigned long long attr_set = 0;  // one bit per device
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    attr = true;
+    if (dev >= 64 || !(attr_set >> dev & 1ULL)) {
+      e = cudaFuncSetAttribute(k_update_tf32<BMAX, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      if (e != cudaSuccess) return e;
+      if (dev < 64) attr_set |= 1ULL << dev;
+    }
   }
   CUtensorMap mR, mQ, mQlo, mQT, mQTlo;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, BM)) return cudaErrorInvalidValue;

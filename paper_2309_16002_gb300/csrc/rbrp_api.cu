@@ -69,8 +69,8 @@ struct Plan {
   size_t pm, pn;  // split-K partial buffer extents (elements per split)
   size_t partial_elems;
   size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
-      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_W32, off_L1Th, off_L1Tl,
-      off_Ldiag, off_samp2, total;
+      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_Wh, off_Wl, off_Gh, off_Gl,
+      off_samp2, total;
 };
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -118,7 +118,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->ldc = round_up(kc, 8);
   p->ldg = p->b;
   p->ldlc = kMaxBlock;
-  p->ldw32 = p->ldl;
+  p->ldw32 = round_up(kc, 32);
   p->ldt = round_up(kc, 32);
   {
     long long np = (n + 7) / 8;
@@ -171,10 +171,10 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->off_Qplo = take(p->prec == RBRP_TF32X3 ? (size_t)p->ldpt * p->ldp * 4 : 0);
   p->off_QpTlo = take(p->prec == RBRP_TF32X3 ? (size_t)p->ldq * p->ldpt * 4 : 0);
   p->off_L1 = take((size_t)kc * kc * 8);
-  p->off_W32 = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
-  p->off_L1Th = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
-  p->off_L1Tl = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
-  p->off_Ldiag = take(p->w32 ? wsolve_diag_floats(kc) * 4 : 0);
+  p->off_Wh = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
+  p->off_Wl = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
+  p->off_Gh = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
+  p->off_Gl = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->off_samp2 = take(sample2_scratch_bytes(n));
   p->total = off;
   return RBRP_OK;
@@ -212,10 +212,10 @@ struct Bufs {
   float* Qp_lo;
   float* QpT_lo;
   double* L1;
-  float* W32;
-  float* L1Th;
-  float* L1Tl;
-  float* Ldiag;
+  float* Wh;
+  float* Wl;
+  float* Gh;
+  float* Gl;
   void* samp2;
   long long* skel;
 };
@@ -245,10 +245,10 @@ Bufs carve(const Plan& p, void* ws) {
   u.Qp_lo = (p.prec == RBRP_TF32X3) ? (float*)(b + p.off_Qplo) : nullptr;
   u.QpT_lo = (p.prec == RBRP_TF32X3) ? (float*)(b + p.off_QpTlo) : nullptr;
   u.L1 = (double*)(b + p.off_L1);
-  u.W32 = p.w32 ? (float*)(b + p.off_W32) : nullptr;
-  u.L1Th = p.w32 ? (float*)(b + p.off_L1Th) : nullptr;
-  u.L1Tl = p.w32 ? (float*)(b + p.off_L1Tl) : nullptr;
-  u.Ldiag = p.w32 ? (float*)(b + p.off_Ldiag) : nullptr;
+  u.Wh = p.w32 ? (float*)(b + p.off_Wh) : nullptr;
+  u.Wl = p.w32 ? (float*)(b + p.off_Wl) : nullptr;
+  u.Gh = p.w32 ? (float*)(b + p.off_Gh) : nullptr;
+  u.Gl = p.w32 ? (float*)(b + p.off_Gl) : nullptr;
   u.samp2 = b + p.off_samp2;
   u.skel = nullptr;
   return u;
@@ -417,12 +417,9 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
     }
     CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));
   } else {
-    // FP32 solve: blocked products on tensor cores (3xTF32) with the triangular
-    // solve fused into their epilogue, then widened into the FP64 output.
-    float* W32 = u.W32;
-    const long long l32 = p.ldw32;
-    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, W32, l32, W, ldw, u.L1, k, u.L1Th, u.L1Tl, p.ldt, u.Ldiag, n, k, u.st,
-                        s));
+    // FP32 solve on tensor cores (3xTF32): every 64-column block of W is one
+    // product with the precomputed block-inverse factor, then W(S, :) = I.
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, k, u.st, s));
     CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));  // W(S, :) = I exactly
   }
   return RBRP_OK;

@@ -172,13 +172,13 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
 int update_tf32_parts(long long n);
 int update_tf32_max_block(int split);
 
-// Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k, FP32,
-// leading dimension ldw, 16-byte aligned rows) from L (FP32 or FP64) and
-// L1 = L(S, :) (FP64, k x k); L1T_hi/lo are k x ldt FP32 scratch.
-// W64 (n x k FP64, leading dimension ldw64) receives the same values widened.
-cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* W, long long ldw, double* W64,
-                             long long ldw64, const double* L1, long long ld1, float* L1T_hi, float* L1T_lo,
-                             long long ldt, float* Ldiag, long long n, long long k, State* st, cudaStream_t s);
-size_t wsolve_diag_floats(long long k);  // size of the Ldiag scratch for k skeletons
+// Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k) from
+// L (FP32 or FP64, leading dimension ldl) and L1 = L(S, :) (FP64, k x k, ld1).
+// Wh/Wl (n x ldw32 FP32 scratch) receive W split into TF32 hi/lo; Gh/Gl
+// (k x ldt FP32 scratch) the transposed block-inverse factor G.  W64 (n x k
+// FP64, leading dimension ldw64) receives the result; rows of S are not set.
+cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* Wh, float* Wl, long long ldw32,
+                             double* W64, long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl,
+                             long long ldt, long long n, long long k, State* st, cudaStream_t s);
 
 }  // namespace rbrp

@@ -127,10 +127,11 @@ __device__ __forceinline__ uint32_t swz(int r, int ch) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4));
 }
 
-// Host: 2-D FP32 tensor map with 128-byte swizzle (inner x outer elements, row
-// pitch in bytes, box of box_inner x box_outer); false if encoding failed.
+// Host: 2-D FP32 (f64: FP64) tensor map with 128-byte swizzle (inner x outer
+// elements, row pitch in bytes, box of box_inner x box_outer); false if
+// encoding failed.
 bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer, long long row_bytes, int box_inner,
-              int box_outer);
+              int box_outer, bool f64 = false);
 
 }  // namespace tc
 }  // namespace rbrp
