@@ -248,26 +248,28 @@ cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, un
 }
 
 // ============================================================================
-// Alg. 2 line 6 (first half): V = R(S_t, :) in FP64.
+// Alg. 2 line 6 (first half): V = R(S_t, :) (FP64, or FP32 on the plain TF32 path).
 // ============================================================================
-template <typename TR>
+template <typename TR, typename TV>
 __global__ void k_gather(const TR* __restrict__ R, long long ldr, const long long* __restrict__ S_t,
-                         double* __restrict__ V, long long ldv, long long d, const State* st) {
+                         TV* __restrict__ V, long long ldv, long long d, const State* st) {
   if (st->done) return;
   const long long i = blockIdx.y;
   if (i >= st->b_t) return;
   const TR* r = R + S_t[i] * ldr;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (long long)gridDim.x * blockDim.x)
-    V[i * ldv + j] = (double)r[j];
+    V[i * ldv + j] = (TV)r[j];
 }
 
-cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t, double* V,
+cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t, void* V, int v_is_fp64,
                           long long ldv, long long d, int b, const State* st, cudaStream_t s) {
   dim3 grid((unsigned)((d + 255) / 256), (unsigned)b);
   if (r_is_fp64)
-    k_gather<double><<<grid, 256, 0, s>>>((const double*)R, ldr, S_t, V, ldv, d, st);
+    k_gather<double, double><<<grid, 256, 0, s>>>((const double*)R, ldr, S_t, (double*)V, ldv, d, st);
+  else if (v_is_fp64)
+    k_gather<float, double><<<grid, 256, 0, s>>>((const float*)R, ldr, S_t, (double*)V, ldv, d, st);
   else
-    k_gather<float><<<grid, 256, 0, s>>>((const float*)R, ldr, S_t, V, ldv, d, st);
+    k_gather<float, float><<<grid, 256, 0, s>>>((const float*)R, ldr, S_t, (float*)V, ldv, d, st);
   return counted(cudaGetLastError());
 }
 
@@ -413,7 +415,8 @@ template cudaError_t launch_gemm<float, double, float, float>(const GemmArgs&, l
 // ============================================================================
 // With the lo buffers set (3xTF32), hi is the FP32 value with the 13 low
 // mantissa bits cleared (exact in TF32) and lo = fp32(q - hi) is the rest.
-__global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* __restrict__ Qp,
+template <typename TQ>
+__global__ void k_qp_lowp(const TQ* __restrict__ Qt, long long ldq, float* __restrict__ Qp,
                           float* __restrict__ Qp_lo, long long ldp, float* __restrict__ QpT, float* __restrict__ QpT_lo,
                           long long ldpt, long long d, int bmax, const State* st) {
   if (st->done) return;
@@ -423,11 +426,11 @@ __global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* _
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / ldp);
     const long long j = e % ldp;
-    const double q = (i < bp && j < d) ? Qt[(k + i) * ldq + j] : 0.0;
+    const TQ q = (i < bp && j < d) ? Qt[(k + i) * ldq + j] : (TQ)0;
     float hi = (float)q, lo = 0.0f;
     if (Qp_lo) {
       hi = __uint_as_float(__float_as_uint(hi) & 0xFFFFE000u);
-      lo = (float)(q - (double)hi);
+      lo = (float)(q - (TQ)hi);
       Qp_lo[(long long)i * ldp + j] = lo;
     }
     Qp[(long long)i * ldp + j] = hi;
@@ -438,12 +441,16 @@ __global__ void k_qp_lowp(const double* __restrict__ Qt, long long ldq, float* _
   }
 }
 
-cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, float* Qp_lo, long long ldp, float* QpT,
-                           float* QpT_lo, long long ldpt, long long d, int b, const State* st, cudaStream_t s) {
+cudaError_t launch_qp_lowp(const void* Qt, int q_is_fp64, long long ldq, float* Qp, float* Qp_lo, long long ldp,
+                           float* QpT, float* QpT_lo, long long ldpt, long long d, int b, const State* st,
+                           cudaStream_t s) {
   long long tot = (long long)b * ldp;
   unsigned g = (unsigned)((tot + 255) / 256);
   if (g > 2048) g = 2048;
-  k_qp_lowp<<<g, 256, 0, s>>>(Qt, ldq, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, d, b, st);
+  if (q_is_fp64)
+    k_qp_lowp<double><<<g, 256, 0, s>>>((const double*)Qt, ldq, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, d, b, st);
+  else
+    k_qp_lowp<float><<<g, 256, 0, s>>>((const float*)Qt, ldq, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, d, b, st);
   return counted(cudaGetLastError());
 }
 

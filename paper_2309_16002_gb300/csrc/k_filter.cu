@@ -302,6 +302,187 @@ __global__ void __launch_bounds__(256) k_pchol_global(const double* __restrict__
 }
 
 
+// FP32 form of the filter for the plain TF32 path, whose residual already
+// carries TF32 rounding (~2^-11 relative), far coarser than FP32: the same
+// pivoting, truncation and outputs as k_pchol_reg, followed in the same CTA by
+// Linv = Lc^{-1} (bp x bp, lower triangular), so that Q'_V = Linv V_perm is one
+// product instead of a serial substitution.
+//
+// The factorisation is left-looking: at step i the new factor column for
+// every remaining candidate j is (G(j, p) - sum_{t<i} L(j, t) L(p, t)) /
+// sqrt(d_p), and the residual norms d_j drop by its square.  Thread j owns
+// candidate j (its factor row in shared memory, its d_j in a register); a step
+// is a warp-shuffle argmax, one block barrier to combine the four warps, and a
+// short dot product with four independent accumulators.  Then the same
+// threads form the inverse, four lanes per column.
+constexpr int kPcholF32Threads = 128;
+
+__global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __restrict__ G, long long ldg,
+                                                                float* __restrict__ Linv, long long ldl,
+                                                                int* __restrict__ perm,
+                                                                const long long* __restrict__ S_t,
+                                                                long long* __restrict__ skel, int* __restrict__ mark,
+                                                                State* st, int mmax) {
+  if (st->done) return;
+  extern __shared__ __align__(16) float fsm[];
+  const int LDF = (mmax + 4) & ~3;  // factor rows: float4 steps over t
+  const int LDG = mmax + 1;         // G rows: odd stride, conflict-free column reads
+  float* Lw = fsm;                  // Lw[j * LDF + t]: factor entry of candidate j at step t
+  float* Gs = fsm + mmax * LDF;     // G, later the pivot-order factor Ls (stride LDF)
+  float* Ls = Gs;
+  float* X = Lw;                    // the inverse, once Ls is built
+  __shared__ float rdg[kRegCholMax];
+  __shared__ int s_perm[kRegCholMax];
+  __shared__ float s_ms[2][4], s_bv[2][4];
+  __shared__ int s_bi[2][4];
+  __shared__ float s_tot[4];
+  const int m = (int)st->b_t;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // thread c stages column c; sixteen loads in flight per thread
+  for (int r0 = 0; r0 < m; r0 += 16) {
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = (r0 + u < m && tid < m) ? G[(long long)(r0 + u) * ldg + tid] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (r0 + u < m && tid < m) Gs[(r0 + u) * LDG + tid] = v[u];
+  }
+  for (int e = tid; e < m * LDF; e += kPcholF32Threads) Lw[e] = 0.f;
+  __syncthreads();
+  double tau_b = st->tau_b;
+  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+  const float tb = (float)tau_b;
+  const int j = tid;
+  bool alive = j < m;
+  float dj = alive ? Gs[j * LDG + j] : 0.f;
+  {
+    float t = dj;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_tot[warp] = t;
+  }
+  __syncthreads();
+  const float total = (s_tot[0] + s_tot[1]) + (s_tot[2] + s_tot[3]);
+  const float* lj = Lw + j * LDF;
+  int bp = 0;
+  for (int i = 0; i < m; ++i) {
+    // trailing mass and pivot (largest residual norm^2, ties to the smaller index)
+    float msum = alive ? dj : 0.f, best = alive ? dj : -1.f;
+    int vi = alive ? j : INT_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      msum += __shfl_xor_sync(0xffffffffu, msum, o);
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+      if (ob > best || (ob == best && oi < vi)) {
+        best = ob;
+        vi = oi;
+      }
+    }
+    const int sl = i & 1;
+    if (lane == 0) {
+      s_ms[sl][warp] = msum;
+      s_bv[sl][warp] = best;
+      s_bi[sl][warp] = vi;
+    }
+    __syncthreads();
+    msum = (s_ms[sl][0] + s_ms[sl][1]) + (s_ms[sl][2] + s_ms[sl][3]);
+    best = s_bv[sl][0];
+    vi = s_bi[sl][0];
+#pragma unroll
+    for (int w = 1; w < 4; ++w) {
+      const float ob = s_bv[sl][w];
+      const int oi = s_bi[sl][w];
+      if (ob > best || (ob == best && oi < vi)) {
+        best = ob;
+        vi = oi;
+      }
+    }
+    if (!(msum >= tb * total && msum > 0.f) || vi == INT_MAX || !(best > 0.f)) break;
+    const int p = vi;
+    const float rinv = rsqrtf(best);
+    if (alive) {
+      if (j == p) {
+        Lw[j * LDF + i] = best * rinv;
+        alive = false;
+      } else {
+        const float* lp = Lw + p * LDF;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int t = 0; t < i; t += 4) {  // entries past step i - 1 are still zero
+          const float4 x = *(const float4*)(lj + t);
+          const float4 y = *(const float4*)(lp + t);
+          a0 = fmaf(x.x, y.x, a0);
+          a1 = fmaf(x.y, y.y, a1);
+          a2 = fmaf(x.z, y.z, a2);
+          a3 = fmaf(x.w, y.w, a3);
+        }
+        const float l = (Gs[j * LDG + p] - ((a0 + a1) + (a2 + a3))) * rinv;
+        Lw[j * LDF + i] = l;
+        dj -= l * l;
+      }
+    }
+    if (tid == 0) {
+      rdg[i] = rinv;
+      s_perm[i] = p;
+      if (perm) perm[i] = p;
+    }
+    bp = i + 1;
+  }
+  __syncthreads();
+  // pivot-order factor (over G, which is no longer needed)
+  for (int e = tid; e < bp * bp; e += kPcholF32Threads) {
+    const int i = e / bp, l = e % bp;
+    Ls[i * LDF + l] = (l <= i) ? Lw[s_perm[i] * LDF + l] : 0.f;
+  }
+  __syncthreads();
+  // Linv = Ls^{-1} by forward substitution, column c by the four lanes of a quad
+  {
+    const int part = tid & 3;
+    const unsigned qmask = 0xFu << (lane & 28);
+    for (int c = tid >> 2; c < bp; c += kPcholF32Threads / 4) {
+      for (int i = c; i < bp; ++i) {
+        float acc = 0.f;
+        for (int l = c + part; l < i; l += 4) acc = fmaf(Ls[i * LDF + l], X[l * LDF + c], acc);
+        acc += __shfl_xor_sync(qmask, acc, 1);
+        acc += __shfl_xor_sync(qmask, acc, 2);
+        if (part == 0) X[i * LDF + c] = ((i == c ? 1.f : 0.f) - acc) * rdg[i];
+        __syncwarp(qmask);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < bp; ++i)
+    for (int c = tid; c < bp; c += kPcholF32Threads) Linv[(long long)i * ldl + c] = (c <= i) ? X[i * LDF + c] : 0.f;
+  {
+    const long long k = st->k;
+    const int tno = (int)(st->t + 1);
+    for (int i = tid; i < bp; i += kPcholF32Threads) {
+      const long long row = S_t[s_perm[i]];
+      skel[k + i] = row;
+      mark[row] = tno;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    st->bp = bp;
+    st->bp_pad = (bp + 15) / 16 * 16;
+    if (bp == 0) st->done = 1;
+  }
+}
+
+cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
+                              int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+  if (b > kRegCholMax) return cudaErrorInvalidValue;
+  const int ldf = (b + 4) & ~3;
+  const size_t smem = (size_t)2 * b * ldf * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_pchol_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_pchol_f32<<<1, kPcholF32Threads, smem, s>>>(G, ldg, Linv, ldl, perm, S_t, skel, mark, st, b);
+  return counted(cudaGetLastError());
+}
+
 static cudaError_t launch_pchol_any(const double* G, long long ldg, double* Lc, long long ldl, int* perm,
                                     const long long* S_t, long long* skel, int* mark, int b, State* st, int pivoted,
                                     cudaStream_t s) {

@@ -8,10 +8,10 @@
 //     logarithms only; FP64 arithmetic is slow on GB300) and an 11 + 11-bit
 //     radix histogram over those keys choose a cut that keeps at least
 //     b + kMargin candidates;
-//  2. one CTA recomputes the FP64 keys of the candidates exactly as the oracle
-//     does, ranks them, and checks that the cut lies more than the FP32 error
-//     bound above the b_t-th exact key, so no row outside the cut can belong
-//     to S_t.  If the check fails (or the candidate list overflows) it raises
+//  2. the compaction pass computes the FP64 keys of the candidates exactly as
+//     the oracle does; one CTA ranks them and checks that the cut lies more
+//     than the FP32 error bound above the b_t-th exact key, so no row outside
+//     the cut can belong to S_t.  If the check fails (or the candidate list overflows) it raises
 //     State::sample_fallback and the exact FP64 tree sampler in k_common.cu
 //     runs instead.
 // The histogram buffers are cleared by the final kernel for the next block.
@@ -26,7 +26,7 @@ namespace rbrp {
 constexpr int kMargin = 32;          // extra candidates kept by the FP32 cut
 constexpr int kBins = 2048;          // 11-bit digits
 constexpr int kSampThreads = 256;
-constexpr int kSampPerThread = 8;
+constexpr int kSampPerThread = 2;
 constexpr float kCutGuard = 2e-4f;   // absolute slack in log space (FP32 key error bound)
 
 // ln(d) from the FP64 bit pattern with FP32 arithmetic: exponent * ln2 + ln(mantissa).
@@ -89,49 +89,65 @@ __global__ void __launch_bounds__(kSampThreads) k_samp_keys(const double* __rest
 
 // Block-wide search over a 2048-bin histogram: the first bin where the running
 // count reaches `want`; returns the count below that bin in *below (or bin
-// kBins and the total when the histogram holds fewer than `want`).
-// Callable from any block size >= kSampThreads (threads beyond the first
-// kSampThreads only take part in the barriers).
+// kBins and the total when the histogram holds fewer than `want`).  The first
+// kSampThreads threads each sum eight bins and take an exclusive scan of those
+// sums; the one thread whose range contains the want-th count walks its bins.
+// Callable from any block size >= kSampThreads (the other threads only take
+// part in the barriers).
 __device__ int find_bin(const unsigned int* __restrict__ hist, unsigned int want, unsigned int* below,
                         unsigned int* total) {
-  __shared__ unsigned int part[kSampThreads];
+  __shared__ unsigned int wsum[kSampThreads / 32];
   __shared__ int s_bin;
   __shared__ unsigned int s_below, s_total;
   constexpr int per = kBins / kSampThreads;  // 8 bins per thread
-  if (threadIdx.x < kSampThreads) {
-    unsigned int sum = 0;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  unsigned int c[per], sum = 0, incl = 0;
+  if (t < kSampThreads) {
 #pragma unroll
-    for (int q = 0; q < per; ++q) sum += hist[threadIdx.x * per + q];
-    part[threadIdx.x] = sum;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int run = 0;
-    int bin = kBins;
-    unsigned int bel = 0;
-    for (int t = 0; t < kSampThreads; ++t) {
-      if (bin == kBins && run + part[t] >= want) {
-        unsigned int r2 = run;
-        for (int q = 0; q < per; ++q) {
-          const unsigned int c = hist[t * per + q];
-          if (r2 + c >= want) {
-            bin = t * per + q;
-            bel = r2;
-            break;
-          }
-          r2 += c;
-        }
-      }
-      run += part[t];
+    for (int q = 0; q < per; ++q) {
+      c[q] = hist[t * per + q];
+      sum += c[q];
     }
-    s_bin = bin;
-    s_below = (bin == kBins) ? run : bel;
-    s_total = run;
+    incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    if (t == 0) {
+      s_bin = kBins;
+      s_below = 0;
+    }
   }
   __syncthreads();
-  *below = s_below;
-  *total = s_total;
+  if (t < kSampThreads) {
+    unsigned int before = 0, all = 0;
+#pragma unroll
+    for (int q = 0; q < kSampThreads / 32; ++q) {
+      if (q < w) before += wsum[q];
+      all += wsum[q];
+    }
+    incl += before;
+    const unsigned int excl = incl - sum;
+    if (excl < want && incl >= want) {
+      unsigned int r2 = excl;
+#pragma unroll
+      for (int q = 0; q < per; ++q) {
+        if (r2 + c[q] >= want) {
+          s_bin = t * per + q;
+          s_below = r2;
+          break;
+        }
+        r2 += c[q];
+      }
+    }
+    if (t == 0) s_total = all;
+  }
+  __syncthreads();
   const int bin = s_bin;
+  *total = s_total;
+  *below = (bin == kBins) ? s_total : s_below;
   __syncthreads();  // the shared results may be overwritten by the next call
   return bin;
 }
@@ -171,14 +187,21 @@ __device__ unsigned int cut22(const unsigned int* hist1, const unsigned int* his
   return ((unsigned int)b1 << 11) | (unsigned int)(b2 >= kBins ? kBins - 1 : b2);
 }
 
-// Pass 3: compact the candidate rows.
-__global__ void __launch_bounds__(kSampThreads) k_samp_compact(const unsigned int* __restrict__ K32, long long n,
+// Pass 3: compact the candidate rows with their exact FP64 keys (computed
+// here, spread over the grid, exactly as the oracle does).
+__global__ void __launch_bounds__(kSampThreads) k_samp_compact(const unsigned int* __restrict__ K32,
+                                                               const double* __restrict__ dvec, long long n,
                                                                const unsigned int* __restrict__ hist1,
                                                                const unsigned int* __restrict__ hist2, int want,
-                                                               int* __restrict__ cand, unsigned int* __restrict__ ncand,
-                                                               int cap, const State* st) {
+                                                               int* __restrict__ cand,
+                                                               unsigned long long* __restrict__ cand_key,
+                                                               double* __restrict__ cand_log,
+                                                               unsigned int* __restrict__ ncand, int cap, int greedy,
+                                                               unsigned long long seed, unsigned long long problem,
+                                                               const State* st) {
   if (st->done) return;
   const unsigned int c22 = cut22(hist1, hist2, want);
+  const unsigned long long block_no = (unsigned long long)st->t + 1ULL;
   const long long base = (long long)blockIdx.x * kSampThreads * kSampPerThread;
 #pragma unroll
   for (int q = 0; q < kSampPerThread; ++q) {
@@ -187,18 +210,33 @@ __global__ void __launch_bounds__(kSampThreads) k_samp_compact(const unsigned in
     const unsigned int k = K32[i];
     if (k != 0xFFFFFFFFu && (k >> 10) <= c22) {
       const unsigned int pos = atomicAdd(ncand, 1u);
-      if ((int)pos < cap) cand[pos] = (int)i;
+      if ((int)pos < cap) {
+        const double di = dvec[i];
+        double key, lg;
+        if (greedy) {
+          key = -di;
+          lg = -log(di);
+        } else {
+          const double u = philox_uniform((unsigned long long)i, block_no, seed, problem);
+          key = -log(u) / di;
+          lg = log(key);
+        }
+        cand[pos] = (int)i;
+        cand_key[pos] = orderable(key);
+        cand_log[pos] = lg;
+      }
     }
   }
 }
 
 // Pass 4 (one CTA): exact FP64 keys of the candidates, ranking, the margin
 // check, S_t and b_t; clears the histograms for the next block.
-__global__ void __launch_bounds__(1024) k_samp_final(const double* __restrict__ dvec, long long n,
-                                                     unsigned int* __restrict__ hist1, unsigned int* __restrict__ hist2,
-                                                     int want, const int* __restrict__ cand,
-                                                     unsigned int* __restrict__ ncand, int cap, int b, int greedy,
-                                                     unsigned long long seed, unsigned long long problem,
+__global__ void __launch_bounds__(1024) k_samp_final(long long n, unsigned int* __restrict__ hist1,
+                                                     unsigned int* __restrict__ hist2, int want,
+                                                     const int* __restrict__ cand,
+                                                     const unsigned long long* __restrict__ cand_key,
+                                                     const double* __restrict__ cand_log,
+                                                     unsigned int* __restrict__ ncand, int cap, int b,
                                                      long long* __restrict__ S_t, State* st) {
   if (st->done) return;
   __shared__ unsigned long long ek[kSampCap];
@@ -210,23 +248,12 @@ __global__ void __launch_bounds__(1024) k_samp_final(const double* __restrict__ 
   find_bin(hist1, (unsigned int)want, &below1, &total1);  // total1 = number of eligible rows
   const unsigned int c22 = cut22(hist1, hist2, want);
   const int nc = (int)*ncand;
-  const unsigned long long block_no = (unsigned long long)st->t + 1ULL;
   const bool overflow = nc > cap;
   const int m = overflow ? 0 : nc;
   for (int e = threadIdx.x; e < m; e += blockDim.x) {
-    const long long i = cand[e];
-    const double di = dvec[i];
-    double key;
-    if (greedy) {
-      key = -di;
-      elog[e] = -log(di);
-    } else {
-      const double u = philox_uniform((unsigned long long)i, block_no, seed, problem);
-      key = -log(u) / di;
-      elog[e] = log(key);
-    }
-    ek[e] = orderable(key);
-    eidx[e] = i;
+    ek[e] = cand_key[e];
+    eidx[e] = cand[e];
+    elog[e] = cand_log[e];
   }
   __syncthreads();
   long long bt = (long long)total1;
@@ -282,7 +309,7 @@ __global__ void k_samp_clear(unsigned int* __restrict__ hist1, unsigned int* __r
 }
 
 size_t sample2_scratch_bytes(long long n) {
-  return (size_t)n * 4 + 2 * kBins * 4 + 64 + (size_t)kSampCap * 4;
+  return (size_t)n * 4 + 2 * kBins * 4 + 64 + (size_t)kSampCap * (4 + 8 + 8) + 16;
 }
 
 cudaError_t launch_sample_clear(void* scratch, long long n, cudaStream_t s) {
@@ -301,6 +328,9 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
   unsigned int* hist2 = hist1 + kBins;
   unsigned int* ncand = hist2 + kBins;
   int* cand = (int*)(ncand + 16);
+  // 8-byte aligned arrays after the candidate rows
+  unsigned long long* cand_key = (unsigned long long*)(((uintptr_t)(cand + kSampCap) + 15) & ~(uintptr_t)15);
+  double* cand_log = (double*)(cand_key + kSampCap);
   const int want = b + kMargin;
   const unsigned grid = (unsigned)((n + kSampThreads * kSampPerThread - 1) / (kSampThreads * kSampPerThread));
   k_samp_keys<<<grid, kSampThreads, 0, s>>>(dvec, n, K32, hist1, greedy, seed, problem, st);
@@ -308,10 +338,10 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
   if (e != cudaSuccess) return e;
   k_samp_hist2<<<grid, kSampThreads, 0, s>>>(K32, n, hist1, hist2, want, st);
   if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
-  k_samp_compact<<<grid, kSampThreads, 0, s>>>(K32, n, hist1, hist2, want, cand, ncand, kSampCap, st);
+  k_samp_compact<<<grid, kSampThreads, 0, s>>>(K32, dvec, n, hist1, hist2, want, cand, cand_key, cand_log, ncand,
+                                                kSampCap, greedy, seed, problem, st);
   if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
-  k_samp_final<<<1, 1024, 0, s>>>(dvec, n, hist1, hist2, want, cand, ncand, kSampCap, b, greedy, seed, problem, S_t,
-                                  st);
+  k_samp_final<<<1, 1024, 0, s>>>(n, hist1, hist2, want, cand, cand_key, cand_log, ncand, kSampCap, b, S_t, st);
   return counted(cudaGetLastError());
 }
 

@@ -62,15 +62,15 @@ cudaError_t timed(EventPool& pool, cudaStream_t s, F&& body) {
 
 struct Plan {
   long long n, d, k_cap;
-  int b, prec, r64, l64, w32, greedy;
+  int b, prec, r64, l64, w32, greedy, f32;
   long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32, ldt;
   int nparts;
-  int s_coef, s_apply, s_gram, s_upd1, s_upd2;
+  int s_upd1, s_upd2;
   size_t pm, pn;  // split-K partial buffer extents (elements per split)
   size_t partial_elems;
   size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
       off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_Wh, off_Wl, off_Gh, off_Gl,
-      off_samp2, total;
+      off_samp2, off_cnt, total;
 };
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -109,6 +109,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->r64 = (o->precision == RBRP_FP64);
   p->l64 = p->r64;
   p->w32 = (o->w_precision == RBRP_W_FP32);
+  p->f32 = (o->precision == RBRP_TF32);  // FP32 storage for the per-block chain
   p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY);
   p->ldr = round_up(d, 32);
   p->ldq = round_up(d, 32);
@@ -125,21 +126,28 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
     p->nparts = (int)std::min(np, 4LL * 152);
   }
   const long long b = p->b;
-  const long long cgs_target = (p->prec == RBRP_FP64) ? 608 : 160;
-  p->s_coef = splits_for(b, kc, d, kGemmTile, cgs_target);
-  p->s_apply = splits_for(b, d, kc, kGemmTile, cgs_target);
-  p->s_gram = splits_for(b, b, d, 32);
   p->s_upd1 = splits_for(n, b, d);
   p->s_upd2 = splits_for(n, d, b);
   size_t need = 0;
-  need = std::max<size_t>(need, (size_t)p->s_coef * b * kc);
-  need = std::max<size_t>(need, (size_t)p->s_apply * b * d);
-  need = std::max<size_t>(need, (size_t)p->s_gram * b * b);
   if (p->prec == RBRP_FP64 || p->prec == RBRP_FP32) {
     need = std::max<size_t>(need, (size_t)p->s_upd1 * n * b);
     need = std::max<size_t>(need, (size_t)p->s_upd2 * n * d);
   }
   need = std::max<size_t>(need, (size_t)splits_for(n, 64, kc) * n * 64);
+  {
+    // small products (k_sgemm.cu): splits x tiles x tile^2 FP64 partials
+    const int cgs64 = (p->prec == RBRP_FP64), gram64 = (p->prec != RBRP_TF32);
+    auto sg_need = [&](long long M, long long N, long long K, int acc64) {
+      const int tile = sgemm_tile(acc64);
+      int sp = 1, kcs = 0;
+      sgemm_splits(M, N, K, tile, acc64 ? 608 : 160, &sp, &kcs);
+      const long long tiles = ((M + tile - 1) / tile) * ((N + tile - 1) / tile);
+      return (size_t)sp * tiles * tile * tile;
+    };
+    need = std::max<size_t>(need, sg_need(b, kc, d, cgs64));
+    need = std::max<size_t>(need, sg_need(b, d, kc, cgs64));
+    need = std::max<size_t>(need, sg_need(b, b, d, gram64));
+  }
   p->partial_elems = need;
 
   size_t off = 0;
@@ -176,6 +184,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->off_Gh = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->off_Gl = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->off_samp2 = take(sample2_scratch_bytes(n));
+  p->off_cnt = take((size_t)kSgemmCounters * 4);
   p->total = off;
   return RBRP_OK;
 }
@@ -217,6 +226,7 @@ struct Bufs {
   float* Gh;
   float* Gl;
   void* samp2;
+  unsigned* cnt;
   long long* skel;
 };
 
@@ -250,6 +260,7 @@ Bufs carve(const Plan& p, void* ws) {
   u.Gh = p.w32 ? (float*)(b + p.off_Gh) : nullptr;
   u.Gl = p.w32 ? (float*)(b + p.off_Gl) : nullptr;
   u.samp2 = b + p.off_samp2;
+  u.cnt = (unsigned*)(b + p.off_cnt);
   u.skel = nullptr;
   return u;
 }
@@ -277,6 +288,44 @@ cudaError_t gemm(const Plan& p, const Bufs& u, MatRef A, MatRef B, MatRef C, Dim
   return launch_gemm<TA, TB, TC, TACC>(g, Mmax, Nmax, splits, tile, s);
 }
 
+// Small product of the per-block chain (k_sgemm.cu); BKC: C = A B^T, else C = A B.
+template <typename TS, typename TACC, bool BKC>
+cudaError_t sgemm(const Plan& p, const Bufs& u, const void* A, DimRef a_off, long long lda, const void* B,
+                  DimRef b_off, long long ldb, void* C, DimRef c_off, long long ldc, DimRef M, DimRef N, DimRef K,
+                  long long Mmax, long long Nmax, long long Kmax, double alpha, double beta, cudaStream_t s,
+                  const int* b_rows = nullptr) {
+  SgemmArgs g;
+  g.b_rows = b_rows;
+  g.A = A;
+  g.a_off = a_off;
+  g.lda = lda;
+  g.B = B;
+  g.b_off = b_off;
+  g.ldb = ldb;
+  g.C = C;
+  g.c_off = c_off;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.partial = u.gp;
+  g.cnt = u.cnt;
+  g.st = u.st;
+  const int acc64 = sizeof(TACC) == 8;
+  const int tile = sgemm_tile(acc64);
+  int splits = 1, kc = 32;
+  sgemm_splits(Mmax, Nmax, Kmax, tile, acc64 ? 608 : 160, &splits, &kc);
+  const long long tiles = ((Mmax + tile - 1) / tile) * ((Nmax + tile - 1) / tile);
+  if ((size_t)splits * tiles * tile * tile > p.partial_elems || tiles > kSgemmCounters) {
+    splits = 1;
+    kc = (int)((Kmax + 31) / 32 * 32);
+  }
+  g.kc = kc;
+  return launch_sgemm<TS, TACC, BKC>(g, Mmax, Nmax, splits, s);
+}
+
 // V <- V - (V Qt^T) Qt on rows [0, rows) of V (rows from the device), in FP64.
 //
 // V and Q stay FP64 and the correction is subtracted in FP64.  On the mixed
@@ -285,24 +334,27 @@ cudaError_t gemm(const Plan& p, const Bufs& u, MatRef A, MatRef B, MatRef C, Dim
 // update's rounding, so the coefficients are small and each pass shrinks the
 // component in span(Q) by the FP32 product accuracy (~1e-7); two passes leave
 // it at FP64 level.  The FP64 path keeps FP64 products throughout.
-template <typename TACC>
-cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, double* V, DimRef voff, DimRef rows, cudaStream_t s) {
+template <typename TS, typename TACC>
+cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, void* V, DimRef voff, DimRef rows, cudaStream_t s) {
   const State* st = u.st;
   const long long kc = p.k_cap, b = p.b;
-  cudaError_t e = gemm<double, double, double, TACC>(
-      p, u, mat(V, voff, p.ldq, 1), mat(u.Qt, dim_const(0), 1, p.ldq), mat(u.C, dim_const(0), p.ldc, 1), rows,
-      dim_dev(&st->k), dim_const(p.d), 1.0, 0.0, b, kc, p.s_coef, st, s);
+  // C = V Qt^T  (rows x k)
+  cudaError_t e = sgemm<TS, TACC, true>(p, u, V, voff, p.ldq, u.Qt, dim_const(0), p.ldq, u.C, dim_const(0), p.ldc,
+                                        rows, dim_dev(&st->k), dim_const(p.d), b, kc, p.d, 1.0, 0.0, s);
   if (e != cudaSuccess) return e;
-  return gemm<double, double, double, TACC>(
-      p, u, mat(u.C, dim_const(0), p.ldc, 1), mat(u.Qt, dim_const(0), p.ldq, 1), mat(V, voff, p.ldq, 1), rows,
-      dim_const(p.d), dim_dev(&st->k), -1.0, 1.0, b, p.d, p.s_apply, st, s);
+  // V -= C Qt
+  return sgemm<TS, TACC, false>(p, u, u.C, dim_const(0), p.ldc, u.Qt, dim_const(0), p.ldq, V, voff, p.ldq, rows,
+                                dim_const(p.d), dim_dev(&st->k), b, p.d, kc, -1.0, 1.0, s);
 }
 
 // V (rows [0, rows) at V + voff, leading dimension ldq) <- V - (V Qt^T) Qt over Qt rows [0, k).
-cudaError_t cgs_pass(const Plan& p, const Bufs& u, double* V, DimRef rows, cudaStream_t s,
+// FP32 storage and products on the plain TF32 path; FP64 storage with FP32
+// products on the other mixed paths; FP64 throughout on the FP64 path.
+cudaError_t cgs_pass(const Plan& p, const Bufs& u, void* V, DimRef rows, cudaStream_t s,
                      DimRef voff = dim_const(0)) {
-  if (p.prec == RBRP_FP64) return cgs_pass_t<double>(p, u, V, voff, rows, s);
-  return cgs_pass_t<float>(p, u, V, voff, rows, s);
+  if (p.f32) return cgs_pass_t<float, float>(p, u, V, voff, rows, s);
+  if (p.prec == RBRP_FP64) return cgs_pass_t<double, double>(p, u, V, voff, rows, s);
+  return cgs_pass_t<double, float>(p, u, V, voff, rows, s);
 }
 
 cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s);
@@ -321,34 +373,49 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
   LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, s));
   // line 6: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
-  LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, p.ldq, d, p.b, st, s));
+  LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
+  // (one pass on the plain TF32 path: the sampled residual rows are orthogonal
+  // to Q up to the TF32 rounding of the update, and one FP32 pass already takes
+  // that to the FP32 floor, which a second FP32 pass cannot lower)
   LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
-  LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
+  if (!p.f32) LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
   // lines 7-9: G = V V^T, pivoted Cholesky with the tail-mass truncation
-  LK((gemm<double, double, double, double>(p, u, mat(u.V, dim_const(0), p.ldq, 1), mat(u.V, dim_const(0), 1, p.ldq),
-                                           mat(u.G, dim_const(0), p.ldg, 1), dim_dev(&st->b_t), dim_dev(&st->b_t),
-                                           dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
-  LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
-  // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 path adds a
-  // second CholQR pass (orthogonality to FP64 rounding); on the mixed paths one
-  // FP64 CholQR already leaves ~u64 * cond^2 <= ~1e-8, far below the rounding of
-  // their residual update, so Q' is written in place and only re-projected.
-  if (p.prec == RBRP_FP64) {
-    LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
-    LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
-    LK((gemm<double, double, double, double>(
-        p, u, mat(u.Y, dim_const(0), p.ldq, 1), mat(u.Y, dim_const(0), 1, p.ldq), mat(u.G, dim_const(0), p.ldg, 1),
-        dim_dev(&st->bp), dim_dev(&st->bp), dim_const(d), 1.0, 0.0, b, b, p.s_gram, st, s, 32)));
-    LK(launch_chol(u.G, p.ldg, u.Lc, p.ldlc, p.b, st, s));
-    LK(launch_trsm_rows(u.Lc, p.ldlc, nullptr, u.Y, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+  if (p.f32) {
+    // FP32 chain: Gram, filter with Lc^{-1}, Q'_V = Lc^{-1} V_perm as one
+    // product.  Q'_V is a combination of rows already projected off Q, so its
+    // component in span(Q) stays ~cond(Lc) times the FP32 floor, far below the
+    // TF32 rounding of the update; it is not projected again.
+    LK((sgemm<float, float, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0), p.ldg,
+                                  dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
+    LK(launch_filter_f32((const float*)u.G, p.ldg, u.S_t, (float*)u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+    LK((sgemm<float, float, false>(p, u, u.Lc, dim_const(0), p.ldlc, u.V, dim_const(0), p.ldq, u.Qt,
+                                   dim_dev(&st->k, p.ldq), p.ldq, dim_dev(&st->bp), dim_const(d), dim_dev(&st->bp), b,
+                                   d, b, 1.0, 0.0, s, u.perm)));
   } else {
-    LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
-    LK(cgs_pass(p, u, u.Qt, dim_dev(&st->bp), s, dim_dev(&st->k, p.ldq)));
+    LK((sgemm<double, double, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0),
+                                    p.ldg, dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
+    LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+    // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 path
+    // adds a second CholQR pass (orthogonality to FP64 rounding); on the mixed
+    // paths one FP64 CholQR already leaves ~u64 * cond^2 <= ~1e-8, far below
+    // the rounding of their residual update, so Q' is written in place and only
+    // re-projected.
+    if (p.prec == RBRP_FP64) {
+      LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
+      LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
+      LK((sgemm<double, double, true>(p, u, u.Y, dim_const(0), p.ldq, u.Y, dim_const(0), p.ldq, u.G, dim_const(0),
+                                      p.ldg, dim_dev(&st->bp), dim_dev(&st->bp), dim_const(d), b, b, d, 1.0, 0.0, s)));
+      LK(launch_chol(u.G, p.ldg, u.Lc, p.ldlc, p.b, st, s));
+      LK(launch_trsm_rows(u.Lc, p.ldlc, nullptr, u.Y, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+    } else {
+      LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Qt, dim_dev(&st->k, p.ldq), p.ldq, d, p.b, st, s));
+      LK(cgs_pass(p, u, u.Qt, dim_dev(&st->bp), s, dim_dev(&st->k, p.ldq)));
+    }
   }
   // lines 12 and 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
   if (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) {
     const int split = (p.prec == RBRP_TF32X3);
-    LK(launch_qp_lowp(u.Qt, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
+    LK(launch_qp_lowp(u.Qt, !p.f32, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
     LK(timed(g_prof.upd, s, [&] {
       return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, (float*)u.L,
                                 p.ldl, u.mark, u.dvec, u.part, st, (int)p.ldpt, split, s);
@@ -443,6 +510,7 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   CK(launch_init_norms(X, x_is_fp64, n, d, ldx, u.R, p.r64, p.ldr, u.dvec, u.mark, u.part, p.nparts, st, s));
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
   CK(launch_sample_clear(u.samp2, n, s));
+  CK(cudaMemsetAsync(u.cnt, 0, (size_t)kSgemmCounters * 4, s));
   // Alg. 2 lines 3-16: blocks are queued in groups and the State is read back
   // after each group.  The group size is the number of blocks still expected,
   // extrapolated from the observed per-block decay of ||d||_1 (or of the rank

@@ -60,6 +60,30 @@ struct GemmArgs {
   const State* st;      // kernels return at once when st->done (if non-null)
 };
 
+// C[M x N] = alpha * A B^T (or A B) + beta * C for the small products of the
+// per-block chain (k_sgemm.cu).  A is M x K with K contiguous; B is N x K with
+// K contiguous (C = A B^T) or K x N with N contiguous (C = A B).  Element type
+// per launch (FP32 or FP64); leading dimensions multiples of 4 and bases
+// 16-byte aligned.
+struct SgemmArgs {
+  const void* A;
+  DimRef a_off;
+  long long lda;
+  const void* B;
+  DimRef b_off;
+  long long ldb;
+  void* C;
+  DimRef c_off;
+  long long ldc;
+  DimRef M, N, K;
+  double alpha, beta;
+  void* partial;      // split-K partial tiles (accumulation type)
+  unsigned* cnt;      // one arrival counter per output tile, zero between launches
+  const int* b_rows;  // C = A B only: row r of B is row b_rows[r] of the array (null: r)
+  int kc;             // K per split, a multiple of 32
+  const State* st;    // kernels return at once when st->done (if non-null)
+};
+
 // ---------------------------------------------------------------- Philox4x64-10
 // Salmon et al. (SC'11): two 64x64->128 multiplies per round, Weyl key bump.
 __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
@@ -129,20 +153,26 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
                            unsigned long long problem, void* scratch, long long* S_t, State* st, cudaStream_t s);
 cudaError_t launch_sample_clear(void* scratch, long long n, cudaStream_t s);
 size_t sample2_scratch_bytes(long long n);
-cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t,
-                          double* V, long long ldv, long long d, int b, const State* st, cudaStream_t s);
+cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t, void* V, int v_is_fp64,
+                          long long ldv, long long d, int b, const State* st, cudaStream_t s);
 template <typename TA, typename TB, typename TC, typename TACC>
 cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, int tile, cudaStream_t s);
 cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
                           int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
+// FP32 filter (plain TF32 path): as launch_filter on an FP32 Gram matrix, but
+// writes Linv = Lc^{-1} (b' x b', FP32, lower triangular, leading dimension
+// ldl) instead of Lc.
+cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
+                              int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
                         State* st, cudaStream_t s);
 cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V,
                              long long ldv, double* Y, DimRef y_off, long long ldy, long long d, int b,
                              const State* st, cudaStream_t s);
-// FP32 copies of the new basis rows Q' (and, when Qp_lo is set, the TF32 hi/lo split).
-cudaError_t launch_qp_lowp(const double* Qt, long long ldq, float* Qp, float* Qp_lo, long long ldp, float* QpT,
-                           float* QpT_lo, long long ldpt, long long d, int b, const State* st, cudaStream_t s);
+// FP32 copies of the new basis rows Q' from Qt (FP64 or FP32; with Qp_lo set, the TF32 hi/lo split).
+cudaError_t launch_qp_lowp(const void* Qt, int q_is_fp64, long long ldq, float* Qp, float* Qp_lo, long long ldp,
+                           float* QpT, float* QpT_lo, long long ldpt, long long d, int b, const State* st,
+                           cudaStream_t s);
 cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d,
                               const int* mark, double* dvec, double* partials, int nparts,
                               const State* st, cudaStream_t s);
@@ -160,6 +190,16 @@ cudaError_t launch_trsm_cols(T* W, long long ldw, long long n, long long j0, int
                              long long ld1, cudaStream_t s);
 cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long long ldw32, long long n,
                             long long k, const long long* skel, cudaStream_t s);
+
+// Small products (k_sgemm.cu).  TS: element type in memory.  TACC = float:
+// FP32 products, 64 x 64 tiles; double: FP64 products, 32 x 32 tiles.  BKC
+// selects C = A B^T.
+template <typename TS, typename TACC, bool BKC>
+cudaError_t launch_sgemm(const SgemmArgs& g, long long Mmax, long long Nmax, int splits, cudaStream_t s);
+int sgemm_tile(int acc_fp64);
+void sgemm_splits(long long Mmax, long long Nmax, long long Kmax, int tile, long long target, int* splits,
+                  int* kc);
+constexpr int kSgemmCounters = 4096;
 
 // tcgen05 fused residual update (k_update_tc.cu): per 128-row tile,
 // Lhat = R Q'^T (TF32 in, FP32 accumulate in TMEM), R -= Lhat Q', d_i = ||R_i||^2,
