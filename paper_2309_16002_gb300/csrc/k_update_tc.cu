@@ -33,20 +33,27 @@
 namespace rbrp {
 namespace tc {
 
-constexpr int BM = 128;           // rows per tile (MMA M)
+constexpr int BM = 128;           // MMA M (TMEM lanes)
+constexpr int ROWS = 64;          // rows of R per CTA; MMA rows ROWS..BM-1 are don't-care
 constexpr int BK1 = 32;           // FP32 elements per 128-byte swizzle row
 constexpr int NB2 = 32;           // d-columns per GEMM-2 chunk (MMA N)
-constexpr int S1 = 3;             // GEMM-1 pipeline stages
-constexpr int S3 = 3;             // GEMM-2 / epilogue stages
 constexpr int kThreads = 192;
 
+// A tile holds ROWS rows of R, half the MMA's M: every CTA's share of R is
+// read twice (GEMM 1, then the subtraction), and with 64-row tiles the data
+// between the two reads of all resident CTAs stays well inside L2, so the
+// second read does not go back to HBM.  An MMA reads BM rows of A; rows
+// ROWS..BM-1 come from whatever shared memory follows the chunk (the next
+// buffer of the ring) and only feed accumulator rows nobody reads.
 template <int BMAX, bool SPLIT>
 struct Cfg {
+  static constexpr int S1 = (BMAX <= 64 && !SPLIT) ? 4 : 3;  // GEMM-1 stages
+  static constexpr int S3 = S1;                              // GEMM-2 / epilogue stages
   static constexpr int NOP = SPLIT ? 2 : 1;            // hi (and lo) copies of an operand
-  static constexpr int A1 = BM * BK1 * 4;              // one R chunk (16 KB)
+  static constexpr int A1 = ROWS * BK1 * 4;            // one R chunk (8 KB)
   static constexpr int B1 = BMAX * BK1 * 4;            // one Q' chunk
   static constexpr int ST1 = NOP * (A1 + B1);          // [A hi][B hi]([A lo][B lo])
-  static constexpr int R3 = BM * NB2 * 4;              // one R chunk for the subtraction (16 KB)
+  static constexpr int R3 = ROWS * NB2 * 4;            // one R chunk for the subtraction (8 KB)
   static constexpr int B2A = NB2 * 128;                // one 32-wide K atom of the GEMM-2 B tile
   static constexpr int B2 = (BMAX / 32) * B2A;
   static constexpr int ST3 = R3 + NOP * B2;
@@ -54,6 +61,8 @@ struct Cfg {
   static constexpr int A2A = BM * 128;                 // one 32-wide K atom of Lhat
   static constexpr int A2 = (BMAX / 32) * A2A;
   static constexpr int BAR_OFF = P + NOP * A2;
+  // the BM-row A reads of GEMM 1 (last stage, lo copy) end inside the Lhat buffers
+  static_assert((S1 - 1) * ST1 + (NOP - 1) * (A1 + B1) + BM * BK1 * 4 <= P + NOP * A2, "A over-read");
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
   static constexpr uint32_t D2COL = BMAX;              // D2 double buffer after D1
@@ -70,6 +79,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
                   long long d, const int* __restrict__ mark, double* __restrict__ dvec,
                   double* __restrict__ partials, State* st) {
   using C = Cfg<BMAX, SPLIT>;
+  constexpr int S1 = C::S1, S3 = C::S3;
   if (st->done) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -94,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
   __shared__ double s_red[4];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long row0 = (long long)blockIdx.x * BM;
+  const long long row0 = (long long)blockIdx.x * ROWS;
   const long long kcol = st->k;
   const int bp = (int)st->bp;
   const int N1 = (int)st->bp_pad;
@@ -227,7 +237,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     const int r = 32 * q + lane;
     const int et = threadIdx.x - 64;
     const long long row = row0 + r;
-    const bool in = row < n;
+    const bool own = r < ROWS;  // warps with q >= 2 own no row of R
+    const bool in = own && row < n;
     const bool marked = in && (mark[row] == tno);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const uint64_t drop = l2_policy_evict_first();
@@ -237,6 +248,10 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
         const int s = kc % S1;
         const uint32_t ph = (uint32_t)(kc / S1) & 1u;
         if (!mbar_wait(full1(s), ph, abort)) break;
+        if (!own) {
+          mbar_arrive(conv1(s));
+          continue;
+        }
         uint8_t* a = smem + s * C::ST1 + (r >> 3) * 1024 + (r & 7) * 128;
         uint8_t* alo = smem + s * C::ST1 + C::A1 + C::B1 + (r >> 3) * 1024 + (r & 7) * 128;
 #pragma unroll
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     double nrm = 0.0;
     if (mbar_wait(d1_full, 0, abort)) {
       tc_after();
-      for (int cb = 0; cb * 32 < N1; ++cb) {
+      for (int cb = 0; own && cb * 32 < N1; ++cb) {
         uint32_t v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)(cb * 32), v);
         tmem_wait_ld();
@@ -290,12 +305,14 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       if (!mbar_wait(d2_full(buf), bph, abort)) break;
       tc_after();
       uint32_t u[32];
-      tmem_ld32(tmem + lane_base + C::D2COL + (uint32_t)(buf * NB2), u);
-      tmem_wait_ld();
+      if (own) {
+        tmem_ld32(tmem + lane_base + C::D2COL + (uint32_t)(buf * NB2), u);
+        tmem_wait_ld();
+      }
       uint8_t* rrow = smem + s * C::ST3;
       float part = 0.f;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
+      for (int ch = 0; ch < 8 && own; ++ch) {
         float4* p = (float4*)(rrow + swz(r, ch));
         float4 x = *p;
         x.x -= __uint_as_float(u[4 * ch]);
@@ -333,7 +350,10 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     if (lane == 0) s_red[q] = t;
     mbar_arrive(red_bar);
     if (et == 0) {
-      if (mbar_wait(red_bar, 0, abort)) partials[blockIdx.x] = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
+      if (mbar_wait(red_bar, 0, abort)) {
+        partials[2 * blockIdx.x] = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
+        partials[2 * blockIdx.x + 1] = 0.0;
+      }
       tma_wait_all0();
     }
   }
@@ -352,6 +372,392 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     tc_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
+}
+
+// ------------------------------------------------------------------ persistent form
+// Plain TF32, b'_pad <= 64.  One CTA per SM walks 128-row tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; GEMM 1 of tile t+1 streams R from HBM through
+// ring 1 while GEMM 2 of tile t re-reads R (mostly from L2) through ring 3.
+//
+// On sm_103a one tcgen05.mma of kind::tf32 (K = 8) occupies the SM's tensor
+// pipe for ~100 cycles up to N = 128 and reaches the full rate only at large N,
+// so the kernel is built to issue few, wide MMAs: all 128 rows of M are real
+// rows; GEMM 2 runs as 128-column chunks (N = 128) with its A operand (Lhat)
+// read straight from the GEMM-1 accumulator in tensor memory; the epilogue
+// then walks each chunk in 32-column pieces through its own shared-memory ring.
+// Loads take 1.5-2.5 us under this traffic; the rings are sized for that.
+// Roles: warp 0 loads ring 1, warp 1 owns TMEM and issues GEMM 1, warp 2 loads
+// the R pieces of ring 3, warp 3 issues GEMM 2, warps 4-7 (one TMEM lane
+// quarter each, thread <-> row) are the epilogue, warp 8 stores finished R
+// pieces, warp 9 loads the Q'^T chunks.  D1 (Lhat) and D2 are double-buffered.
+constexpr int PROWS = 128;        // rows of R per tile
+constexpr int PNB = 128;          // columns per GEMM-2 chunk (MMA N)
+constexpr int PPC = PNB / NB2;    // 32-column epilogue pieces per chunk
+constexpr int PS1 = 4;            // ring-1 stages (R chunk + Q' chunk)
+constexpr int PS3 = 4;            // ring-3 R stages: load, epilogue, store
+constexpr int PSB = 2;            // Q'^T chunk stages: load, MMA
+constexpr int kPThreads = 320;
+
+template <int BMAX>
+struct PCfg {
+  static constexpr int A1 = PROWS * BK1 * 4;          // 16 KB of R
+  static constexpr int B1 = BMAX * BK1 * 4;           // Q' chunk
+  static constexpr int ST1 = A1 + B1;
+  static constexpr int R3 = PROWS * NB2 * 4;          // 16 KB of R
+  static constexpr int B2A = PNB * 128;               // one 32-wide K atom of a Q'^T chunk (16 KB)
+  static constexpr int B2 = (BMAX / 32) * B2A;
+  static constexpr int OFF3 = PS1 * ST1;
+  static constexpr int OFFB = OFF3 + PS3 * R3;
+  static constexpr int BAR_OFF = OFFB + PSB * B2;
+  static constexpr int SMEM = BAR_OFF + 512 + 1024;
+  static constexpr uint32_t D2COL = 2 * BMAX;          // D1 x2, then D2 x2 (PNB columns each)
+  static constexpr uint32_t TMEM_COLS = (2 * BMAX + 2 * PNB <= 256) ? 256 : 512;
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+template <int BMAX>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
+                   const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
+                   long long d, const int* __restrict__ mark, double* __restrict__ dvec,
+                   double* __restrict__ partials, State* st) {
+  using C = PCfg<BMAX>;
+  if (st->done) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sb = smem_u32(smem);
+  const uint32_t sBar = sb + C::BAR_OFF;
+  auto full1 = [&](int s) { return sBar + 8u * s; };
+  auto empty1 = [&](int s) { return sBar + 8u * (PS1 + s); };
+  auto full3 = [&](int s) { return sBar + 8u * (2 * PS1 + s); };
+  auto empty3 = [&](int s) { return sBar + 8u * (2 * PS1 + PS3 + s); };
+  auto epi_done = [&](int s) { return sBar + 8u * (2 * PS1 + 2 * PS3 + s); };
+  auto fullb = [&](int s) { return sBar + 8u * (2 * PS1 + 3 * PS3 + s); };
+  auto emptyb = [&](int s) { return sBar + 8u * (2 * PS1 + 3 * PS3 + PSB + s); };
+  const uint32_t x0 = sBar + 8u * (2 * PS1 + 3 * PS3 + 2 * PSB);
+  auto d1_full = [&](int b) { return x0 + 8u * b; };
+  auto d1_empty = [&](int b) { return x0 + 16u + 8u * b; };
+  auto d2_full = [&](int b) { return x0 + 32u + 8u * b; };
+  auto d2_empty = [&](int b) { return x0 + 48u + 8u * b; };
+  uint32_t* tmem_slot = (uint32_t*)(smem + (x0 + 64u - sb));
+
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long kcol = st->k;
+  const int bp = (int)st->bp;
+  const int N1 = (int)st->bp_pad;
+  const int tno = (int)(st->t + 1);
+  const int nK1 = (int)((d + BK1 - 1) / BK1);  // 32-column chunks of GEMM 1 (and epilogue pieces)
+  const int nJ = (int)((d + PNB - 1) / PNB);   // GEMM-2 chunks
+  const long long ntiles = (n + PROWS - 1) / PROWS;
+  // GEMM 2 walks its chunks from the last (the most recently read columns
+  // first); a chunk j covers pieces 4j .. min(4j + 4, nK1) - 1.
+  auto npieces = [&](int j) { const int r = nK1 - PPC * j; return r < PPC ? r : PPC; };
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < PS1; ++s) {
+      mbar_init(full1(s), 1);
+      mbar_init(empty1(s), 1);
+    }
+    for (int s = 0; s < PS3; ++s) {
+      mbar_init(full3(s), 1);
+      mbar_init(empty3(s), 1);
+      mbar_init(epi_done(s), 128);
+    }
+    for (int s = 0; s < PSB; ++s) {
+      mbar_init(fullb(s), 1);
+      mbar_init(emptyb(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(d1_full(b), 1);
+      mbar_init(d1_empty(b), 129);  // the epilogue (128) and the last GEMM-2 commit of the tile
+      mbar_init(d2_full(b), 1);
+      mbar_init(d2_empty(b), 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+  volatile int* abort = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- ring 1: R and Q' chunks for GEMM 1 (R asked to stay in L2)
+    if (lane == 0) {
+      const uint64_t keep = l2_policy_evict_last();
+      uint32_t g = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int kc = 0; kc < nK1; ++kc, ++g) {
+          const int s = (int)(g % PS1);
+          if (!mbar_wait(empty1(s), ((g / PS1) & 1u) ^ 1u, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full1(s), (uint32_t)(C::A1 + C::B1));
+          const uint32_t base = sb + s * C::ST1;
+          tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)(tile * PROWS), keep);
+          tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- GEMM 1: D1[it & 1] = R_tile Q'^T
+    if (lane == 0) {
+      const uint32_t id1 = idesc_tf32(BM, N1);
+      uint32_t g = 0, it = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (!mbar_wait(d1_empty(buf), ((it >> 1) & 1u) ^ 1u, abort)) break;
+        tc_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * BMAX);
+        for (int kc = 0; kc < nK1; ++kc, ++g) {
+          const int s = (int)(g % PS1);
+          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t a = sb + s * C::ST1, b = a + C::A1;
+#pragma unroll
+          for (int kk = 0; kk < BK1 / 8; ++kk)
+            mma_tf32(dt, sdesc(a + kk * 32), sdesc(b + kk * 32), id1, (kc | kk) != 0 ? 1u : 0u);
+          mma_commit(empty1(s));
+        }
+        if (!ok) break;
+        mma_commit(d1_full(buf));
+      }
+    }
+  } else if (warp == 2) {
+    // ---------------- ring 3: R pieces of GEMM 2 (second read), for the epilogue
+    if (lane == 0) {
+      const uint64_t drop = l2_policy_evict_first();
+      uint32_t g = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int jj = 0; jj < nJ && ok; ++jj) {
+          const int j = nJ - 1 - jj;
+          for (int pc = 0; pc < npieces(j); ++pc, ++g) {
+            const int s = (int)(g % PS3);
+            if (!mbar_wait(empty3(s), ((g / PS3) & 1u) ^ 1u, abort)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full3(s), (uint32_t)C::R3);
+            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, &tmR, full3(s), (PPC * j + pc) * NB2, (int)(tile * PROWS),
+                             drop);
+          }
+        }
+      }
+    }
+  } else if (warp == 9) {
+    // ---------------- Q'^T chunks of GEMM 2, for the MMA
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int jj = 0; jj < nJ; ++jj, ++g) {
+          const int j = nJ - 1 - jj;
+          const int s = (int)(g % PSB);
+          if (!mbar_wait(emptyb(s), ((g / PSB) & 1u) ^ 1u, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(fullb(s), (uint32_t)C::B2);
+          const uint32_t base = sb + C::OFFB + s * C::B2;
+#pragma unroll
+          for (int a = 0; a < BMAX / 32; ++a) tma_load_2d(base + a * C::B2A, &tmQT, fullb(s), a * 32, j * PNB);
+        }
+      }
+    }
+  } else if (warp == 3) {
+    // ---------------- GEMM 2: D2[g & 1] = Lhat Q'(:, chunk), Lhat = D1[it & 1] in TMEM
+    if (lane == 0) {
+      const uint32_t id2 = idesc_tf32(BM, PNB);
+      const int nk2 = N1 / 8;
+      uint32_t g = 0, it = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        const int dbuf = it & 1;
+        if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort)) break;
+        tc_after();
+        const uint32_t a1 = tmem + (uint32_t)(dbuf * BMAX);
+        for (int jj = 0; jj < nJ; ++jj, ++g) {
+          const int s = (int)(g % PSB);
+          const int buf = g & 1;
+          if (!mbar_wait(fullb(s), (g / PSB) & 1u, abort) || !mbar_wait(d2_empty(buf), ((g >> 1) & 1u) ^ 1u, abort)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t dt = tmem + C::D2COL + (uint32_t)(buf * PNB);
+          const uint32_t b2 = sb + C::OFFB + s * C::B2;
+          for (int q = 0; q < nk2; ++q) {
+            const int a = q >> 2, kk = q & 3;
+            mma_tf32_ta(dt, a1 + (uint32_t)(q * 8), sdesc(b2 + a * C::B2A + kk * 32), id2, q != 0 ? 1u : 0u);
+          }
+          mma_commit(emptyb(s));
+          mma_commit(d2_full(buf));
+        }
+        if (!ok) break;
+        mma_commit(d1_empty(dbuf));  // Lhat of this tile is no longer read
+      }
+    }
+  } else if (warp >= 4 && warp <= 7) {
+    // ---------------- epilogue: TMEM lane quarter q = warp & 3, thread <-> row
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    uint32_t g = 0, gj = 0, it = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+      const long long row = tile * PROWS + r;
+      const bool in = row < n;
+      const bool marked = in && (mark[row] == tno);
+      // Lhat: TMEM -> registers -> L (GEMM 2 reads it from TMEM itself)
+      const int dbuf = it & 1;
+      if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort)) break;
+      tc_after();
+      uint32_t v[BMAX];
+      tmem_ld32(tmem + lane_base + (uint32_t)(dbuf * BMAX), *(uint32_t(*)[32])&v[0]);
+      if (BMAX > 32) tmem_ld32(tmem + lane_base + (uint32_t)(dbuf * BMAX) + 32u, *(uint32_t(*)[32])&v[32 % BMAX]);
+      tmem_wait_ld();
+      tc_before();
+      mbar_arrive(d1_empty(dbuf));
+      if (in) {
+        float* lrow = L + row * ldl + kcol;
+#pragma unroll
+        for (int jx = 0; jx < BMAX; ++jx)
+          if (jx < bp) lrow[jx] = __uint_as_float(v[jx]);
+      }
+      // GEMM 2 chunks, 32-column pieces: R -= Lhat Q', row norms, accepted rows zeroed
+      float nrm = 0.f;  // FP32: the residual itself carries TF32 rounding
+      for (int jj = 0; jj < nJ && ok; ++jj, ++gj) {
+        const int j = nJ - 1 - jj;
+        const int b2 = gj & 1;
+        if (!mbar_wait(d2_full(b2), (gj >> 1) & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        tc_after();
+        for (int pc = 0; pc < npieces(j); ++pc, ++g) {
+          const int s = (int)(g % PS3);
+          if (!mbar_wait(full3(s), (g / PS3) & 1u, abort)) {
+            ok = false;
+            break;
+          }
+          uint32_t u[32];
+          tmem_ld32(tmem + lane_base + C::D2COL + (uint32_t)(b2 * PNB + pc * NB2), u);
+          tmem_wait_ld();
+          uint8_t* rrow = smem + C::OFF3 + s * C::R3;
+          // all loads first, then the arithmetic, then all stores
+          float4 x[8];
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) x[ch] = *(const float4*)(rrow + swz(r, ch));
+          float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            x[ch].x -= __uint_as_float(u[4 * ch]);
+            x[ch].y -= __uint_as_float(u[4 * ch + 1]);
+            x[ch].z -= __uint_as_float(u[4 * ch + 2]);
+            x[ch].w -= __uint_as_float(u[4 * ch + 3]);
+            if (marked) x[ch] = make_float4(0.f, 0.f, 0.f, 0.f);
+            p0 = fmaf(x[ch].x, x[ch].x, p0);
+            p1 = fmaf(x[ch].y, x[ch].y, p1);
+            p2 = fmaf(x[ch].z, x[ch].z, p2);
+            p3 = fmaf(x[ch].w, x[ch].w, p3);
+          }
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) *(float4*)(rrow + swz(r, ch)) = x[ch];
+          nrm += (p0 + p1) + (p2 + p3);
+          fence_async_smem();
+          mbar_arrive(epi_done(s));
+        }
+        tc_before();
+        mbar_arrive(d2_empty(b2));
+      }
+      if (!ok) break;
+      if (in) dvec[row] = marked ? 0.0 : (double)nrm;
+      double t = in ? (double)nrm : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) partials[4 * tile + q] = t;
+    }
+  } else if (warp == 8) {
+    // ---------------- stores of finished R pieces; a stage is released once its store has read it
+    if (lane == 0) {
+      const uint64_t drop = l2_policy_evict_first();
+      uint32_t g = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int jj = 0; jj < nJ && ok; ++jj) {
+          const int j = nJ - 1 - jj;
+          for (int pc = 0; pc < npieces(j); ++pc, ++g) {
+            const int s = (int)(g % PS3);
+            if (!mbar_wait(epi_done(s), (g / PS3) & 1u, abort)) {
+              ok = false;
+              break;
+            }
+            tma_store_2d_hint(&tmR, sb + C::OFF3 + s * C::R3, (PPC * j + pc) * NB2, (int)(tile * PROWS), drop);
+            tma_commit();
+            tma_wait_read<0>();
+            mbar_arrive(empty3(s));
+          }
+        }
+      }
+      tma_wait_all0();
+    }
+  }
+
+  tc_before();
+  __syncthreads();
+  if (s_abort) {
+    for (int i = 0; i < 64; ++i) __nanosleep(1000);
+    if (threadIdx.x == 0) {
+      st->status = RBRP_ETIMEOUT;
+      st->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
+template <int BMAX>
+cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long ldp,
+                        const float* QpT, long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
+                        double* partials, const State* st, cudaStream_t s) {
+  using C = PCfg<BMAX>;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static unsigned long long attr_set = 0;  // one bit per device
+  if (dev >= 64 || !(attr_set >> dev & 1ULL)) {
+    e = cudaFuncSetAttribute(k_update_tf32p<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_set |= 1ULL << dev;
+  }
+  CUtensorMap mR, mQ, mQT;
+  if (!make_map(&mR, R, d, n, ldr * 4, 32, PROWS)) return cudaErrorInvalidValue;
+  if (!make_map(&mQ, Qp, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+  if (!make_map(&mQT, QpT, ldpt, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (n + PROWS - 1) / PROWS;
+  const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+  k_update_tf32p<BMAX><<<grid, kPThreads, C::SMEM, s>>>(mR, mQ, mQT, L, ldl, n, d, mark, dvec, partials,
+                                                        const_cast<State*>(st));
+  return counted(cudaGetLastError());
 }
 
 // ------------------------------------------------------------------ host side
@@ -400,7 +806,7 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
     }
   }
   CUtensorMap mR, mQ, mQlo, mQT, mQTlo;
-  if (!make_map(&mR, R, d, n, ldr * 4, 32, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mR, R, d, n, ldr * 4, 32, ROWS)) return cudaErrorInvalidValue;
   if (!make_map(&mQ, Qp, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, ldpt, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
   if (SPLIT) {
@@ -410,7 +816,7 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
     mQlo = mQ;
     mQTlo = mQT;
   }
-  const unsigned grid = (unsigned)((n + BM - 1) / BM);
+  const unsigned grid = (unsigned)((n + ROWS - 1) / ROWS);
   k_update_tf32<BMAX, SPLIT><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark, dvec,
                                                              partials, const_cast<State*>(st));
   return counted(cudaGetLastError());
@@ -418,7 +824,12 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
 
 }  // namespace tc
 
-int update_tf32_parts(long long n) { return (int)((n + tc::BM - 1) / tc::BM); }
+// Partial sums the update leaves for launch_finalize_block: 4 per 128-row tile
+// (persistent form) or 2 per 64-row tile.
+int update_tf32_parts(long long n, int bmax, int split) {
+  if (!split && bmax <= 64) return 4 * (int)((n + tc::PROWS - 1) / tc::PROWS);
+  return 2 * (int)((n + tc::ROWS - 1) / tc::ROWS);
+}
 
 int update_tf32_max_block(int split) { return split ? 64 : 128; }
 
@@ -432,8 +843,10 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
     if (bmax <= 64) return tc::launch_cfg<64, true>(RBRP_TC_ARGS);
     return cudaErrorInvalidValue;
   }
-  if (bmax <= 32) return tc::launch_cfg<32, false>(RBRP_TC_ARGS);
-  if (bmax <= 64) return tc::launch_cfg<64, false>(RBRP_TC_ARGS);
+  if (bmax <= 32)
+    return tc::launch_pcfg<32>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+  if (bmax <= 64)
+    return tc::launch_pcfg<64>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
   if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
 #undef RBRP_TC_ARGS
   return cudaErrorInvalidValue;

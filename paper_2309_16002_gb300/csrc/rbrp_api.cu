@@ -162,7 +162,9 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->off_Q = take((size_t)kc * p->ldq * 8 + (size_t)kMaxBlock * p->ldq * 8);
   p->off_d = take((size_t)n * 8);
   p->off_mark = take((size_t)n * 4);
-  p->off_part = take((size_t)std::max<long long>(std::max(p->nparts, 1024), update_tf32_parts(n)) * 8);
+  p->off_part = take((size_t)std::max<long long>(std::max(p->nparts, 1024),
+                                                  std::max(update_tf32_parts(n, 64, 0), update_tf32_parts(n, 128, 0))) *
+                     8);
   p->off_state = take(sizeof(State));
   p->off_St = take((size_t)kMaxBlock * 8);
   p->off_ca = take(sample_scratch_pairs(n, p->b) * 16);
@@ -420,7 +422,7 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
       return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, (float*)u.L,
                                 p.ldl, u.mark, u.dvec, u.part, st, (int)p.ldpt, split, s);
     }));
-    LK(launch_finalize_block(u.part, update_tf32_parts(n), st, s));
+    LK(launch_finalize_block(u.part, update_tf32_parts(n, (int)p.ldpt, split), st, s));
     return cudaSuccess;
   }
   LK(timed(g_prof.upd, s, [&] { return enqueue_update_simt(p, u, s); }));

@@ -209,7 +209,7 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
                                const float* Qp_lo, long long ldp, const float* QpT, const float* QpT_lo,
                                long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
                                double* partials, const State* st, int bmax, int split, cudaStream_t s);
-int update_tf32_parts(long long n);
+int update_tf32_parts(long long n, int bmax, int split);
 int update_tf32_max_block(int split);
 
 // Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k) from
