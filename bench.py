@@ -26,6 +26,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ID time-to-tol (ms) at 1e5×1e3, rel err ≤1e-4; % of HBM/TC roofline"
+# DRAM bytes (read + write) per launch of the persistent tensor-core update, per
+# row of R, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
+# of the 40000 x 1000 zipf_gmm workload at b = 64 (profiles/k_update_tf32p_*.md).
+UPD_TRAFFIC_PER_ROW = (254.376192e6 + 90.944256e6) / 40000
+UPD_TRAFFIC_D = 1000
 FALLBACK_HBM = 6800.0
 
 
@@ -247,9 +252,14 @@ def run_ours(a):
                           "real_blocks": blocks, "GB/s": upd_gbs},
                "w_solve": {"ms_per_step": w_ms / a.steps, "TFLOP/s": (w_flops / (w_ms / 1e3) / 1e12) if w_ms else None},
                "other_ms_per_step": ms - (upd_ms + w_ms) / a.steps}
-    roofline = {"bound": "hbm", "kernel": "k_update_tf32" if a.precision.startswith("tf32") else "update_simt",
+    persistent = a.precision == "tf32" and a.block <= 64
+    kname = ("k_update_tf32p" if persistent else "k_update_tf32") if a.precision.startswith("tf32") else "update_simt"
+    traffic = UPD_TRAFFIC_PER_ROW * n if (persistent and d == UPD_TRAFFIC_D) else None
+    roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
-                "peak_kind": peak_kind, "traffic": None,
+                "peak_kind": peak_kind, "traffic": traffic,
+                "traffic_note": ("DRAM read+write bytes per launch from one ncu capture of the 40000 x 1000 "
+                                 "workload, scaled by rows" if traffic else None),
                 "bytes_per_launch": upd_bytes / max(1, blocks),
                 "note": "achieved = (2 n d s + 16 n) per block + n k s for Lhat, over CUDA-event time of all "
                         "update launches in the timed region (including no-op launches queued after the stop)"}

@@ -394,8 +394,8 @@ constexpr int PROWS = 128;        // rows of R per tile
 constexpr int PNB = 128;          // columns per GEMM-2 chunk (MMA N)
 constexpr int PPC = PNB / NB2;    // 32-column epilogue pieces per chunk
 constexpr int PS1 = 4;            // ring-1 stages (R chunk + Q' chunk)
-constexpr int PS3 = 4;            // ring-3 R stages: load, epilogue, store
-constexpr int PSB = 2;            // Q'^T chunk stages: load, MMA
+constexpr int PS3 = 6;            // ring-3 R stages: load, epilogue, store
+constexpr int PSB = 1;            // Q'^T chunk stages: load, MMA (a chunk lasts ~8 kcycles)
 constexpr int kPThreads = 320;
 
 template <int BMAX>
