@@ -188,6 +188,41 @@ rbrp_status rbrp_id_noalloc(const void *X, int x_is_fp64, int64_t n, int64_t d, 
                             double tol, const rbrp_opts *o, int64_t *skel, double *W, int64_t ldw,
                             rbrp_result *res, rbrp_stream_t stream);
 
+/*
+ * rbrp_id_batched -- P independent row IDs (Alg. 2 then Alg. 3 for each) in one
+ * persistent launch: each CTA takes whole problems from a work queue, largest
+ * first, and runs the method for one problem at a time.
+ *
+ * Problem p is X[p] (device, row-major m[p] x n[p] with leading dimension n[p],
+ * FP32, or FP64 when x_is_fp64), solved to tol with the options o (block b,
+ * tau_b, k_max, seed, sampler); its Philox problem id is p (o->problem is not
+ * used) and its skeletons are drawn exactly as rbrp_id would draw them.
+ * Precision: o->precision == RBRP_FP64 keeps the residual and every step in
+ * FP64; any other value keeps the residual, the products and the W solve in
+ * FP32 (row norms and their sums in FP64, sampling keys exact FP64);
+ * o->w_precision is not used.
+ * Limits: 1 <= m[p] <= 4096, 1 <= n[p] <= 256, 1 <= o->block <= 32; otherwise
+ * RBRP_EINVAL before anything is launched.
+ * Arguments: X, m, n, skel and W are HOST arrays of P entries (X, skel and W
+ * hold device pointers); they may be released when the call returns.
+ * Outputs (caller-owned, device): skel[p] receives k_p <= k_cap_p =
+ * min(m[p], n[p], k_max) row indices in acceptance order; W[p] (m[p] x k_cap_p
+ * FP64, leading dimension k_cap_p) receives columns 0..k_p-1 of W with the rows
+ * of S set to unit rows; k_out[p] = k_p, rel_err_sq[p] = ||d||_1 / ||d0||_1 and
+ * status[p] (RBRP_OK, RBRP_ENOTCONVERGED or RBRP_ENONFINITE) are written to the
+ * device arrays k_out, rel_err_sq and status (P entries each), valid once the
+ * stream has reached the end of the call.
+ * Workspace: device, 256-byte aligned, at least rbrp_batched_workspace_size
+ * bytes; its contents need not be initialised.
+ * Errors: RBRP_EINVAL, RBRP_EWORKSPACE, RBRP_ECUDA as for rbrp_id.
+ */
+rbrp_status rbrp_batched_workspace_size(int32_t P, const int64_t *m, const int64_t *n, const rbrp_opts *o,
+                                        size_t *bytes);
+rbrp_status rbrp_id_batched(int32_t P, const void *const *X, const int64_t *m, const int64_t *n, int x_is_fp64,
+                            double tol, const rbrp_opts *o, void *workspace, size_t ws_bytes,
+                            int64_t *const *skel, double *const *W, int64_t *k_out, double *rel_err_sq,
+                            int32_t *status, rbrp_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *rbrp_status_string(rbrp_status s);
 

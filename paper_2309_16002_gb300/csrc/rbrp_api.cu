@@ -643,6 +643,108 @@ rbrp_status rbrp_id(const void* X, int x_is_fp64, int64_t n, int64_t d, int64_t 
              (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+struct BatchPlan {
+  long long m_max, n_max, kc_max;
+  int ctas, fp64;
+  size_t off_X, off_rows, off_cols, off_order, off_skel, off_W, off_next, slot, off_slots, total;
+};
+
+rbrp_status batch_plan(int32_t P, const int64_t* m, const int64_t* n, const rbrp_opts* o, BatchPlan* bp) {
+  if (P < 0 || !o || !bp || (P > 0 && (!m || !n))) return RBRP_EINVAL;
+  if (o->block < 1 || o->block > kBatchMaxBlock || o->tau_b > 1.0) return RBRP_EINVAL;
+  if (o->precision < RBRP_FP64 || o->precision > RBRP_TF32X3) return RBRP_EINVAL;
+  if (o->sampler != RBRP_SAMPLER_RANDOM && o->sampler != RBRP_SAMPLER_GREEDY) return RBRP_EINVAL;
+  memset(bp, 0, sizeof(*bp));
+  bp->m_max = bp->n_max = bp->kc_max = 1;
+  for (int32_t p = 0; p < P; ++p) {
+    if (m[p] < 1 || m[p] > kBatchMaxRows || n[p] < 1 || n[p] > kBatchMaxCols) return RBRP_EINVAL;
+    long long kc = std::min<long long>(m[p], n[p]);
+    if (o->k_max > 0) kc = std::min<long long>(kc, o->k_max);
+    bp->m_max = std::max<long long>(bp->m_max, m[p]);
+    bp->n_max = std::max<long long>(bp->n_max, n[p]);
+    bp->kc_max = std::max<long long>(bp->kc_max, kc);
+  }
+  bp->fp64 = (o->precision == RBRP_FP64);
+  bp->ctas = std::max(1, std::min<int>(P, batched_ctas()));
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o2 = off;
+    off = (size_t)round_up((long long)(off + bytes), 256);
+    return o2;
+  };
+  bp->off_X = take((size_t)P * 8);
+  bp->off_rows = take((size_t)P * 8);
+  bp->off_cols = take((size_t)P * 8);
+  bp->off_order = take((size_t)P * 4);
+  bp->off_skel = take((size_t)P * 8);
+  bp->off_W = take((size_t)P * 8);
+  bp->off_next = take(16);
+  bp->slot = batched_slot_bytes(bp->m_max, bp->n_max, bp->kc_max, o->block, bp->fp64);
+  bp->off_slots = take((size_t)bp->ctas * bp->slot);
+  bp->total = off;
+  return RBRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rbrp_status rbrp_batched_workspace_size(int32_t P, const int64_t* m, const int64_t* n, const rbrp_opts* o,
+                                        size_t* bytes) {
+  if (!bytes) return RBRP_EINVAL;
+  BatchPlan bp;
+  rbrp_status rs = batch_plan(P, m, n, o, &bp);
+  if (rs != RBRP_OK) return rs;
+  *bytes = bp.total;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_id_batched(int32_t P, const void* const* X, const int64_t* m, const int64_t* n, int x_is_fp64,
+                            double tol, const rbrp_opts* o, void* workspace, size_t ws_bytes, int64_t* const* skel,
+                            double* const* W, int64_t* k_out, double* rel_err_sq, int32_t* status,
+                            rbrp_stream_t stream) {
+  BatchPlan bp;
+  rbrp_status rs = batch_plan(P, m, n, o, &bp);
+  if (rs != RBRP_OK) return rs;
+  if (P == 0) return RBRP_OK;
+  if (!X || !skel || !W || !k_out || !rel_err_sq || !status || !workspace) return RBRP_EINVAL;
+  if (!(tol < 1.0)) return RBRP_EINVAL;
+  for (int32_t p = 0; p < P; ++p)
+    if (!X[p] || !skel[p] || !W[p]) return RBRP_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0 || ws_bytes < bp.total) return RBRP_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)workspace;
+  std::vector<long long> rows(P), cols(P);
+  std::vector<int> order(P);
+  for (int32_t p = 0; p < P; ++p) {
+    rows[p] = m[p];
+    cols[p] = n[p];
+    order[p] = p;
+  }
+  // largest problems first, so the last problems to start are short ones
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return rows[a] * cols[a] > rows[b] * cols[b]; });
+  CK(cudaMemcpyAsync(ws + bp.off_X, X, (size_t)P * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ws + bp.off_rows, rows.data(), (size_t)P * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ws + bp.off_cols, cols.data(), (size_t)P * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ws + bp.off_order, order.data(), (size_t)P * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ws + bp.off_skel, skel, (size_t)P * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ws + bp.off_W, W, (size_t)P * 8, cudaMemcpyHostToDevice, s));
+  // (copies from pageable host memory return once the source has been read, so
+  // the vectors above may be released on return)
+  CK(launch_batched(P, (const void* const*)(ws + bp.off_X), (const long long*)(ws + bp.off_rows),
+                    (const long long*)(ws + bp.off_cols), (const int*)(ws + bp.off_order),
+                    (long long* const*)(ws + bp.off_skel), (double* const*)(ws + bp.off_W), (long long*)k_out,
+                    rel_err_sq, (int*)status, tol, o->tau_b, o->block, o->sampler == RBRP_SAMPLER_GREEDY, x_is_fp64,
+                    o->k_max, o->seed, bp.fp64, ws + bp.off_slots, bp.slot, bp.m_max, bp.n_max, bp.kc_max,
+                    (unsigned int*)(ws + bp.off_next), bp.ctas, s));
+  return RBRP_OK;
+}
+
 rbrp_status rbrp_host_workspace_size(int64_t n, int64_t d, int x_is_fp64, const rbrp_opts* o, size_t* bytes) {
   if (!bytes) return RBRP_EINVAL;
   Plan p;

@@ -221,4 +221,17 @@ cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float*
                              double* W64, long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl,
                              long long ldt, long long n, long long k, State* st, cudaStream_t s);
 
+// Batched form (k_batched.cu): one persistent launch over P small problems.
+size_t batched_slot_bytes(long long m_max, long long n_max, long long kc_max, int b, int fp64);
+int batched_ctas();
+cudaError_t launch_batched(int P, const void* const* X_dev, const long long* rows_dev, const long long* cols_dev,
+                           const int* order_dev, long long* const* skel_dev, double* const* W_dev, long long* k_out,
+                           double* err, int* status, double tau, double tau_b, int b, int greedy, int x_is_fp64,
+                           long long k_max, unsigned long long seed, int fp64, void* slots, size_t slot_bytes,
+                           long long m_max, long long n_max, long long kc_max, unsigned int* next, int ctas,
+                           cudaStream_t s);
+constexpr long long kBatchMaxRows = 4096;
+constexpr long long kBatchMaxCols = 256;
+constexpr int kBatchMaxBlock = 32;
+
 }  // namespace rbrp

@@ -27,7 +27,7 @@ RBRP_ENOTCONVERGED = 5
 
 EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_workspace_size", "rbrp_id_host",
            "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
-           "rbrp_id_noalloc"]
+           "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched"]
 
 
 class Opts(ctypes.Structure):
@@ -88,6 +88,13 @@ def load():
     L.rbrp_id_noalloc.argtypes = [vp, ctypes.c_int, i64, i64, i64, dbl, ctypes.POINTER(Opts), vp, vp, i64,
                                   ctypes.POINTER(Result), vp]
     L.rbrp_id_noalloc.restype = ctypes.c_int
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    L.rbrp_batched_workspace_size.argtypes = [ctypes.c_int32, P64, P64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    L.rbrp_batched_workspace_size.restype = ctypes.c_int
+    L.rbrp_id_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(vp), P64, P64, ctypes.c_int, dbl,
+                                  ctypes.POINTER(Opts), vp, sz, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp,
+                                  vp]
+    L.rbrp_id_batched.restype = ctypes.c_int
     L.rbrp_profile_begin.argtypes = []
     L.rbrp_profile_begin.restype = None
     L.rbrp_profile_end.argtypes = [ctypes.POINTER(Profile)]
@@ -282,3 +289,55 @@ def exported_symbols():
 
 def as_numpy(t):
     return t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)
+
+
+def rbrp_id_batched(Xs, tol, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random",
+                    stream=None):
+    """P independent row IDs in one launch (rbrp_id_batched of include/rbrp.h).
+
+    Xs: list of CUDA tensors (all FP32 or all FP64, row-major, m <= 4096 rows,
+    n <= 256 columns); problem p uses Philox problem id p.  Returns one dict per
+    problem: S (int64 CUDA tensor, acceptance order), W (m x k FP64 CUDA tensor),
+    k, rel_err_sq, status.
+    """
+    import torch
+    P = len(Xs)
+    if P == 0:
+        return []
+    dt = Xs[0].dtype
+    dev = Xs[0].device
+    for X in Xs:
+        if not X.is_cuda or X.dim() != 2 or X.dtype != dt or not X.is_contiguous():
+            raise ValueError("Xs must be contiguous 2-D CUDA tensors of one dtype")
+    opts = make_opts(block, precision, tau_b, k_max, seed, 0, sampler, "fp64")
+    m = (ctypes.c_int64 * P)(*[int(X.shape[0]) for X in Xs])
+    n = (ctypes.c_int64 * P)(*[int(X.shape[1]) for X in Xs])
+    need = ctypes.c_size_t(0)
+    st = load().rbrp_batched_workspace_size(P, m, n, ctypes.byref(opts), ctypes.byref(need))
+    _check(st, "rbrp_batched_workspace_size", allow_notconverged=False)
+    ws = torch.empty(need.value + 256, dtype=torch.uint8, device=dev)
+    wp = (ws.data_ptr() + 255) // 256 * 256
+    kcs = [k_cap(int(X.shape[0]), int(X.shape[1]), k_max) for X in Xs]
+    S = [torch.empty(kc, dtype=torch.int64, device=dev) for kc in kcs]
+    Wt = [torch.empty((int(X.shape[0]), kc), dtype=torch.float64, device=dev) for X, kc in zip(Xs, kcs)]
+    k_out = torch.empty(P, dtype=torch.int64, device=dev)
+    err = torch.empty(P, dtype=torch.float64, device=dev)
+    status = torch.empty(P, dtype=torch.int32, device=dev)
+    xp = (ctypes.c_void_p * P)(*[X.data_ptr() for X in Xs])
+    sp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in S])
+    wpp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in Wt])
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    st = load().rbrp_id_batched(P, xp, m, n, int(dt == torch.float64), float(tol), ctypes.byref(opts),
+                                ctypes.c_void_p(wp), need.value, sp, wpp, ctypes.c_void_p(k_out.data_ptr()),
+                                ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                ctypes.c_void_p(s.cuda_stream))
+    _check(st, "rbrp_id_batched", allow_notconverged=False)
+    s.synchronize()
+    ks, es, ss = k_out.tolist(), err.tolist(), status.tolist()
+    out = []
+    for p in range(P):
+        k = int(ks[p])
+        out.append(dict(S=S[p][:k], W=Wt[p][:, :k], k=k, rel_err_sq=es[p], status=int(ss[p]),
+                        converged=(ss[p] == 0)))
+    return out
+

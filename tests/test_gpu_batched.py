@@ -1,0 +1,141 @@
+"""GPU parity of the batched entry point (rbrp_id_batched, one launch for P problems).
+
+Problem p of a batch uses Philox problem id p, so it must reproduce the single-problem
+oracle run with problem = p.  Bars, problem by problem (as in test_gpu_parity):
+  FP64  skeleton indices identical to the oracle's (or a near-tie the oracle logged) and
+        |e_gpu - e_oracle| <= 1e-10, e = ||X - W X_S||_F / ||X||_F;
+  FP32  e_gpu <= max(1.05 e_same, e_same + 1e-5) with e_same the oracle's exact error for
+        the same skeletons (W = X X_S^+), e_gpu^2 <= 1.05 tol, k <= 1.1 k_oracle + b.
+W(S, :) = I exactly in both.
+"""
+import numpy as np
+import pytest
+
+from oracle import rbrp as O
+from paper_2309_16002_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+NEAR_TIE = 1e-12
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2309_16002_gb300 import rbrp
+    rbrp.load()
+    return rbrp
+
+
+def _problems(dtype):
+    """Kernel blocks of the batched workload's kind (smaller), plus edge cases."""
+    rng = np.random.default_rng(41)
+    Xs = [WL.kernel_block(rng, m, n, dtype=np.float32).astype(dtype)
+          for m, n in [(64, 32), (200, 48), (333, 64), (97, 256), (130, 33), (600, 200)]]
+    Xs.append((rng.standard_normal((150, 3)) @ rng.standard_normal((3, 40))).astype(dtype))  # exact rank 3
+    Xs.append(np.zeros((70, 20), dtype=dtype))                                               # D0 = 0
+    Xs.append(np.repeat(rng.standard_normal((8, 30)), 12, axis=0).astype(dtype))             # duplicated rows
+    Xs.append(rng.standard_normal((20, 50)).astype(dtype))                                   # m < n
+    Xs.append(rng.standard_normal((1, 16)).astype(dtype))                                    # one row
+    Xs.append(rng.standard_normal((40, 1)).astype(dtype))                                    # one column
+    return Xs
+
+
+def _run(G, Xs, tol, **kw):
+    import torch
+    Xd = [torch.from_numpy(np.ascontiguousarray(X)).to("cuda:0") for X in Xs]
+    outs = G.rbrp_id_batched(Xd, tol, **kw)
+    for o in outs:
+        o["S"] = o["S"].cpu().numpy()
+        o["W"] = o["W"].cpu().numpy()
+    return outs
+
+
+def _e(X, S, W):
+    return float(np.sqrt(O.id_error_sq(X, S, W)))
+
+
+@pytest.mark.parametrize("tol,b", [(1e-5, 16), (1e-9, 8)])
+def test_batched_fp64_matches_oracle(G, tol, b):
+    Xs = _problems(np.float64)
+    outs = _run(G, Xs, tol, block=b, seed=7, precision="fp64")
+    for p, (X, out) in enumerate(zip(Xs, outs)):
+        ref = O.rbrp_id(X, tau=tol, b=b, seed=7, problem=p)
+        S, S_ref = out["S"].tolist(), ref["S"].tolist()
+        assert out["status"] in (0, 5), (p, out["status"])
+        if S != S_ref:
+            gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
+            assert gaps and min(gaps) < NEAR_TIE, (p, S[:10], S_ref[:10])
+            continue
+        k = len(S)
+        assert np.array_equal(out["W"][out["S"]], np.eye(k)), p
+        if k:
+            assert abs(_e(X, out["S"], out["W"]) - _e(X, ref["S"], ref["W"])) <= 1e-10, p
+        assert abs(out["rel_err_sq"] - ref["rel_err_sq"]) <= 1e-10 * max(1.0, ref["rel_err_sq"]) + 1e-13, p
+
+
+@pytest.mark.parametrize("tol,b", [(1e-5, 16), (1e-4, 32)])
+def test_batched_fp32_bar(G, tol, b):
+    Xs = _problems(np.float32)
+    outs = _run(G, Xs, tol, block=b, seed=3, precision="fp32")
+    for p, (X, out) in enumerate(zip(Xs, outs)):
+        X64 = X.astype(np.float64)
+        k = len(out["S"])
+        assert out["status"] in (0, 5), (p, out["status"])
+        assert np.array_equal(out["W"][out["S"]], np.eye(k)), p
+        assert len(set(out["S"].tolist())) == k, p
+        if not np.any(X64):
+            assert k == 0
+            continue
+        ref = O.rbrp_id(X64, tau=tol, b=b, seed=3, problem=p)
+        e_gpu = _e(X64, out["S"], out["W"])
+        e_same = float(np.sqrt(O.skeleton_error_sq(X64, out["S"])))
+        assert e_gpu <= max(1.05 * e_same, e_same + 1e-5), (p, e_gpu, e_same)
+        if out["status"] == 0:
+            assert e_gpu ** 2 <= 1.05 * tol + 1e-10, (p, e_gpu ** 2, tol)
+        assert k <= 1.1 * len(ref["S"]) + b, (p, k, len(ref["S"]))
+
+
+def test_batched_fixed_rank_and_options(G):
+    """Fixed-rank mode (tol < 0 with k_max), plain BRP (tau_b = 0) and the greedy sampler."""
+    Xs = _problems(np.float64)[:6]
+    for kw, okw in [(dict(tau_b=0.0), dict(tau_b=0.0)), (dict(sampler="greedy"), dict(sampler="greedy"))]:
+        outs = _run(G, Xs, 1e-7, block=8, seed=1, precision="fp64", **kw)
+        for p, (X, out) in enumerate(zip(Xs, outs)):
+            ref = O.rbrp_id(X, tau=1e-7, b=8, seed=1, problem=p, **okw)
+            if out["S"].tolist() != ref["S"].tolist():
+                gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
+                assert gaps and min(gaps) < NEAR_TIE, (kw, p)
+    outs = _run(G, Xs, -1.0, block=4, seed=2, precision="fp64", k_max=10)
+    for p, (X, out) in enumerate(zip(Xs, outs)):
+        ref = O.rbrp_id(X, b=4, seed=2, problem=p, k=10)
+        assert out["k"] == len(ref["S"]), p
+        if out["S"].tolist() != ref["S"].tolist():
+            gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
+            assert gaps and min(gaps) < NEAR_TIE, p
+
+
+def test_batched_same_as_single_problem_calls(G):
+    """A batch and P separate rbrp_id calls (problem id p, FP64) give the same skeletons."""
+    import torch
+    Xs = _problems(np.float64)[:5]
+    outs = _run(G, Xs, 1e-6, block=16, seed=11, precision="fp64")
+    for p, (X, out) in enumerate(zip(Xs, outs)):
+        one = G.rbrp_id(torch.from_numpy(X).to("cuda:0"), 1e-6, block=16, seed=11, problem=p, precision="fp64")
+        assert one["S"].cpu().numpy().tolist() == out["S"].tolist(), p
+
+
+def test_batched_nonfinite_and_limits(G):
+    import torch
+    X = np.ones((30, 6))
+    X[4, 1] = np.nan
+    outs = _run(G, [X, np.eye(6)], 1e-3, block=4, precision="fp64")
+    assert outs[0]["status"] == 4 and outs[1]["status"] == 0 and outs[1]["k"] == 6
+    with pytest.raises(G.RBRPError):
+        G.rbrp_id_batched([torch.zeros((10, 300), dtype=torch.float64, device="cuda:0")], 1e-3)
+    with pytest.raises(G.RBRPError):
+        G.rbrp_id_batched([torch.zeros((10, 30), dtype=torch.float64, device="cuda:0")], 1e-3, block=64)
