@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU baseline run (0: all rows)")
     ap.add_argument("--ref-rows", type=int, default=20000, help="row sample per step of the reference arm")
+    ap.add_argument("--workload", default="zipf_gmm", choices=["zipf_gmm", "kernel_blocks"],
+                    help="kernel_blocks: the batched workload (one rbrp_id_batched launch per step)")
+    ap.add_argument("--batch", type=int, default=4096, help="problems in the batched workload")
+    ap.add_argument("--single-sample", type=int, default=128,
+                    help="problems timed with one rbrp_id call each, for the per-matrix comparison")
     return ap.parse_args()
 
 
@@ -312,8 +317,72 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(a):
+    """The batched workload: P Gaussian-kernel blocks (m ~ U[64, 2048], n ~ U[32, 256], h = 0.5,
+    cubes 2 apart, FP32), tol 1e-5, b = 16, one rbrp_id_batched launch per step, against
+    per-matrix rbrp_id calls timed on a sample and scaled to P."""
+    import torch
+    from paper_2309_16002_gb300 import rbrp as G
+    from paper_2309_16002_gb300 import workloads as WL
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    G.load()
+    Xs_np = WL.kernel_blocks(P=a.batch, seed=4)
+    Xs = [torch.from_numpy(X).to(dev) for X in Xs_np]
+    tol = 1e-5 if a.tol == 1e-4 else a.tol
+    block = 16 if a.block == 64 else a.block
+    prec = "fp32" if a.precision in ("tf32", "tf32x3") else a.precision
+    B = G.Batch(Xs, block=block, seed=0, precision=prec)
+    s = torch.cuda.current_stream(dev)
+    for _ in range(a.warmup):
+        B.run(tol, s)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    G.rbrp_profile_begin()
+    ev0.record(s)
+    for _ in range(a.steps):
+        B.run(tol, s)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    prof = G.rbrp_profile_end()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    res = B.results()
+    ks = [r["k"] for r in res]
+    st = [r["status"] for r in res]
+    # per-matrix launches on a sample (each problem its own rbrp_id call, same precision and options)
+    samp = list(range(0, a.batch, max(1, a.batch // max(1, a.single_sample))))[:a.single_sample]
+    single_prec = "fp64" if prec == "fp64" else "fp32"
+    for p in samp[:4]:
+        G.rbrp_id(Xs[p], tol, block=block, seed=0, problem=p, precision=single_prec, w_precision="fp64")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for p in samp:
+        G.rbrp_id(Xs[p], tol, block=block, seed=0, problem=p, precision=single_prec, w_precision="fp64")
+    e1.record(s)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) * a.batch / len(samp)
+    elems = sum(int(X.shape[0]) * int(X.shape[1]) for X in Xs_np)
+    line = {"metric": "batched ID time (ms) for %d kernel blocks, tol %g, b %d" % (a.batch, tol, block),
+            "value": ms, "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32+f64", "fp64": "f64"}[prec], "data": "synthetic",
+            "config": {"workload": "kernel_blocks", "P": a.batch, "m": [64, 2048], "n": [32, 256], "h": 0.5,
+                       "gap": 2.0, "dtype_in": "fp32", "tol_sq_rel": tol, "block": block, "seed": 4,
+                       "elements": elems},
+            "k_mean": sum(ks) / len(ks), "k_max": max(ks), "not_converged": sum(1 for x in st if x == 5),
+            "nonfinite": sum(1 for x in st if x == 4),
+            "per_matrix_launches_ms": single_ms, "per_matrix_sample": len(samp),
+            "speedup_vs_per_matrix": single_ms / ms if ms > 0 else None,
+            "gpu_launches": prof["launches"] // max(1, a.steps)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "kernel_blocks":
+        run_batched(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

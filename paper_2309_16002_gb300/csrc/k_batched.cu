@@ -401,12 +401,12 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
     R[e] = a.x_is_fp64 ? (T)((const double*)a.X[p])[e] : (T)((const float*)a.X[p])[e];
   __syncthreads();
   for (long long i = w; i < m; i += kWarps) {
-    double s = 0.0;
+    T sl = 0;  // per lane in T (FP64 arithmetic costs ~64 cycles per warp instruction on GB300)
     for (long long c = lane; c < n; c += 32) {
-      const double x = (double)R[i * n + c];
-      s += x * x;
+      const T x = R[i * n + c];
+      sl += x * x;
     }
-    s = warp_sum(s);
+    const double s = warp_sum((double)sl);
     if (lane == 0) {
       d[i] = s;
       mark[i] = 0;
@@ -508,7 +508,7 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
           if (j == lane) mine = lh[j];
         L[(k + lane) * m + i] = mine;
       }
-      double nr = 0.0;
+      T nr = 0;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const long long c = lane + 32 * u;
@@ -521,10 +521,10 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
         }
         if (acc) v = (T)0;
         R[i * n + c] = v;
-        nr += (double)v * (double)v;
+        nr += v * v;
       }
-      nr = warp_sum(nr);
-      if (lane == 0) d[i] = acc ? 0.0 : nr;
+      const double nrd = warp_sum((double)nr);
+      if (lane == 0) d[i] = acc ? 0.0 : nrd;
     }
     __syncthreads();
     double dp = 0.0;

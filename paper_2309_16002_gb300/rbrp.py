@@ -291,6 +291,62 @@ def as_numpy(t):
     return t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)
 
 
+class Batch:
+    """Preallocated outputs and workspace for repeated rbrp_id_batched calls on one list of problems."""
+
+    def __init__(self, Xs, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random"):
+        import torch
+        self.P = len(Xs)
+        if self.P == 0:
+            raise ValueError("empty batch")
+        dt = Xs[0].dtype
+        dev = Xs[0].device
+        for X in Xs:
+            if not X.is_cuda or X.dim() != 2 or X.dtype != dt or not X.is_contiguous():
+                raise ValueError("Xs must be contiguous 2-D CUDA tensors of one dtype")
+        self.Xs = Xs
+        self.fp64_in = int(dt == torch.float64)
+        self.opts = make_opts(block, precision, tau_b, k_max, seed, 0, sampler, "fp64")
+        P = self.P
+        self.m = (ctypes.c_int64 * P)(*[int(X.shape[0]) for X in Xs])
+        self.n = (ctypes.c_int64 * P)(*[int(X.shape[1]) for X in Xs])
+        need = ctypes.c_size_t(0)
+        st = load().rbrp_batched_workspace_size(P, self.m, self.n, ctypes.byref(self.opts), ctypes.byref(need))
+        _check(st, "rbrp_batched_workspace_size", allow_notconverged=False)
+        self.need = need.value
+        self.ws = torch.empty(self.need + 256, dtype=torch.uint8, device=dev)
+        self.wp = (self.ws.data_ptr() + 255) // 256 * 256
+        kcs = [k_cap(int(X.shape[0]), int(X.shape[1]), k_max) for X in Xs]
+        self.S = [torch.empty(kc, dtype=torch.int64, device=dev) for kc in kcs]
+        self.W = [torch.empty((int(X.shape[0]), kc), dtype=torch.float64, device=dev) for X, kc in zip(Xs, kcs)]
+        self.k_out = torch.empty(P, dtype=torch.int64, device=dev)
+        self.err = torch.empty(P, dtype=torch.float64, device=dev)
+        self.status = torch.empty(P, dtype=torch.int32, device=dev)
+        self.xp = (ctypes.c_void_p * P)(*[X.data_ptr() for X in Xs])
+        self.sp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in self.S])
+        self.wpp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in self.W])
+        self.device = dev
+
+    def run(self, tol, stream=None):
+        """Queue one batched call on the stream (no synchronisation)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = load().rbrp_id_batched(self.P, self.xp, self.m, self.n, self.fp64_in, float(tol), ctypes.byref(self.opts),
+                                    ctypes.c_void_p(self.wp), self.need, self.sp, self.wpp,
+                                    ctypes.c_void_p(self.k_out.data_ptr()), ctypes.c_void_p(self.err.data_ptr()),
+                                    ctypes.c_void_p(self.status.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+        _check(st, "rbrp_id_batched", allow_notconverged=False)
+
+    def results(self):
+        ks, es, ss = self.k_out.tolist(), self.err.tolist(), self.status.tolist()
+        out = []
+        for p in range(self.P):
+            k = int(ks[p])
+            out.append(dict(S=self.S[p][:k], W=self.W[p][:, :k], k=k, rel_err_sq=es[p], status=int(ss[p]),
+                            converged=(ss[p] == 0)))
+        return out
+
+
 def rbrp_id_batched(Xs, tol, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random",
                     stream=None):
     """P independent row IDs in one launch (rbrp_id_batched of include/rbrp.h).
@@ -301,43 +357,10 @@ def rbrp_id_batched(Xs, tol, block=16, seed=0, precision="fp32", tau_b=-1.0, k_m
     k, rel_err_sq, status.
     """
     import torch
-    P = len(Xs)
-    if P == 0:
+    if len(Xs) == 0:
         return []
-    dt = Xs[0].dtype
-    dev = Xs[0].device
-    for X in Xs:
-        if not X.is_cuda or X.dim() != 2 or X.dtype != dt or not X.is_contiguous():
-            raise ValueError("Xs must be contiguous 2-D CUDA tensors of one dtype")
-    opts = make_opts(block, precision, tau_b, k_max, seed, 0, sampler, "fp64")
-    m = (ctypes.c_int64 * P)(*[int(X.shape[0]) for X in Xs])
-    n = (ctypes.c_int64 * P)(*[int(X.shape[1]) for X in Xs])
-    need = ctypes.c_size_t(0)
-    st = load().rbrp_batched_workspace_size(P, m, n, ctypes.byref(opts), ctypes.byref(need))
-    _check(st, "rbrp_batched_workspace_size", allow_notconverged=False)
-    ws = torch.empty(need.value + 256, dtype=torch.uint8, device=dev)
-    wp = (ws.data_ptr() + 255) // 256 * 256
-    kcs = [k_cap(int(X.shape[0]), int(X.shape[1]), k_max) for X in Xs]
-    S = [torch.empty(kc, dtype=torch.int64, device=dev) for kc in kcs]
-    Wt = [torch.empty((int(X.shape[0]), kc), dtype=torch.float64, device=dev) for X, kc in zip(Xs, kcs)]
-    k_out = torch.empty(P, dtype=torch.int64, device=dev)
-    err = torch.empty(P, dtype=torch.float64, device=dev)
-    status = torch.empty(P, dtype=torch.int32, device=dev)
-    xp = (ctypes.c_void_p * P)(*[X.data_ptr() for X in Xs])
-    sp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in S])
-    wpp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in Wt])
-    s = stream if stream is not None else torch.cuda.current_stream(dev)
-    st = load().rbrp_id_batched(P, xp, m, n, int(dt == torch.float64), float(tol), ctypes.byref(opts),
-                                ctypes.c_void_p(wp), need.value, sp, wpp, ctypes.c_void_p(k_out.data_ptr()),
-                                ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(status.data_ptr()),
-                                ctypes.c_void_p(s.cuda_stream))
-    _check(st, "rbrp_id_batched", allow_notconverged=False)
+    b = Batch(Xs, block, seed, precision, tau_b, k_max, sampler)
+    s = stream if stream is not None else torch.cuda.current_stream(b.device)
+    b.run(tol, s)
     s.synchronize()
-    ks, es, ss = k_out.tolist(), err.tolist(), status.tolist()
-    out = []
-    for p in range(P):
-        k = int(ks[p])
-        out.append(dict(S=S[p][:k], W=Wt[p][:, :k], k=k, rel_err_sq=es[p], status=int(ss[p]),
-                        converged=(ss[p] == 0)))
-    return out
-
+    return b.results()
