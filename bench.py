@@ -200,8 +200,10 @@ def run_ours(a):
 
     X = WL.zipf_gmm(n=a.n, d=a.d)
     Xd = torch.from_numpy(X).to(dev)
-    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=rank)
-    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, rank, "random", a.w_precision)
+    from paper_2309_16002_gb300 import shard
+    pid = shard.replica_problem_id(rank)
+    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=pid)
+    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, pid, "random", a.w_precision)
     wsp = G.Workspace(a.n, a.d, opts, dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -233,11 +235,7 @@ def run_ours(a):
     barrier()
     prof = G.rbrp_profile_end()
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1)
-    if ws_n > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = shard.max_over_ranks(ev0.elapsed_time(ev1), dev)
     ms = elapsed / a.steps
 
     # roofline of the fused residual update (Alg. 2 lines 12/16), events on the launch stream
@@ -298,11 +296,7 @@ def run_ours(a):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
-        if ws_n > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1) / a.e2e_steps, dev)
         if line is not None:
             line["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": a.n * a.d * 4,
                            "d2h_bytes_per_step": o2["k"] * 8 + a.n * o2["k"] * 8}
@@ -322,60 +316,101 @@ def run_batched(a):
     cubes 2 apart, FP32), tol 1e-5, b = 16, one rbrp_id_batched launch per step, against
     per-matrix rbrp_id calls timed on a sample and scaled to P."""
     import torch
+
+    import __graft_entry__ as ge
+    from paper_2309_16002_gb300 import shard
+    ws_n, rank, local = dist_init()
+    if ws_n > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        ge.build()
+    if ws_n > 1:
+        torch.distributed.barrier()
+    ge.build()
     from paper_2309_16002_gb300 import rbrp as G
     from paper_2309_16002_gb300 import workloads as WL
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     G.load()
-    Xs_np = WL.kernel_blocks(P=a.batch, seed=4)
+    # weak scaling: the job is a list of batch x N problems; every rank draws the
+    # shapes of the whole list, cuts it into cost-balanced contiguous shards,
+    # draws only its own shard's blocks and passes the shard's first index as
+    # Philox problem-id base
+    P_all = a.batch * ws_n
+    sizes = WL.kernel_block_sizes(P=P_all, seed=4)
+    lo, hi = shard.my_shard([shard.problem_cost(m, n) for m, n in sizes], ws_n, rank)
+    Xs_np = WL.kernel_blocks(P=P_all, seed=4, lo=lo, hi=hi)
     Xs = [torch.from_numpy(X).to(dev) for X in Xs_np]
     tol = 1e-5 if a.tol == 1e-4 else a.tol
     block = 16 if a.block == 64 else a.block
     prec = "fp32" if a.precision in ("tf32", "tf32x3") else a.precision
-    B = G.Batch(Xs, block=block, seed=0, precision=prec)
+    B = G.Batch(Xs, block=block, seed=0, precision=prec, problem=lo) if Xs else None
     s = torch.cuda.current_stream(dev)
+
+    def run_all():
+        if B is not None:
+            B.run(tol, s)
+
     for _ in range(a.warmup):
-        B.run(tol, s)
+        run_all()
     torch.cuda.synchronize()
+    if ws_n > 1:
+        torch.distributed.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     G.rbrp_profile_begin()
     ev0.record(s)
     for _ in range(a.steps):
-        B.run(tol, s)
+        run_all()
     ev1.record(s)
     torch.cuda.synchronize()
+    if ws_n > 1:
+        torch.distributed.barrier()
     prof = G.rbrp_profile_end()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    res = B.results()
+    ms = shard.max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
+    launches = shard.sum_over_ranks(prof["launches"] // max(1, a.steps), dev)
+    res = B.results() if B is not None else []
+    if ws_n > 1:
+        gathered = [None] * ws_n
+        torch.distributed.all_gather_object(gathered, [(r["k"], r["status"]) for r in res])
+        res = [dict(k=k, status=st) for part in gathered for k, st in part]
+        if rank != 0:
+            torch.distributed.destroy_process_group()
+            return
     ks = [r["k"] for r in res]
     st = [r["status"] for r in res]
     # per-matrix launches on a sample (each problem its own rbrp_id call, same precision and options)
-    samp = list(range(0, a.batch, max(1, a.batch // max(1, a.single_sample))))[:a.single_sample]
+    samp = list(range(0, len(Xs), max(1, len(Xs) // max(1, a.single_sample))))[:a.single_sample]
     single_prec = "fp64" if prec == "fp64" else "fp32"
     for p in samp[:4]:
-        G.rbrp_id(Xs[p], tol, block=block, seed=0, problem=p, precision=single_prec, w_precision="fp64")
+        G.rbrp_id(Xs[p], tol, block=block, seed=0, problem=lo + p, precision=single_prec, w_precision="fp64")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     for p in samp:
-        G.rbrp_id(Xs[p], tol, block=block, seed=0, problem=p, precision=single_prec, w_precision="fp64")
+        G.rbrp_id(Xs[p], tol, block=block, seed=0, problem=lo + p, precision=single_prec, w_precision="fp64")
     e1.record(s)
     torch.cuda.synchronize()
-    single_ms = e0.elapsed_time(e1) * a.batch / len(samp)
-    elems = sum(int(X.shape[0]) * int(X.shape[1]) for X in Xs_np)
-    line = {"metric": "batched ID time (ms) for %d kernel blocks, tol %g, b %d" % (a.batch, tol, block),
-            "value": ms, "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+    # per-matrix launches of the whole job on one GPU (rank 0's sample, scaled)
+    single_ms = e0.elapsed_time(e1) * P_all / len(samp)
+    elems = sum(m * n for m, n in sizes)
+    line = {"metric": "batched ID time (ms) for %d kernel blocks per GPU, tol %g, b %d" % (a.batch, tol, block),
+            "value": ms, "unit": "ms", "n_gpus": ws_n, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32+f64", "fp64": "f64"}[prec], "data": "synthetic",
-            "config": {"workload": "kernel_blocks", "P": a.batch, "m": [64, 2048], "n": [32, 256], "h": 0.5,
+            "config": {"workload": "kernel_blocks", "P": P_all, "P_per_gpu": a.batch, "m": [64, 2048],
+                       "n": [32, 256], "h": 0.5,
                        "gap": 2.0, "dtype_in": "fp32", "tol_sq_rel": tol, "block": block, "seed": 4,
                        "elements": elems},
             "k_mean": sum(ks) / len(ks), "k_max": max(ks), "not_converged": sum(1 for x in st if x == 5),
             "nonfinite": sum(1 for x in st if x == 4),
             "per_matrix_launches_ms": single_ms, "per_matrix_sample": len(samp),
             "speedup_vs_per_matrix": single_ms / ms if ms > 0 else None,
-            "gpu_launches": prof["launches"] // max(1, a.steps)}
+            "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
+    if ws_n > 1:
+        torch.distributed.destroy_process_group()
 
 
 def main():

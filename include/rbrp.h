@@ -195,8 +195,11 @@ rbrp_status rbrp_id_noalloc(const void *X, int x_is_fp64, int64_t n, int64_t d, 
  *
  * Problem p is X[p] (device, row-major m[p] x n[p] with leading dimension n[p],
  * FP32, or FP64 when x_is_fp64), solved to tol with the options o (block b,
- * tau_b, k_max, seed, sampler); its Philox problem id is p (o->problem is not
- * used) and its skeletons are drawn exactly as rbrp_id would draw them.
+ * tau_b, k_max, seed, sampler); its Philox problem id is o->problem + p, so
+ * its skeletons are drawn exactly as rbrp_id would draw them with that problem
+ * id, and a caller that splits one list of problems into contiguous shards
+ * (one call per shard, o->problem = index of the shard's first problem) gets
+ * the same results as one call over the whole list.
  * Precision: o->precision == RBRP_FP64 keeps the residual and every step in
  * FP64; any other value keeps the residual, the products and the W solve in
  * FP32 (row norms and their sums in FP64, sampling keys exact FP64);

@@ -23,7 +23,7 @@ Everything is FP64 (FP32 inputs are upcast exactly).  Library primitives
 (matrix products, solve_triangular, SVD, lstsq) serve as single steps; there is
 no blocking or fusion beyond what the algorithms state.
 
-Readings of points where the paper is silent (each is listed in the design doc):
+Readings of points where the paper is silent:
   R1  tau bounds the squared relative residual ||d||_1 / ||d0||_1 (Alg. 2 line 3).
   R2  "sample without replacement" is realised as an exponential race: keys
       kappa_i = -log(u_i) / d_i over eligible rows, the b_t smallest in

@@ -17,7 +17,7 @@
 // log-domain keys choose >= b_t + 32 candidates, their FP64 keys are ranked,
 // and a margin check against the FP32 error bound proves that no other row
 // could be drawn (else every eligible row is keyed in FP64).  Problem p uses
-// Philox problem id p.
+// Philox problem id pbase + p.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -50,6 +50,7 @@ struct Args {
   int b, greedy, x_is_fp64;
   long long k_max;
   unsigned long long seed;
+  unsigned long long pbase;  // Philox problem id of problem 0
   uint8_t* slots;            // per-CTA workspace slots
   size_t slot_bytes;
   long long m_max, n_max, kc_max;
@@ -437,7 +438,7 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
     const int bt = (int)btl;
     ++t;
     // line 5
-    sample_cta(d, mark, m, bt, ne, t, a, (unsigned long long)p, K64, sm);
+    sample_cta(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
     // line 6: V = R(S_t, :), CGS2
     for (long long e = tid; e < bt * n; e += kThreads) V[e] = R[(long long)sm.St[e / n] * n + e % n];
     __syncthreads();
@@ -604,7 +605,7 @@ int batched_ctas() {
 cudaError_t launch_batched(int P, const void* const* X_dev, const long long* rows_dev, const long long* cols_dev,
                            const int* order_dev, long long* const* skel_dev, double* const* W_dev, long long* k_out,
                            double* err, int* status, double tau, double tau_b, int b, int greedy, int x_is_fp64,
-                           long long k_max, unsigned long long seed, int fp64, void* slots, size_t slot_bytes,
+                           long long k_max, unsigned long long seed, unsigned long long pbase, int fp64, void* slots, size_t slot_bytes,
                            long long m_max, long long n_max, long long kc_max, unsigned int* next, int ctas,
                            cudaStream_t s) {
   bt::Args a;
@@ -625,6 +626,7 @@ cudaError_t launch_batched(int P, const void* const* X_dev, const long long* row
   a.x_is_fp64 = x_is_fp64;
   a.k_max = k_max;
   a.seed = seed;
+  a.pbase = pbase;
   a.slots = (uint8_t*)slots;
   a.slot_bytes = slot_bytes;
   a.m_max = m_max;

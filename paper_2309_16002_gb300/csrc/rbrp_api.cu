@@ -740,7 +740,7 @@ rbrp_status rbrp_id_batched(int32_t P, const void* const* X, const int64_t* m, c
                     (const long long*)(ws + bp.off_cols), (const int*)(ws + bp.off_order),
                     (long long* const*)(ws + bp.off_skel), (double* const*)(ws + bp.off_W), (long long*)k_out,
                     rel_err_sq, (int*)status, tol, o->tau_b, o->block, o->sampler == RBRP_SAMPLER_GREEDY, x_is_fp64,
-                    o->k_max, o->seed, bp.fp64, ws + bp.off_slots, bp.slot, bp.m_max, bp.n_max, bp.kc_max,
+                    o->k_max, o->seed, o->problem, bp.fp64, ws + bp.off_slots, bp.slot, bp.m_max, bp.n_max, bp.kc_max,
                     (unsigned int*)(ws + bp.off_next), bp.ctas, s));
   return RBRP_OK;
 }

@@ -227,7 +227,7 @@ int batched_ctas();
 cudaError_t launch_batched(int P, const void* const* X_dev, const long long* rows_dev, const long long* cols_dev,
                            const int* order_dev, long long* const* skel_dev, double* const* W_dev, long long* k_out,
                            double* err, int* status, double tau, double tau_b, int b, int greedy, int x_is_fp64,
-                           long long k_max, unsigned long long seed, int fp64, void* slots, size_t slot_bytes,
+                           long long k_max, unsigned long long seed, unsigned long long pbase, int fp64, void* slots, size_t slot_bytes,
                            long long m_max, long long n_max, long long kc_max, unsigned int* next, int ctas,
                            cudaStream_t s);
 constexpr long long kBatchMaxRows = 4096;

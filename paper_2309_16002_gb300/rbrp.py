@@ -294,7 +294,7 @@ def as_numpy(t):
 class Batch:
     """Preallocated outputs and workspace for repeated rbrp_id_batched calls on one list of problems."""
 
-    def __init__(self, Xs, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random"):
+    def __init__(self, Xs, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random", problem=0):
         import torch
         self.P = len(Xs)
         if self.P == 0:
@@ -306,7 +306,7 @@ class Batch:
                 raise ValueError("Xs must be contiguous 2-D CUDA tensors of one dtype")
         self.Xs = Xs
         self.fp64_in = int(dt == torch.float64)
-        self.opts = make_opts(block, precision, tau_b, k_max, seed, 0, sampler, "fp64")
+        self.opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, "fp64")
         P = self.P
         self.m = (ctypes.c_int64 * P)(*[int(X.shape[0]) for X in Xs])
         self.n = (ctypes.c_int64 * P)(*[int(X.shape[1]) for X in Xs])
@@ -348,18 +348,18 @@ class Batch:
 
 
 def rbrp_id_batched(Xs, tol, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random",
-                    stream=None):
+                    stream=None, problem=0):
     """P independent row IDs in one launch (rbrp_id_batched of include/rbrp.h).
 
     Xs: list of CUDA tensors (all FP32 or all FP64, row-major, m <= 4096 rows,
-    n <= 256 columns); problem p uses Philox problem id p.  Returns one dict per
+    n <= 256 columns); problem p uses Philox problem id problem + p.  Returns one dict per
     problem: S (int64 CUDA tensor, acceptance order), W (m x k FP64 CUDA tensor),
     k, rel_err_sq, status.
     """
     import torch
     if len(Xs) == 0:
         return []
-    b = Batch(Xs, block, seed, precision, tau_b, k_max, sampler)
+    b = Batch(Xs, block, seed, precision, tau_b, k_max, sampler, problem)
     s = stream if stream is not None else torch.cuda.current_stream(b.device)
     b.run(tol, s)
     s.synchronize()

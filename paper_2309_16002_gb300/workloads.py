@@ -102,12 +102,25 @@ def kernel_block(rng, m, n, h=0.5, gap=2.0, dtype=np.float32):
     return np.exp(-r2 / (h * h)).astype(dtype)
 
 
-def kernel_blocks(P=4096, m_range=(64, 2048), n_range=(32, 256), h=0.5, gap=2.0, seed=4, dtype=np.float32):
-    """P independent kernel blocks with m ~ U[m_range], n ~ U[n_range] (inclusive integers)."""
+def kernel_block_sizes(P=4096, m_range=(64, 2048), n_range=(32, 256), seed=4):
+    """Shapes (m_p, n_p) of P kernel blocks: m ~ U[m_range], n ~ U[n_range] (inclusive integers)."""
     rng = _rng(seed)
     ms = rng.integers(m_range[0], m_range[1] + 1, size=P)
     ns = rng.integers(n_range[0], n_range[1] + 1, size=P)
-    return [kernel_block(rng, int(m), int(n), h, gap, dtype) for m, n in zip(ms, ns)]
+    return [(int(m), int(n)) for m, n in zip(ms, ns)]
+
+
+def kernel_blocks(P=4096, m_range=(64, 2048), n_range=(32, 256), h=0.5, gap=2.0, seed=4, dtype=np.float32,
+                  lo=0, hi=None):
+    """Kernel blocks lo..hi-1 of a list of P (shapes from kernel_block_sizes).
+
+    Block p draws its points from its own generator (seed, p), so any slice of
+    the list can be drawn without drawing the rest.
+    """
+    sizes = kernel_block_sizes(P, m_range, n_range, seed)
+    hi = P if hi is None else hi
+    return [kernel_block(np.random.Generator(np.random.PCG64([seed, p])), m, n, h, gap, dtype)
+            for p, (m, n) in enumerate(sizes[lo:hi], start=lo)]
 
 
 def random_features(n=1000000, d=512, latent=64, comps=20, mean_var=4.0, seed=5, dtype=np.float32,

@@ -1,7 +1,7 @@
 """GPU parity of the batched entry point (rbrp_id_batched, one launch for P problems).
 
-Problem p of a batch uses Philox problem id p, so it must reproduce the single-problem
-oracle run with problem = p.  Bars, problem by problem (as in test_gpu_parity):
+Problem p of a batch uses Philox problem id (base + p), base 0 unless given, so it must
+reproduce the single-problem oracle run with that problem id.  Bars, problem by problem (as in test_gpu_parity):
   FP64  skeleton indices identical to the oracle's (or a near-tie the oracle logged) and
         |e_gpu - e_oracle| <= 1e-10, e = ||X - W X_S||_F / ||X||_F;
   FP32  e_gpu <= max(1.05 e_same, e_same + 1e-5) with e_same the oracle's exact error for
@@ -127,6 +127,23 @@ def test_batched_same_as_single_problem_calls(G):
     for p, (X, out) in enumerate(zip(Xs, outs)):
         one = G.rbrp_id(torch.from_numpy(X).to("cuda:0"), 1e-6, block=16, seed=11, problem=p, precision="fp64")
         assert one["S"].cpu().numpy().tolist() == out["S"].tolist(), p
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_shards_with_problem_base_match_one_call(G, precision):
+    """Contiguous shards, each called with problem = its first index, reproduce one call."""
+    from paper_2309_16002_gb300 import shard
+    Xs = _problems(np.float64 if precision == "fp64" else np.float32)
+    whole = _run(G, Xs, 1e-6, block=8, seed=5, precision=precision)
+    for lo, hi in shard.shard_bounds([shard.problem_cost(*X.shape) for X in Xs], 3):
+        if lo == hi:
+            continue
+        part = _run(G, Xs[lo:hi], 1e-6, block=8, seed=5, precision=precision, problem=lo)
+        for j, out in enumerate(part):
+            ref = whole[lo + j]
+            assert out["S"].tolist() == ref["S"].tolist(), (lo + j)
+            assert out["k"] == ref["k"] and out["rel_err_sq"] == ref["rel_err_sq"], (lo + j)
+            assert np.array_equal(out["W"], ref["W"]), (lo + j)
 
 
 def test_batched_nonfinite_and_limits(G):
