@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--workload", default="zipf_gmm", choices=["zipf_gmm", "kernel_blocks"],
                     help="kernel_blocks: the batched workload (one rbrp_id_batched launch per step)")
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched workload")
+    ap.add_argument("--no-fp64-form", action="store_true", help="batched workload: skip the FP64 form")
     ap.add_argument("--single-sample", type=int, default=128,
                     help="problems timed with one rbrp_id call each, for the per-matrix comparison")
     return ap.parse_args()
@@ -348,10 +349,17 @@ def run_batched(a):
     prec = "fp32" if a.precision in ("tf32", "tf32x3") else a.precision
     B = G.Batch(Xs, block=block, seed=0, precision=prec, problem=lo) if Xs else None
     s = torch.cuda.current_stream(dev)
+    # schedule picked by the autotuner (untimed), then the solve captured in a CUDA graph
+    tuned = B.tune(tol, reps=2) if B is not None else None
+    graph, per_graph = None, 0
+    if B is not None:
+        G.rbrp_profile_begin()
+        graph = B.graph(tol)
+        per_graph = G.rbrp_profile_end()["launches"]
 
     def run_all():
-        if B is not None:
-            B.run(tol, s)
+        if graph is not None:
+            graph.replay()
 
     for _ in range(a.warmup):
         run_all()
@@ -359,7 +367,6 @@ def run_batched(a):
     if ws_n > 1:
         torch.distributed.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    G.rbrp_profile_begin()
     ev0.record(s)
     for _ in range(a.steps):
         run_all()
@@ -367,10 +374,30 @@ def run_batched(a):
     torch.cuda.synchronize()
     if ws_n > 1:
         torch.distributed.barrier()
-    prof = G.rbrp_profile_end()
     ms = shard.max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
-    launches = shard.sum_over_ranks(prof["launches"] // max(1, a.steps), dev)
+    launches = shard.sum_over_ranks(per_graph, dev)
     res = B.results() if B is not None else []
+    # the plain FP64 GPU form of the same batch (one-shot calls, same options)
+    fp64_form = None
+    if B is not None and prec != "fp64" and not a.no_fp64_form:
+        B64 = G.Batch(Xs, block=block, seed=0, precision="fp64", problem=lo)
+        B64.tune(tol, reps=1)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(s)
+        for _ in range(2):
+            B64.run(tol, s)
+        f1.record(s)
+        torch.cuda.synchronize()
+        r64 = B64.results()
+        e32 = [r["rel_err_sq"] ** 0.5 for r in res]
+        e64 = [r["rel_err_sq"] ** 0.5 for r in r64]
+        fp64_form = {"ms": f0.elapsed_time(f1) / 2, "schedule": B64.schedule(),
+                     "k_mean": sum(r["k"] for r in r64) / len(r64),
+                     "same_k": sum(1 for x, y in zip(res, r64) if x["k"] == y["k"]) / len(r64),
+                     "max_e_fp32_minus_e_fp64": max(x - y for x, y in zip(e32, e64)),
+                     "within_bar": sum(1 for x, y in zip(e32, e64) if x <= max(1.05 * y, y + 1e-5)) / len(r64)}
+        del B64
+    res = [dict(k=r["k"], status=r["status"]) for r in res]
     if ws_n > 1:
         gathered = [None] * ws_n
         torch.distributed.all_gather_object(gathered, [(r["k"], r["status"]) for r in res])
@@ -407,7 +434,8 @@ def run_batched(a):
             "nonfinite": sum(1 for x in st if x == 4),
             "per_matrix_launches_ms": single_ms, "per_matrix_sample": len(samp),
             "speedup_vs_per_matrix": single_ms / ms if ms > 0 else None,
-            "gpu_launches": int(launches)}
+            "gpu_launches": int(launches) * a.steps, "graph": True, "schedule": tuned,
+            "fp64_form": fp64_form}
     print(json.dumps(line), flush=True)
     if ws_n > 1:
         torch.distributed.destroy_process_group()

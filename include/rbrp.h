@@ -226,6 +226,53 @@ rbrp_status rbrp_id_batched(int32_t P, const void *const *X, const int64_t *m, c
                             int64_t *const *skel, double *const *W, int64_t *k_out, double *rel_err_sq,
                             int32_t *status, rbrp_stream_t stream);
 
+/*
+ * Batch handle: the same computation as rbrp_id_batched, split so that the
+ * device work can be replayed and captured in a CUDA graph.
+ *
+ * rbrp_batch_create validates the problems exactly as rbrp_id_batched does,
+ * writes the problem table (pointers, sizes, processing order) into the
+ * workspace with copies queued on `stream`, and returns a host handle that
+ * remembers the workspace, the output arrays and the options (the caller
+ * keeps all of them alive and unchanged until rbrp_batch_destroy).  The
+ * handle allocates only host memory.
+ *
+ * rbrp_batch_run queues one solve of every problem to tolerance tol on
+ * `stream`: a 4-byte memset of the work counter and one kernel launch, no
+ * host synchronisation and no host-to-device copy, so it may be captured in a
+ * CUDA graph (the graph then replays the solve with that tol; outputs are
+ * rewritten in full on every run).  Runs on one handle must not overlap on
+ * the GPU (they share the workspace).
+ *
+ * Schedule: the kernel runs `threads` (256 or 512) threads per CTA with
+ * `ctas_per_sm` (1 or 2) CTAs resident on every SM.  Results do not depend
+ * on the schedule.  A new handle takes the schedule that rbrp_batch_autotune
+ * last chose for a batch of the same shape in this process (same precision,
+ * block, P, largest m and n, total elements), else 256 threads, one CTA per
+ * SM.  rbrp_batch_autotune times every schedule that fits on the device
+ * (one warm-up and `reps` timed runs of rbrp_batch_run each, CUDA events on
+ * `stream`, synchronising the stream), keeps the fastest on the handle and
+ * in the process-wide table, and returns its time per run in *best_ms (may
+ * be NULL); it must not be called while `stream` is being captured, and it
+ * overwrites the outputs (with the same values any run produces).
+ * rbrp_batch_set_schedule returns RBRP_EINVAL for a schedule the device
+ * cannot hold (shared memory or registers); rbrp_batch_get_schedule reports
+ * the current one and the number of CTAs launched.
+ *
+ * Errors: as rbrp_id_batched; RBRP_EINVAL for a NULL handle, RBRP_ENOMEM if
+ * the host handle cannot be allocated.
+ */
+typedef struct rbrp_batch_s *rbrp_batch;
+rbrp_status rbrp_batch_create(int32_t P, const void *const *X, const int64_t *m, const int64_t *n, int x_is_fp64,
+                              const rbrp_opts *o, void *workspace, size_t ws_bytes, int64_t *const *skel,
+                              double *const *W, int64_t *k_out, double *rel_err_sq, int32_t *status,
+                              rbrp_stream_t stream, rbrp_batch *out);
+rbrp_status rbrp_batch_run(rbrp_batch h, double tol, rbrp_stream_t stream);
+rbrp_status rbrp_batch_autotune(rbrp_batch h, double tol, int32_t reps, rbrp_stream_t stream, float *best_ms);
+rbrp_status rbrp_batch_set_schedule(rbrp_batch h, int32_t threads, int32_t ctas_per_sm);
+rbrp_status rbrp_batch_get_schedule(rbrp_batch h, int32_t *threads, int32_t *ctas_per_sm, int32_t *ctas);
+void rbrp_batch_destroy(rbrp_batch h);
+
 /* Human-readable name of a status code (static string). */
 const char *rbrp_status_string(rbrp_status s);
 

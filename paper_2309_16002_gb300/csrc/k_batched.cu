@@ -12,12 +12,22 @@
 // (L2-resident) and the small b x b steps run in shared memory; no step needs
 // more than one SM, and the only inter-CTA traffic is the work counter.
 //
-// T is the storage and arithmetic type (float or double).  Sampling keys are
-// exact FP64 keys of Alg. 2 line 5 as in the single-problem sampler: FP32
-// log-domain keys choose >= b_t + 32 candidates, their FP64 keys are ranked,
-// and a margin check against the FP32 error bound proves that no other row
-// could be drawn (else every eligible row is keyed in FP64).  Problem p uses
-// Philox problem id pbase + p.
+// Every pass over rows (initial norms, CGS, residual update) is one routine:
+// a warp holds a group of rows in registers (n <= 256: eight values a lane),
+// issues all their loads at once, and for each basis row forms the
+// coefficients (a butterfly all-reduce over the warp) and subtracts.  Loads
+// of a group are in flight together, which is what bounds these passes: a
+// problem's residual sits in L2 and each pass is a few hundred kilobytes.
+//
+// T is the storage and arithmetic type (float or double); NT (256 or 512) the
+// CTA size, a schedule parameter chosen by the host (autotuned per batch).
+// Results do not depend on NT: sums over rows use a fixed 256-way partition
+// and every other reduction is per warp.  Sampling keys are the exact FP64
+// keys of Alg. 2 line 5 as in the single-problem sampler: FP32 log-domain
+// keys choose >= b_t + 32 candidates, their FP64 keys are ranked, and a margin
+// check against the FP32 error bound proves that no other row could be drawn
+// (else every eligible row is keyed in FP64).  Problem p uses Philox problem
+// id pbase + p.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -31,35 +41,14 @@
 namespace rbrp {
 namespace bt {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kCand = 1024;  // candidates the sampler ranks exactly
-
-struct Args {
-  int P;
-  const void* const* X;      // device array: problem p is m_p x n_p, row-major, ld = n_p
-  const long long* rows;     // m_p
-  const long long* cols;     // n_p
-  const int* order;          // processing order
-  long long* const* skel;    // device array: k_cap_p entries each
-  double* const* W;          // device array: m_p x k_cap_p FP64 each, ld = k_cap_p
-  long long* k_out;          // P
-  double* err;               // P: ||d||_1 / ||d0||_1
-  int* status;               // P: rbrp_status
-  double tau, tau_b;
-  int b, greedy, x_is_fp64;
-  long long k_max;
-  unsigned long long seed;
-  unsigned long long pbase;  // Philox problem id of problem 0
-  uint8_t* slots;            // per-CTA workspace slots
-  size_t slot_bytes;
-  long long m_max, n_max, kc_max;
-  unsigned int* next;        // work counter, zero before the launch
-};
+constexpr int kMaxWarps = kBatchMaxThreads / 32;
+constexpr int kSumLanes = 256;   // fixed partition of sums over rows
+constexpr int kCand = 1024;      // candidates the sampler ranks exactly
+constexpr int kRowVec = 8;       // values of a row per lane (n <= 256)
 
 // Offsets of one slot (bytes), for the batch maxima.
 struct Slot {
-  size_t R, L, Q, d, mark, V, Y, C, K64, Wt, total;
+  size_t R, L, Q, d, mark, V, Y, K64, Wt, total;
 };
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 __host__ __device__ inline Slot slot_layout(long long m, long long n, long long kc, int b, size_t sT) {
@@ -79,8 +68,6 @@ __host__ __device__ inline Slot slot_layout(long long m, long long n, long long 
   o = al256(o + (size_t)b * n * sT);
   s.Y = o;
   o = al256(o + (size_t)b * n * sT);
-  s.C = o;
-  o = al256(o + (size_t)b * kc * sT);
   s.K64 = o;  // fallback sampler keys
   o = al256(o + (size_t)m * 8);
   s.Wt = o;   // W solve scratch, column-major
@@ -90,7 +77,7 @@ __host__ __device__ inline Slot slot_layout(long long m, long long n, long long 
 }
 
 struct Smem {
-  unsigned int keys[4096];
+  unsigned int keys[kBatchMaxRows];
   unsigned int hist[kBins];
   unsigned long long ek[kCand];
   int cand[kCand];
@@ -98,20 +85,23 @@ struct Smem {
   int perm[32];
   double G[32][33];   // Gram / Schur complement
   double Lw[32][33];  // factor, candidate-indexed then pivot-indexed
-  double red[kWarps];
+  double red[kMaxWarps];
   unsigned int cnt;
   int bin, bp;
   unsigned int below, total;
   int flag;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Sum of one value per thread in a fixed order; every thread gets the result.
+// Sum of one value per thread, warps in order; every thread gets the result.
+// Callers fill only threads < kSumLanes, so the value does not depend on NT.
+template <int NT>
 __device__ double block_sum(double v, Smem& sm) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5;
@@ -120,14 +110,16 @@ __device__ double block_sum(double v, Smem& sm) {
   __syncthreads();
   double s = 0.0;
 #pragma unroll
-  for (int q = 0; q < kWarps; ++q) s += sm.red[q];
+  for (int q = 0; q < NT / 32; ++q) s += sm.red[q];
   return s;
 }
 
 // First bin of sm.hist where the running count reaches want (kBins if never),
 // with the count below it; every thread gets both.
+template <int NT>
 __device__ int find_bin_cta(Smem& sm, unsigned int want, unsigned int* below) {
-  constexpr int per = kBins / kThreads;
+  constexpr int per = kBins / NT;
+  constexpr int NW = NT / 32;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   unsigned int c[per], sum = 0;
 #pragma unroll
@@ -147,7 +139,7 @@ __device__ int find_bin_cta(Smem& sm, unsigned int want, unsigned int* below) {
   __syncthreads();
   unsigned int before = 0, all = 0;
 #pragma unroll
-  for (int q = 0; q < kWarps; ++q) {
+  for (int q = 0; q < NW; ++q) {
     const unsigned int x = (unsigned int)sm.red[q];
     if (q < w) before += x;
     all += x;
@@ -189,34 +181,35 @@ __device__ __forceinline__ void exact_key(double di, long long i, unsigned long 
 }
 
 // S_t (bt rows, in draw order) into sm.St.  ne = number of eligible rows.
+template <int NT>
 __device__ void sample_cta(const double* d, const int* mark, long long m, int bt, long long ne, unsigned long long t,
-                           const Args& a, unsigned long long p, unsigned long long* K64, Smem& sm) {
+                           const BatchedArgs& a, unsigned long long p, unsigned long long* K64, Smem& sm) {
   const int tid = threadIdx.x;
-  for (long long i = tid; i < m; i += kThreads) {
+  for (long long i = tid; i < m; i += NT) {
     const bool elig = mark[i] == 0 && d[i] > 0.0;
     sm.keys[i] = elig ? approx_key(d[i], i, t, a.seed, p, a.greedy) : 0xFFFFFFFFu;
   }
   const unsigned int want = (unsigned int)(bt + kMargin < ne ? bt + kMargin : ne);
-  for (int j = tid; j < kBins; j += kThreads) sm.hist[j] = 0;
+  for (int j = tid; j < kBins; j += NT) sm.hist[j] = 0;
   __syncthreads();
-  for (long long i = tid; i < m; i += kThreads)
+  for (long long i = tid; i < m; i += NT)
     if (sm.keys[i] != 0xFFFFFFFFu) atomicAdd(&sm.hist[sm.keys[i] >> 21], 1u);
   __syncthreads();
   unsigned int below1 = 0, below2 = 0;
-  const int b1 = find_bin_cta(sm, want, &below1);
-  for (int j = tid; j < kBins; j += kThreads) sm.hist[j] = 0;
+  const int b1 = find_bin_cta<NT>(sm, want, &below1);
+  for (int j = tid; j < kBins; j += NT) sm.hist[j] = 0;
   __syncthreads();
-  for (long long i = tid; i < m; i += kThreads) {
+  for (long long i = tid; i < m; i += NT) {
     const unsigned int k = sm.keys[i];
     if (k != 0xFFFFFFFFu && (int)(k >> 21) == b1) atomicAdd(&sm.hist[(k >> 10) & 0x7FF], 1u);
   }
   __syncthreads();
-  int b2 = find_bin_cta(sm, want - below1, &below2);
+  int b2 = find_bin_cta<NT>(sm, want - below1, &below2);
   if (b2 >= kBins) b2 = kBins - 1;
   const unsigned int c22 = ((unsigned int)b1 << 11) | (unsigned int)b2;
   if (tid == 0) sm.cnt = 0;
   __syncthreads();
-  for (long long i = tid; i < m; i += kThreads) {
+  for (long long i = tid; i < m; i += NT) {
     const unsigned int k = sm.keys[i];
     if (k != 0xFFFFFFFFu && (k >> 10) <= c22) {
       const unsigned int pos = atomicAdd(&sm.cnt, 1u);
@@ -227,12 +220,12 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
   const int nc = (int)sm.cnt;
   const bool overflow = nc > kCand;
   const int mc = overflow ? 0 : nc;
-  for (int e = tid; e < mc; e += kThreads) {
+  for (int e = tid; e < mc; e += NT) {
     double lg;
     exact_key(d[sm.cand[e]], sm.cand[e], t, a.seed, p, a.greedy, &sm.ek[e], &lg);
   }
   __syncthreads();
-  for (int e = tid; e < mc; e += kThreads) {
+  for (int e = tid; e < mc; e += NT) {
     int rank = 0;
     const unsigned long long ke = sm.ek[e];
     const int ie = sm.cand[e];
@@ -256,7 +249,7 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
   __syncthreads();
   if (!sm.flag) return;
   // fallback: FP64 keys of every eligible row, ranked by counting
-  for (long long i = tid; i < m; i += kThreads) {
+  for (long long i = tid; i < m; i += NT) {
     unsigned long long k = kIneligible;
     if (mark[i] == 0 && d[i] > 0.0) {
       double lg;
@@ -265,7 +258,7 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
     K64[i] = k;
   }
   __syncthreads();
-  for (long long i = tid; i < m; i += kThreads) {
+  for (long long i = tid; i < m; i += NT) {
     const unsigned long long ki = K64[i];
     if (ki == kIneligible) continue;
     long long rank = 0;
@@ -278,34 +271,108 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
   __syncthreads();
 }
 
-// Dot products of rows of A (ra rows) with rows of B (rb rows), length n, into
-// Cm (ra x ldc); one warp per pair.
-template <typename T>
-__device__ void rows_dot(const T* A, const T* B, int ra, int rb, long long n, T* Cm, long long ldc) {
+// Rows i < nrows of src (row-major, leading dimension n <= 256; row i read
+// from src row rowmap[i] when rowmap is given): c_ij = <src_i, B_j> for
+// j < nb, every c_ij from the original row (classical Gram-Schmidt), and
+// y_i = src_i - sum_j c_ij B_j with the terms subtracted in ascending j.
+// COEF: coef[j * ldc + i] = c_ij.  y_i goes to dst row i, zeroed when
+// mark && mark[i] != 0; NORM: dn[i] = ||y_i||^2 (0 for zeroed rows).  One warp
+// per group of RPW rows, whose loads are all issued before any arithmetic.
+// dst may alias src (each group is read completely before it is written).
+// No barrier inside; the caller synchronises.
+template <int NT, int RPW, bool COEF, bool NORM, typename T, typename TS>
+__device__ void project_rows(const TS* src, const int* rowmap, T* dst, long long nrows, long long n, const T* B,
+                             int nb, T* coef, long long ldc, double* dn, const int* mark) {
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int pr = w; pr < ra * rb; pr += kWarps) {
-    const int i = pr / rb, j = pr % rb;
-    T s = 0;
-    for (long long c = lane; c < n; c += 32) s += A[i * n + c] * B[j * n + c];
+  for (long long i0 = (long long)w * RPW; i0 < nrows; i0 += (long long)NW * RPW) {
+    T x[RPW][kRowVec], y[RPW][kRowVec];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) Cm[i * ldc + j] = s;
+    for (int r = 0; r < RPW; ++r) {
+      const long long i = i0 + r;
+      const long long si = (i < nrows) ? (rowmap ? (long long)rowmap[i] : i) : 0;
+#pragma unroll
+      for (int u = 0; u < kRowVec; ++u) {
+        const long long c = lane + 32 * u;
+        x[r][u] = (i < nrows && c < n) ? (T)src[si * n + c] : (T)0;
+        y[r][u] = x[r][u];
+      }
+    }
+    for (int j = 0; j < nb; ++j) {
+      T q[kRowVec];
+#pragma unroll
+      for (int u = 0; u < kRowVec; ++u) {
+        const long long c = lane + 32 * u;
+        q[u] = c < n ? B[(long long)j * n + c] : (T)0;
+      }
+      T s[RPW];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        T acc = 0;
+#pragma unroll
+        for (int u = 0; u < kRowVec; ++u) acc += x[r][u] * q[u];
+        s[r] = acc;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+#pragma unroll
+        for (int u = 0; u < kRowVec; ++u) y[r][u] -= s[r] * q[u];
+        if (COEF && lane == 0 && i0 + r < nrows) coef[(long long)j * ldc + i0 + r] = s[r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const long long i = i0 + r;
+      if (i >= nrows) break;
+      const bool zero = mark && mark[i] != 0;
+      T nr = 0;
+#pragma unroll
+      for (int u = 0; u < kRowVec; ++u) {
+        const long long c = lane + 32 * u;
+        if (c >= n) continue;
+        const T v = zero ? (T)0 : y[r][u];
+        dst[i * n + c] = v;
+        nr += v * v;
+      }
+      if (NORM) {
+        const double s = warp_sum((double)nr);
+        if (lane == 0) dn[i] = zero ? 0.0 : s;
+      }
+    }
   }
 }
 
-// V (rows x n) <- V - (V Q^T) Q over the first k rows of Q (CGS).
-template <typename T>
-__device__ void cgs(T* V, int rows, const T* Q, long long k, long long n, T* C, long long ldc) {
-  if (k <= 0) return;
-  rows_dot<T>(V, Q, rows, (int)k, n, C, ldc);
-  __syncthreads();
-  for (long long e = threadIdx.x; e < rows * n; e += kThreads) {
-    const long long i = e / n, c = e % n;
-    T s = 0;
-    for (long long j = 0; j < k; ++j) s += C[i * ldc + j] * Q[j * n + c];
-    V[e] -= s;
+// sm.G[i][j] = <V_i, V_j> for i, j < rows (V row-major, leading dimension n);
+// row i's values stay in registers while its warp walks j <= i.
+template <int NT, typename T>
+__device__ void gram_rows(const T* V, int rows, long long n, Smem& sm) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = w; i < rows; i += NW) {
+    T x[kRowVec];
+#pragma unroll
+    for (int u = 0; u < kRowVec; ++u) {
+      const long long c = lane + 32 * u;
+      x[u] = c < n ? V[(long long)i * n + c] : (T)0;
+    }
+    for (int j = 0; j <= i; ++j) {
+      T acc = 0;
+#pragma unroll
+      for (int u = 0; u < kRowVec; ++u) {
+        const long long c = lane + 32 * u;
+        acc += x[u] * (c < n ? V[(long long)j * n + c] : (T)0);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        sm.G[i][j] = (double)acc;
+        sm.G[j][i] = (double)acc;
+      }
+    }
   }
-  __syncthreads();
 }
 
 // Pivoted (piv = 1) or plain Cholesky of sm.G (m x m, in T precision) by warp 0;
@@ -320,10 +387,10 @@ __device__ void chol_warp(Smem& sm, int m, double tau_b, int piv) {
   const int j = threadIdx.x;
   bool alive = j < m;
   T dj = alive ? (T)sm.G[j][j] : (T)0;
-  const T total = (T)warp_sum(alive ? (double)dj : 0.0);
+  const T total = warp_sum<T>(alive ? dj : (T)0);
   int bp = 0;
   for (int i = 0; i < m; ++i) {
-    const T msum = (T)warp_sum(alive ? (double)dj : 0.0);
+    const T msum = warp_sum<T>(alive ? dj : (T)0);
     T best = alive ? dj : (T)-1;
     int vi = alive ? j : INT_MAX;
     if (!piv) {
@@ -366,9 +433,9 @@ __device__ void chol_warp(Smem& sm, int m, double tau_b, int piv) {
 }
 
 // Y (bp x n) = Lc^{-1} V(perm) with Lc = sm.G (lower), one thread per column.
-template <typename T>
+template <int NT, typename T>
 __device__ void trsm_cols(Smem& sm, const T* V, const int* perm, T* Y, int bp, long long n) {
-  for (long long c = threadIdx.x; c < n; c += kThreads) {
+  for (long long c = threadIdx.x; c < n; c += NT) {
     for (int i = 0; i < bp; ++i) {
       T y = V[(perm ? perm[i] : i) * n + c];
       for (int l = 0; l < i; ++l) y -= (T)sm.G[i][l] * Y[l * n + c];
@@ -378,9 +445,19 @@ __device__ void trsm_cols(Smem& sm, const T* V, const int* perm, T* Y, int bp, l
   __syncthreads();
 }
 
-template <typename T>
-__device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T* sQp) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+// Sum over rows of a per-row value, in the fixed kSumLanes partition.
+template <int NT, typename F>
+__device__ double rows_sum(long long m, Smem& sm, F f) {
+  double part = 0.0;
+  if (threadIdx.x < kSumLanes)
+    for (long long i = threadIdx.x; i < m; i += kSumLanes) part += f(i);
+  return block_sum<NT>(part, sm);
+}
+
+template <int NT, typename T>
+__device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem& sm, T* sQp) {
+  constexpr int RPW = sizeof(T) == 4 ? 4 : 2;  // rows per warp group in the row passes
+  const int tid = threadIdx.x;
   const long long m = a.rows[p], n = a.cols[p];
   long long kc = m < n ? m : n;
   if (a.k_max > 0 && a.k_max < kc) kc = a.k_max;
@@ -392,31 +469,20 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
   int* mark = (int*)(slotp + so.mark);
   T* V = (T*)(slotp + so.V);
   T* Y = (T*)(slotp + so.Y);
-  T* C = (T*)(slotp + so.C);
   unsigned long long* K64 = (unsigned long long*)(slotp + so.K64);
   T* Wt = (T*)(slotp + so.Wt);  // column-major
   long long* skel = a.skel[p];
 
-  // Alg. 2 lines 1-2
-  for (long long e = tid; e < m * n; e += kThreads)
-    R[e] = a.x_is_fp64 ? (T)((const double*)a.X[p])[e] : (T)((const float*)a.X[p])[e];
+  // Alg. 2 lines 1-2: R = X and d_i = ||X_i||^2 in one pass over X
+  if (a.x_is_fp64)
+    project_rows<NT, RPW, false, true, T, double>((const double*)a.X[p], nullptr, R, m, n, (const T*)nullptr, 0,
+                                                  nullptr, 0, d, nullptr);
+  else
+    project_rows<NT, RPW, false, true, T, float>((const float*)a.X[p], nullptr, R, m, n, (const T*)nullptr, 0,
+                                                 nullptr, 0, d, nullptr);
+  for (long long i = tid; i < m; i += NT) mark[i] = 0;
   __syncthreads();
-  for (long long i = w; i < m; i += kWarps) {
-    T sl = 0;  // per lane in T (FP64 arithmetic costs ~64 cycles per warp instruction on GB300)
-    for (long long c = lane; c < n; c += 32) {
-      const T x = R[i * n + c];
-      sl += x * x;
-    }
-    const double s = warp_sum((double)sl);
-    if (lane == 0) {
-      d[i] = s;
-      mark[i] = 0;
-    }
-  }
-  __syncthreads();
-  double part = 0.0;
-  for (long long i = tid; i < m; i += kThreads) part += d[i];
-  const double D0 = block_sum(part, sm);
+  const double D0 = rows_sum<NT>(m, sm, [&](long long i) { return d[i]; });
   double D = D0;
   long long k = 0;
   unsigned long long t = 0;
@@ -429,108 +495,53 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
       if (a.tau >= 0.0) status = RBRP_ENOTCONVERGED;
       break;
     }
-    double ecount = 0.0;
-    for (long long i = tid; i < m; i += kThreads) ecount += (mark[i] == 0 && d[i] > 0.0) ? 1.0 : 0.0;
-    const long long ne = (long long)block_sum(ecount, sm);
+    const long long ne =
+        (long long)rows_sum<NT>(m, sm, [&](long long i) { return (mark[i] == 0 && d[i] > 0.0) ? 1.0 : 0.0; });
     if (ne == 0) break;
     long long btl = (long long)a.b < ne ? (long long)a.b : ne;
     if (kc - k < btl) btl = kc - k;
     const int bt = (int)btl;
     ++t;
     // line 5
-    sample_cta(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
-    // line 6: V = R(S_t, :), CGS2
-    for (long long e = tid; e < bt * n; e += kThreads) V[e] = R[(long long)sm.St[e / n] * n + e % n];
+    sample_cta<NT>(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
+    // line 6: V = R(S_t, :) projected against Q twice (CGS2)
+    project_rows<NT, RPW, false, false, T, T>(R, sm.St, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
     __syncthreads();
-    cgs<T>(V, bt, Q, k, n, C, kc);
-    cgs<T>(V, bt, Q, k, n, C, kc);
-    // lines 7-8: G = V V^T, pivoted Cholesky with the tail-mass truncation
-    {
-      T* Gt = Y;  // bt x bt scratch
-      rows_dot<T>(V, V, bt, bt, n, Gt, bt);
-      __syncthreads();
-      for (int e = tid; e < bt * bt; e += kThreads) sm.G[e / bt][e % bt] = (double)Gt[e];
+    if (k > 0) {
+      project_rows<NT, RPW, false, false, T, T>(V, nullptr, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
       __syncthreads();
     }
+    // lines 7-8: G = V V^T, pivoted Cholesky with the tail-mass truncation
+    gram_rows<NT, T>(V, bt, n, sm);
+    __syncthreads();
     const double tau_b = a.tau_b >= 0.0 ? a.tau_b : 1.0 / (double)bt;
     chol_warp<T>(sm, bt, tau_b, 1);
     const int bp = sm.bp;
     if (bp == 0) break;
     // lines 9-10, 13: Q'_V by CholQR of V(perm), a CGS pass against Q, a second CholQR
-    trsm_cols<T>(sm, V, sm.perm, Y, bp, n);
-    for (int i = tid; i < bp; i += kThreads) {
+    trsm_cols<NT, T>(sm, V, sm.perm, Y, bp, n);
+    for (int i = tid; i < bp; i += NT) {
       const long long row = sm.St[sm.perm[i]];
       skel[k + i] = row;
       mark[row] = (int)t;
     }
-    cgs<T>(Y, bp, Q, k, n, C, kc);
-    {
-      T* Gt = V;
-      rows_dot<T>(Y, Y, bp, bp, n, Gt, bp);
-      __syncthreads();
-      for (int e = tid; e < bp * bp; e += kThreads) sm.G[e / bp][e % bp] = (double)Gt[e];
-      __syncthreads();
-    }
+    if (k > 0) project_rows<NT, RPW, false, false, T, T>(Y, nullptr, Y, bp, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+    __syncthreads();
+    gram_rows<NT, T>(Y, bp, n, sm);
+    __syncthreads();
     chol_warp<T>(sm, bp, 0.0, 0);
     if (sm.bp < bp) {
       status = RBRP_ENONFINITE;
       break;
     }
-    trsm_cols<T>(sm, Y, nullptr, Q + k * n, bp, n);
-    for (long long e = tid; e < bp * n; e += kThreads) sQp[e] = Q[k * n + e];
+    trsm_cols<NT, T>(sm, Y, nullptr, Q + k * n, bp, n);
+    for (long long e = tid; e < bp * n; e += NT) sQp[e] = Q[k * n + e];
     __syncthreads();
-    // lines 12, 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2; accepted rows zeroed
-    for (long long i = w; i < m; i += kWarps) {
-      T x[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const long long c = lane + 32 * u;
-        x[u] = c < n ? R[i * n + c] : (T)0;
-      }
-      const bool acc = mark[i] != 0;
-      T lh[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (j >= bp) break;
-        T s = 0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const long long c = lane + 32 * u;
-          if (c < n) s += x[u] * sQp[j * n + c];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        lh[j] = s;
-      }
-      if (lane < bp) {
-        T mine = 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j == lane) mine = lh[j];
-        L[(k + lane) * m + i] = mine;
-      }
-      T nr = 0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const long long c = lane + 32 * u;
-        if (c >= n) continue;
-        T v = x[u];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j >= bp) break;
-          v -= lh[j] * sQp[j * n + c];
-        }
-        if (acc) v = (T)0;
-        R[i * n + c] = v;
-        nr += v * v;
-      }
-      const double nrd = warp_sum((double)nr);
-      if (lane == 0) d[i] = acc ? 0.0 : nrd;
-    }
+    // lines 12, 16 (residual form): Lhat = R Q'^T into L(:, k : k + b'), R -= Lhat Q',
+    // d_i = ||R_i||^2, rows accepted so far zeroed
+    project_rows<NT, RPW, true, true, T, T>(R, nullptr, R, m, n, sQp, bp, L + k * m, m, d, mark);
     __syncthreads();
-    double dp = 0.0;
-    for (long long i = tid; i < m; i += kThreads) dp += d[i];
-    D = block_sum(dp, sm);
+    D = rows_sum<NT>(m, sm, [&](long long i) { return d[i]; });
     k += bp;
     if (!isfinite(D)) {
       status = RBRP_ENONFINITE;
@@ -541,9 +552,9 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
   // Alg. 3: W L1 = L with L1 = L(S, :); W(S, :) = I.  Row i of W by back
   // substitution over the columns from the last, one thread per row.
   if (status != RBRP_ENONFINITE) {
-    for (long long e = tid; e < k * m; e += kThreads) Wt[e] = L[e];
+    for (long long e = tid; e < k * m; e += NT) Wt[e] = L[e];
     __syncthreads();
-    for (long long i = tid; i < m; i += kThreads) {
+    for (long long i = tid; i < m; i += NT) {
       for (long long jj = k - 1; jj >= 0; --jj) {
         const long long sj = skel[jj];
         const T wj = Wt[jj * m + i] / L[jj * m + sj];
@@ -553,12 +564,12 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
     }
     __syncthreads();
     double* Wp = a.W[p];
-    for (long long e = tid; e < m * k; e += kThreads) {
+    for (long long e = tid; e < m * k; e += NT) {
       const long long i = e / k, j = e % k;
       Wp[i * kc + j] = mark[i] ? 0.0 : (double)Wt[j * m + i];
     }
     __syncthreads();
-    for (long long j = tid; j < k; j += kThreads) Wp[skel[j] * kc + j] = 1.0;
+    for (long long j = tid; j < k; j += NT) Wp[skel[j] * kc + j] = 1.0;
   }
   if (tid == 0) {
     a.k_out[p] = k;
@@ -568,8 +579,8 @@ __device__ void solve_problem(const Args& a, int p, uint8_t* slotp, Smem& sm, T*
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_batched(Args a) {
+template <int NT, typename T>
+__global__ void __launch_bounds__(NT) k_batched(BatchedArgs a) {
   extern __shared__ __align__(16) uint8_t dyn[];
   Smem& sm = *(Smem*)dyn;
   T* sQp = (T*)(dyn + (sizeof(Smem) + 15) / 16 * 16);  // Q' (b' x n)
@@ -584,8 +595,14 @@ __global__ void __launch_bounds__(kThreads) k_batched(Args a) {
     const int p = s_p;
     __syncthreads();
     if (p < 0) break;
-    solve_problem<T>(a, p, slotp, sm, sQp);
+    solve_problem<NT, T>(a, p, slotp, sm, sQp);
   }
+}
+
+const void* pick(int threads, int fp64) {
+  if (threads == 256) return fp64 ? (const void*)k_batched<256, double> : (const void*)k_batched<256, float>;
+  if (threads == 512) return fp64 ? (const void*)k_batched<512, double> : (const void*)k_batched<512, float>;
+  return nullptr;
 }
 
 }  // namespace bt
@@ -596,56 +613,36 @@ size_t batched_slot_bytes(long long m_max, long long n_max, long long kc_max, in
   return bt::slot_layout(m_max, n_max, kc_max, b, fp64 ? 8 : 4).total;
 }
 
-int batched_ctas() {
+int batched_sms() {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return sms;
 }
 
-cudaError_t launch_batched(int P, const void* const* X_dev, const long long* rows_dev, const long long* cols_dev,
-                           const int* order_dev, long long* const* skel_dev, double* const* W_dev, long long* k_out,
-                           double* err, int* status, double tau, double tau_b, int b, int greedy, int x_is_fp64,
-                           long long k_max, unsigned long long seed, unsigned long long pbase, int fp64, void* slots, size_t slot_bytes,
-                           long long m_max, long long n_max, long long kc_max, unsigned int* next, int ctas,
-                           cudaStream_t s) {
-  bt::Args a;
-  a.P = P;
-  a.X = X_dev;
-  a.rows = rows_dev;
-  a.cols = cols_dev;
-  a.order = order_dev;
-  a.skel = skel_dev;
-  a.W = W_dev;
-  a.k_out = k_out;
-  a.err = err;
-  a.status = status;
-  a.tau = tau;
-  a.tau_b = tau_b;
-  a.b = b;
-  a.greedy = greedy;
-  a.x_is_fp64 = x_is_fp64;
-  a.k_max = k_max;
-  a.seed = seed;
-  a.pbase = pbase;
-  a.slots = (uint8_t*)slots;
-  a.slot_bytes = slot_bytes;
-  a.m_max = m_max;
-  a.n_max = n_max;
-  a.kc_max = kc_max;
-  a.next = next;
-  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned int), s);
+size_t batched_dyn_smem(long long n_max, int fp64) {
+  return (sizeof(bt::Smem) + 15) / 16 * 16 + (size_t)kBatchMaxBlock * n_max * (fp64 ? 8 : 4);
+}
+
+cudaError_t batched_configure(int threads, int fp64, long long n_max, int* per_sm) {
+  *per_sm = 0;
+  const void* f = bt::pick(threads, fp64);
+  if (!f) return cudaErrorInvalidValue;
+  const size_t dyn = batched_dyn_smem(n_max, fp64);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
-  const size_t dyn = (sizeof(bt::Smem) + 15) / 16 * 16 + (size_t)32 * n_max * (fp64 ? 8 : 4);
-  if (fp64) {
-    e = cudaFuncSetAttribute(bt::k_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-    bt::k_batched<double><<<ctas, bt::kThreads, dyn, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(bt::k_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-    bt::k_batched<float><<<ctas, bt::kThreads, dyn, s>>>(a);
-  }
-  return counted(cudaGetLastError());
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, threads, dyn);
+}
+
+cudaError_t launch_batched(const BatchedArgs& a, int threads, int ctas, cudaStream_t s) {
+  const void* f = bt::pick(threads, a.fp64);
+  if (!f || ctas < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(a.next, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  const size_t dyn = batched_dyn_smem(a.n_max, a.fp64);
+  BatchedArgs arg = a;
+  void* params[] = {&arg};
+  e = cudaLaunchKernel(f, dim3((unsigned)ctas), dim3((unsigned)threads), params, dyn, s);
+  return counted(e);
 }
 
 }  // namespace rbrp

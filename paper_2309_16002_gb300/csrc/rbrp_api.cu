@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "rbrp_internal.cuh"
@@ -648,8 +649,8 @@ rbrp_status rbrp_id(const void* X, int x_is_fp64, int64_t n, int64_t d, int64_t 
 namespace {
 
 struct BatchPlan {
-  long long m_max, n_max, kc_max;
-  int ctas, fp64;
+  long long m_max, n_max, kc_max, elems;
+  int slots, fp64;
   size_t off_X, off_rows, off_cols, off_order, off_skel, off_W, off_next, slot, off_slots, total;
 };
 
@@ -667,9 +668,11 @@ rbrp_status batch_plan(int32_t P, const int64_t* m, const int64_t* n, const rbrp
     bp->m_max = std::max<long long>(bp->m_max, m[p]);
     bp->n_max = std::max<long long>(bp->n_max, n[p]);
     bp->kc_max = std::max<long long>(bp->kc_max, kc);
+    bp->elems += (long long)m[p] * n[p];
   }
   bp->fp64 = (o->precision == RBRP_FP64);
-  bp->ctas = std::max(1, std::min<int>(P, batched_ctas()));
+  // one slot per CTA of the largest schedule (kBatchMaxCtasPerSm CTAs on every SM)
+  bp->slots = std::max(1, std::min<int>(P, batched_sms() * kBatchMaxCtasPerSm));
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o2 = off;
@@ -684,8 +687,70 @@ rbrp_status batch_plan(int32_t P, const int64_t* m, const int64_t* n, const rbrp
   bp->off_W = take((size_t)P * 8);
   bp->off_next = take(16);
   bp->slot = batched_slot_bytes(bp->m_max, bp->n_max, bp->kc_max, o->block, bp->fp64);
-  bp->off_slots = take((size_t)bp->ctas * bp->slot);
+  bp->off_slots = take((size_t)bp->slots * bp->slot);
   bp->total = off;
+  return RBRP_OK;
+}
+
+// Autotuner memory: the fastest schedule measured for a batch of this shape.
+struct TuneKey {
+  int fp64, block;
+  long long P, m_max, n_max, elems;
+  bool operator<(const TuneKey& o) const {
+    if (fp64 != o.fp64) return fp64 < o.fp64;
+    if (block != o.block) return block < o.block;
+    if (P != o.P) return P < o.P;
+    if (m_max != o.m_max) return m_max < o.m_max;
+    if (n_max != o.n_max) return n_max < o.n_max;
+    return elems < o.elems;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;
+
+bool tune_lookup(const TuneKey& k, int* threads, int* per_sm) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : g_tune_cache)
+    if (!(e.first < k) && !(k < e.first)) {
+      *threads = e.second.first;
+      *per_sm = e.second.second;
+      return true;
+    }
+  return false;
+}
+
+void tune_store(const TuneKey& k, int threads, int per_sm) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : g_tune_cache)
+    if (!(e.first < k) && !(k < e.first)) {
+      e.second = {threads, per_sm};
+      return;
+    }
+  g_tune_cache.push_back({k, {threads, per_sm}});
+}
+
+constexpr int kSchedThreads[] = {256, 512};
+
+}  // namespace
+
+struct rbrp_batch_s {
+  BatchPlan plan;
+  BatchedArgs args;  // tau set per run
+  TuneKey key;
+  int threads, per_sm, ctas;
+};
+
+namespace {
+
+// Makes (threads, per_sm) the handle's schedule if the kernel shape fits.
+rbrp_status apply_schedule(rbrp_batch_s* h, int threads, int per_sm) {
+  if (per_sm < 1 || per_sm > kBatchMaxCtasPerSm) return RBRP_EINVAL;
+  int fit = 0;
+  CK(batched_configure(threads, h->plan.fp64, h->plan.n_max, &fit));
+  if (fit < per_sm) return RBRP_EINVAL;
+  h->threads = threads;
+  h->per_sm = per_sm;
+  h->ctas = std::max(1, std::min<int>(h->plan.slots, batched_sms() * per_sm));
   return RBRP_OK;
 }
 
@@ -703,16 +768,17 @@ rbrp_status rbrp_batched_workspace_size(int32_t P, const int64_t* m, const int64
   return RBRP_OK;
 }
 
-rbrp_status rbrp_id_batched(int32_t P, const void* const* X, const int64_t* m, const int64_t* n, int x_is_fp64,
-                            double tol, const rbrp_opts* o, void* workspace, size_t ws_bytes, int64_t* const* skel,
-                            double* const* W, int64_t* k_out, double* rel_err_sq, int32_t* status,
-                            rbrp_stream_t stream) {
+rbrp_status rbrp_batch_create(int32_t P, const void* const* X, const int64_t* m, const int64_t* n, int x_is_fp64,
+                              const rbrp_opts* o, void* workspace, size_t ws_bytes, int64_t* const* skel,
+                              double* const* W, int64_t* k_out, double* rel_err_sq, int32_t* status,
+                              rbrp_stream_t stream, rbrp_batch* out) {
+  if (!out) return RBRP_EINVAL;
+  *out = nullptr;
   BatchPlan bp;
   rbrp_status rs = batch_plan(P, m, n, o, &bp);
   if (rs != RBRP_OK) return rs;
-  if (P == 0) return RBRP_OK;
+  if (P < 1) return RBRP_EINVAL;
   if (!X || !skel || !W || !k_out || !rel_err_sq || !status || !workspace) return RBRP_EINVAL;
-  if (!(tol < 1.0)) return RBRP_EINVAL;
   for (int32_t p = 0; p < P; ++p)
     if (!X[p] || !skel[p] || !W[p]) return RBRP_EINVAL;
   if (((uintptr_t)workspace & 255) != 0 || ws_bytes < bp.total) return RBRP_EWORKSPACE;
@@ -736,13 +802,130 @@ rbrp_status rbrp_id_batched(int32_t P, const void* const* X, const int64_t* m, c
   CK(cudaMemcpyAsync(ws + bp.off_W, W, (size_t)P * 8, cudaMemcpyHostToDevice, s));
   // (copies from pageable host memory return once the source has been read, so
   // the vectors above may be released on return)
-  CK(launch_batched(P, (const void* const*)(ws + bp.off_X), (const long long*)(ws + bp.off_rows),
-                    (const long long*)(ws + bp.off_cols), (const int*)(ws + bp.off_order),
-                    (long long* const*)(ws + bp.off_skel), (double* const*)(ws + bp.off_W), (long long*)k_out,
-                    rel_err_sq, (int*)status, tol, o->tau_b, o->block, o->sampler == RBRP_SAMPLER_GREEDY, x_is_fp64,
-                    o->k_max, o->seed, o->problem, bp.fp64, ws + bp.off_slots, bp.slot, bp.m_max, bp.n_max, bp.kc_max,
-                    (unsigned int*)(ws + bp.off_next), bp.ctas, s));
+  rbrp_batch_s* h = new (std::nothrow) rbrp_batch_s();
+  if (!h) return RBRP_ENOMEM;
+  h->plan = bp;
+  BatchedArgs& a = h->args;
+  a.P = P;
+  a.X = (const void* const*)(ws + bp.off_X);
+  a.rows = (const long long*)(ws + bp.off_rows);
+  a.cols = (const long long*)(ws + bp.off_cols);
+  a.order = (const int*)(ws + bp.off_order);
+  a.skel = (long long* const*)(ws + bp.off_skel);
+  a.W = (double* const*)(ws + bp.off_W);
+  a.k_out = (long long*)k_out;
+  a.err = rel_err_sq;
+  a.status = (int*)status;
+  a.tau = 0.0;
+  a.tau_b = o->tau_b;
+  a.b = o->block;
+  a.greedy = o->sampler == RBRP_SAMPLER_GREEDY;
+  a.x_is_fp64 = x_is_fp64 ? 1 : 0;
+  a.fp64 = bp.fp64;
+  a.k_max = o->k_max;
+  a.seed = o->seed;
+  a.pbase = o->problem;
+  a.slots = ws + bp.off_slots;
+  a.slot_bytes = bp.slot;
+  a.m_max = bp.m_max;
+  a.n_max = bp.n_max;
+  a.kc_max = bp.kc_max;
+  a.next = (unsigned int*)(ws + bp.off_next);
+  h->key = TuneKey{bp.fp64, o->block, (long long)P, bp.m_max, bp.n_max, bp.elems};
+  // schedule: the tuned one for this shape if any, else 256 threads, one CTA per SM
+  int th = 256, per = 1;
+  tune_lookup(h->key, &th, &per);
+  rs = apply_schedule(h, th, per);
+  if (rs != RBRP_OK) rs = apply_schedule(h, 256, 1);
+  if (rs != RBRP_OK) {
+    delete h;
+    return rs;
+  }
+  *out = h;
   return RBRP_OK;
+}
+
+rbrp_status rbrp_batch_set_schedule(rbrp_batch h, int32_t threads, int32_t ctas_per_sm) {
+  if (!h) return RBRP_EINVAL;
+  return apply_schedule(h, threads, ctas_per_sm);
+}
+
+rbrp_status rbrp_batch_get_schedule(rbrp_batch h, int32_t* threads, int32_t* ctas_per_sm, int32_t* ctas) {
+  if (!h) return RBRP_EINVAL;
+  if (threads) *threads = h->threads;
+  if (ctas_per_sm) *ctas_per_sm = h->per_sm;
+  if (ctas) *ctas = h->ctas;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_batch_run(rbrp_batch h, double tol, rbrp_stream_t stream) {
+  if (!h) return RBRP_EINVAL;
+  if (!(tol < 1.0)) return RBRP_EINVAL;
+  BatchedArgs a = h->args;
+  a.tau = tol;
+  CK(launch_batched(a, h->threads, h->ctas, (cudaStream_t)stream));
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_batch_autotune(rbrp_batch h, double tol, int32_t reps, rbrp_stream_t stream, float* best_ms) {
+  if (!h || reps < 1) return RBRP_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best_t = h->threads, best_p = h->per_sm;
+  float best = -1.f;
+  rbrp_status rs = RBRP_OK;
+  for (int th : kSchedThreads) {
+    for (int per = 1; per <= kBatchMaxCtasPerSm && rs == RBRP_OK; ++per) {
+      if (apply_schedule(h, th, per) != RBRP_OK) continue;  // shape does not fit
+      rs = rbrp_batch_run(h, tol, stream);                   // warm-up
+      cudaError_t e = cudaSuccess;
+      if (rs == RBRP_OK) e = cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && rs == RBRP_OK && e == cudaSuccess; ++r) rs = rbrp_batch_run(h, tol, stream);
+      if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        rs = RBRP_ECUDA;
+      }
+      if (rs == RBRP_OK && (best < 0.f || ms < best)) {
+        best = ms;
+        best_t = th;
+        best_p = per;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs != RBRP_OK) return rs;
+  rs = apply_schedule(h, best_t, best_p);
+  if (rs != RBRP_OK) return rs;
+  tune_store(h->key, best_t, best_p);
+  if (best_ms) *best_ms = best / (float)reps;
+  return RBRP_OK;
+}
+
+void rbrp_batch_destroy(rbrp_batch h) { delete h; }
+
+rbrp_status rbrp_id_batched(int32_t P, const void* const* X, const int64_t* m, const int64_t* n, int x_is_fp64,
+                            double tol, const rbrp_opts* o, void* workspace, size_t ws_bytes, int64_t* const* skel,
+                            double* const* W, int64_t* k_out, double* rel_err_sq, int32_t* status,
+                            rbrp_stream_t stream) {
+  if (P == 0) {
+    BatchPlan bp;
+    return batch_plan(P, m, n, o, &bp);
+  }
+  if (!(tol < 1.0)) return RBRP_EINVAL;
+  rbrp_batch h = nullptr;
+  rbrp_status rs = rbrp_batch_create(P, X, m, n, x_is_fp64, o, workspace, ws_bytes, skel, W, k_out, rel_err_sq,
+                                     status, stream, &h);
+  if (rs != RBRP_OK) return rs;
+  rs = rbrp_batch_run(h, tol, stream);
+  rbrp_batch_destroy(h);
+  return rs;
 }
 
 rbrp_status rbrp_host_workspace_size(int64_t n, int64_t d, int x_is_fp64, const rbrp_opts* o, size_t* bytes) {

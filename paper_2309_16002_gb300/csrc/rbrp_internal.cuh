@@ -222,16 +222,41 @@ cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float*
                              long long ldt, long long n, long long k, State* st, cudaStream_t s);
 
 // Batched form (k_batched.cu): one persistent launch over P small problems.
-size_t batched_slot_bytes(long long m_max, long long n_max, long long kc_max, int b, int fp64);
-int batched_ctas();
-cudaError_t launch_batched(int P, const void* const* X_dev, const long long* rows_dev, const long long* cols_dev,
-                           const int* order_dev, long long* const* skel_dev, double* const* W_dev, long long* k_out,
-                           double* err, int* status, double tau, double tau_b, int b, int greedy, int x_is_fp64,
-                           long long k_max, unsigned long long seed, unsigned long long pbase, int fp64, void* slots, size_t slot_bytes,
-                           long long m_max, long long n_max, long long kc_max, unsigned int* next, int ctas,
-                           cudaStream_t s);
 constexpr long long kBatchMaxRows = 4096;
 constexpr long long kBatchMaxCols = 256;
 constexpr int kBatchMaxBlock = 32;
+constexpr int kBatchMaxThreads = 512;
+constexpr int kBatchMaxCtasPerSm = 2;
+struct BatchedArgs {
+  int P;
+  const void* const* X;      // device array: problem p is m_p x n_p, row-major, ld = n_p
+  const long long* rows;     // m_p
+  const long long* cols;     // n_p
+  const int* order;          // processing order
+  long long* const* skel;    // device array: k_cap_p entries each
+  double* const* W;          // device array: m_p x k_cap_p FP64 each, ld = k_cap_p
+  long long* k_out;          // P
+  double* err;               // P: ||d||_1 / ||d0||_1
+  int* status;               // P: rbrp_status
+  double tau, tau_b;
+  int b, greedy, x_is_fp64, fp64;
+  long long k_max;
+  unsigned long long seed;
+  unsigned long long pbase;  // Philox problem id of problem 0
+  uint8_t* slots;            // per-CTA workspace slots
+  size_t slot_bytes;
+  long long m_max, n_max, kc_max;
+  unsigned int* next;        // work counter, zeroed by launch_batched
+};
+size_t batched_slot_bytes(long long m_max, long long n_max, long long kc_max, int b, int fp64);
+int batched_sms();
+size_t batched_dyn_smem(long long n_max, int fp64);
+// Sets the kernel's shared-memory limit for (threads, precision, n_max) and
+// reports how many such CTAs fit on one SM (0: the shape cannot run).
+cudaError_t batched_configure(int threads, int fp64, long long n_max, int* per_sm);
+// Zeroes the work counter and launches ctas CTAs of `threads` threads: two
+// stream operations and nothing else, so the call can be captured in a graph
+// (batched_configure must have run for this shape).
+cudaError_t launch_batched(const BatchedArgs& a, int threads, int ctas, cudaStream_t s);
 
 }  // namespace rbrp

@@ -27,7 +27,9 @@ RBRP_ENOTCONVERGED = 5
 
 EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_workspace_size", "rbrp_id_host",
            "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
-           "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched"]
+           "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched", "rbrp_batch_create",
+           "rbrp_batch_run", "rbrp_batch_autotune", "rbrp_batch_set_schedule", "rbrp_batch_get_schedule",
+           "rbrp_batch_destroy"]
 
 
 class Opts(ctypes.Structure):
@@ -95,6 +97,21 @@ def load():
                                   ctypes.POINTER(Opts), vp, sz, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp,
                                   vp]
     L.rbrp_id_batched.restype = ctypes.c_int
+    L.rbrp_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(vp), P64, P64, ctypes.c_int, ctypes.POINTER(Opts),
+                                    vp, sz, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp, vp,
+                                    ctypes.POINTER(vp)]
+    L.rbrp_batch_create.restype = ctypes.c_int
+    L.rbrp_batch_run.argtypes = [vp, dbl, vp]
+    L.rbrp_batch_run.restype = ctypes.c_int
+    L.rbrp_batch_autotune.argtypes = [vp, dbl, ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_float)]
+    L.rbrp_batch_autotune.restype = ctypes.c_int
+    L.rbrp_batch_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    L.rbrp_batch_set_schedule.restype = ctypes.c_int
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    L.rbrp_batch_get_schedule.argtypes = [vp, P32, P32, P32]
+    L.rbrp_batch_get_schedule.restype = ctypes.c_int
+    L.rbrp_batch_destroy.argtypes = [vp]
+    L.rbrp_batch_destroy.restype = None
     L.rbrp_profile_begin.argtypes = []
     L.rbrp_profile_begin.restype = None
     L.rbrp_profile_end.argtypes = [ctypes.POINTER(Profile)]
@@ -292,9 +309,15 @@ def as_numpy(t):
 
 
 class Batch:
-    """Preallocated outputs and workspace for repeated rbrp_id_batched calls on one list of problems."""
+    """One list of problems bound to preallocated outputs and workspace (rbrp_batch_* of include/rbrp.h).
 
-    def __init__(self, Xs, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random", problem=0):
+    run(tol, stream) queues one solve of every problem (a memset and one kernel
+    launch); graph(tol) captures that in a torch.cuda.CUDAGraph for replay;
+    tune(tol) times the kernel schedules and keeps the fastest.
+    """
+
+    def __init__(self, Xs, block=16, seed=0, precision="fp32", tau_b=-1.0, k_max=0, sampler="random", problem=0,
+                 stream=None, handle=True):
         import torch
         self.P = len(Xs)
         if self.P == 0:
@@ -310,8 +333,9 @@ class Batch:
         P = self.P
         self.m = (ctypes.c_int64 * P)(*[int(X.shape[0]) for X in Xs])
         self.n = (ctypes.c_int64 * P)(*[int(X.shape[1]) for X in Xs])
+        L = load()
         need = ctypes.c_size_t(0)
-        st = load().rbrp_batched_workspace_size(P, self.m, self.n, ctypes.byref(self.opts), ctypes.byref(need))
+        st = L.rbrp_batched_workspace_size(P, self.m, self.n, ctypes.byref(self.opts), ctypes.byref(need))
         _check(st, "rbrp_batched_workspace_size", allow_notconverged=False)
         self.need = need.value
         self.ws = torch.empty(self.need + 256, dtype=torch.uint8, device=dev)
@@ -326,16 +350,75 @@ class Batch:
         self.sp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in self.S])
         self.wpp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in self.W])
         self.device = dev
+        self._lib = L
+        self.h = None
+        if not handle:
+            return
+        s = self._stream(stream)
+        h = ctypes.c_void_p(0)
+        st = L.rbrp_batch_create(P, self.xp, self.m, self.n, self.fp64_in, ctypes.byref(self.opts),
+                                 ctypes.c_void_p(self.wp), self.need, self.sp, self.wpp,
+                                 ctypes.c_void_p(self.k_out.data_ptr()), ctypes.c_void_p(self.err.data_ptr()),
+                                 ctypes.c_void_p(self.status.data_ptr()), ctypes.c_void_p(s.cuda_stream),
+                                 ctypes.byref(h))
+        _check(st, "rbrp_batch_create", allow_notconverged=False)
+        self.h = h
+
+    def _stream(self, stream):
+        import torch
+        return stream if stream is not None else torch.cuda.current_stream(self.device)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self._lib.rbrp_batch_destroy(h)
+            self.h = None
 
     def run(self, tol, stream=None):
-        """Queue one batched call on the stream (no synchronisation)."""
-        import torch
-        s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        st = load().rbrp_id_batched(self.P, self.xp, self.m, self.n, self.fp64_in, float(tol), ctypes.byref(self.opts),
-                                    ctypes.c_void_p(self.wp), self.need, self.sp, self.wpp,
-                                    ctypes.c_void_p(self.k_out.data_ptr()), ctypes.c_void_p(self.err.data_ptr()),
-                                    ctypes.c_void_p(self.status.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+        """Queue one batched solve on the stream (no synchronisation)."""
+        st = self._lib.rbrp_batch_run(self.h, float(tol), ctypes.c_void_p(self._stream(stream).cuda_stream))
+        _check(st, "rbrp_batch_run", allow_notconverged=False)
+
+    def run_once(self, tol, stream=None):
+        """One solve through the single-call entry point rbrp_id_batched (no handle)."""
+        st = self._lib.rbrp_id_batched(self.P, self.xp, self.m, self.n, self.fp64_in, float(tol),
+                                       ctypes.byref(self.opts), ctypes.c_void_p(self.wp), self.need, self.sp,
+                                       self.wpp, ctypes.c_void_p(self.k_out.data_ptr()),
+                                       ctypes.c_void_p(self.err.data_ptr()), ctypes.c_void_p(self.status.data_ptr()),
+                                       ctypes.c_void_p(self._stream(stream).cuda_stream))
         _check(st, "rbrp_id_batched", allow_notconverged=False)
+
+    def graph(self, tol):
+        """A torch.cuda.CUDAGraph holding one solve at tol (replay() re-solves every problem)."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                self.run(float(tol), side)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        return g
+
+    def tune(self, tol, reps=2, stream=None):
+        """Time every schedule that fits, keep the fastest; returns the schedule and its ms per run."""
+        best = ctypes.c_float(0.0)
+        st = self._lib.rbrp_batch_autotune(self.h, float(tol), int(reps),
+                                           ctypes.c_void_p(self._stream(stream).cuda_stream), ctypes.byref(best))
+        _check(st, "rbrp_batch_autotune", allow_notconverged=False)
+        out = self.schedule()
+        out["ms"] = float(best.value)
+        return out
+
+    def schedule(self):
+        t, p, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self._lib.rbrp_batch_get_schedule(self.h, ctypes.byref(t), ctypes.byref(p), ctypes.byref(c)),
+               "rbrp_batch_get_schedule", allow_notconverged=False)
+        return dict(threads=t.value, ctas_per_sm=p.value, ctas=c.value)
+
+    def set_schedule(self, threads, ctas_per_sm):
+        _check(self._lib.rbrp_batch_set_schedule(self.h, int(threads), int(ctas_per_sm)), "rbrp_batch_set_schedule",
+               allow_notconverged=False)
 
     def results(self):
         ks, es, ss = self.k_out.tolist(), self.err.tolist(), self.status.tolist()
@@ -359,8 +442,8 @@ def rbrp_id_batched(Xs, tol, block=16, seed=0, precision="fp32", tau_b=-1.0, k_m
     import torch
     if len(Xs) == 0:
         return []
-    b = Batch(Xs, block, seed, precision, tau_b, k_max, sampler, problem)
+    b = Batch(Xs, block, seed, precision, tau_b, k_max, sampler, problem, handle=False)
     s = stream if stream is not None else torch.cuda.current_stream(b.device)
-    b.run(tol, s)
+    b.run_once(tol, s)
     s.synchronize()
     return b.results()

@@ -146,6 +146,51 @@ def test_batched_shards_with_problem_base_match_one_call(G, precision):
             assert np.array_equal(out["W"], ref["W"]), (lo + j)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_schedules_graph_and_autotune_agree(G, precision):
+    """Every kernel schedule, a CUDA-graph replay and the autotuned schedule give the one-shot results."""
+    import torch
+    dt = np.float64 if precision == "fp64" else np.float32
+    Xs = [torch.from_numpy(np.ascontiguousarray(X)).to("cuda:0") for X in _problems(dt)]
+    ref = G.rbrp_id_batched(Xs, 1e-6, block=8, seed=9, precision=precision)
+
+    def same(outs):
+        for p, (o, r) in enumerate(zip(outs, ref)):
+            assert o["k"] == r["k"] and o["status"] == r["status"], p
+            assert o["rel_err_sq"] == r["rel_err_sq"], p
+            assert torch.equal(o["S"], r["S"]) and torch.equal(o["W"], r["W"]), p
+
+    B = G.Batch(Xs, block=8, seed=9, precision=precision)
+    tried = 0
+    for threads in (256, 512):
+        for per_sm in (1, 2):
+            try:
+                B.set_schedule(threads, per_sm)
+            except G.RBRPError:
+                continue  # does not fit (FP64 at two CTAs per SM)
+            tried += 1
+            assert B.schedule()["threads"] == threads and B.schedule()["ctas_per_sm"] == per_sm
+            B.k_out.fill_(-1)
+            B.run(1e-6)
+            torch.cuda.synchronize()
+            same(B.results())
+    assert tried >= 2
+    with pytest.raises(G.RBRPError):
+        B.set_schedule(384, 1)
+    g = B.graph(1e-6)
+    B.k_out.fill_(-1)
+    B.err.fill_(-1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    same(B.results())
+    info = B.tune(1e-6, reps=1)
+    assert info["threads"] in (256, 512) and info["ctas_per_sm"] in (1, 2) and info["ms"] > 0
+    same(B.results())
+    # a new batch of the same shape starts from the tuned schedule
+    B2 = G.Batch(Xs, block=8, seed=9, precision=precision)
+    assert B2.schedule()["threads"] == info["threads"] and B2.schedule()["ctas_per_sm"] == info["ctas_per_sm"]
+
+
 def test_batched_nonfinite_and_limits(G):
     import torch
     X = np.ones((30, 6))
