@@ -80,6 +80,7 @@ struct Smem {
   unsigned int keys[kBatchMaxRows];
   unsigned int hist[kBins];
   unsigned long long ek[kCand];
+  double elg[kCand];  // log of each candidate's exact key
   int cand[kCand];
   int St[32];
   int perm[32];
@@ -223,28 +224,22 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
   for (int e = tid; e < mc; e += NT) {
     double lg;
     exact_key(d[sm.cand[e]], sm.cand[e], t, a.seed, p, a.greedy, &sm.ek[e], &lg);
+    sm.elg[e] = lg;
   }
+  if (tid == 0) sm.flag = (!overflow && mc >= bt) ? 0 : 1;
   __syncthreads();
+  const float outside = key_to_float(((c22 + 1u) << 10));
   for (int e = tid; e < mc; e += NT) {
     int rank = 0;
     const unsigned long long ke = sm.ek[e];
     const int ie = sm.cand[e];
     for (int f = 0; f < mc; ++f) rank += (sm.ek[f] < ke || (sm.ek[f] == ke && sm.cand[f] < ie)) ? 1 : 0;
     if (rank < bt) sm.St[rank] = ie;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    bool exact = !overflow && mc >= bt;
-    if (exact && (long long)mc < ne) {
-      // every row outside the cut has an FP32 key >= the smallest key above the cut;
-      // the bt-th exact key must lie below that by more than the FP32 error bound
-      double lg;
-      unsigned long long kk;
-      exact_key(d[sm.St[bt - 1]], sm.St[bt - 1], t, a.seed, p, a.greedy, &kk, &lg);
-      const float outside = key_to_float(((c22 + 1u) << 10));
-      exact = lg < (double)outside - (double)kCutGuard - 1e-6 * fabs((double)outside);
-    }
-    sm.flag = exact ? 0 : 1;
+    // every row outside the cut has an FP32 key >= the smallest key above the
+    // cut; the bt-th exact key must lie below that by more than the FP32 error bound
+    if (rank == bt - 1 && (long long)mc < ne &&
+        !(sm.elg[e] < (double)outside - (double)kCutGuard - 1e-6 * fabs((double)outside)))
+      sm.flag = 1;
   }
   __syncthreads();
   if (!sm.flag) return;
@@ -274,73 +269,83 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
 // Rows i < nrows of src (row-major, leading dimension n <= 256; row i read
 // from src row rowmap[i] when rowmap is given): c_ij = <src_i, B_j> for
 // j < nb, every c_ij from the original row (classical Gram-Schmidt), and
-// y_i = src_i - sum_j c_ij B_j with the terms subtracted in ascending j.
-// COEF: coef[j * ldc + i] = c_ij.  y_i goes to dst row i, zeroed when
-// mark && mark[i] != 0; NORM: dn[i] = ||y_i||^2 (0 for zeroed rows).  One warp
-// per group of RPW rows, whose loads are all issued before any arithmetic.
-// dst may alias src (each group is read completely before it is written).
-// No barrier inside; the caller synchronises.
-template <int NT, int RPW, bool COEF, bool NORM, typename T, typename TS>
+// y_i = src_i - sum_j c_ij B_j with the terms subtracted in ascending j
+// (BASIS = false: no basis, y_i = src_i).  COEF: coef[j * ldc + i] = c_ij.
+// y_i goes to dst row i, zeroed when mark && mark[i] != 0; NORM:
+// dn[i] = ||y_i||^2 (0 for zeroed rows), the per-lane partial sums and their
+// warp reduction in T.  One warp per group of RPW rows, whose loads are all
+// issued before any arithmetic.  dst may alias src (each group is read
+// completely before it is written).  STREAM: src is read once (the input X),
+// with evict-first loads so that it does not push the residuals of the
+// resident problems out of L2.  No barrier inside; the caller synchronises.
+template <int NT, int RPW, bool BASIS, bool COEF, bool NORM, typename T, typename TS, bool STREAM = false>
 __device__ void project_rows(const TS* src, const int* rowmap, T* dst, long long nrows, long long n, const T* B,
                              int nb, T* coef, long long ldc, double* dn, const int* mark) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long long i0 = (long long)w * RPW; i0 < nrows; i0 += (long long)NW * RPW) {
     T x[RPW][kRowVec], y[RPW][kRowVec];
+    bool zero[RPW];
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
       const long long i = i0 + r;
       const long long si = (i < nrows) ? (rowmap ? (long long)rowmap[i] : i) : 0;
+      zero[r] = mark && i < nrows && mark[i] != 0;  // read with the row, before any store of the group
 #pragma unroll
       for (int u = 0; u < kRowVec; ++u) {
         const long long c = lane + 32 * u;
-        x[r][u] = (i < nrows && c < n) ? (T)src[si * n + c] : (T)0;
+        if (i < nrows && c < n) x[r][u] = STREAM ? (T)__ldcs(src + si * n + c) : (T)src[si * n + c];
+        else x[r][u] = (T)0;
         y[r][u] = x[r][u];
       }
     }
-    for (int j = 0; j < nb; ++j) {
-      T q[kRowVec];
+    if (BASIS) {
+      for (int j = 0; j < nb; ++j) {
+        T q[kRowVec];
 #pragma unroll
-      for (int u = 0; u < kRowVec; ++u) {
-        const long long c = lane + 32 * u;
-        q[u] = c < n ? B[(long long)j * n + c] : (T)0;
-      }
-      T s[RPW];
+        for (int u = 0; u < kRowVec; ++u) {
+          const long long c = lane + 32 * u;
+          q[u] = c < n ? B[(long long)j * n + c] : (T)0;
+        }
+        T s[RPW];
 #pragma unroll
-      for (int r = 0; r < RPW; ++r) {
-        T acc = 0;
+        for (int r = 0; r < RPW; ++r) {
+          T acc = 0;
 #pragma unroll
-        for (int u = 0; u < kRowVec; ++u) acc += x[r][u] * q[u];
-        s[r] = acc;
-      }
+          for (int u = 0; u < kRowVec; ++u) acc += x[r][u] * q[u];
+          s[r] = acc;
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int r = 0; r < RPW; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
+          for (int r = 0; r < RPW; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
 #pragma unroll
-      for (int r = 0; r < RPW; ++r) {
+        for (int r = 0; r < RPW; ++r) {
 #pragma unroll
-        for (int u = 0; u < kRowVec; ++u) y[r][u] -= s[r] * q[u];
-        if (COEF && lane == 0 && i0 + r < nrows) coef[(long long)j * ldc + i0 + r] = s[r];
+          for (int u = 0; u < kRowVec; ++u) y[r][u] -= s[r] * q[u];
+          if (COEF && lane == 0 && i0 + r < nrows) coef[(long long)j * ldc + i0 + r] = s[r];
+        }
       }
     }
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
       const long long i = i0 + r;
       if (i >= nrows) break;
-      const bool zero = mark && mark[i] != 0;
       T nr = 0;
 #pragma unroll
       for (int u = 0; u < kRowVec; ++u) {
         const long long c = lane + 32 * u;
         if (c >= n) continue;
-        const T v = zero ? (T)0 : y[r][u];
+        const T v = zero[r] ? (T)0 : y[r][u];
         dst[i * n + c] = v;
         nr += v * v;
       }
       if (NORM) {
-        const double s = warp_sum((double)nr);
-        if (lane == 0) dn[i] = zero ? 0.0 : s;
+        // the warp reduction in T: on GB300 every FP64 warp instruction costs
+        // about 64 issue cycles, which made FP64 shuffles and adds the largest
+        // part of this pass
+        const T s = warp_sum(nr);
+        if (lane == 0) dn[i] = zero[r] ? 0.0 : (double)s;
       }
     }
   }
@@ -445,6 +450,77 @@ __device__ void trsm_cols(Smem& sm, const T* V, const int* perm, T* Y, int bp, l
   __syncthreads();
 }
 
+// Triangle of Alg. 3 inside one chunk of columns off .. off + kk - 1 (kk <= K):
+// w_j = (w_j - sum_{j < a < kk} w_a L1(off + a, off + j)) / L1(off + j, off + j),
+// from the last column; L1(a, b) = L1s[a * 32 + b].  Fully unrolled, so w
+// stays in registers.
+template <int K, typename T>
+__device__ __forceinline__ void tri_solve(T (&w)[K], int kk, const T* L1s, int off) {
+#pragma unroll
+  for (int j = K - 1; j >= 0; --j) {
+    if (j < kk) {
+      T acc = w[j];
+#pragma unroll
+      for (int a2 = j + 1; a2 < K; ++a2)
+        if (a2 < kk) acc -= w[a2] * L1s[(off + a2) * 32 + off + j];
+      w[j] = acc / L1s[(off + j) * 32 + off + j];
+    }
+  }
+}
+
+// wl_j -= sum_{a < kh} wh_a L1(offh + a, j) for j < K (the solved later chunk
+// applied to the earlier one).
+template <int K, typename T>
+__device__ __forceinline__ void chunk_sub(T (&wl)[K], const T (&wh)[K], int kh, const T* L1s, int offh) {
+#pragma unroll
+  for (int a2 = 0; a2 < K; ++a2) {
+    if (a2 < kh) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) wl[j] -= wh[a2] * L1s[(offh + a2) * 32 + j];
+    }
+  }
+}
+
+// Alg. 3 for k <= 32: w L1 = L(i, :) for every row i, with L1(a, b) =
+// L1s[a * 32 + b] lower triangular, solved from the last column,
+// w_j = (L(i, j) - sum_{a > j} w_a L1(a, j)) / L1(j, j); one thread per row, w
+// in registers (columns 16 .. k - 1 first when k > 16).  Rows of S get zeros
+// here (their unit entries are set afterwards).  W is written with streaming
+// stores (it is output only).
+template <int NT, typename T>
+__device__ void wsolve_rows(const T* L, long long m, int k, const T* L1s, const int* mark, double* Wp, long long kc) {
+  for (long long i = threadIdx.x; i < m; i += NT) {
+    const bool sk = mark[i] != 0;
+    if (k <= 8) {
+      T w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = (j < k) ? L[(long long)j * m + i] : (T)0;
+      tri_solve<8, T>(w, k, L1s, 0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < k) __stcs(Wp + i * kc + j, sk ? 0.0 : (double)w[j]);
+    } else {
+      const int kh = k > 16 ? k - 16 : 0;
+      T lo[16], hi[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        lo[j] = (j < k) ? L[(long long)j * m + i] : (T)0;
+        hi[j] = (j < kh) ? L[(long long)(16 + j) * m + i] : (T)0;
+      }
+      if (kh > 0) {
+        tri_solve<16, T>(hi, kh, L1s, 16);
+        chunk_sub<16, T>(lo, hi, kh, L1s, 16);
+      }
+      tri_solve<16, T>(lo, k < 16 ? k : 16, L1s, 0);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j < k) __stcs(Wp + i * kc + j, sk ? 0.0 : (double)lo[j]);
+        if (j < kh) __stcs(Wp + i * kc + 16 + j, sk ? 0.0 : (double)hi[j]);
+      }
+    }
+  }
+}
+
 // Sum over rows of a per-row value, in the fixed kSumLanes partition.
 template <int NT, typename F>
 __device__ double rows_sum(long long m, Smem& sm, F f) {
@@ -457,6 +533,7 @@ __device__ double rows_sum(long long m, Smem& sm, F f) {
 template <int NT, typename T>
 __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem& sm, T* sQp) {
   constexpr int RPW = sizeof(T) == 4 ? 4 : 2;  // rows per warp group in the row passes
+  constexpr int RPW0 = sizeof(T) == 4 ? 8 : 4;  // the same for the pass over X (no basis)
   const int tid = threadIdx.x;
   const long long m = a.rows[p], n = a.cols[p];
   long long kc = m < n ? m : n;
@@ -475,11 +552,11 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
 
   // Alg. 2 lines 1-2: R = X and d_i = ||X_i||^2 in one pass over X
   if (a.x_is_fp64)
-    project_rows<NT, RPW, false, true, T, double>((const double*)a.X[p], nullptr, R, m, n, (const T*)nullptr, 0,
-                                                  nullptr, 0, d, nullptr);
+    project_rows<NT, RPW0, false, false, true, T, double, true>((const double*)a.X[p], nullptr, R, m, n,
+                                                                (const T*)nullptr, 0, nullptr, 0, d, nullptr);
   else
-    project_rows<NT, RPW, false, true, T, float>((const float*)a.X[p], nullptr, R, m, n, (const T*)nullptr, 0,
-                                                 nullptr, 0, d, nullptr);
+    project_rows<NT, RPW0, false, false, true, T, float, true>((const float*)a.X[p], nullptr, R, m, n,
+                                                               (const T*)nullptr, 0, nullptr, 0, d, nullptr);
   for (long long i = tid; i < m; i += NT) mark[i] = 0;
   __syncthreads();
   const double D0 = rows_sum<NT>(m, sm, [&](long long i) { return d[i]; });
@@ -505,10 +582,10 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     // line 5
     sample_cta<NT>(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
     // line 6: V = R(S_t, :) projected against Q twice (CGS2)
-    project_rows<NT, RPW, false, false, T, T>(R, sm.St, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+    project_rows<NT, RPW, true, false, false, T, T>(R, sm.St, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
     __syncthreads();
     if (k > 0) {
-      project_rows<NT, RPW, false, false, T, T>(V, nullptr, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+      project_rows<NT, RPW, true, false, false, T, T>(V, nullptr, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
       __syncthreads();
     }
     // lines 7-8: G = V V^T, pivoted Cholesky with the tail-mass truncation
@@ -525,7 +602,8 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
       skel[k + i] = row;
       mark[row] = (int)t;
     }
-    if (k > 0) project_rows<NT, RPW, false, false, T, T>(Y, nullptr, Y, bp, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+    if (k > 0)
+      project_rows<NT, RPW, true, false, false, T, T>(Y, nullptr, Y, bp, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
     __syncthreads();
     gram_rows<NT, T>(Y, bp, n, sm);
     __syncthreads();
@@ -539,7 +617,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     __syncthreads();
     // lines 12, 16 (residual form): Lhat = R Q'^T into L(:, k : k + b'), R -= Lhat Q',
     // d_i = ||R_i||^2, rows accepted so far zeroed
-    project_rows<NT, RPW, true, true, T, T>(R, nullptr, R, m, n, sQp, bp, L + k * m, m, d, mark);
+    project_rows<NT, RPW, true, true, true, T, T>(R, nullptr, R, m, n, sQp, bp, L + k * m, m, d, mark);
     __syncthreads();
     D = rows_sum<NT>(m, sm, [&](long long i) { return d[i]; });
     k += bp;
@@ -549,9 +627,21 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     }
   }
 
-  // Alg. 3: W L1 = L with L1 = L(S, :); W(S, :) = I.  Row i of W by back
-  // substitution over the columns from the last, one thread per row.
-  if (status != RBRP_ENONFINITE) {
+  // Alg. 3: W L1 = L with L1 = L(S, :); W(S, :) = I.
+  if (status != RBRP_ENONFINITE && k <= 32) {
+    T* L1s = (T*)&sm.Lw[0][0];  // L1 as a 32 x 32 array of T
+    for (long long e = tid; e < k * k; e += NT) {
+      const long long a2 = e / k, b2 = e % k;
+      L1s[a2 * 32 + b2] = L[b2 * m + skel[a2]];
+    }
+    __syncthreads();
+    double* Wp = a.W[p];
+    wsolve_rows<NT, T>(L, m, (int)k, L1s, mark, Wp, kc);
+    __syncthreads();
+    for (long long j = tid; j < k; j += NT) Wp[skel[j] * kc + j] = 1.0;
+  } else if (status != RBRP_ENONFINITE) {
+    // k > 32: row i of W by back substitution over the columns from the last,
+    // one thread per row, through a column-major scratch copy of L
     for (long long e = tid; e < k * m; e += NT) Wt[e] = L[e];
     __syncthreads();
     for (long long i = tid; i < m; i += NT) {

@@ -82,13 +82,30 @@ cudaError_t launch_init_norms(const void* X, int x_is_fp64, long long n, long lo
 }
 
 // Deterministic warp sum of partials[0..np) (fixed lane assignment and tree).
-__device__ __forceinline__ double warp_fixed_sum(const double* partials, int np) {
-  const int lane = threadIdx.x & 31;
+// Sum of np partials in a fixed order (independent of timing), by a CTA of
+// kFixedSumThreads threads; every thread gets the result.  Thread t adds
+// partials t, t + 256, ... in order (eight loads in flight), then the warps'
+// sums are combined in warp order.
+constexpr int kFixedSumThreads = 256;
+__device__ __forceinline__ double block_fixed_sum(const double* partials, int np) {
+  __shared__ double red[kFixedSumThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31;
   double s = 0.0;
-  for (int i = lane; i < np; i += 32) s += partials[i];
+  for (int i0 = tid; i0 < np; i0 += 8 * kFixedSumThreads) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (i0 + u * kFixedSumThreads < np) ? partials[i0 + u * kFixedSumThreads] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
+  if (lane == 0) red[tid >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kFixedSumThreads / 32; ++w) t += red[w];
+  return t;
 }
 
 __device__ __forceinline__ void stop_test(State* st) {
@@ -99,7 +116,7 @@ __device__ __forceinline__ void stop_test(State* st) {
 
 __global__ void k_finish_init(const double* __restrict__ partials, int np, State* st, double tau, double tau_b,
                               long long k_cap) {
-  const double D0 = warp_fixed_sum(partials, np);
+  const double D0 = block_fixed_sum(partials, np);
   if (threadIdx.x == 0) {
     st->tau = tau;
     st->tau_b = tau_b;
@@ -124,7 +141,7 @@ __global__ void k_finish_init(const double* __restrict__ partials, int np, State
 
 cudaError_t launch_finish_init(const double* partials, int nparts, State* st, double tau, double tau_b,
                                long long k_cap, cudaStream_t s) {
-  k_finish_init<<<1, 32, 0, s>>>(partials, nparts, st, tau, tau_b, k_cap);
+  k_finish_init<<<1, kFixedSumThreads, 0, s>>>(partials, nparts, st, tau, tau_b, k_cap);
   return counted(cudaGetLastError());
 }
 
@@ -504,7 +521,7 @@ cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n
 // Alg. 2 line 3 after a block: D = ||d||_1, k += b', t += 1, stopping test.
 __global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st) {
   if (st->done) return;
-  const double D = warp_fixed_sum(partials, np);
+  const double D = block_fixed_sum(partials, np);
   if (threadIdx.x == 0) {
     st->D = D;
     st->k += st->bp;
@@ -519,7 +536,7 @@ __global__ void k_finalize_block(const double* __restrict__ partials, int np, St
 }
 
 cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s) {
-  k_finalize_block<<<1, 32, 0, s>>>(partials, nparts, st);
+  k_finalize_block<<<1, kFixedSumThreads, 0, s>>>(partials, nparts, st);
   return counted(cudaGetLastError());
 }
 

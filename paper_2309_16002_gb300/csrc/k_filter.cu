@@ -470,9 +470,179 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
   }
 }
 
+// The same filter for blocks of at most 64 candidates, built around latency.
+// One warp runs the pivot loop: lane l owns candidates l and l + 32 (factor
+// rows in shared memory, d_j in registers); the pivot is two warp reductions
+// (redux.sync max over the FP32 bit patterns of d_j, which order like the
+// values for d_j >= 0, then min over the indices of the maxima: the largest
+// d_j, ties to the smaller index) and no block barrier; the trailing mass of
+// Alg. 2 line 8 is a shuffle reduction that runs beside them, and the two
+// candidates' dot products share one loop over the pivot's factor row.  The
+// inverse is column substitution with the column in registers: thread c
+// holds column c of Lc^{-1} and applies x_i = b_i / Lc(i, i),
+// b_r -= Lc(r, i) x_i for r > i, fully unrolled over the 64 rows so that every
+// thread runs the same instruction stream (entries above the diagonal stay
+// zero without a branch on c).
+constexpr int kPchol64 = 64;
+constexpr int kPchol64Threads = 64;
+constexpr int kPchol64LDF = 68;  // factor rows: float4 steps over t
+constexpr int kPchol64LDG = 65;  // G rows: odd stride, conflict-free column reads
+
+__global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* __restrict__ G, long long ldg,
+                                                                  float* __restrict__ Linv, long long ldl,
+                                                                  int* __restrict__ perm,
+                                                                  const long long* __restrict__ S_t,
+                                                                  long long* __restrict__ skel,
+                                                                  int* __restrict__ mark, State* st) {
+  if (st->done) return;
+  __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];   // Lw[j * LDF + t]: candidate j, step t
+  __shared__ __align__(16) float Gs[kPchol64 * kPchol64LDG];   // G, later the pivot-order factor
+  __shared__ float rdg[kPchol64];
+  __shared__ int s_perm[kPchol64];
+  __shared__ int s_bp;
+  const int m = (int)st->b_t;
+  const int tid = threadIdx.x, lane = tid & 31;
+  {
+    float v[kPchol64];
+#pragma unroll
+    for (int r = 0; r < kPchol64; ++r) v[r] = (r < m && tid < m) ? G[(long long)r * ldg + tid] : 0.f;
+#pragma unroll
+    for (int r = 0; r < kPchol64; ++r) Gs[r * kPchol64LDG + tid] = v[r];
+  }
+  for (int e = tid; e < kPchol64 * kPchol64LDF; e += kPchol64Threads) Lw[e] = 0.f;
+  __syncthreads();
+  if (tid < 32) {
+    double tau_b = st->tau_b;
+    if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+    const float tb = (float)tau_b;
+    const int j0 = lane, j1 = lane + 32;
+    bool al0 = j0 < m, al1 = j1 < m;
+    float d0 = al0 ? Gs[j0 * kPchol64LDG + j0] : 0.f;
+    float d1 = al1 ? Gs[j1 * kPchol64LDG + j1] : 0.f;
+    float total = d0 + d1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    const float* lj0 = Lw + j0 * kPchol64LDF;
+    const float* lj1 = Lw + j1 * kPchol64LDF;
+    int steps = 0;
+    for (int i = 0; i < m; ++i) {
+      // trailing mass of the remaining candidates (its shuffles overlap the pivot search)
+      float msum = (al0 ? d0 : 0.f) + (al1 ? d1 : 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
+      // pivot: the largest remaining d_j (> 0), ties to the smaller index
+      const float v0 = (al0 && d0 > 0.f) ? d0 : 0.f, v1 = (al1 && d1 > 0.f) ? d1 : 0.f;
+      const bool second = v1 > v0;
+      const unsigned bits = __float_as_uint(second ? v1 : v0);
+      const unsigned mx = __reduce_max_sync(0xffffffffu, bits);
+      if (mx == 0u) break;  // no positive pivot left
+      const unsigned mine = (bits == mx) ? (unsigned)(second ? j1 : j0) : 0xffffffffu;
+      const int p = (int)__reduce_min_sync(0xffffffffu, mine);
+      const float best = __uint_as_float(mx);
+      const float rinv = rsqrtf(best);
+      // both candidates' dot products over steps < i in one loop (the pivot's
+      // factor row is loaded once); rows past m are zero
+      const float* lp = Lw + p * kPchol64LDF;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+      for (int t = 0; t < i; t += 4) {  // entries past step i - 1 are still zero
+        const float4 y = *(const float4*)(lp + t);
+        const float4 x = *(const float4*)(lj0 + t);
+        const float4 z = *(const float4*)(lj1 + t);
+        a0 = fmaf(x.x, y.x, a0);
+        a1 = fmaf(x.y, y.y, a1);
+        a2 = fmaf(x.z, y.z, a2);
+        a3 = fmaf(x.w, y.w, a3);
+        c0 = fmaf(z.x, y.x, c0);
+        c1 = fmaf(z.y, y.y, c1);
+        c2 = fmaf(z.z, y.z, c2);
+        c3 = fmaf(z.w, y.w, c3);
+      }
+      if (!(msum >= tb * total && msum > 0.f)) break;  // Alg. 2 line 8: b' = i
+      const float l0 = (Gs[j0 * kPchol64LDG + p] - ((a0 + a1) + (a2 + a3))) * rinv;
+      const float l1 = (Gs[j1 * kPchol64LDG + p] - ((c0 + c1) + (c2 + c3))) * rinv;
+      if (al0) {
+        if (j0 == p) {
+          Lw[j0 * kPchol64LDF + i] = best * rinv;
+          al0 = false;
+        } else {
+          Lw[j0 * kPchol64LDF + i] = l0;
+          d0 -= l0 * l0;
+        }
+      }
+      if (al1) {
+        if (j1 == p) {
+          Lw[j1 * kPchol64LDF + i] = best * rinv;
+          al1 = false;
+        } else {
+          Lw[j1 * kPchol64LDF + i] = l1;
+          d1 -= l1 * l1;
+        }
+      }
+      if (lane == 0) {
+        rdg[i] = rinv;
+        s_perm[i] = p;
+      }
+      __syncwarp();
+      steps = i + 1;
+    }
+    if (lane == 0) s_bp = steps;
+  }
+  __syncthreads();
+  const int bp = s_bp;
+  // pivot-order factor over G (no longer needed), one row per thread; zero
+  // outside 0 <= l <= i < b'
+  {
+    const int i = tid;
+    const float* src = Lw + (i < bp ? s_perm[i] : 0) * kPchol64LDF;
+#pragma unroll 16
+    for (int l = 0; l < kPchol64; ++l) Gs[i * kPchol64LDG + l] = (l <= i && i < bp) ? src[l] : 0.f;
+  }
+  for (int i = bp + tid; i < kPchol64; i += kPchol64Threads) rdg[i] = 0.f;
+  __syncthreads();
+  {
+    const int c = tid;
+    float x[kPchol64];
+#pragma unroll
+    for (int r = 0; r < kPchol64; ++r) x[r] = (r == c) ? 1.f : 0.f;
+#pragma unroll
+    for (int i = 0; i < kPchol64; ++i) {
+      const float xi = x[i] * rdg[i];
+      x[i] = xi;
+#pragma unroll
+      for (int r = i + 1; r < kPchol64; ++r) x[r] = fmaf(-Gs[r * kPchol64LDG + i], xi, x[r]);
+    }
+    if (c < bp) {
+#pragma unroll
+      for (int i = 0; i < kPchol64; ++i)
+        if (i < bp) Linv[(long long)i * ldl + c] = (c <= i) ? x[i] : 0.f;
+    }
+  }
+  {
+    const long long k = st->k;
+    const int tno = (int)(st->t + 1);
+    for (int i = tid; i < bp; i += kPchol64Threads) {
+      const int pi = s_perm[i];
+      if (perm) perm[i] = pi;
+      const long long row = S_t[pi];
+      skel[k + i] = row;
+      mark[row] = tno;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    st->bp = bp;
+    st->bp_pad = (bp + 15) / 16 * 16;
+    if (bp == 0) st->done = 1;
+  }
+}
+
 cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
   if (b > kRegCholMax) return cudaErrorInvalidValue;
+  if (b <= kPchol64) {
+    k_pchol_f32_64<<<1, kPchol64Threads, 0, s>>>(G, ldg, Linv, ldl, perm, S_t, skel, mark, st);
+    return counted(cudaGetLastError());
+  }
   const int ldf = (b + 4) & ~3;
   const size_t smem = (size_t)2 * b * ldf * sizeof(float);
   if (smem > 48 * 1024) {

@@ -12,6 +12,7 @@
 // order and applies C = alpha * sum + beta * C.  The sum
 // order is fixed, so results do not depend on CTA scheduling, and no separate
 // reduction launch is needed.  Counters are reset by the CTA that used them.
+#include <cooperative_groups.h>
 #include <limits.h>
 
 #include <algorithm>
@@ -71,32 +72,22 @@ __device__ __forceinline__ void ld_vec(const T* p, T (&v)[R]) {
   }
 }
 
-// TS: storage type of A, B, C; TACC: products, per-CTA sums, partials and
-// their sum.  BKC: B is N x K with K contiguous (C = A B^T); otherwise K x N
-// with N contiguous (C = A B, optionally with gathered rows).
+// The product of one TILE x TILE output tile over K range [kb, ke): thread
+// (tx, ty) accumulates rows m0 + ty R + i, columns n0 + tx R + j in acc.
+// TS: storage type of A, B; TACC: products and sums.  BKC: B is N x K with K
+// contiguous (C = A B^T); otherwise K x N with N contiguous (C = A B,
+// optionally with gathered rows).
 template <typename TS, typename TACC, bool BKC, int TILE>
-__global__ void __launch_bounds__(256) k_sgemm(SgemmArgs g) {
+__device__ __forceinline__ void tile_product(const SgemmArgs& g, const TS* A, const TS* B, long long M, long long N,
+                                             long long m0, long long n0, long long kb, long long ke,
+                                             TACC (*As)[TILE + 4], TACC (*Bs)[TILE + 4],
+                                             TACC (&acc)[TILE / 16][TILE / 16]) {
   constexpr int R = TILE / 16;              // outputs per thread along each axis
-  constexpr int LD = TILE + 4;              // padded shared-memory row
   constexpr int VN = Vec16<TS>::N;          // elements per 16-byte load
   constexpr int VPR = KS / VN;              // loads per K-row of a K-contiguous tile
   constexpr int NL = TILE * VPR / 256;      // loads per thread per operand and step
   static_assert(NL >= 1 && TILE * VPR % 256 == 0, "tile");
-  if (g.st && g.st->done) return;
-  const long long M = dim_val(g.M), N = dim_val(g.N), K = dim_val(g.K);
-  const long long m0 = (long long)blockIdx.y * TILE, n0 = (long long)blockIdx.x * TILE;
-  if (m0 >= M || n0 >= N) return;
-  const TS* A = (const TS*)g.A + dim_val(g.a_off);
-  const TS* B = (const TS*)g.B + dim_val(g.b_off);
-  TS* C = (TS*)g.C + dim_val(g.c_off);
-  const long long kb = (long long)blockIdx.z * g.kc;
-  const long long ke = (kb + g.kc < K) ? kb + g.kc : K;
-
-  __shared__ __align__(16) TACC As[KS][LD];
-  __shared__ __align__(16) TACC Bs[KS][LD];
-  __shared__ int s_last;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  TACC acc[R][R];
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
@@ -153,6 +144,27 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs g) {
         for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
   }
+}
+
+template <typename TS, typename TACC, bool BKC, int TILE>
+__global__ void __launch_bounds__(256) k_sgemm(SgemmArgs g) {
+  constexpr int R = TILE / 16;
+  constexpr int LD = TILE + 4;
+  if (g.st && g.st->done) return;
+  const long long M = dim_val(g.M), N = dim_val(g.N), K = dim_val(g.K);
+  const long long m0 = (long long)blockIdx.y * TILE, n0 = (long long)blockIdx.x * TILE;
+  if (m0 >= M || n0 >= N) return;
+  const TS* A = (const TS*)g.A + dim_val(g.a_off);
+  const TS* B = (const TS*)g.B + dim_val(g.b_off);
+  TS* C = (TS*)g.C + dim_val(g.c_off);
+  const long long kb = (long long)blockIdx.z * g.kc;
+  const long long ke = (kb + g.kc < K) ? kb + g.kc : K;
+  __shared__ __align__(16) TACC As[KS][LD];
+  __shared__ __align__(16) TACC Bs[KS][LD];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  TACC acc[R][R];
+  tile_product<TS, TACC, BKC, TILE>(g, A, B, M, N, m0, n0, kb, ke, As, Bs, acc);
 
   const TS alpha = (TS)g.alpha, beta = (TS)g.beta;
   const int splits = (int)gridDim.z;
@@ -229,9 +241,116 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs g) {
   if (tid == 0) g.cnt[t] = 0u;
 }
 
+// FP32 accumulation with the K splits of a tile as one thread-block cluster
+// (cluster rank = split index, gridDim.z = cluster size CS in {2, 4, 8, 16}):
+// each CTA leaves its partial tile in shared memory; after a cluster barrier
+// CTA r sums rows [r 64 / CS, (r + 1) 64 / CS) of the tile over the cluster's
+// CTAs in rank order through distributed shared memory and writes them, and a
+// second barrier keeps every CTA's shared memory alive until all have read
+// it.  The sum order is fixed, and nothing goes through global memory but the
+// operands and the result.
+template <typename TS, bool BKC>
+__global__ void __launch_bounds__(256) k_sgemm_cl(SgemmArgs g) {
+  constexpr int TILE = 64, R = TILE / 16, LD = TILE + 4, LP = TILE + 1;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  // every early exit below is taken by all CTAs of a cluster (same tile, same State)
+  if (g.st && g.st->done) return;
+  const long long M = dim_val(g.M), N = dim_val(g.N), K = dim_val(g.K);
+  const long long m0 = (long long)blockIdx.y * TILE, n0 = (long long)blockIdx.x * TILE;
+  if (m0 >= M || n0 >= N) return;
+  const TS* A = (const TS*)g.A + dim_val(g.a_off);
+  const TS* B = (const TS*)g.B + dim_val(g.b_off);
+  TS* C = (TS*)g.C + dim_val(g.c_off);
+  const long long kb = (long long)blockIdx.z * g.kc;
+  const long long ke = (kb + g.kc < K) ? kb + g.kc : K;
+  __shared__ __align__(16) float As[KS][LD];
+  __shared__ __align__(16) float Bs[KS][LD];
+  __shared__ float P[TILE * LP];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[R][R];
+  tile_product<TS, float, BKC, TILE>(g, A, B, M, N, m0, n0, kb, ke, As, Bs, acc);
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) P[(ty * R + i) * LP + tx * R + j] = acc[i][j];
+  cluster.sync();
+  const int cs = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int rows = TILE / cs;
+  const TS alpha = (TS)g.alpha, beta = (TS)g.beta;
+  for (int e = tid; e < rows * TILE; e += 256) {
+    const int r = rank * rows + e / TILE, c = e % TILE;
+    float v = 0.f;
+    for (int z = 0; z < cs; ++z) v += cluster.map_shared_rank(P, z)[r * LP + c];
+    const long long gm = m0 + r, gn = n0 + c;
+    if (gm < M && gn < N) {
+      TS* cp = C + gm * g.ldc + gn;
+      TS w = alpha * (TS)v;
+      if (g.beta != 0.0) w += beta * *cp;
+      *cp = w;
+    }
+  }
+  cluster.sync();
+}
+
 }  // namespace
 
 int sgemm_tile(int acc_fp64) { return acc_fp64 ? 32 : 64; }
+
+// Cluster size (power of two, <= 16) for FP32 split-K products: about
+// `target` CTAs over the (Mmax x Nmax) tiles of 64, and K per split a
+// multiple of KS.
+void sgemm_cluster(long long Mmax, long long Nmax, long long Kmax, long long target, int* cs, int* kc) {
+  const long long tiles = ((Mmax + 63) / 64) * ((Nmax + 63) / 64);
+  int c = 1;
+  while (c < 16 && tiles * c < target && (long long)(c * 2) * KS <= std::max<long long>(Kmax, KS)) c *= 2;
+  long long k = (Kmax + c - 1) / c;
+  k = std::max<long long>(KS, (k + KS - 1) / KS * KS);
+  *cs = c;
+  *kc = (int)k;
+}
+
+template <typename TS, bool BKC>
+cudaError_t launch_sgemm_cluster(const SgemmArgs& g, long long Mmax, long long Nmax, int cs, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_sgemm_cl<TS, BKC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((Nmax + 63) / 64), (unsigned)((Mmax + 63) / 64), (unsigned)cs);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = (unsigned)cs;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cs > 8) {
+    // 16 CTAs per cluster is beyond the portable size: use it only where the
+    // device can hold such a cluster (asked once per process), else two
+    // splits per CTA
+    static int ok16 = -1;
+    if (ok16 < 0) {
+      int nclusters = 0;
+      ok16 = (cudaOccupancyMaxActiveClusters(&nclusters, k_sgemm_cl<TS, BKC>, &cfg) == cudaSuccess && nclusters >= 1);
+      (void)cudaGetLastError();
+    }
+    if (!ok16) {
+      SgemmArgs g2 = g;
+      g2.kc = g.kc * 2;
+      at[0].val.clusterDim.z = 8;
+      cfg.gridDim.z = 8;
+      return counted(cudaLaunchKernelEx(&cfg, k_sgemm_cl<TS, BKC>, g2));
+    }
+  }
+  return counted(cudaLaunchKernelEx(&cfg, k_sgemm_cl<TS, BKC>, g));
+}
+
+template cudaError_t launch_sgemm_cluster<float, true>(const SgemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_sgemm_cluster<float, false>(const SgemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_sgemm_cluster<double, true>(const SgemmArgs&, long long, long long, int, cudaStream_t);
+template cudaError_t launch_sgemm_cluster<double, false>(const SgemmArgs&, long long, long long, int, cudaStream_t);
 
 // K per split (multiple of KS) and the resulting number of splits for about
 // `target` CTAs over the (Mmax x Nmax) tiles.

@@ -317,6 +317,15 @@ cudaError_t sgemm(const Plan& p, const Bufs& u, const void* A, DimRef a_off, lon
   g.cnt = u.cnt;
   g.st = u.st;
   const int acc64 = sizeof(TACC) == 8;
+  if (!acc64) {
+    // FP32 accumulation: split-K reduced inside a thread-block cluster
+    int cs = 1, kcl = 32;
+    sgemm_cluster(Mmax, Nmax, Kmax, 160, &cs, &kcl);
+    if (cs > 1) {
+      g.kc = kcl;
+      return launch_sgemm_cluster<TS, BKC>(g, Mmax, Nmax, cs, s);
+    }
+  }
   const int tile = sgemm_tile(acc64);
   int splits = 1, kc = 32;
   sgemm_splits(Mmax, Nmax, Kmax, tile, acc64 ? 608 : 160, &splits, &kc);

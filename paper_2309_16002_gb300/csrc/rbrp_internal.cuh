@@ -197,6 +197,11 @@ cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long lon
 template <typename TS, typename TACC, bool BKC>
 cudaError_t launch_sgemm(const SgemmArgs& g, long long Mmax, long long Nmax, int splits, cudaStream_t s);
 int sgemm_tile(int acc_fp64);
+// FP32-accumulating products with the K splits of a tile as one thread-block
+// cluster (cs in {2, 4, 8, 16}) reduced through distributed shared memory.
+void sgemm_cluster(long long Mmax, long long Nmax, long long Kmax, long long target, int* cs, int* kc);
+template <typename TS, bool BKC>
+cudaError_t launch_sgemm_cluster(const SgemmArgs& g, long long Mmax, long long Nmax, int cs, cudaStream_t s);
 void sgemm_splits(long long Mmax, long long Nmax, long long Kmax, int tile, long long target, int* splits,
                   int* kc);
 constexpr int kSgemmCounters = 4096;
