@@ -51,8 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU baseline run (0: all rows)")
     ap.add_argument("--ref-rows", type=int, default=20000, help="row sample per step of the reference arm")
-    ap.add_argument("--workload", default="zipf_gmm", choices=["zipf_gmm", "kernel_blocks"],
-                    help="kernel_blocks: the batched workload (one rbrp_id_batched launch per step)")
+    ap.add_argument("--workload", default="zipf_gmm", choices=["zipf_gmm", "kernel_blocks", "gmm_fixed_rank"],
+                    help="kernel_blocks: the batched workload (one rbrp_id_batched launch per step); "
+                         "gmm_fixed_rank: the adversarial GMM of Sec. 4 at fixed ranks (context for the "
+                         "paper's GPU table)")
+    ap.add_argument("--ranks", default="52,100,220,346,472", help="gmm_fixed_rank: the fixed ranks k")
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched workload")
     ap.add_argument("--no-fp64-form", action="store_true", help="batched workload: skip the FP64 form")
     ap.add_argument("--single-sample", type=int, default=128,
@@ -441,10 +444,68 @@ def run_batched(a):
         torch.distributed.destroy_process_group()
 
 
+# RBRP-ID times of the paper's GPU table (V100, cuBLAS + MAGMA, precision not
+# stated, block size not stated) on the 1e5 x 1e3 adversarial GMM, in seconds,
+# by fixed rank: context only (other hardware, other precision).
+PAPER_GPU_RBRP_S = {52: 4.448e-2, 100: 7.231e-2, 220: 1.073e-1, 346: 1.336e-1, 472: 1.596e-1}
+
+
+def run_fixed_rank(a):
+    """The adversarial GMM of Sec. 4 (means 10 j e_j, identity covariance, 100 clusters of
+    1000 points, 1e5 x 1e3, FP32 storage) at fixed ranks k (tol < 0, k_max = k), TF32 and
+    FP64 forms, each k timed with CUDA events over a few steps."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2309_16002_gb300 import rbrp as G
+    from paper_2309_16002_gb300 import workloads as WL
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X = WL.gmm_pitfall(n=a.n, d=a.d, k=100, seed=6, dtype=np.float32)
+    Xd = torch.from_numpy(X).to(dev)
+    s = torch.cuda.current_stream(dev)
+    ks = [int(x) for x in a.ranks.split(",") if x]
+    rows = []
+    for prec, wprec in (("tf32", "fp32"), ("fp64", "fp64")):
+        kmax = max(ks)
+        opts = G.make_opts(a.block, prec, -1.0, kmax, 0, 0, "random", wprec)
+        wsp = G.Workspace(a.n, a.d, opts, dev)
+        for k in ks:
+            kw = dict(block=a.block, seed=0, precision=prec, w_precision=wprec, k_max=k)
+            steps = max(1, a.steps if prec == "tf32" else min(a.steps, 3))
+            for _ in range(max(1, min(a.warmup, 2))):
+                out = G.rbrp_id(Xd, -1.0, workspace=wsp, stream=s, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                out = G.rbrp_id(Xd, -1.0, workspace=wsp, stream=s, **kw)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            paper = PAPER_GPU_RBRP_S.get(k)
+            rows.append({"precision": prec, "k": k, "k_out": out["k"], "ms": ms, "rel_err_sq": out["rel_err_sq"],
+                         "paper_v100_ms": paper * 1e3 if paper else None})
+        del wsp
+        torch.cuda.empty_cache()
+    line = {"metric": "ID time at fixed rank (ms), adversarial GMM 1e5 x 1e3", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "tf32+f64 / f64",
+            "config": {"workload": "gmm_fixed_rank", "n": a.n, "d": a.d, "clusters": 100, "means": "10 j e_j",
+                       "block": a.block, "seed": 0},
+            "value": next(r["ms"] for r in rows if r["precision"] == "tf32"), "ranks": rows,
+            "note": "paper_v100_ms: the paper's RBRP-ID GPU times (V100, cuBLAS + MAGMA), other hardware and "
+                    "precision; context, not a target"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.workload == "kernel_blocks":
         run_batched(a)
+        return
+    if a.workload == "gmm_fixed_rank":
+        run_fixed_rank(a)
         return
     if a.impl == "reference":
         run_reference(a)

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
                                                                   int* __restrict__ mark, State* st) {
   if (st->done) return;
   __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];   // Lw[j * LDF + t]: candidate j, step t
-  __shared__ __align__(16) float Gs[kPchol64 * kPchol64LDG];   // G, later the pivot-order factor
+  __shared__ __align__(16) float Gs[kPchol64 * kPchol64LDF];   // G (stride LDG), later the factor transposed (LDF)
   __shared__ float rdg[kPchol64];
   __shared__ int s_perm[kPchol64];
   __shared__ int s_bp;
@@ -544,6 +544,7 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
       // factor row is loaded once); rows past m are zero
       const float* lp = Lw + p * kPchol64LDF;
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll 4
       for (int t = 0; t < i; t += 4) {  // entries past step i - 1 are still zero
         const float4 y = *(const float4*)(lp + t);
         const float4 x = *(const float4*)(lj0 + t);
@@ -589,13 +590,15 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
   }
   __syncthreads();
   const int bp = s_bp;
-  // pivot-order factor over G (no longer needed), one row per thread; zero
-  // outside 0 <= l <= i < b'
+  // the pivot-order factor Lc, transposed, over G (no longer needed):
+  // LT[l][i] = Lc(i, l) = Lw[perm[i]][l] for l <= i < b', zero elsewhere; one
+  // factor row per thread
+  float* LT = Gs;
   {
     const int i = tid;
     const float* src = Lw + (i < bp ? s_perm[i] : 0) * kPchol64LDF;
 #pragma unroll 16
-    for (int l = 0; l < kPchol64; ++l) Gs[i * kPchol64LDG + l] = (l <= i && i < bp) ? src[l] : 0.f;
+    for (int l = 0; l < kPchol64; ++l) LT[l * kPchol64LDF + i] = (l <= i && i < bp) ? src[l] : 0.f;
   }
   for (int i = bp + tid; i < kPchol64; i += kPchol64Threads) rdg[i] = 0.f;
   __syncthreads();
@@ -608,8 +611,15 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
     for (int i = 0; i < kPchol64; ++i) {
       const float xi = x[i] * rdg[i];
       x[i] = xi;
+      // x_r -= Lc(r, i) x_i for r > i, four rows of column i per load
 #pragma unroll
-      for (int r = i + 1; r < kPchol64; ++r) x[r] = fmaf(-Gs[r * kPchol64LDG + i], xi, x[r]);
+      for (int r4 = (i + 1) & ~3; r4 < kPchol64; r4 += 4) {
+        const float4 v = *(const float4*)(LT + i * kPchol64LDF + r4);
+        if (r4 + 0 > i) x[r4 + 0] = fmaf(-v.x, xi, x[r4 + 0]);
+        if (r4 + 1 > i) x[r4 + 1] = fmaf(-v.y, xi, x[r4 + 1]);
+        if (r4 + 2 > i) x[r4 + 2] = fmaf(-v.z, xi, x[r4 + 2]);
+        if (r4 + 3 > i) x[r4 + 3] = fmaf(-v.w, xi, x[r4 + 3]);
+      }
     }
     if (c < bp) {
 #pragma unroll
