@@ -60,7 +60,13 @@ typedef enum {
 
 typedef enum {
   RBRP_SAMPLER_RANDOM = 0,  /* Alg. 2 line 5: sample ~ d/||d||_1 without replacement */
-  RBRP_SAMPLER_GREEDY = 1   /* blockwise greedy remark (Sec. 4): top-b of d          */
+  RBRP_SAMPLER_GREEDY = 1,  /* blockwise greedy remark (Sec. 4): top-b of d          */
+  /* The same draws as RANDOM / GREEDY (identical S_t), always computed by the
+   * single-stage exact sampler (FP64 keys of every eligible row, ranked in full)
+   * instead of the FP32 cut with its exact check: a slower reference form, also
+   * the path the fast sampler falls back to when its check fails.              */
+  RBRP_SAMPLER_RANDOM_EXACT = 2,
+  RBRP_SAMPLER_GREEDY_EXACT = 3
 } rbrp_sampler;
 
 typedef enum {

@@ -181,10 +181,52 @@ __device__ __forceinline__ void exact_key(double di, long long i, unsigned long 
   }
 }
 
+template <int NT>
+__device__ void sample_cut(const double* d, const int* mark, long long m, int bt, long long ne, unsigned long long t,
+                           const BatchedArgs& a, unsigned long long p, Smem& sm);
+
 // S_t (bt rows, in draw order) into sm.St.  ne = number of eligible rows.
+// The two-stage draw, or (a.exact, or when its check fails) the full ranking.
 template <int NT>
 __device__ void sample_cta(const double* d, const int* mark, long long m, int bt, long long ne, unsigned long long t,
                            const BatchedArgs& a, unsigned long long p, unsigned long long* K64, Smem& sm) {
+  const int tid = threadIdx.x;
+  if (a.exact) {
+    if (tid == 0) sm.flag = 1;
+    __syncthreads();
+  } else {
+    sample_cut<NT>(d, mark, m, bt, ne, t, a, p, sm);
+  }
+  if (!sm.flag) return;
+  // full ranking: FP64 keys of every eligible row, ranked by counting
+  for (long long i = tid; i < m; i += NT) {
+    unsigned long long k = kIneligible;
+    if (mark[i] == 0 && d[i] > 0.0) {
+      double lg;
+      exact_key(d[i], i, t, a.seed, p, a.greedy, &k, &lg);
+    }
+    K64[i] = k;
+  }
+  __syncthreads();
+  for (long long i = tid; i < m; i += NT) {
+    const unsigned long long ki = K64[i];
+    if (ki == kIneligible) continue;
+    long long rank = 0;
+    for (long long j = 0; j < m && rank < bt; ++j) {
+      const unsigned long long kj = K64[j];
+      rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+    }
+    if (rank < bt) sm.St[rank] = (int)i;
+  }
+  __syncthreads();
+}
+
+// The two-stage draw: FP32 keys, a 2 x 11-bit radix cut keeping >= bt + kMargin
+// candidates, their exact keys ranked; sm.flag = 1 when the margin check
+// fails or the candidates overflow (the caller then ranks every row).
+template <int NT>
+__device__ void sample_cut(const double* d, const int* mark, long long m, int bt, long long ne, unsigned long long t,
+                           const BatchedArgs& a, unsigned long long p, Smem& sm) {
   const int tid = threadIdx.x;
   for (long long i = tid; i < m; i += NT) {
     const bool elig = mark[i] == 0 && d[i] > 0.0;
@@ -240,28 +282,6 @@ __device__ void sample_cta(const double* d, const int* mark, long long m, int bt
     if (rank == bt - 1 && (long long)mc < ne &&
         !(sm.elg[e] < (double)outside - (double)kCutGuard - 1e-6 * fabs((double)outside)))
       sm.flag = 1;
-  }
-  __syncthreads();
-  if (!sm.flag) return;
-  // fallback: FP64 keys of every eligible row, ranked by counting
-  for (long long i = tid; i < m; i += NT) {
-    unsigned long long k = kIneligible;
-    if (mark[i] == 0 && d[i] > 0.0) {
-      double lg;
-      exact_key(d[i], i, t, a.seed, p, a.greedy, &k, &lg);
-    }
-    K64[i] = k;
-  }
-  __syncthreads();
-  for (long long i = tid; i < m; i += NT) {
-    const unsigned long long ki = K64[i];
-    if (ki == kIneligible) continue;
-    long long rank = 0;
-    for (long long j = 0; j < m && rank < bt; ++j) {
-      const unsigned long long kj = K64[j];
-      rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
-    }
-    if (rank < bt) sm.St[rank] = (int)i;
   }
   __syncthreads();
 }

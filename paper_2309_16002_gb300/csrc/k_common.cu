@@ -167,9 +167,11 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
                                                        Pair* __restrict__ out, int b, int greedy,
                                                        unsigned long long seed, unsigned long long problem,
                                                        long long* __restrict__ S_t, State* st, int first,
-                                                       int last) {
-  // exact FP64 sampler: runs only when the two-stage sampler asked for it
-  if (st->done || !st->sample_fallback) return;
+                                                       int last, int force) {
+  // exact FP64 sampler: runs when the two-stage sampler asked for it, or always
+  // (force, on the first level, which then raises the flag for the later levels)
+  if (st->done || (!force && !st->sample_fallback)) return;
+  if (force && blockIdx.x == 0 && threadIdx.x == 0 && !last) st->sample_fallback = 1;
   __shared__ Pair sh[kSortChunk];
   const unsigned long long block_no = (unsigned long long)st->t + 1ULL;  // the paper's t
   const long long base = (long long)blockIdx.x * kSortChunk;
@@ -244,19 +246,19 @@ size_t sample_scratch_pairs(long long n, int b) {
 
 cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
                           unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
-                          State* st, cudaStream_t s) {
+                          State* st, int force, cudaStream_t s) {
   long long groups = (n + kSortChunk - 1) / kSortChunk;
   Pair* bufs[2] = {(Pair*)cand_a, (Pair*)cand_b};
   int cur = 0;
   k_sample_level<<<(unsigned)groups, 1024, 0, s>>>(dvec, n, nullptr, 0, bufs[cur], b, greedy, seed, problem,
-                                                   S_t, st, 1, groups == 1 ? 1 : 0);
+                                                   S_t, st, 1, groups == 1 ? 1 : 0, force);
   cudaError_t e = counted(cudaGetLastError());
   if (e != cudaSuccess) return e;
   while (groups > 1) {
     const long long n_in = groups * b;
     groups = (n_in + kSortChunk - 1) / kSortChunk;
     k_sample_level<<<(unsigned)groups, 1024, 0, s>>>(dvec, n, bufs[cur], n_in, bufs[cur ^ 1], b, greedy, seed,
-                                                     problem, S_t, st, 0, groups == 1 ? 1 : 0);
+                                                     problem, S_t, st, 0, groups == 1 ? 1 : 0, 0);
     e = counted(cudaGetLastError());
     if (e != cudaSuccess) return e;
     cur ^= 1;

@@ -63,7 +63,7 @@ cudaError_t timed(EventPool& pool, cudaStream_t s, F&& body) {
 
 struct Plan {
   long long n, d, k_cap;
-  int b, prec, r64, l64, w32, greedy, f32;
+  int b, prec, r64, l64, w32, greedy, f32, exact_sampler;
   long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32, ldt;
   int nparts;
   int s_upd1, s_upd2;
@@ -92,7 +92,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   if (!o || n <= 0 || d <= 0) return RBRP_EINVAL;
   if (o->block < 1 || o->block > kMaxBlock) return RBRP_EINVAL;
   if (o->precision < RBRP_FP64 || o->precision > RBRP_TF32X3) return RBRP_EINVAL;
-  if (o->sampler != RBRP_SAMPLER_RANDOM && o->sampler != RBRP_SAMPLER_GREEDY) return RBRP_EINVAL;
+  if (o->sampler < RBRP_SAMPLER_RANDOM || o->sampler > RBRP_SAMPLER_GREEDY_EXACT) return RBRP_EINVAL;
   if (o->w_precision != RBRP_W_FP64 && o->w_precision != RBRP_W_FP32) return RBRP_EINVAL;
   if (o->tau_b > 1.0) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
@@ -111,7 +111,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->l64 = p->r64;
   p->w32 = (o->w_precision == RBRP_W_FP32);
   p->f32 = (o->precision == RBRP_TF32);  // FP32 storage for the per-block chain
-  p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY);
+  p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
+  p->exact_sampler = (o->sampler == RBRP_SAMPLER_RANDOM_EXACT || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
   p->ldr = round_up(d, 32);
   p->ldq = round_up(d, 32);
   p->ldl = round_up(kc, 8);
@@ -382,8 +383,8 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     if (e != cudaSuccess) return e;  \
   } while (0)
   // line 5: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it)
-  LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
-  LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, s));
+  if (!p.exact_sampler) LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
+  LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, p.exact_sampler, s));
   // line 6: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
   LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
   // (one pass on the plain TF32 path: the sampled residual rows are orthogonal
@@ -667,7 +668,7 @@ rbrp_status batch_plan(int32_t P, const int64_t* m, const int64_t* n, const rbrp
   if (P < 0 || !o || !bp || (P > 0 && (!m || !n))) return RBRP_EINVAL;
   if (o->block < 1 || o->block > kBatchMaxBlock || o->tau_b > 1.0) return RBRP_EINVAL;
   if (o->precision < RBRP_FP64 || o->precision > RBRP_TF32X3) return RBRP_EINVAL;
-  if (o->sampler != RBRP_SAMPLER_RANDOM && o->sampler != RBRP_SAMPLER_GREEDY) return RBRP_EINVAL;
+  if (o->sampler < RBRP_SAMPLER_RANDOM || o->sampler > RBRP_SAMPLER_GREEDY_EXACT) return RBRP_EINVAL;
   memset(bp, 0, sizeof(*bp));
   bp->m_max = bp->n_max = bp->kc_max = 1;
   for (int32_t p = 0; p < P; ++p) {
@@ -828,7 +829,8 @@ rbrp_status rbrp_batch_create(int32_t P, const void* const* X, const int64_t* m,
   a.tau = 0.0;
   a.tau_b = o->tau_b;
   a.b = o->block;
-  a.greedy = o->sampler == RBRP_SAMPLER_GREEDY;
+  a.greedy = (o->sampler == RBRP_SAMPLER_GREEDY || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
+  a.exact = (o->sampler == RBRP_SAMPLER_RANDOM_EXACT || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
   a.x_is_fp64 = x_is_fp64 ? 1 : 0;
   a.fp64 = bp.fp64;
   a.k_max = o->k_max;

@@ -144,7 +144,7 @@ cudaError_t launch_finish_init(const double* partials, int nparts, State* st, do
                                long long k_cap, cudaStream_t s);
 cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
                           unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
-                          State* st, cudaStream_t s);
+                          State* st, int force, cudaStream_t s);
 size_t sample_scratch_pairs(long long n, int b);
 // Two-stage sampler (k_sample.cu): FP32 log-domain cut + exact FP64 ranking of
 // the candidates; sets State::sample_fallback when the exact tree sampler
@@ -244,7 +244,7 @@ struct BatchedArgs {
   double* err;               // P: ||d||_1 / ||d0||_1
   int* status;               // P: rbrp_status
   double tau, tau_b;
-  int b, greedy, x_is_fp64, fp64;
+  int b, greedy, exact, x_is_fp64, fp64;  // exact: always the full FP64 ranking
   long long k_max;
   unsigned long long seed;
   unsigned long long pbase;  // Philox problem id of problem 0

@@ -19,7 +19,7 @@ _LIBPATH = os.path.join(_HERE, "librbrp.so")
 _lib = None
 
 PRECISIONS = {"fp64": 0, "tf32": 1, "fp32": 2, "tf32x3": 3}
-SAMPLERS = {"random": 0, "greedy": 1}
+SAMPLERS = {"random": 0, "greedy": 1, "random_exact": 2, "greedy_exact": 3}
 W_PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "non-finite value",
           5: "not converged", 6: "timeout", 7: "workspace"}

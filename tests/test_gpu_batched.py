@@ -191,6 +191,25 @@ def test_batch_schedules_graph_and_autotune_agree(G, precision):
     assert B2.schedule()["threads"] == info["threads"] and B2.schedule()["ctas_per_sm"] == info["ctas_per_sm"]
 
 
+@pytest.mark.parametrize("sampler", ["random_exact", "greedy_exact", "greedy"])
+def test_batched_exact_sampler_and_tie_fallback(G, sampler):
+    """The full FP64 ranking (forced, or reached when 2000 tied greedy keys overflow the
+    candidate list) draws the oracle's skeletons (FP64, problem by problem)."""
+    rng = np.random.default_rng(13)
+    ties = np.zeros((2000, 40))
+    for i in range(2000):
+        cols = rng.choice(40, size=4, replace=False)
+        ties[i, cols] = rng.choice([-1.0, 1.0], size=4)
+    Xs = _problems(np.float64)[:6] + [ties]
+    outs = _run(G, Xs, 1e-6, block=8, seed=2, precision="fp64", sampler=sampler)
+    base = sampler.replace("_exact", "")
+    for p, (X, out) in enumerate(zip(Xs, outs)):
+        ref = O.rbrp_id(X, tau=1e-6, b=8, seed=2, problem=p, sampler=base)
+        if out["S"].tolist() != ref["S"].tolist():
+            gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
+            assert gaps and min(gaps) < NEAR_TIE, (p, out["S"][:10], ref["S"][:10])
+
+
 def test_batched_nonfinite_and_limits(G):
     import torch
     X = np.ones((30, 6))

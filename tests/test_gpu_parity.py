@@ -261,3 +261,38 @@ def test_tf32_zipf_gmm_full_size(G):
     assert out["k"] <= 1.1 * len(ref["S"]) + 64, (out["k"], len(ref["S"]))
     assert np.array_equal(out["W"][out["S"]], np.eye(out["k"]))
     assert out["rel_err_sq"] <= tol
+
+
+# ------------------------------------------------------------------ exact sampler forms
+def _equal_norm_rows(n=3000, d=40, nz=4, seed=12):
+    """Rows with exactly nz entries of +-1 (every squared norm is exactly nz, in any
+    summation order): the blockwise greedy keys all tie, so the two-stage sampler's FP32
+    cut keeps every row, overflows its candidate list and falls back to the exact sampler."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, d))
+    for i in range(n):
+        cols = rng.choice(d, size=nz, replace=False)
+        X[i, cols] = rng.choice([-1.0, 1.0], size=nz)
+    return X
+
+
+@pytest.mark.parametrize("sampler", ["random", "greedy"])
+def test_fp64_exact_sampler_form_draws_the_same(G, sampler):
+    """RBRP_SAMPLER_*_EXACT (always the single-stage FP64 sampler) gives the two-stage
+    sampler's skeletons and the oracle's (Alg. 2 line 5, reading R2)."""
+    X, _ = WL.spectral(n=2500, d=120, rate=0.93, seed=3)
+    fast = _run(G, X, 1e-6, block=16, seed=4, precision="fp64", sampler=sampler)
+    exact = _run(G, X, 1e-6, block=16, seed=4, precision="fp64", sampler=sampler + "_exact")
+    assert exact["S"].tolist() == fast["S"].tolist()
+    ref = O.rbrp_id(X, tau=1e-6, b=16, seed=4, sampler=sampler)
+    _assert_fp64_parity(X, ref, exact)
+
+
+def test_fp64_greedy_ties_take_the_fallback(G):
+    """All greedy keys tie in the first block: the candidate list overflows and the exact
+    tree sampler draws; the ties go to the smaller row, as in the oracle."""
+    X = _equal_norm_rows()
+    out = _run(G, X, 1e-3, block=16, seed=0, precision="fp64", sampler="greedy")
+    ref = O.rbrp_id(X, tau=1e-3, b=16, seed=0, sampler="greedy")
+    assert out["S"][:1].tolist() == [0]
+    _assert_fp64_parity(X, ref, out)
