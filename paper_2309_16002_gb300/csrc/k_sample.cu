@@ -15,6 +15,8 @@
 //     State::sample_fallback and the exact FP64 tree sampler in k_common.cu
 //     runs instead.
 // The histogram buffers are cleared by the final kernel for the next block.
+// Where the device supports cooperative launches the four passes run as one
+// launch (k_sample_coop) with grid barriers between them.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -267,6 +269,177 @@ __global__ void k_samp_clear(unsigned int* __restrict__ hist1, unsigned int* __r
     hist1[j] = 0;
     hist2[j] = 0;
   }
+  if (threadIdx.x < 16) ncand[threadIdx.x] = 0;  // the count, and the grid barrier words
+}
+
+// ---------------------------------------------------------------- one cooperative launch
+// The same four passes in one launch of one CTA per SM (cooperative, so all
+// CTAs are resident), separated by grid barriers instead of kernel
+// boundaries: keys + first histogram | second histogram | compaction with
+// exact keys | ranking, margin check and S_t by CTA 0.  Results are those of
+// the four kernels above (same keys, cut, candidates and ranking).
+constexpr int kCoopThreads = 512;
+constexpr unsigned kBarSpins = 1u << 22;  // ~2 s at 512 ns a poll, then the barrier gives up
+
+// Grid barrier over gridDim.x CTAs: arrival counter bar[0] (reset by the last
+// arriver) and generation bar[1].  The wait is bounded: on timeout the CTA
+// records RBRP_ETIMEOUT in the State and carries on (every CTA still passes
+// every barrier, so no CTA is left waiting).
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, State* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int gen0 = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned int spins = 0;
+      while (*vgen == gen0) {
+        if (++spins > kBarSpins) {
+          st->status = RBRP_ETIMEOUT;
+          st->done = 1;
+          break;
+        }
+        __nanosleep(512);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __restrict__ dvec, long long n,
+                                                              unsigned int* __restrict__ K32,
+                                                              unsigned int* __restrict__ hist1,
+                                                              unsigned int* __restrict__ hist2, int want,
+                                                              int* __restrict__ cand,
+                                                              unsigned long long* __restrict__ cand_key,
+                                                              double* __restrict__ cand_log,
+                                                              unsigned int* __restrict__ ncand, int cap, int b,
+                                                              int greedy, unsigned long long seed,
+                                                              unsigned long long problem, long long* __restrict__ S_t,
+                                                              State* st) {
+  if (st->done) return;  // read before any CTA writes the State: the same for every CTA
+  __shared__ unsigned int h[kBins];
+  unsigned int* bar = ncand + 2;
+  const unsigned long long block_no = (unsigned long long)st->t + 1ULL;
+  const long long gstride = (long long)gridDim.x * kCoopThreads;
+  const long long g0 = (long long)blockIdx.x * kCoopThreads + threadIdx.x;
+  // pass 1: keys and the histogram of their top 11 bits
+  for (int j = threadIdx.x; j < kBins; j += kCoopThreads) h[j] = 0;
+  __syncthreads();
+  for (long long i = g0; i < n; i += gstride) {
+    const unsigned int k = approx_key(dvec[i], i, block_no, seed, problem, greedy);
+    K32[i] = k;
+    if (k != 0xFFFFFFFFu) atomicAdd(&h[k >> 21], 1u);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kBins; j += kCoopThreads)
+    if (h[j]) atomicAdd(&hist1[j], h[j]);
+  grid_barrier(bar, st);
+  // pass 2: histogram of the next 11 bits inside the cut bin
+  unsigned int below1, total1;
+  const int b1 = find_bin(hist1, (unsigned int)want, &below1, &total1);
+  if (b1 < kBins) {
+    for (int j = threadIdx.x; j < kBins; j += kCoopThreads) h[j] = 0;
+    __syncthreads();
+    for (long long i = g0; i < n; i += gstride) {
+      const unsigned int k = K32[i];
+      if ((int)(k >> 21) == b1 && k != 0xFFFFFFFFu) atomicAdd(&h[(k >> 10) & 0x7FF], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kBins; j += kCoopThreads)
+      if (h[j]) atomicAdd(&hist2[j], h[j]);
+  }
+  grid_barrier(bar, st);
+  // pass 3: candidates with their exact FP64 keys
+  unsigned int c22 = 0x3FFFFFu;
+  if (b1 < kBins) {
+    unsigned int below2, total2;
+    const int b2 = find_bin(hist2, (unsigned int)(want - (int)below1), &below2, &total2);
+    c22 = ((unsigned int)b1 << 11) | (unsigned int)(b2 >= kBins ? kBins - 1 : b2);
+  }
+  for (long long i = g0; i < n; i += gstride) {
+    const unsigned int k = K32[i];
+    if (k != 0xFFFFFFFFu && (k >> 10) <= c22) {
+      const unsigned int pos = atomicAdd(ncand, 1u);
+      if ((int)pos < cap) {
+        const double di = dvec[i];
+        double key, lg;
+        if (greedy) {
+          key = -di;
+          lg = -log(di);
+        } else {
+          const double u = philox_uniform((unsigned long long)i, block_no, seed, problem);
+          key = -log(u) / di;
+          lg = log(key);
+        }
+        cand[pos] = (int)i;
+        cand_key[pos] = orderable(key);
+        cand_log[pos] = lg;
+      }
+    }
+  }
+  grid_barrier(bar, st);
+  if (blockIdx.x != 0) return;
+  // pass 4 (CTA 0): rank the candidates, check the margin, write S_t and b_t
+  __shared__ unsigned long long ek[kSampCap];
+  __shared__ int eidx[kSampCap];
+  __shared__ double elog[kSampCap];
+  __shared__ long long sorted_idx[kMaxBlock];
+  __shared__ double sorted_log[kMaxBlock];
+  const int nc = (int)*ncand;
+  const bool overflow = nc > cap;
+  const int m = overflow ? 0 : nc;
+  for (int e = threadIdx.x; e < m; e += kCoopThreads) {  // written by other CTAs: read from L2
+    ek[e] = __ldcg(cand_key + e);
+    eidx[e] = __ldcg(cand + e);
+    elog[e] = __ldcg(cand_log + e);
+  }
+  __syncthreads();
+  long long bt = (long long)total1;
+  if (bt > b) bt = b;
+  const long long room = st->k_cap - st->k;
+  if (bt > room) bt = room;
+  if (bt < 0) bt = 0;
+  for (int e = threadIdx.x; e < m; e += kCoopThreads) {
+    int rank = 0;
+    const unsigned long long ke = ek[e];
+    const int ie = eidx[e];
+    for (int f = 0; f < m; ++f) rank += (ek[f] < ke || (ek[f] == ke && eidx[f] < ie)) ? 1 : 0;
+    if (rank < bt) {
+      sorted_idx[rank] = ie;
+      sorted_log[rank] = elog[e];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !st->done) {
+    bool exact = !overflow && m >= bt;
+    if (exact && bt > 0 && (long long)m < (long long)total1 && c22 != 0x3FFFFFu) {
+      // every row outside the cut has an FP32 key >= the smallest key above the cut
+      const float outside = key_to_float(((c22 + 1u) << 10));
+      exact = sorted_log[bt - 1] < (double)outside - (double)kCutGuard - 1e-6 * fabs((double)outside);
+    }
+    if (!exact) {
+      st->sample_fallback = 1;
+    } else {
+      st->sample_fallback = 0;
+      st->b_t = bt;
+      if (bt == 0) st->done = 1;
+    }
+  }
+  __syncthreads();
+  if (!st->sample_fallback)
+    for (int e = threadIdx.x; e < bt; e += kCoopThreads) S_t[e] = sorted_idx[e];
+  // clear the pass buffers for the next block (every other CTA is past its last read)
+  for (int j = threadIdx.x; j < kBins; j += kCoopThreads) {
+    hist1[j] = 0;
+    hist2[j] = 0;
+  }
   if (threadIdx.x == 0) *ncand = 0;
 }
 
@@ -294,6 +467,31 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
   unsigned long long* cand_key = (unsigned long long*)(((uintptr_t)(cand + kSampCap) + 15) & ~(uintptr_t)15);
   double* cand_log = (double*)(cand_key + kSampCap);
   const int want = b + kMargin;
+  {
+    // one cooperative launch, one CTA per SM, when the device allows it (asked once per device)
+    static int coop_sms[64] = {0};  // 0: not asked, -1: not available, else the SM count
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (coop_sms[dev] == 0) {
+      int sms = 0, per_sm = 0, coop = 0;
+      const bool ok = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+                      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_coop, kCoopThreads, 0) ==
+                          cudaSuccess &&
+                      per_sm >= 1;
+      (void)cudaGetLastError();
+      coop_sms[dev] = ok ? sms : -1;
+    }
+    if (coop_sms[dev] > 0) {
+      const int sms = coop_sms[dev];
+      int cap = kSampCap;
+      void* args[] = {(void*)&dvec, (void*)&n, (void*)&K32, (void*)&hist1, (void*)&hist2, (void*)&want,
+                      (void*)&cand, (void*)&cand_key, (void*)&cand_log, (void*)&ncand, (void*)&cap, (void*)&b,
+                      (void*)&greedy, (void*)&seed, (void*)&problem, (void*)&S_t, (void*)&st};
+      return counted(cudaLaunchCooperativeKernel((const void*)k_sample_coop, dim3((unsigned)sms), dim3(kCoopThreads),
+                                                 args, 0, s));
+    }
+  }
   const unsigned grid = (unsigned)((n + kSampThreads * kSampPerThread - 1) / (kSampThreads * kSampPerThread));
   k_samp_keys<<<grid, kSampThreads, 0, s>>>(dvec, n, K32, hist1, greedy, seed, problem, st);
   cudaError_t e = counted(cudaGetLastError());
