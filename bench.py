@@ -27,9 +27,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ID time-to-tol (ms) at 1e5×1e3, rel err ≤1e-4; % of HBM/TC roofline"
 # DRAM bytes (read + write) per launch of the persistent tensor-core update, per
-# row of R, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-# of the 40000 x 1000 zipf_gmm workload at b = 64 (profiles/k_update_tf32p_*.md).
-UPD_TRAFFIC_PER_ROW = (254.376192e6 + 90.944256e6) / 40000
+# row of R, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# caches left as the preceding kernels leave them) of the 40000 x 1000 zipf_gmm
+# workload at b = 64 (profiles/k_update_tf32p_*.md).
+UPD_TRAFFIC_PER_ROW = (196233472 + 132443136) / 40000
 UPD_TRAFFIC_D = 1000
 FALLBACK_HBM = 6800.0
 
@@ -42,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "tf32x3", "fp32", "fp64"])
     ap.add_argument("--w-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--form", default="residual", choices=["residual", "downdate"],
+                    help="update form of Alg. 2 lines 12/16 (downdate: as printed, FP64 only)")
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--n", type=int, default=100000)
@@ -66,7 +69,7 @@ def parse():
 def workload_config(a):
     return {"workload": "zipf_gmm_near_duplicates", "n": a.n, "d": a.d, "dtype_in": "fp32", "clusters": 100,
             "zipf_s": 1.5, "within_var": 1e-6, "extra_rows": 0.05, "extra_var": 0.01, "tol_sq_rel": a.tol,
-            "block": a.block, "seed": 0, "update": a.precision, "w_solve": a.w_precision,
+            "block": a.block, "seed": 0, "update": a.precision, "form": a.form, "w_solve": a.w_precision,
             "l2": "inputs larger than L2 (X is %.0f MB, residual copy %.0f MB per step)" % (a.n * a.d * 4 / 1e6,
                                                                                             a.n * a.d * 4 / 1e6)}
 
@@ -206,8 +209,8 @@ def run_ours(a):
     Xd = torch.from_numpy(X).to(dev)
     from paper_2309_16002_gb300 import shard
     pid = shard.replica_problem_id(rank)
-    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=pid)
-    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, pid, "random", a.w_precision)
+    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=pid, form=a.form)
+    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, pid, "random", a.w_precision, a.form)
     wsp = G.Workspace(a.n, a.d, opts, dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -266,7 +269,8 @@ def run_ours(a):
                 "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
                 "peak_kind": peak_kind, "traffic": traffic,
                 "traffic_note": ("DRAM read+write bytes per launch from one ncu capture of the 40000 x 1000 "
-                                 "workload, scaled by rows" if traffic else None),
+                                 "workload (L2 as the preceding kernels leave it), scaled by rows"
+                                 if traffic else None),
                 "bytes_per_launch": upd_bytes / max(1, blocks),
                 "note": "achieved = (2 n d s + 16 n) per block + n k s for Lhat, over CUDA-event time of all "
                         "update launches in the timed region (including no-op launches queued after the stop)"}

@@ -69,6 +69,16 @@ typedef enum {
   RBRP_SAMPLER_GREEDY_EXACT = 3
 } rbrp_sampler;
 
+/* How lines 12 and 16 of Alg. 2 are carried out. */
+typedef enum {
+  RBRP_FORM_RESIDUAL = 0,   /* R <- R - (R Q'^T) Q' in a residual copy of X, d_i =
+                               ||R_i||^2 recomputed (robust at any precision)       */
+  RBRP_FORM_DOWNDATE = 1    /* as printed: X read-only, Lhat = X Q'^T, d_i -=
+                               ||Lhat_i||^2; half the memory traffic of the residual
+                               form and no residual copy, FP64 only (the downdate
+                               cancels: it needs FP64 to stay accurate)           */
+} rbrp_form;
+
 typedef enum {
   RBRP_W_FP64 = 0,          /* Alg. 3 triangular solve in FP64                      */
   RBRP_W_FP32 = 1           /* same solve in FP32 (for the TF32 path)               */
@@ -85,6 +95,8 @@ typedef struct {
   uint64_t problem;     /* Philox4x64-10 key word 1 (problem id)                  */
   int32_t sampler;      /* rbrp_sampler                                           */
   int32_t w_precision;  /* rbrp_w_precision                                       */
+  int32_t form;         /* rbrp_form (rbrp_id only; the batched call ignores it)  */
+  int32_t reserved;     /* must be 0                                              */
 } rbrp_opts;
 
 typedef struct {
@@ -96,7 +108,7 @@ typedef struct {
 } rbrp_result;
 
 /* Fill *o with the defaults: TF32, b = 64, tau_b = 1/b_t, k_max = min(n, d),
- * seed 0, problem 0, random sampler, W in FP64. */
+ * seed 0, problem 0, random sampler, W in FP64, residual form. */
 void rbrp_default_opts(rbrp_opts *o);
 
 /* Bytes of device workspace rbrp_id needs for an n x d problem with options o

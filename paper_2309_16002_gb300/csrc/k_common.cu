@@ -26,23 +26,24 @@ __global__ void __launch_bounds__(256) k_init_norms(const TX* __restrict__ X, lo
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double wsum[8];
   double mine = 0.0;
+  const long long lim = R ? ldr : d;  // no residual copy (downdate form): norms only
   for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
     const TX* x = X + i * ldx;
-    TR* r = R + i * ldr;
+    TR* r = R ? R + i * ldr : nullptr;
     double s = 0.0;
     if (sizeof(TR) == 8) {
-      for (long long j = lane; j < ldr; j += 32) {
+      for (long long j = lane; j < lim; j += 32) {
         TR v = (j < d) ? (TR)x[j] : (TR)0;
-        r[j] = v;
+        if (r) r[j] = v;
         const double dv = (double)v;
         s = fma(dv, dv, s);
       }
     } else {
       // FP32 residual: per-lane FP32 partial sums (FP64 FMAs run at ~2/clock/SM on GB300)
       float sf = 0.f;
-      for (long long j = lane; j < ldr; j += 32) {
+      for (long long j = lane; j < lim; j += 32) {
         TR v = (j < d) ? (TR)x[j] : (TR)0;
-        r[j] = v;
+        if (r) r[j] = v;
         const float fv = (float)v;
         sf = fmaf(fv, fv, sf);
       }
@@ -426,6 +427,7 @@ template cudaError_t launch_gemm<double, double, double, double>(const GemmArgs&
 template cudaError_t launch_gemm<float, float, float, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
 template cudaError_t launch_gemm<double, double, double, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
 template cudaError_t launch_gemm<float, double, float, float>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
+template cudaError_t launch_gemm<float, double, double, double>(const GemmArgs&, long long, long long, int, int, cudaStream_t);
 
 // ============================================================================
 // FP32 copies of the new basis rows for the low-precision update:
@@ -517,6 +519,52 @@ cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n
     k_norms_zero<double><<<nparts, 256, 0, s>>>((double*)R, ldr, n, d, mark, dvec, partials, st);
   else
     k_norms_zero<float><<<nparts, 256, 0, s>>>((float*)R, ldr, n, d, mark, dvec, partials, st);
+  return counted(cudaGetLastError());
+}
+
+// Alg. 2 line 16 as printed (downdate form): with Lhat = X Q'^T in columns
+// k .. k + b' - 1 of L, d_i -= ||Lhat_i||^2 for the rows not yet in S, d_i = 0
+// for the rows accepted in this block (their Lhat row is kept), and Lhat_i = 0
+// for rows accepted in earlier blocks (their residual is zero, so their Lhat
+// row is, and L(S, :) stays lower triangular).  FP64; one warp per row.
+__global__ void __launch_bounds__(256) k_downdate(double* __restrict__ L, long long ldl, long long n,
+                                                  const int* __restrict__ mark, double* __restrict__ dvec,
+                                                  double* __restrict__ partials, const State* st) {
+  if (st->done) return;
+  const int tno = (int)(st->t + 1);
+  const long long k = st->k;
+  const int bp = (int)st->bp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double wsum[8];
+  double mine = 0.0;
+  for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
+    double* l = L + i * ldl + k;
+    const int mk = mark[i];
+    double di = 0.0;
+    if (mk != 0 && mk != tno) {
+      for (int j = lane; j < bp; j += 32) l[j] = 0.0;
+    } else if (mk == 0) {
+      double s = 0.0;
+      for (int j = lane; j < bp; j += 32) s = fma(l[j], l[j], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      di = dvec[i] - s;  // may round below zero for an exhausted row: d_i <= 0 is not eligible
+    }
+    if (lane == 0) dvec[i] = di;
+    mine += di;
+  }
+  if (lane == 0) wsum[warp] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* mark, double* dvec, double* partials,
+                            int nparts, const State* st, cudaStream_t s) {
+  k_downdate<<<nparts, 256, 0, s>>>(L, ldl, n, mark, dvec, partials, st);
   return counted(cudaGetLastError());
 }
 

@@ -279,7 +279,7 @@ __global__ void k_samp_clear(unsigned int* __restrict__ hist1, unsigned int* __r
 // exact keys | ranking, margin check and S_t by CTA 0.  Results are those of
 // the four kernels above (same keys, cut, candidates and ranking).
 constexpr int kCoopThreads = 512;
-constexpr unsigned kBarSpins = 1u << 22;  // ~2 s at 512 ns a poll, then the barrier gives up
+constexpr unsigned kBarSpins = 1u << 25;  // ~1-2 s of polls, then the barrier gives up
 
 // Grid barrier over gridDim.x CTAs: arrival counter bar[0] (reset by the last
 // arriver) and generation bar[1].  The wait is bounded: on timeout the CTA
@@ -304,7 +304,7 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, State* st) {
           st->done = 1;
           break;
         }
-        __nanosleep(512);
+        __nanosleep(32);
       }
     }
     __threadfence();

@@ -450,6 +450,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const int nK1 = (int)((d + BK1 - 1) / BK1);  // 32-column chunks of GEMM 1 (and epilogue pieces)
   const int nJ = (int)((d + PNB - 1) / PNB);   // GEMM-2 chunks
   const long long ntiles = (n + PROWS - 1) / PROWS;
+  // Odd blocks walk the tiles from the last: a block then starts on the tiles the
+  // previous block wrote last, which are still in L2 (the residual is larger
+  // than L2, so a fixed order would always start on the least recent tiles).
+  // Partial sums stay indexed by the tile's position, so their order is fixed.
+  const bool rev = (st->t & 1) != 0;
+  auto ptile = [&](long long tl) { return rev ? ntiles - 1 - tl : tl; };
   // GEMM 2 walks its chunks from the last (the most recently read columns
   // first); a chunk j covers pieces 4j .. min(4j + 4, nK1) - 1.
   auto npieces = [&](int j) { const int r = nK1 - PPC * j; return r < PPC ? r : PPC; };
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
           mbar_expect_tx(full1(s), (uint32_t)(C::A1 + C::B1));
           const uint32_t base = sb + s * C::ST1;
-          tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)(tile * PROWS), keep);
+          tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)(ptile(tile) * PROWS), keep);
           tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
         }
       }
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               break;
             }
             mbar_expect_tx(full3(s), (uint32_t)C::R3);
-            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, &tmR, full3(s), (PPC * j + pc) * NB2, (int)(tile * PROWS),
+            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, &tmR, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS),
                              drop);
           }
         }
@@ -620,7 +626,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     uint32_t g = 0, gj = 0, it = 0;
     bool ok = true;
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-      const long long row = tile * PROWS + r;
+      const long long row = ptile(tile) * PROWS + r;
       const bool in = row < n;
       const bool marked = in && (mark[row] == tno);
       // Lhat: TMEM -> registers -> L (GEMM 2 reads it from TMEM itself)
@@ -690,7 +696,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       double t = in ? (double)nrm : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) partials[4 * tile + q] = t;
+      if (lane == 0) partials[4 * ptile(tile) + q] = t;
     }
   } else if (warp == 8) {
     // ---------------- stores of finished R pieces; a stage is released once its store has read it
@@ -707,7 +713,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               ok = false;
               break;
             }
-            tma_store_2d_hint(&tmR, sb + C::OFF3 + s * C::R3, (PPC * j + pc) * NB2, (int)(tile * PROWS), drop);
+            tma_store_2d_hint(&tmR, sb + C::OFF3 + s * C::R3, (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS), drop);
             tma_commit();
             tma_wait_read<0>();
             mbar_arrive(empty3(s));

@@ -63,7 +63,7 @@ cudaError_t timed(EventPool& pool, cudaStream_t s, F&& body) {
 
 struct Plan {
   long long n, d, k_cap;
-  int b, prec, r64, l64, w32, greedy, f32, exact_sampler;
+  int b, prec, r64, l64, w32, greedy, f32, exact_sampler, downdate;
   long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32, ldt;
   int nparts;
   int s_upd1, s_upd2;
@@ -95,6 +95,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   if (o->sampler < RBRP_SAMPLER_RANDOM || o->sampler > RBRP_SAMPLER_GREEDY_EXACT) return RBRP_EINVAL;
   if (o->w_precision != RBRP_W_FP64 && o->w_precision != RBRP_W_FP32) return RBRP_EINVAL;
   if (o->tau_b > 1.0) return RBRP_EINVAL;
+  if (o->form != RBRP_FORM_RESIDUAL && o->form != RBRP_FORM_DOWNDATE) return RBRP_EINVAL;
+  if (o->form == RBRP_FORM_DOWNDATE && o->precision != RBRP_FP64) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
   // the tensor-core update keeps Lhat (128 x b'_pad) in shared memory: b <= 128
   if (o->precision == RBRP_TF32 && o->block > update_tf32_max_block(0)) return RBRP_EINVAL;
@@ -113,6 +115,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->f32 = (o->precision == RBRP_TF32);  // FP32 storage for the per-block chain
   p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
   p->exact_sampler = (o->sampler == RBRP_SAMPLER_RANDOM_EXACT || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
+  p->downdate = (o->form == RBRP_FORM_DOWNDATE);
   p->ldr = round_up(d, 32);
   p->ldq = round_up(d, 32);
   p->ldl = round_up(kc, 8);
@@ -159,7 +162,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
     return o2;
   };
   const size_t sR = p->r64 ? 8 : 4, sL = p->l64 ? 8 : 4;
-  p->off_R = take((size_t)n * p->ldr * sR);
+  p->off_R = take(p->downdate ? 0 : (size_t)n * p->ldr * sR);  // the downdate form keeps no residual
   p->off_L = take((size_t)n * p->ldl * sL);
   p->off_Q = take((size_t)kc * p->ldq * 8 + (size_t)kMaxBlock * p->ldq * 8);
   p->off_d = take((size_t)n * 8);
@@ -203,6 +206,9 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   } while (0)
 
 struct Bufs {
+  const void* X;  // the input (read by the downdate form)
+  int x64;
+  long long ldx;
   void* R;
   void* L;
   double* Qt;
@@ -386,7 +392,10 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   if (!p.exact_sampler) LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
   LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, p.exact_sampler, s));
   // line 6: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
-  LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
+  if (p.downdate)  // Alg. 2 line 6 as printed: V = X(S_t, :), projected below
+    LK(launch_gather(const_cast<void*>(u.X), u.x64, u.ldx, u.S_t, u.V, 1, p.ldq, d, p.b, st, s));
+  else
+    LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
   // (one pass on the plain TF32 path: the sampled residual rows are orthogonal
   // to Q up to the TF32 rounding of the update, and one FP32 pass already takes
   // that to the FP32 floor, which a second FP32 pass cannot lower)
@@ -452,6 +461,21 @@ cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s) {
     e = (call);                      \
     if (e != cudaSuccess) return e;  \
   } while (0)
+  if (p.downdate) {
+    // Alg. 2 lines 12 and 16 as printed: Lhat = X Q'^T into L(:, k : k + b'), d_i -= ||Lhat_i||^2
+    if (u.x64)
+      LK((gemm<double, double, double, double>(
+          p, u, mat(const_cast<void*>(u.X), dim_const(0), u.ldx, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), 1, p.ldq),
+          mat(u.L, dim_dev(&st->k), p.ldl, 1), dim_const(n), dim_dev(&st->bp), dim_const(d), 1.0, 0.0, n, b,
+          p.s_upd1, st, s)));
+    else
+      LK((gemm<float, double, double, double>(
+          p, u, mat(const_cast<void*>(u.X), dim_const(0), u.ldx, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), 1, p.ldq),
+          mat(u.L, dim_dev(&st->k), p.ldl, 1), dim_const(n), dim_dev(&st->bp), dim_const(d), 1.0, 0.0, n, b,
+          p.s_upd1, st, s)));
+    LK(launch_downdate((double*)u.L, p.ldl, n, u.mark, u.dvec, u.part, p.nparts, st, s));
+    return cudaSuccess;
+  }
   if (p.prec == RBRP_FP64) {
     LK((gemm<double, double, double, double>(
         p, u, mat(u.R, dim_const(0), p.ldr, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), 1, p.ldq),
@@ -518,9 +542,13 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   memset(res, 0, sizeof(*res));
   Bufs u = carve(p, ws);
   u.skel = skel;
+  u.X = X;
+  u.x64 = x_is_fp64 ? 1 : 0;
+  u.ldx = ldx;
   State* st = u.st;
-  // Alg. 2 lines 1-2
-  CK(launch_init_norms(X, x_is_fp64, n, d, ldx, u.R, p.r64, p.ldr, u.dvec, u.mark, u.part, p.nparts, st, s));
+  // Alg. 2 lines 1-2 (the residual form also copies X into R)
+  CK(launch_init_norms(X, x_is_fp64, n, d, ldx, p.downdate ? nullptr : u.R, p.r64, p.ldr, u.dvec, u.mark, u.part,
+                       p.nparts, st, s));
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
   CK(launch_sample_clear(u.samp2, n, s));
   CK(cudaMemsetAsync(u.cnt, 0, (size_t)kSgemmCounters * 4, s));

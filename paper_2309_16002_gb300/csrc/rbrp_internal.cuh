@@ -173,6 +173,8 @@ cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, c
 cudaError_t launch_qp_lowp(const void* Qt, int q_is_fp64, long long ldq, float* Qp, float* Qp_lo, long long ldp,
                            float* QpT, float* QpT_lo, long long ldpt, long long d, int b, const State* st,
                            cudaStream_t s);
+cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* mark, double* dvec, double* partials,
+                            int nparts, const State* st, cudaStream_t s);
 cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d,
                               const int* mark, double* dvec, double* partials, int nparts,
                               const State* st, cudaStream_t s);

@@ -35,7 +35,8 @@ EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_wor
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("block", ctypes.c_int32), ("tau_b", ctypes.c_double),
                 ("k_max", ctypes.c_int64), ("seed", ctypes.c_uint64), ("problem", ctypes.c_uint64),
-                ("sampler", ctypes.c_int32), ("w_precision", ctypes.c_int32)]
+                ("sampler", ctypes.c_int32), ("w_precision", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -132,8 +133,11 @@ def rbrp_profile_end():
     return {f: getattr(p, f) for f, _ in Profile._fields_}
 
 
+FORMS = {"residual": 0, "downdate": 1}
+
+
 def make_opts(block=64, precision="tf32", tau_b=-1.0, k_max=0, seed=0, problem=0, sampler="random",
-              w_precision="fp64"):
+              w_precision="fp64", form="residual"):
     o = Opts()
     load().rbrp_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -144,6 +148,7 @@ def make_opts(block=64, precision="tf32", tau_b=-1.0, k_max=0, seed=0, problem=0
     o.problem = int(problem)
     o.sampler = SAMPLERS[sampler]
     o.w_precision = W_PRECISIONS[w_precision]
+    o.form = FORMS[form]
     return o
 
 
@@ -201,7 +206,7 @@ class Workspace:
 
 
 def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0, sampler="random",
-            w_precision="fp64", workspace=None, stream=None):
+            w_precision="fp64", workspace=None, stream=None, form="residual"):
     """Row ID of a CUDA tensor X (n x d, FP32/FP64, row-major rows) by RBRP (Alg. 2) and Alg. 3.
 
     Returns dict(S (int64 CUDA tensor, acceptance order), W (n x k FP64 CUDA tensor), k, blocks,
@@ -213,7 +218,7 @@ def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, pro
     if X.dtype not in (torch.float32, torch.float64):
         raise ValueError("X must be float32 or float64")
     n, d = X.shape
-    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form)
     ws = workspace if workspace is not None else Workspace(n, d, opts, X.device)
     res = Result()
     s = stream if stream is not None else torch.cuda.current_stream(X.device)
@@ -269,7 +274,7 @@ class HostWorkspace:
 
 
 def rbrp_id_host(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0, sampler="random",
-                 w_precision="fp64", workspace=None, skel_out=None, W_out=None, stream=None):
+                 w_precision="fp64", workspace=None, skel_out=None, W_out=None, stream=None, form="residual"):
     """rbrp_id on host buffers: X (numpy array or CPU tensor, C-contiguous FP32/FP64).
 
     skel_out / W_out: optional preallocated host outputs (int64[k_cap], FP64 n x k_cap, pinned
@@ -281,7 +286,7 @@ def rbrp_id_host(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0
         raise ValueError("X must be a C-contiguous 2-D host array")
     n, d = Xt.shape
     fp64 = int(Xt.dtype == torch.float64)
-    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form)
     kc = k_cap(n, d, k_max)
     ws = workspace if workspace is not None else HostWorkspace(n, d, fp64, opts)
     skel = skel_out if skel_out is not None else torch.empty(kc, dtype=torch.int64)

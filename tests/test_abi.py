@@ -64,6 +64,12 @@ def test_workspace_size_and_validation_on_host(libpath):
         rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=300, precision="fp64"))
     with pytest.raises(rbrp.RBRPError):
         rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=256, precision="tf32"))
+    # the downdate form: FP64 only, and it keeps no residual copy of X
+    with pytest.raises(rbrp.RBRPError):
+        rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(precision="tf32", form="downdate"))
+    res = rbrp.rbrp_workspace_size(100000, 1000, rbrp.make_opts(precision="fp64"))
+    dd = rbrp.rbrp_workspace_size(100000, 1000, rbrp.make_opts(precision="fp64", form="downdate"))
+    assert res - dd >= 100000 * 1000 * 8
     with pytest.raises(rbrp.RBRPError):
         rbrp.rbrp_workspace_size(0, 10, o)
     assert rbrp.rbrp_host_workspace_size(1000, 50, 0, o) > rbrp.rbrp_workspace_size(1000, 50, o)

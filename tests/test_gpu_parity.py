@@ -296,3 +296,33 @@ def test_fp64_greedy_ties_take_the_fallback(G):
     ref = O.rbrp_id(X, tau=1e-3, b=16, seed=0, sampler="greedy")
     assert out["S"][:1].tolist() == [0]
     _assert_fp64_parity(X, ref, out)
+
+
+# ------------------------------------------------------------------ downdate form
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_fp64_downdate_form_matches_oracle(G, dtype):
+    """Alg. 2 lines 12 and 16 as printed (X read-only, d downdated): the oracle's
+    downdate form draws the same skeletons; the error bar of the FP64 path."""
+    X, _ = WL.spectral(n=1800, d=150, rate=0.9, seed=21)
+    X = X.astype(dtype)
+    out = _run(G, X, 1e-7, block=16, seed=5, precision="fp64", form="downdate")
+    ref = O.rbrp_id(X, tau=1e-7, b=16, seed=5, form="downdate")
+    _assert_fp64_parity(X, ref, out)
+    res = _run(G, X, 1e-7, block=16, seed=5, precision="fp64")
+    # the two forms agree up to rounding: same skeletons here (no near-tie)
+    assert out["S"].tolist() == res["S"].tolist()
+
+
+def test_downdate_form_fixed_rank_and_ragged(G):
+    X, _ = WL.spectral(n=1037, d=97, rate=0.85, seed=22)
+    out = _run(G, X, -1.0, block=24, seed=1, precision="fp64", form="downdate", k_max=50)
+    ref = O.rbrp_id(X, k=50, b=24, seed=1, form="downdate")
+    assert len(out["S"]) == 50
+    _assert_fp64_parity(X, ref, out)
+
+
+def test_downdate_form_needs_fp64(G):
+    import torch
+    X = torch.zeros((64, 16), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(G.RBRPError):
+        G.rbrp_id(X, 1e-3, precision="tf32", form="downdate")
