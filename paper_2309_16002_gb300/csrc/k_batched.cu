@@ -55,7 +55,7 @@ __host__ __device__ inline Slot slot_layout(long long m, long long n, long long 
   Slot s;
   size_t o = 0;
   s.R = o;
-  o = al256(o + (size_t)m * n * sT);
+  o = al256(o + (size_t)m * ((n + 3) / 4 * 4) * sT);  // leading dimension n rounded up to 4
   s.L = o;
   o = al256(o + (size_t)m * kc * sT);
   s.Q = o;
@@ -286,12 +286,14 @@ __device__ void sample_cut(const double* d, const int* mark, long long m, int bt
   __syncthreads();
 }
 
-// Rows i < nrows of src (row-major, leading dimension n <= 256; row i read
-// from src row rowmap[i] when rowmap is given): c_ij = <src_i, B_j> for
+// Rows i < nrows of src (row-major, leading dimension ls, n <= 256 columns;
+// row i read from src row rowmap[i] when rowmap is given; B has leading
+// dimension n): c_ij = <src_i, B_j> for
 // j < nb, every c_ij from the original row (classical Gram-Schmidt), and
 // y_i = src_i - sum_j c_ij B_j with the terms subtracted in ascending j
 // (BASIS = false: no basis, y_i = src_i).  COEF: coef[j * ldc + i] = c_ij.
-// y_i goes to dst row i, zeroed when mark && mark[i] != 0; NORM:
+// y_i goes to dst row i (leading dimension ldd >= n, columns n .. ldd - 1
+// written as zeros), zeroed when mark && mark[i] != 0; NORM:
 // dn[i] = ||y_i||^2 (0 for zeroed rows), the per-lane partial sums and their
 // warp reduction in T.  One warp per group of RPW rows, whose loads are all
 // issued before any arithmetic.  dst may alias src (each group is read
@@ -299,8 +301,8 @@ __device__ void sample_cut(const double* d, const int* mark, long long m, int bt
 // with evict-first loads so that it does not push the residuals of the
 // resident problems out of L2.  No barrier inside; the caller synchronises.
 template <int NT, int RPW, bool BASIS, bool COEF, bool NORM, typename T, typename TS, bool STREAM = false>
-__device__ void project_rows(const TS* src, const int* rowmap, T* dst, long long nrows, long long n, const T* B,
-                             int nb, T* coef, long long ldc, double* dn, const int* mark) {
+__device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* dst, long long ldd, long long nrows,
+                             long long n, const T* B, int nb, T* coef, long long ldc, double* dn, const int* mark) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long long i0 = (long long)w * RPW; i0 < nrows; i0 += (long long)NW * RPW) {
@@ -314,7 +316,7 @@ __device__ void project_rows(const TS* src, const int* rowmap, T* dst, long long
 #pragma unroll
       for (int u = 0; u < kRowVec; ++u) {
         const long long c = lane + 32 * u;
-        if (i < nrows && c < n) x[r][u] = STREAM ? (T)__ldcs(src + si * n + c) : (T)src[si * n + c];
+        if (i < nrows && c < n) x[r][u] = STREAM ? (T)__ldcs(src + si * ls + c) : (T)src[si * ls + c];
         else x[r][u] = (T)0;
         y[r][u] = x[r][u];
       }
@@ -355,9 +357,9 @@ __device__ void project_rows(const TS* src, const int* rowmap, T* dst, long long
 #pragma unroll
       for (int u = 0; u < kRowVec; ++u) {
         const long long c = lane + 32 * u;
-        if (c >= n) continue;
-        const T v = zero[r] ? (T)0 : y[r][u];
-        dst[i * n + c] = v;
+        if (c >= ldd) continue;
+        const T v = (zero[r] || c >= n) ? (T)0 : y[r][u];  // columns n .. ldd - 1: zero padding
+        dst[i * ldd + c] = v;
         nr += v * v;
       }
       if (NORM) {
@@ -368,6 +370,85 @@ __device__ void project_rows(const TS* src, const int* rowmap, T* dst, long long
         if (lane == 0) dn[i] = zero[r] ? 0.0 : (double)s;
       }
     }
+  }
+}
+
+// The residual update of the FP32 form (Alg. 2 lines 12 and 16), with a row
+// spread over eight lanes instead of 32: lanes 8g .. 8g + 7 of a warp hold row
+// i0 + g (four rows a warp), lane q of the octet the float4 at columns
+// 4q + 32u .. 4q + 32u + 3 for u < 8, so that the octet reads 128 contiguous
+// bytes of a row per load (R and Q' with leading dimension ldr, a multiple of
+// 4, padding columns zero).  A coefficient then takes three shuffle levels, each serving
+// the warp's four rows at once, where the 32-lane layout takes five per row.
+// c_ij = <R_i, Q'_j> from the original row, R_i -= sum_j c_ij Q'_j in
+// ascending j, coef[j * ldc + i] = c_ij, dn[i] = ||R_i||^2; rows with
+// mark[i] != 0 are zeroed (dn = 0).
+template <int NT>
+__device__ void update_rows_oct(float* R, long long ldr, long long m, const float* Qs, int bp, float* coef,
+                                long long ldc, double* dn, const int* mark) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 3, q = lane & 7;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i0 = (long long)w * 4; i0 < m; i0 += (long long)NW * 4) {
+    const long long i = i0 + g;
+    const bool valid = i < m;
+    const bool zero = valid && mark[i] != 0;
+    float4 x[8], y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long c = 4 * q + 32 * u;
+      x[u] = (valid && c < ldr) ? *(const float4*)(R + i * ldr + c) : z4;
+      y[u] = x[u];
+    }
+    const int nu = (int)((ldr - 4 * q + 31) / 32);  // float4 groups this lane holds
+    for (int j = 0; j < bp; ++j) {
+      const float* qj = Qs + (long long)j * ldr + 4 * q;
+      // Q'_j is read from shared memory twice (dot, then subtraction) to keep
+      // the registers for the row
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const float4 q0 = (u < nu) ? *(const float4*)(qj + 32 * u) : z4;
+        const float4 q1 = (u + 1 < nu) ? *(const float4*)(qj + 32 * u + 32) : z4;
+        a0 = fmaf(x[u].x, q0.x, a0);
+        a0 = fmaf(x[u].y, q0.y, a0);
+        a0 = fmaf(x[u].z, q0.z, a0);
+        a0 = fmaf(x[u].w, q0.w, a0);
+        a1 = fmaf(x[u + 1].x, q1.x, a1);
+        a1 = fmaf(x[u + 1].y, q1.y, a1);
+        a1 = fmaf(x[u + 1].z, q1.z, a1);
+        a1 = fmaf(x[u + 1].w, q1.w, a1);
+      }
+      float acc = a0 + a1;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 qv = (u < nu) ? *(const float4*)(qj + 32 * u) : z4;
+        y[u].x = fmaf(-acc, qv.x, y[u].x);
+        y[u].y = fmaf(-acc, qv.y, y[u].y);
+        y[u].z = fmaf(-acc, qv.z, y[u].z);
+        y[u].w = fmaf(-acc, qv.w, y[u].w);
+      }
+      if (q == 0 && valid) coef[(long long)j * ldc + i] = acc;
+    }
+    float nr = 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long c = 4 * q + 32 * u;
+      if (zero) y[u] = z4;
+      if (valid && c < ldr) *(float4*)(R + i * ldr + c) = y[u];
+      nr = fmaf(y[u].x, y[u].x, nr);
+      nr = fmaf(y[u].y, y[u].y, nr);
+      nr = fmaf(y[u].z, y[u].z, nr);
+      nr = fmaf(y[u].w, y[u].w, nr);
+    }
+    nr += __shfl_xor_sync(0xffffffffu, nr, 4);
+    nr += __shfl_xor_sync(0xffffffffu, nr, 2);
+    nr += __shfl_xor_sync(0xffffffffu, nr, 1);
+    if (q == 0 && valid) dn[i] = zero ? 0.0 : (double)nr;
   }
 }
 
@@ -559,6 +640,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
   long long kc = m < n ? m : n;
   if (a.k_max > 0 && a.k_max < kc) kc = a.k_max;
   const Slot so = slot_layout(a.m_max, a.n_max, a.kc_max, a.b, sizeof(T));
+  const long long ldr = (n + 3) / 4 * 4;  // leading dimension of R (and of Q' in shared memory on the FP32 form)
   T* R = (T*)(slotp + so.R);
   T* L = (T*)(slotp + so.L);   // column-major: L[j * m + i]
   T* Q = (T*)(slotp + so.Q);   // rows of Q^T, ld = n
@@ -572,10 +654,10 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
 
   // Alg. 2 lines 1-2: R = X and d_i = ||X_i||^2 in one pass over X
   if (a.x_is_fp64)
-    project_rows<NT, RPW0, false, false, true, T, double, true>((const double*)a.X[p], nullptr, R, m, n,
+    project_rows<NT, RPW0, false, false, true, T, double, true>((const double*)a.X[p], n, nullptr, R, ldr, m, n,
                                                                 (const T*)nullptr, 0, nullptr, 0, d, nullptr);
   else
-    project_rows<NT, RPW0, false, false, true, T, float, true>((const float*)a.X[p], nullptr, R, m, n,
+    project_rows<NT, RPW0, false, false, true, T, float, true>((const float*)a.X[p], n, nullptr, R, ldr, m, n,
                                                                (const T*)nullptr, 0, nullptr, 0, d, nullptr);
   for (long long i = tid; i < m; i += NT) mark[i] = 0;
   __syncthreads();
@@ -602,10 +684,12 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     // line 5
     sample_cta<NT>(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
     // line 6: V = R(S_t, :) projected against Q twice (CGS2)
-    project_rows<NT, RPW, true, false, false, T, T>(R, sm.St, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+    project_rows<NT, RPW, true, false, false, T, T>(R, ldr, sm.St, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
+                                                    nullptr);
     __syncthreads();
     if (k > 0) {
-      project_rows<NT, RPW, true, false, false, T, T>(V, nullptr, V, bt, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+      project_rows<NT, RPW, true, false, false, T, T>(V, n, nullptr, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
+                                                      nullptr);
       __syncthreads();
     }
     // lines 7-8: G = V V^T, pivoted Cholesky with the tail-mass truncation
@@ -623,7 +707,8 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
       mark[row] = (int)t;
     }
     if (k > 0)
-      project_rows<NT, RPW, true, false, false, T, T>(Y, nullptr, Y, bp, n, Q, (int)k, nullptr, 0, nullptr, nullptr);
+      project_rows<NT, RPW, true, false, false, T, T>(Y, n, nullptr, Y, n, bp, n, Q, (int)k, nullptr, 0, nullptr,
+                                                      nullptr);
     __syncthreads();
     gram_rows<NT, T>(Y, bp, n, sm);
     __syncthreads();
@@ -633,11 +718,21 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
       break;
     }
     trsm_cols<NT, T>(sm, Y, nullptr, Q + k * n, bp, n);
-    for (long long e = tid; e < bp * n; e += NT) sQp[e] = Q[k * n + e];
+    if constexpr (sizeof(T) == 4) {
+      for (long long e = tid; e < bp * ldr; e += NT) {
+        const long long r = e / ldr, c = e % ldr;
+        sQp[e] = c < n ? Q[(k + r) * n + c] : (T)0;
+      }
+    } else {
+      for (long long e = tid; e < bp * n; e += NT) sQp[e] = Q[k * n + e];
+    }
     __syncthreads();
     // lines 12, 16 (residual form): Lhat = R Q'^T into L(:, k : k + b'), R -= Lhat Q',
     // d_i = ||R_i||^2, rows accepted so far zeroed
-    project_rows<NT, RPW, true, true, true, T, T>(R, nullptr, R, m, n, sQp, bp, L + k * m, m, d, mark);
+    if constexpr (sizeof(T) == 4)
+      update_rows_oct<NT>(R, ldr, m, sQp, bp, L + k * m, m, d, mark);
+    else
+      project_rows<NT, RPW, true, true, true, T, T>(R, ldr, nullptr, R, ldr, m, n, sQp, bp, L + k * m, m, d, mark);
     __syncthreads();
     D = rows_sum<NT>(m, sm, [&](long long i) { return d[i]; });
     k += bp;
@@ -690,7 +785,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
 }
 
 template <int NT, typename T>
-__global__ void __launch_bounds__(NT) k_batched(BatchedArgs a) {
+__global__ void __launch_bounds__(NT, kBatchMaxThreads / NT) k_batched(BatchedArgs a) {
   extern __shared__ __align__(16) uint8_t dyn[];
   Smem& sm = *(Smem*)dyn;
   T* sQp = (T*)(dyn + (sizeof(Smem) + 15) / 16 * 16);  // Q' (b' x n)
@@ -730,7 +825,7 @@ int batched_sms() {
 }
 
 size_t batched_dyn_smem(long long n_max, int fp64) {
-  return (sizeof(bt::Smem) + 15) / 16 * 16 + (size_t)kBatchMaxBlock * n_max * (fp64 ? 8 : 4);
+  return (sizeof(bt::Smem) + 15) / 16 * 16 + (size_t)kBatchMaxBlock * ((n_max + 3) / 4 * 4) * (fp64 ? 8 : 4);
 }
 
 cudaError_t batched_configure(int threads, int fp64, long long n_max, int* per_sm) {
