@@ -12,12 +12,15 @@
 // (L2-resident) and the small b x b steps run in shared memory; no step needs
 // more than one SM, and the only inter-CTA traffic is the work counter.
 //
-// Every pass over rows (initial norms, CGS, residual update) is one routine:
-// a warp holds a group of rows in registers (n <= 256: eight values a lane),
-// issues all their loads at once, and for each basis row forms the
-// coefficients (a butterfly all-reduce over the warp) and subtracts.  Loads
-// of a group are in flight together, which is what bounds these passes: a
-// problem's residual sits in L2 and each pass is a few hundred kilobytes.
+// The passes over rows (initial norms, CGS, FP64 residual update) share one
+// routine: a warp holds a group of rows in registers (n <= 256: eight values
+// a lane), issues all their loads at once, and for each basis row forms the
+// coefficients (a butterfly all-reduce over the warp) and subtracts.  The FP32
+// residual update, the largest pass, spreads a row over eight lanes instead
+// (four rows a warp, float4 columns), which cuts the shuffle levels per
+// coefficient from five per row to three for four rows.  Loads of a group are
+// in flight together; a problem's residual sits in L2 and each pass is a few
+// hundred kilobytes.
 //
 // T is the storage and arithmetic type (float or double); NT (256 or 512) the
 // CTA size, a schedule parameter chosen by the host (autotuned per batch).
