@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
                                                        unsigned long long seed, unsigned long long problem,
                                                        long long* __restrict__ S_t, State* st, int first,
                                                        int last, int force) {
+  pdl_wait();
   // exact FP64 sampler: runs when the two-stage sampler asked for it, or always
   // (force, on the first level, which then raises the flag for the later levels)
   if (st->done || (!force && !st->sample_fallback)) return;
@@ -251,16 +252,15 @@ cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, un
   long long groups = (n + kSortChunk - 1) / kSortChunk;
   Pair* bufs[2] = {(Pair*)cand_a, (Pair*)cand_b};
   int cur = 0;
-  k_sample_level<<<(unsigned)groups, 1024, 0, s>>>(dvec, n, nullptr, 0, bufs[cur], b, greedy, seed, problem,
-                                                   S_t, st, 1, groups == 1 ? 1 : 0, force);
-  cudaError_t e = counted(cudaGetLastError());
+  cudaError_t e = counted(launch_pdl(k_sample_level, dim3((unsigned)groups), dim3(1024), 0, s, dvec, n,
+                                     (const Pair*)nullptr, 0LL, bufs[cur], b, greedy, seed, problem, S_t, st, 1,
+                                     groups == 1 ? 1 : 0, force));
   if (e != cudaSuccess) return e;
   while (groups > 1) {
     const long long n_in = groups * b;
     groups = (n_in + kSortChunk - 1) / kSortChunk;
-    k_sample_level<<<(unsigned)groups, 1024, 0, s>>>(dvec, n, bufs[cur], n_in, bufs[cur ^ 1], b, greedy, seed,
-                                                     problem, S_t, st, 0, groups == 1 ? 1 : 0, 0);
-    e = counted(cudaGetLastError());
+    e = counted(launch_pdl(k_sample_level, dim3((unsigned)groups), dim3(1024), 0, s, dvec, n, (const Pair*)bufs[cur],
+                           n_in, bufs[cur ^ 1], b, greedy, seed, problem, S_t, st, 0, groups == 1 ? 1 : 0, 0));
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
@@ -273,6 +273,7 @@ cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, un
 template <typename TR, typename TV>
 __global__ void k_gather(const TR* __restrict__ R, long long ldr, const long long* __restrict__ S_t,
                          TV* __restrict__ V, long long ldv, long long d, const State* st) {
+  pdl_wait();
   if (st->done) return;
   const long long i = blockIdx.y;
   if (i >= st->b_t) return;
@@ -285,12 +286,13 @@ cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const lon
                           long long ldv, long long d, int b, const State* st, cudaStream_t s) {
   dim3 grid((unsigned)((d + 255) / 256), (unsigned)b);
   if (r_is_fp64)
-    k_gather<double, double><<<grid, 256, 0, s>>>((const double*)R, ldr, S_t, (double*)V, ldv, d, st);
-  else if (v_is_fp64)
-    k_gather<float, double><<<grid, 256, 0, s>>>((const float*)R, ldr, S_t, (double*)V, ldv, d, st);
-  else
-    k_gather<float, float><<<grid, 256, 0, s>>>((const float*)R, ldr, S_t, (float*)V, ldv, d, st);
-  return counted(cudaGetLastError());
+    return counted(launch_pdl(k_gather<double, double>, grid, dim3(256), 0, s, (const double*)R, ldr, S_t, (double*)V,
+                              ldv, d, st));
+  if (v_is_fp64)
+    return counted(launch_pdl(k_gather<float, double>, grid, dim3(256), 0, s, (const float*)R, ldr, S_t, (double*)V,
+                              ldv, d, st));
+  return counted(launch_pdl(k_gather<float, float>, grid, dim3(256), 0, s, (const float*)R, ldr, S_t, (float*)V, ldv,
+                            d, st));
 }
 
 // ============================================================================
@@ -440,6 +442,7 @@ template <typename TQ>
 __global__ void k_qp_lowp(const TQ* __restrict__ Qt, long long ldq, float* __restrict__ Qp,
                           float* __restrict__ Qp_lo, long long ldp, float* __restrict__ QpT, float* __restrict__ QpT_lo,
                           long long ldpt, long long d, int bmax, const State* st) {
+  pdl_wait();
   if (st->done) return;
   const long long k = st->k;
   const int bp = (int)st->bp;
@@ -469,10 +472,10 @@ cudaError_t launch_qp_lowp(const void* Qt, int q_is_fp64, long long ldq, float* 
   unsigned g = (unsigned)((tot + 255) / 256);
   if (g > 2048) g = 2048;
   if (q_is_fp64)
-    k_qp_lowp<double><<<g, 256, 0, s>>>((const double*)Qt, ldq, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, d, b, st);
-  else
-    k_qp_lowp<float><<<g, 256, 0, s>>>((const float*)Qt, ldq, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, d, b, st);
-  return counted(cudaGetLastError());
+    return counted(launch_pdl(k_qp_lowp<double>, dim3(g), dim3(256), 0, s, (const double*)Qt, ldq, Qp, Qp_lo, ldp, QpT,
+                              QpT_lo, ldpt, d, b, st));
+  return counted(launch_pdl(k_qp_lowp<float>, dim3(g), dim3(256), 0, s, (const float*)Qt, ldq, Qp, Qp_lo, ldp, QpT,
+                            QpT_lo, ldpt, d, b, st));
 }
 
 // ============================================================================
@@ -570,6 +573,7 @@ cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* ma
 
 // Alg. 2 line 3 after a block: D = ||d||_1, k += b', t += 1, stopping test.
 __global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st) {
+  pdl_wait();
   if (st->done) return;
   const double D = block_fixed_sum(partials, np);
   if (threadIdx.x == 0) {
@@ -586,8 +590,7 @@ __global__ void k_finalize_block(const double* __restrict__ partials, int np, St
 }
 
 cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s) {
-  k_finalize_block<<<1, kFixedSumThreads, 0, s>>>(partials, nparts, st);
-  return counted(cudaGetLastError());
+  return counted(launch_pdl(k_finalize_block, dim3(1), dim3(kFixedSumThreads), 0, s, partials, nparts, st));
 }
 
 // ============================================================================

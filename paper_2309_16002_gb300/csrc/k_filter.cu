@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
                                                                   const long long* __restrict__ S_t,
                                                                   long long* __restrict__ skel,
                                                                   int* __restrict__ mark, State* st) {
+  pdl_wait();
   if (st->done) return;
   __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];   // Lw[j * LDF + t]: candidate j, step t
   __shared__ __align__(16) float Gs[kPchol64 * kPchol64LDF];   // G (stride LDG), later the factor transposed (LDF)
@@ -650,8 +651,8 @@ cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
   if (b > kRegCholMax) return cudaErrorInvalidValue;
   if (b <= kPchol64) {
-    k_pchol_f32_64<<<1, kPchol64Threads, 0, s>>>(G, ldg, Linv, ldl, perm, S_t, skel, mark, st);
-    return counted(cudaGetLastError());
+    return counted(launch_pdl(k_pchol_f32_64, dim3(1), dim3(kPchol64Threads), 0, s, G, ldg, Linv, ldl, perm, S_t,
+                              skel, mark, st));
   }
   const int ldf = (b + 4) & ~3;
   const size_t smem = (size_t)2 * b * ldf * sizeof(float);

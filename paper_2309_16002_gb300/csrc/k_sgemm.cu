@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(256) k_sgemm_cl(SgemmArgs g) {
   constexpr int TILE = 64, R = TILE / 16, LD = TILE + 4, LP = TILE + 1;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
+  pdl_wait();
   // every early exit below is taken by all CTAs of a cluster (same tile, same State)
   if (g.st && g.st->done) return;
   const long long M = dim_val(g.M), N = dim_val(g.N), K = dim_val(g.K);
@@ -319,13 +320,15 @@ cudaError_t launch_sgemm_cluster(const SgemmArgs& g, long long Mmax, long long N
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = 1;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = (unsigned)cs;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // the kernel starts with pdl_wait()
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   if (cs > 8) {
     // 16 CTAs per cluster is beyond the portable size: use it only where the
     // device can hold such a cluster (asked once per process), else two

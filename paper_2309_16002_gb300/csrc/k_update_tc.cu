@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                    long long d, const int* __restrict__ mark, double* __restrict__ dvec,
                    double* __restrict__ partials, State* st) {
   using C = PCfg<BMAX>;
+  pdl_wait();
   if (st->done) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -761,9 +762,8 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (n + PROWS - 1) / PROWS;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  k_update_tf32p<BMAX><<<grid, kPThreads, C::SMEM, s>>>(mR, mQ, mQT, L, ldl, n, d, mark, dvec, partials,
-                                                        const_cast<State*>(st));
-  return counted(cudaGetLastError());
+  return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mQ, mQT, L,
+                            ldl, n, d, mark, dvec, partials, const_cast<State*>(st)));
 }
 
 // ------------------------------------------------------------------ host side

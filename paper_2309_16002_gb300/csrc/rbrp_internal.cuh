@@ -120,6 +120,31 @@ __device__ __forceinline__ unsigned long long orderable(double x) {
 }
 constexpr unsigned long long kIneligible = 0xFFFFFFFFFFFFFFFFULL;
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// The kernels of the per-block chain are launched with launch_pdl: the next
+// kernel in the stream may then be scheduled as the one before it drains, and
+// its first statement, pdl_wait(), returns once that kernel has completed and
+// its writes are visible (at once after an ordinary launch).  Nothing calls
+// the early trigger, so a kernel's CTAs are only scheduled after every CTA of
+// the kernel before it has exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---------------------------------------------------------------- instrumentation
 // Number of kernels the library has launched (read by rbrp_profile_end).
 extern long long g_kernel_launches;
