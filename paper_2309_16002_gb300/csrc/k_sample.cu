@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
                                                               int greedy, unsigned long long seed,
                                                               unsigned long long problem, long long* __restrict__ S_t,
                                                               State* st) {
+  pdl_wait();
   if (st->done) return;  // read before any CTA writes the State: the same for every CTA
   __shared__ unsigned int h[kBins];
   unsigned int* bar = ncand + 2;
@@ -485,6 +486,27 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
     if (coop_sms[dev] > 0) {
       const int sms = coop_sms[dev];
       int cap = kSampCap;
+      // cooperative, and allowed to be scheduled as the previous kernel drains
+      // (programmatic dependent launch; the kernel starts with pdl_wait())
+      static int pdl_ok = 1;
+      if (pdl_ok) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)sms);
+        cfg.blockDim = dim3(kCoopThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_sample_coop, dvec, n, K32, hist1, hist2, want, cand,
+                                                 cand_key, cand_log, ncand, cap, b, greedy, seed, problem, S_t, st);
+        if (e == cudaSuccess) return counted(e);
+        (void)cudaGetLastError();  // the combination is not supported: plain cooperative launches from now on
+        pdl_ok = 0;
+      }
       void* args[] = {(void*)&dvec, (void*)&n, (void*)&K32, (void*)&hist1, (void*)&hist2, (void*)&want,
                       (void*)&cand, (void*)&cand_key, (void*)&cand_log, (void*)&ncand, (void*)&cap, (void*)&b,
                       (void*)&greedy, (void*)&seed, (void*)&problem, (void*)&S_t, (void*)&st};

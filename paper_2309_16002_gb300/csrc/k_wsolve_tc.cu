@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
                   const __grid_constant__ CUtensorMap tmGl, double* __restrict__ W64, long long ldw64, int w64_vec,
                   int n, int k, State* st) {
   using C = WCfg;
+  pdl_wait();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -389,6 +390,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
 // MMA B operand: Gh/Gl[(j0 + c) * ldt + r].
 __global__ void __launch_bounds__(128) k_wsolve_g(const double* __restrict__ L1, long long ld1, int k,
                                                   float* __restrict__ Gh, float* __restrict__ Gl, long long ldt) {
+  pdl_wait();
   const int J = blockIdx.y, j0 = J * WN;
   const int r0 = blockIdx.x * 128;
   if (r0 + 128 <= j0 || r0 >= k) return;
@@ -453,7 +455,9 @@ cudaError_t wsolve_all(const void* L, long long ldl, float* Wh, float* Wl, long 
     if (dev < 64) attr_set |= 1ULL << dev;
   }
   const int nblk = (int)((k + WN - 1) / WN);
-  k_wsolve_g<<<dim3((unsigned)((k + 127) / 128), (unsigned)nblk), 128, 0, s>>>(L1, ld1, (int)k, Gh, Gl, ldt);
+  cudaError_t eg = launch_pdl(k_wsolve_g, dim3((unsigned)((k + 127) / 128), (unsigned)nblk), dim3(128), 0, s, L1, ld1,
+                              (int)k, Gh, Gl, ldt);
+  if (eg != cudaSuccess) return eg;
   e = counted(cudaGetLastError());
   if (e != cudaSuccess) return e;
 
@@ -472,7 +476,9 @@ cudaError_t wsolve_all(const void* L, long long ldl, float* Wh, float* Wl, long 
   const long long ntiles = (n + WM - 1) / WM;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);  // persistent: one CTA per SM
   const int vec = (((uintptr_t)W64 & 15) == 0 && (ldw64 & 1) == 0) ? 1 : 0;
-  k_wsolve_rows<L64><<<grid, kWThreads, C::SMEM, s>>>(mL, mWh, mWl, mGh, mGl, W64, ldw64, vec, (int)n, (int)k, st);
+  cudaError_t er = launch_pdl(k_wsolve_rows<L64>, dim3(grid), dim3(kWThreads), (size_t)C::SMEM, s, mL, mWh, mWl, mGh,
+                              mGl, W64, ldw64, vec, (int)n, (int)k, st);
+  if (er != cudaSuccess) return er;
   return counted(cudaGetLastError());
 }
 
