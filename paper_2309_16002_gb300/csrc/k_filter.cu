@@ -502,93 +502,82 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
   __shared__ int s_perm[kPchol64];
   __shared__ int s_bp;
   const int m = (int)st->b_t;
-  const int tid = threadIdx.x, lane = tid & 31;
-  {
-    float v[kPchol64];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  __shared__ __align__(16) float lv[kPchol64];  // the pivot's factor column, published each step
+  __shared__ float s_ms[2][2];
+  __shared__ unsigned s_mx[2][2], s_ix[2][2];
+  // thread r holds column r of the Schur complement (= row r) in registers
+  float col[kPchol64];
+  float dr = 0.f;
 #pragma unroll
-    for (int r = 0; r < kPchol64; ++r) v[r] = (r < m && tid < m) ? G[(long long)r * ldg + tid] : 0.f;
-#pragma unroll
-    for (int r = 0; r < kPchol64; ++r) Gs[r * kPchol64LDG + tid] = v[r];
+  for (int j = 0; j < kPchol64; ++j) {
+    col[j] = (j < m && tid < m) ? G[(long long)j * ldg + tid] : 0.f;
+    if (j == tid) dr = col[j];
   }
   for (int e = tid; e < kPchol64 * kPchol64LDF; e += kPchol64Threads) Lw[e] = 0.f;
-  __syncthreads();
-  if (tid < 32) {
-    double tau_b = st->tau_b;
-    if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
-    const float tb = (float)tau_b;
-    const int j0 = lane, j1 = lane + 32;
-    bool al0 = j0 < m, al1 = j1 < m;
-    float d0 = al0 ? Gs[j0 * kPchol64LDG + j0] : 0.f;
-    float d1 = al1 ? Gs[j1 * kPchol64LDG + j1] : 0.f;
-    float total = d0 + d1;
+  double tau_b = st->tau_b;
+  if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
+  const float tb = (float)tau_b;
+  bool alive = tid < m;
+  {
+    float t = alive ? dr : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    const float* lj0 = Lw + j0 * kPchol64LDF;
-    const float* lj1 = Lw + j1 * kPchol64LDF;
-    int steps = 0;
-    for (int i = 0; i < m; ++i) {
-      // trailing mass of the remaining candidates (its shuffles overlap the pivot search)
-      float msum = (al0 ? d0 : 0.f) + (al1 ? d1 : 0.f);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
-      // pivot: the largest remaining d_j (> 0), ties to the smaller index
-      const float v0 = (al0 && d0 > 0.f) ? d0 : 0.f, v1 = (al1 && d1 > 0.f) ? d1 : 0.f;
-      const bool second = v1 > v0;
-      const unsigned bits = __float_as_uint(second ? v1 : v0);
-      const unsigned mx = __reduce_max_sync(0xffffffffu, bits);
-      if (mx == 0u) break;  // no positive pivot left
-      const unsigned mine = (bits == mx) ? (unsigned)(second ? j1 : j0) : 0xffffffffu;
-      const int p = (int)__reduce_min_sync(0xffffffffu, mine);
-      const float best = __uint_as_float(mx);
-      const float rinv = rsqrtf(best);
-      // both candidates' dot products over steps < i in one loop (the pivot's
-      // factor row is loaded once); rows past m are zero
-      const float* lp = Lw + p * kPchol64LDF;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-#pragma unroll 4
-      for (int t = 0; t < i; t += 4) {  // entries past step i - 1 are still zero
-        const float4 y = *(const float4*)(lp + t);
-        const float4 x = *(const float4*)(lj0 + t);
-        const float4 z = *(const float4*)(lj1 + t);
-        a0 = fmaf(x.x, y.x, a0);
-        a1 = fmaf(x.y, y.y, a1);
-        a2 = fmaf(x.z, y.z, a2);
-        a3 = fmaf(x.w, y.w, a3);
-        c0 = fmaf(z.x, y.x, c0);
-        c1 = fmaf(z.y, y.y, c1);
-        c2 = fmaf(z.z, y.z, c2);
-        c3 = fmaf(z.w, y.w, c3);
-      }
-      if (!(msum >= tb * total && msum > 0.f)) break;  // Alg. 2 line 8: b' = i
-      const float l0 = (Gs[j0 * kPchol64LDG + p] - ((a0 + a1) + (a2 + a3))) * rinv;
-      const float l1 = (Gs[j1 * kPchol64LDG + p] - ((c0 + c1) + (c2 + c3))) * rinv;
-      if (al0) {
-        if (j0 == p) {
-          Lw[j0 * kPchol64LDF + i] = best * rinv;
-          al0 = false;
-        } else {
-          Lw[j0 * kPchol64LDF + i] = l0;
-          d0 -= l0 * l0;
-        }
-      }
-      if (al1) {
-        if (j1 == p) {
-          Lw[j1 * kPchol64LDF + i] = best * rinv;
-          al1 = false;
-        } else {
-          Lw[j1 * kPchol64LDF + i] = l1;
-          d1 -= l1 * l1;
-        }
-      }
-      if (lane == 0) {
-        rdg[i] = rinv;
-        s_perm[i] = p;
-      }
-      __syncwarp();
-      steps = i + 1;
-    }
-    if (lane == 0) s_bp = steps;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_ms[1][w] = t;
   }
+  __syncthreads();
+  const float total = s_ms[1][0] + s_ms[1][1];
+  int steps = 0;
+  for (int i = 0; i < m; ++i) {
+    const int sl = i & 1;
+    // trailing mass and pivot (largest remaining d_r > 0, ties to the smaller index),
+    // per warp, then the two warps combined through shared memory
+    float ms = alive ? dr : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, o);
+    const unsigned bits = (alive && dr > 0.f) ? __float_as_uint(dr) : 0u;
+    const unsigned mxw = __reduce_max_sync(0xffffffffu, bits);
+    const unsigned ixw = __reduce_min_sync(0xffffffffu, (bits == mxw && mxw != 0u) ? (unsigned)tid : 0xffffffffu);
+    if (lane == 0) {
+      s_ms[sl][w] = ms;
+      s_mx[sl][w] = mxw;
+      s_ix[sl][w] = ixw;
+    }
+    __syncthreads();
+    const float msum = s_ms[sl][0] + s_ms[sl][1];
+    unsigned mx = s_mx[sl][0], p = s_ix[sl][0];
+    if (s_mx[sl][1] > mx || (s_mx[sl][1] == mx && s_ix[sl][1] < p)) {
+      mx = s_mx[sl][1];
+      p = s_ix[sl][1];
+    }
+    if (mx == 0u || !(msum >= tb * total && msum > 0.f)) break;  // the same on every thread; b' = i
+    const float rinv = rsqrtf(__uint_as_float(mx));
+    if (tid == (int)p) {  // the pivot's owner publishes l = S(:, p) / sqrt(d_p)
+#pragma unroll
+      for (int j = 0; j < kPchol64; j += 4)
+        *(float4*)(lv + j) = make_float4(col[j] * rinv, col[j + 1] * rinv, col[j + 2] * rinv, col[j + 3] * rinv);
+    }
+    __syncthreads();
+    const float lr = lv[tid];
+    if (alive) Lw[tid * kPchol64LDF + i] = lr;
+    if (tid == (int)p) alive = false;
+    dr -= lr * lr;
+    // rank-1 update of this column: S(j, r) -= l_j l_r
+#pragma unroll
+    for (int j = 0; j < kPchol64; j += 4) {
+      const float4 l4 = *(const float4*)(lv + j);
+      col[j] = fmaf(-l4.x, lr, col[j]);
+      col[j + 1] = fmaf(-l4.y, lr, col[j + 1]);
+      col[j + 2] = fmaf(-l4.z, lr, col[j + 2]);
+      col[j + 3] = fmaf(-l4.w, lr, col[j + 3]);
+    }
+    if (tid == 0) {
+      rdg[i] = rinv;
+      s_perm[i] = (int)p;
+    }
+    steps = i + 1;
+  }
+  if (tid == 0) s_bp = steps;
   __syncthreads();
   const int bp = s_bp;
   // the pivot-order factor Lc, transposed, over G (no longer needed):
