@@ -471,25 +471,24 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
 }
 
 // The same filter for blocks of at most 64 candidates, built around latency.
-// One warp runs the pivot loop: lane l owns candidates l and l + 32 (factor
-// rows in shared memory, d_j in registers); the pivot is two warp reductions
-// (redux.sync max over the FP32 bit patterns of d_j, which order like the
-// values for d_j >= 0, then min over the indices of the maxima: the largest
-// d_j, ties to the smaller index) and no block barrier; the trailing mass of
-// Alg. 2 line 8 is a shuffle reduction that runs beside them, and the two
-// candidates' dot products share one loop over the pivot's factor row.  The
-// inverse is column substitution with the column in registers: thread c
-// holds column c of Lc^{-1} and applies x_i = b_i / Lc(i, i),
-// b_r -= Lc(r, i) x_i for r > i, fully unrolled over the 64 rows so that every
-// thread runs the same instruction stream (entries above the diagonal stay
-// zero without a branch on c).
+// Right-looking: thread r holds column r of the Schur complement (the Gram
+// matrix minus the factor so far) in registers.  Each step takes the trailing
+// mass and the pivot (the largest remaining d_r > 0, ties to the smaller
+// index: redux.sync max over the FP32 bit patterns, which order like the
+// values for d_r >= 0, then min over the indices of the maxima) per warp,
+// combines the two warps through shared memory, and stops at the first step
+// whose trailing mass fails the test of Alg. 2 line 8; the pivot's owner then
+// publishes its scaled column l = S(:, p) / sqrt(d_p) and every thread applies
+// the rank-1 update S(:, r) -= l l_r to its column.  The kernel writes the
+// pivot-order factor Lc; Q'_V = Lc^{-1} V_perm follows as a column-parallel
+// substitution (k_trsm_rows_f32).
 constexpr int kPchol64 = 64;
 constexpr int kPchol64Threads = 64;
 constexpr int kPchol64LDF = 68;  // factor rows: float4 steps over t
 constexpr int kPchol64LDG = 65;  // G rows: odd stride, conflict-free column reads
 
 __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* __restrict__ G, long long ldg,
-                                                                  float* __restrict__ Linv, long long ldl,
+                                                                  float* __restrict__ Lc_out, long long ldl,
                                                                   int* __restrict__ perm,
                                                                   const long long* __restrict__ S_t,
                                                                   long long* __restrict__ skel,
@@ -497,8 +496,6 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
   pdl_wait();
   if (st->done) return;
   __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];   // Lw[j * LDF + t]: candidate j, step t
-  __shared__ __align__(16) float Gs[kPchol64 * kPchol64LDF];   // G (stride LDG), later the factor transposed (LDF)
-  __shared__ float rdg[kPchol64];
   __shared__ int s_perm[kPchol64];
   __shared__ int s_bp;
   const int m = (int)st->b_t;
@@ -571,50 +568,21 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
       col[j + 2] = fmaf(-l4.z, lr, col[j + 2]);
       col[j + 3] = fmaf(-l4.w, lr, col[j + 3]);
     }
-    if (tid == 0) {
-      rdg[i] = rinv;
-      s_perm[i] = (int)p;
-    }
+    if (tid == 0) s_perm[i] = (int)p;
     steps = i + 1;
   }
   if (tid == 0) s_bp = steps;
   __syncthreads();
   const int bp = s_bp;
-  // the pivot-order factor Lc, transposed, over G (no longer needed):
-  // LT[l][i] = Lc(i, l) = Lw[perm[i]][l] for l <= i < b', zero elsewhere; one
-  // factor row per thread
-  float* LT = Gs;
-  {
-    const int i = tid;
-    const float* src = Lw + (i < bp ? s_perm[i] : 0) * kPchol64LDF;
-#pragma unroll 16
-    for (int l = 0; l < kPchol64; ++l) LT[l * kPchol64LDF + i] = (l <= i && i < bp) ? src[l] : 0.f;
-  }
-  for (int i = bp + tid; i < kPchol64; i += kPchol64Threads) rdg[i] = 0.f;
-  __syncthreads();
+  // the pivot-order factor Lc(i, l) = Lw[perm[i]][l] for l <= i < b' (zero
+  // elsewhere) to Lc_out, one column per thread (coalesced across threads);
+  // Q'_V = Lc^{-1} V_perm is then a column-parallel substitution (k_trsm_rows_f32)
   {
     const int c = tid;
-    float x[kPchol64];
-#pragma unroll
-    for (int r = 0; r < kPchol64; ++r) x[r] = (r == c) ? 1.f : 0.f;
-#pragma unroll
+#pragma unroll 8
     for (int i = 0; i < kPchol64; ++i) {
-      const float xi = x[i] * rdg[i];
-      x[i] = xi;
-      // x_r -= Lc(r, i) x_i for r > i, four rows of column i per load
-#pragma unroll
-      for (int r4 = (i + 1) & ~3; r4 < kPchol64; r4 += 4) {
-        const float4 v = *(const float4*)(LT + i * kPchol64LDF + r4);
-        if (r4 + 0 > i) x[r4 + 0] = fmaf(-v.x, xi, x[r4 + 0]);
-        if (r4 + 1 > i) x[r4 + 1] = fmaf(-v.y, xi, x[r4 + 1]);
-        if (r4 + 2 > i) x[r4 + 2] = fmaf(-v.z, xi, x[r4 + 2]);
-        if (r4 + 3 > i) x[r4 + 3] = fmaf(-v.w, xi, x[r4 + 3]);
-      }
-    }
-    if (c < bp) {
-#pragma unroll
-      for (int i = 0; i < kPchol64; ++i)
-        if (i < bp) Linv[(long long)i * ldl + c] = (c <= i) ? x[i] : 0.f;
+      const float v = (c <= i && i < bp) ? Lw[s_perm[i] * kPchol64LDF + c] : 0.f;
+      Lc_out[(long long)i * ldl + c] = v;
     }
   }
   {
@@ -635,6 +603,72 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
     if (bp == 0) st->done = 1;
   }
 }
+
+// Q'_V = Lc^{-1} V(perm, :) on the plain TF32 path (Alg. 2 lines 9-10): rows by
+// forward substitution, Y(i, :) = (V(perm[i], :) - sum_{l<i} Lc(i, l) Y(l, :)) / Lc(i, i)
+// for i < b' <= 64, FP32.  32 columns per CTA, one octet of lanes per column;
+// lane q of the octet holds rows q, q + 8, ... of its column in registers and,
+// right-looking, subtracts Lc(r, i) y_i from its remaining rows as soon as
+// y_i is known (one shuffle from the lane that owns row i), so a row costs a
+// multiply, a shuffle and a fused multiply-add on the critical path.
+__global__ void __launch_bounds__(256) k_trsm_rows_f32(const float* __restrict__ Lc, long long ldl,
+                                                       const int* __restrict__ perm, const float* __restrict__ V,
+                                                       long long ldv, float* __restrict__ Ybase, DimRef y_off,
+                                                       long long ldy, long long d, const State* st) {
+  pdl_wait();
+  if (st->done) return;
+  __shared__ float Ls[kPchol64][kPchol64 + 1];
+  __shared__ float rdiag[kPchol64];
+  const int bp = (int)st->bp;
+  const int lane = threadIdx.x & 31, cl = threadIdx.x >> 3, part = threadIdx.x & 7;
+  const long long c = (long long)blockIdx.x * 32 + cl;
+  for (int e = threadIdx.x; e < kPchol64 * kPchol64; e += blockDim.x) {
+    const int r = e >> 6, l = e & 63;
+    Ls[r][l] = (r < bp && l < bp) ? Lc[(long long)r * ldl + l] : 0.f;
+  }
+  for (int r = threadIdx.x; r < kPchol64; r += blockDim.x) rdiag[r] = (r < bp) ? 1.f / Lc[(long long)r * ldl + r] : 0.f;
+  float b[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int r = part + 8 * q;
+    b[q] = (r < bp && c < d) ? V[(long long)perm[r] * ldv + c] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int qi = 0; qi < 8; ++qi) {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int i = 8 * qi + o;
+      if (i < bp) {
+        float yi = b[qi] * rdiag[i];                           // right on the lane that owns row i
+        yi = __shfl_sync(0xffffffffu, yi, (lane & ~7) | o);
+        if (part == o) b[qi] = yi;
+#pragma unroll
+        for (int q = qi; q < 8; ++q) {
+          const int r = part + 8 * q;
+          if (r > i) b[q] = fmaf(-Ls[r][i], yi, b[q]);
+        }
+      }
+    }
+  }
+  if (c < d) {
+    float* Y = Ybase + dim_val(y_off);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = part + 8 * q;
+      if (r < bp) Y[(long long)r * ldy + c] = b[q];
+    }
+  }
+}
+
+cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm, const float* V, long long ldv,
+                                 float* Y, DimRef y_off, long long ldy, long long d, const State* st,
+                                 cudaStream_t s) {
+  return counted(launch_pdl(k_trsm_rows_f32, dim3((unsigned)((d + 31) / 32)), dim3(256), 0, s, Lc, ldl, perm, V, ldv,
+                            Y, y_off, ldy, d, st));
+}
+
+int filter_f32_writes_factor(int b) { return b <= kPchol64; }
 
 cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {

@@ -410,9 +410,13 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     LK((sgemm<float, float, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0), p.ldg,
                                   dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
     LK(launch_filter_f32((const float*)u.G, p.ldg, u.S_t, (float*)u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
-    LK((sgemm<float, float, false>(p, u, u.Lc, dim_const(0), p.ldlc, u.V, dim_const(0), p.ldq, u.Qt,
-                                   dim_dev(&st->k, p.ldq), p.ldq, dim_dev(&st->bp), dim_const(d), dim_dev(&st->bp), b,
-                                   d, b, 1.0, 0.0, s, u.perm)));
+    if (filter_f32_writes_factor((int)p.b))
+      LK(launch_trsm_rows_f32((const float*)u.Lc, p.ldlc, u.perm, (const float*)u.V, p.ldq, (float*)u.Qt,
+                              dim_dev(&st->k, p.ldq), p.ldq, d, st, s));
+    else
+      LK((sgemm<float, float, false>(p, u, u.Lc, dim_const(0), p.ldlc, u.V, dim_const(0), p.ldq, u.Qt,
+                                     dim_dev(&st->k, p.ldq), p.ldq, dim_dev(&st->bp), dim_const(d), dim_dev(&st->bp),
+                                     b, d, b, 1.0, 0.0, s, u.perm)));
   } else {
     LK((sgemm<double, double, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0),
                                     p.ldg, dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));

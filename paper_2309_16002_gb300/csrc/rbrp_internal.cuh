@@ -187,6 +187,11 @@ cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, 
 // FP32 filter (plain TF32 path): as launch_filter on an FP32 Gram matrix, but
 // writes Linv = Lc^{-1} (b' x b', FP32, lower triangular, leading dimension
 // ldl) instead of Lc.
+// b <= 64: launch_filter_f32 writes the pivot-order factor Lc (then Q'_V by
+// launch_trsm_rows_f32); larger b: the explicit inverse Lc^{-1}.
+int filter_f32_writes_factor(int b);
+cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm, const float* V, long long ldv,
+                                 float* Y, DimRef y_off, long long ldy, long long d, const State* st, cudaStream_t s);
 cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
