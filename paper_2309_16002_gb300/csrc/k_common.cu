@@ -82,33 +82,6 @@ cudaError_t launch_init_norms(const void* X, int x_is_fp64, long long n, long lo
   return counted(cudaGetLastError());
 }
 
-// Deterministic warp sum of partials[0..np) (fixed lane assignment and tree).
-// Sum of np partials in a fixed order (independent of timing), by a CTA of
-// kFixedSumThreads threads; every thread gets the result.  Thread t adds
-// partials t, t + 256, ... in order (eight loads in flight), then the warps'
-// sums are combined in warp order.
-constexpr int kFixedSumThreads = 256;
-__device__ __forceinline__ double block_fixed_sum(const double* partials, int np) {
-  __shared__ double red[kFixedSumThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31;
-  double s = 0.0;
-  for (int i0 = tid; i0 < np; i0 += 8 * kFixedSumThreads) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (i0 + u * kFixedSumThreads < np) ? partials[i0 + u * kFixedSumThreads] : 0.0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) s += v[u];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) red[tid >> 5] = s;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < kFixedSumThreads / 32; ++w) t += red[w];
-  return t;
-}
-
 __device__ __forceinline__ void stop_test(State* st) {
   const bool cap = st->k >= st->k_cap;
   const bool tol_met = (st->tau >= 0.0) && !(st->D > st->tau * st->D0);
@@ -117,7 +90,7 @@ __device__ __forceinline__ void stop_test(State* st) {
 
 __global__ void k_finish_init(const double* __restrict__ partials, int np, State* st, double tau, double tau_b,
                               long long k_cap) {
-  const double D0 = block_fixed_sum(partials, np);
+  const double D0 = fixed_sum_partials<kFixedSumThreads>(partials, np);
   if (threadIdx.x == 0) {
     st->tau = tau;
     st->tau_b = tau_b;
@@ -575,18 +548,8 @@ cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* ma
 __global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st) {
   pdl_wait();
   if (st->done) return;
-  const double D = block_fixed_sum(partials, np);
-  if (threadIdx.x == 0) {
-    st->D = D;
-    st->k += st->bp;
-    st->t += 1;
-    if (!isfinite(D)) {
-      st->status = RBRP_ENONFINITE;
-      st->done = 1;
-    } else {
-      stop_test(st);
-    }
-  }
+  const double D = fixed_sum_partials<kFixedSumThreads>(partials, np);
+  if (threadIdx.x == 0) finish_block(st, D);
 }
 
 cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s) {

@@ -19,6 +19,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "rbrp_internal.cuh"
 
 namespace rbrp {
@@ -611,10 +613,15 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
 // right-looking, subtracts Lc(r, i) y_i from its remaining rows as soon as
 // y_i is known (one shuffle from the lane that owns row i), so a row costs a
 // multiply, a shuffle and a fused multiply-add on the critical path.
+// With Qp set, the kernel also writes the update's operand copies of Q'
+// (rows of Qp, ld ldp, and the transpose QpT, ld ldpt, rows >= b' and columns
+// >= d zero; Qp covers qrows rows), which k_qp_lowp makes otherwise.
 __global__ void __launch_bounds__(256) k_trsm_rows_f32(const float* __restrict__ Lc, long long ldl,
                                                        const int* __restrict__ perm, const float* __restrict__ V,
                                                        long long ldv, float* __restrict__ Ybase, DimRef y_off,
-                                                       long long ldy, long long d, const State* st) {
+                                                       long long ldy, long long d, float* __restrict__ Qp,
+                                                       long long ldp, float* __restrict__ QpT, long long ldpt,
+                                                       int qrows, const State* st) {
   pdl_wait();
   if (st->done) return;
   __shared__ float Ls[kPchol64][kPchol64 + 1];
@@ -659,13 +666,23 @@ __global__ void __launch_bounds__(256) k_trsm_rows_f32(const float* __restrict__
       if (r < bp) Y[(long long)r * ldy + c] = b[q];
     }
   }
+  if (Qp && c < ldp) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = part + 8 * q;
+      const float v = (r < bp && c < d) ? b[q] : 0.f;
+      if (r < qrows) Qp[(long long)r * ldp + c] = v;
+      if (r < qrows && c < d) QpT[c * ldpt + r] = v;
+    }
+  }
 }
 
 cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm, const float* V, long long ldv,
-                                 float* Y, DimRef y_off, long long ldy, long long d, const State* st,
-                                 cudaStream_t s) {
-  return counted(launch_pdl(k_trsm_rows_f32, dim3((unsigned)((d + 31) / 32)), dim3(256), 0, s, Lc, ldl, perm, V, ldv,
-                            Y, y_off, ldy, d, st));
+                                 float* Y, DimRef y_off, long long ldy, long long d, float* Qp, long long ldp,
+                                 float* QpT, long long ldpt, int qrows, const State* st, cudaStream_t s) {
+  const long long cols = Qp ? std::max(d, ldp) : d;
+  return counted(launch_pdl(k_trsm_rows_f32, dim3((unsigned)((cols + 31) / 32)), dim3(256), 0, s, Lc, ldl, perm, V,
+                            ldv, Y, y_off, ldy, d, Qp, ldp, QpT, ldpt, qrows, st));
 }
 
 int filter_f32_writes_factor(int b) { return b <= kPchol64; }

@@ -342,10 +342,14 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
   for (int j = threadIdx.x; j < kBins; j += kCoopThreads)
     if (h[j]) atomicAdd(&hist1[j], h[j]);
   grid_barrier(bar, st);
-  // pass 2: histogram of the next 11 bits inside the cut bin
+  // pass 2: histogram of the next 11 bits inside the cut bin -- skipped (with
+  // its barrier) when the whole cut bin adds few candidates (the final ranking
+  // is quadratic in their number), which every CTA decides alike from the
+  // same first histogram
   unsigned int below1, total1;
   const int b1 = find_bin(hist1, (unsigned int)want, &below1, &total1);
-  if (b1 < kBins) {
+  const bool one_level = b1 < kBins && below1 + __ldcg(hist1 + b1) <= (unsigned int)(2 * want);
+  if (b1 < kBins && !one_level) {
     for (int j = threadIdx.x; j < kBins; j += kCoopThreads) h[j] = 0;
     __syncthreads();
     for (long long i = g0; i < n; i += gstride) {
@@ -356,10 +360,12 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
     for (int j = threadIdx.x; j < kBins; j += kCoopThreads)
       if (h[j]) atomicAdd(&hist2[j], h[j]);
   }
-  grid_barrier(bar, st);
+  if (!one_level) grid_barrier(bar, st);
   // pass 3: candidates with their exact FP64 keys
   unsigned int c22 = 0x3FFFFFu;
-  if (b1 < kBins) {
+  if (one_level) {
+    c22 = ((unsigned int)b1 << 11) | 0x7FFu;  // every row of the cut bin
+  } else if (b1 < kBins) {
     unsigned int below2, total2;
     const int b2 = find_bin(hist2, (unsigned int)(want - (int)below1), &below2, &total2);
     c22 = ((unsigned int)b1 << 11) | (unsigned int)(b2 >= kBins ? kBins - 1 : b2);

@@ -410,9 +410,9 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     LK((sgemm<float, float, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0), p.ldg,
                                   dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
     LK(launch_filter_f32((const float*)u.G, p.ldg, u.S_t, (float*)u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
-    if (filter_f32_writes_factor((int)p.b))
+    if (filter_f32_writes_factor((int)p.b))  // also writes the update's copies of Q' (no k_qp_lowp)
       LK(launch_trsm_rows_f32((const float*)u.Lc, p.ldlc, u.perm, (const float*)u.V, p.ldq, (float*)u.Qt,
-                              dim_dev(&st->k, p.ldq), p.ldq, d, st, s));
+                              dim_dev(&st->k, p.ldq), p.ldq, d, u.Qp, p.ldp, u.QpT, p.ldpt, (int)p.ldpt, st, s));
     else
       LK((sgemm<float, float, false>(p, u, u.Lc, dim_const(0), p.ldlc, u.V, dim_const(0), p.ldq, u.Qt,
                                      dim_dev(&st->k, p.ldq), p.ldq, dim_dev(&st->bp), dim_const(d), dim_dev(&st->bp),
@@ -441,7 +441,8 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   // lines 12 and 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
   if (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) {
     const int split = (p.prec == RBRP_TF32X3);
-    LK(launch_qp_lowp(u.Qt, !p.f32, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
+    if (!(p.f32 && filter_f32_writes_factor((int)p.b)))  // else the Q' substitution wrote them
+      LK(launch_qp_lowp(u.Qt, !p.f32, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
     LK(timed(g_prof.upd, s, [&] {
       return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, (float*)u.L,
                                 p.ldl, u.mark, u.dvec, u.part, st, (int)p.ldpt, split, s);

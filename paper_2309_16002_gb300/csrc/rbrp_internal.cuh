@@ -120,6 +120,52 @@ __device__ __forceinline__ unsigned long long orderable(double x) {
 }
 constexpr unsigned long long kIneligible = 0xFFFFFFFFFFFFFFFFULL;
 
+// ---------------------------------------------------------------- end of a block
+// Sum of np partials in a fixed order (independent of timing and of NT >= 256):
+// thread t < 256 adds partials t, t + 256, ... in order (eight loads in
+// flight), then the warps' sums are combined in warp order (warps past the
+// eighth add exact zeros).  Every thread of the CTA calls it and gets the sum.
+constexpr int kFixedSumThreads = 256;
+template <int NT>
+__device__ __forceinline__ double fixed_sum_partials(const double* partials, int np) {
+  static_assert(NT >= kFixedSumThreads && NT % 32 == 0, "CTA size");
+  __shared__ double red[NT / 32];
+  const int tid = threadIdx.x, lane = tid & 31;
+  double s = 0.0;
+  if (tid < kFixedSumThreads) {
+    for (int i0 = tid; i0 < np; i0 += 8 * kFixedSumThreads) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (i0 + u * kFixedSumThreads < np) ? partials[i0 + u * kFixedSumThreads] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[tid >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) t += red[w];
+  return t;
+}
+
+// Alg. 2 line 3 after a block: D = ||d||_1, k += b', t += 1, stopping test.
+__device__ __forceinline__ void finish_block(State* st, double D) {
+  st->D = D;
+  st->k += st->bp;
+  st->t += 1;
+  if (!isfinite(D)) {
+    st->status = RBRP_ENONFINITE;
+    st->done = 1;
+  } else {
+    const bool cap = st->k >= st->k_cap;
+    const bool tol_met = (st->tau >= 0.0) && !(st->D > st->tau * st->D0);
+    st->done = (cap || tol_met) ? 1 : 0;
+  }
+}
+
 // ---------------------------------------------------------------- programmatic dependent launch
 // The kernels of the per-block chain are launched with launch_pdl: the next
 // kernel in the stream may then be scheduled as the one before it drains, and
@@ -191,7 +237,8 @@ cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, 
 // launch_trsm_rows_f32); larger b: the explicit inverse Lc^{-1}.
 int filter_f32_writes_factor(int b);
 cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm, const float* V, long long ldv,
-                                 float* Y, DimRef y_off, long long ldy, long long d, const State* st, cudaStream_t s);
+                                 float* Y, DimRef y_off, long long ldy, long long d, float* Qp, long long ldp,
+                                 float* QpT, long long ldpt, int qrows, const State* st, cudaStream_t s);
 cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
