@@ -687,8 +687,9 @@ cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm
 
 int filter_f32_writes_factor(int b) { return b <= kPchol64; }
 
-cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
+cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Lout, long long ldl,
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+  float* Linv = Lout;  // the factor for b <= 64, its inverse above
   if (b > kRegCholMax) return cudaErrorInvalidValue;
   if (b <= kPchol64) {
     return counted(launch_pdl(k_pchol_f32_64, dim3(1), dim3(kPchol64Threads), 0, s, G, ldg, Linv, ldl, perm, S_t,

@@ -230,16 +230,17 @@ template <typename TA, typename TB, typename TC, typename TACC>
 cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, int tile, cudaStream_t s);
 cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
                           int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
-// FP32 filter (plain TF32 path): as launch_filter on an FP32 Gram matrix, but
-// writes Linv = Lc^{-1} (b' x b', FP32, lower triangular, leading dimension
-// ldl) instead of Lc.
-// b <= 64: launch_filter_f32 writes the pivot-order factor Lc (then Q'_V by
-// launch_trsm_rows_f32); larger b: the explicit inverse Lc^{-1}.
+// FP32 filter (plain TF32 path): as launch_filter on an FP32 Gram matrix.  Into
+// Lout (b' x b', FP32, lower triangular, leading dimension ldl) it writes, for
+// b <= 64 (filter_f32_writes_factor), the pivot-order factor Lc, after which
+// launch_trsm_rows_f32 forms Q'_V = Lc^{-1} V_perm (and the update's copies of
+// Q' when Qp is given); for larger b the explicit inverse Lc^{-1}, which a
+// product with V_perm turns into Q'_V.
 int filter_f32_writes_factor(int b);
 cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm, const float* V, long long ldv,
                                  float* Y, DimRef y_off, long long ldy, long long d, float* Qp, long long ldp,
                                  float* QpT, long long ldpt, int qrows, const State* st, cudaStream_t s);
-cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Linv, long long ldl,
+cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Lout, long long ldl,
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
                         State* st, cudaStream_t s);
