@@ -80,3 +80,44 @@ def test_status_strings(libpath):
     L = rbrp.load()
     assert L.rbrp_status_string(0) == b"ok"
     assert b"workspace" in L.rbrp_status_string(7)
+
+
+def test_batched_workspace_validation_on_host(libpath):
+    """Host logic of the batched entry points: sizes and limits, no GPU needed."""
+    import ctypes
+    from paper_2309_16002_gb300 import rbrp
+    L = rbrp.load()
+
+    def size(ms, ns, **kw):
+        P = len(ms)
+        m = (ctypes.c_int64 * max(P, 1))(*ms)
+        n = (ctypes.c_int64 * max(P, 1))(*ns)
+        o = rbrp.make_opts(**kw)
+        out = ctypes.c_size_t(0)
+        st = L.rbrp_batched_workspace_size(P, m, n, ctypes.byref(o), ctypes.byref(out))
+        return st, out.value
+
+    st, a = size([100, 2000], [30, 256], block=16, precision="fp32")
+    assert st == 0 and a > 0
+    # one slot per resident CTA of the largest schedule, each for the largest problem
+    st, b = size([100, 2000, 50], [30, 256, 10], block=16, precision="fp32")
+    assert st == 0 and b >= a
+    st64, c = size([100, 2000], [30, 256], block=16, precision="fp64")
+    assert st64 == 0 and c > a
+    assert size([4097], [10], block=16, precision="fp32")[0] == 1   # m > 4096
+    assert size([10], [257], block=16, precision="fp32")[0] == 1    # n > 256
+    assert size([10], [10], block=33, precision="fp32")[0] == 1     # b > 32
+    assert size([0], [10], block=16, precision="fp32")[0] == 1      # empty problem
+    assert size([10], [10], block=8, precision="fp32", sampler="greedy_exact")[0] == 0
+    assert size([], [], block=8, precision="fp32")[0] == 0          # P = 0 is valid (nothing to do)
+
+
+def test_opts_layout_matches_the_header(libpath):
+    """rbrp_default_opts fills every field the binding declares (same layout as rbrp.h)."""
+    import ctypes
+    from paper_2309_16002_gb300 import rbrp
+    o = rbrp.Opts()
+    ctypes.memset(ctypes.byref(o), 0xAB, ctypes.sizeof(o))
+    rbrp.load().rbrp_default_opts(ctypes.byref(o))
+    assert (o.precision, o.block, o.tau_b, o.k_max, o.seed, o.problem) == (1, 64, -1.0, 0, 0, 0)
+    assert (o.sampler, o.w_precision, o.form, o.reserved) == (0, 0, 0, 0)
