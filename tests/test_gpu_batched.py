@@ -220,3 +220,38 @@ def test_batched_nonfinite_and_limits(G):
         G.rbrp_id_batched([torch.zeros((10, 300), dtype=torch.float64, device="cuda:0")], 1e-3)
     with pytest.raises(G.RBRPError):
         G.rbrp_id_batched([torch.zeros((10, 30), dtype=torch.float64, device="cuda:0")], 1e-3, block=64)
+
+
+def test_batched_full_workload_sampled(G):
+    """The batched benchmark's workload at full size and in its launch configuration (4096
+    kernel blocks, FP32 form, tol 1e-5, b = 16, autotuned schedule, one CUDA-graph replay):
+    every problem converges with W(S, :) = I, and a sample of problems meets the FP32 bar
+    against the oracle run with the same Philox problem id."""
+    import torch
+    tol, b = 1e-5, 16
+    Xs_np = WL.kernel_blocks(P=4096, seed=4)
+    Xs = [torch.from_numpy(X).to("cuda:0") for X in Xs_np]
+    B = G.Batch(Xs, block=b, seed=0, precision="fp32")
+    B.tune(tol, reps=1)
+    g = B.graph(tol)
+    B.k_out.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    st = B.status.cpu().numpy()
+    ks = B.k_out.cpu().numpy()
+    assert (st == 0).all(), np.unique(st, return_counts=True)
+    assert (ks > 0).all()
+    errs = B.err.cpu().numpy()
+    assert (errs <= tol).all()
+    for p in range(0, 4096, 256):  # 16 problems across the size range
+        X64 = Xs_np[p].astype(np.float64)
+        S = B.S[p][:int(ks[p])].cpu().numpy()
+        W = B.W[p][:, :int(ks[p])].cpu().numpy()
+        k = len(S)
+        assert np.array_equal(W[S], np.eye(k)), p
+        ref = O.rbrp_id(X64, tau=tol, b=b, seed=0, problem=p)
+        e_gpu = _e(X64, S, W)
+        e_same = float(np.sqrt(O.skeleton_error_sq(X64, S)))
+        assert e_gpu <= max(1.05 * e_same, e_same + 1e-5), (p, e_gpu, e_same)
+        assert e_gpu ** 2 <= 1.05 * tol + 1e-10, (p, e_gpu ** 2)
+        assert k <= 1.1 * len(ref["S"]) + b, (p, k, len(ref["S"]))
