@@ -148,7 +148,10 @@ rbrp_status rbrp_host_workspace_size(int64_t n, int64_t d, int x_is_fp64, const 
  * leading dimension d) to the device, runs rbrp_id, copies S and W back.
  * skel_host: int64[k_cap]; W_host: FP64 n x k_cap row-major (ldw = k_cap),
  * columns >= k left untouched.  Pinned host memory makes the copies
- * asynchronous; pageable memory works but is slower.
+ * asynchronous; pageable memory works but is slower.  W is copied out in row
+ * ranges on a second stream (created and destroyed inside the call) while the
+ * W solve (Alg. 3) of the later ranges still runs on `stream`.  The call is
+ * synchronous: every copy has completed when it returns, on success or error.
  */
 rbrp_status rbrp_id_host(const void *X_host, int x_is_fp64, int64_t n, int64_t d, double tol,
                          const rbrp_opts *o, void *workspace, size_t ws_bytes,

@@ -673,10 +673,12 @@ __global__ void k_w_finish(double* __restrict__ W, long long ldw, const float* _
     if (W32) W[i * ldw + j] = (double)W32[i * ldw32 + j];
   }
 }
-__global__ void k_w_identity(double* __restrict__ W, long long ldw, long long k, const long long* __restrict__ skel) {
+__global__ void k_w_identity(double* __restrict__ W, long long ldw, long long k, const long long* __restrict__ skel,
+                             long long r0, long long r1) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / k, j = e % k;
-    W[skel[i] * ldw + j] = (i == j) ? 1.0 : 0.0;
+    const long long r = skel[i];
+    if (r >= r0 && r < r1) W[r * ldw + j] = (i == j) ? 1.0 : 0.0;
   }
 }
 
@@ -688,7 +690,14 @@ cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long lon
     cudaError_t e = counted(cudaGetLastError());
     if (e != cudaSuccess) return e;
   }
-  k_w_identity<<<grid_for(k * k), 256, 0, s>>>(W, ldw, k, skel);
+  k_w_identity<<<grid_for(k * k), 256, 0, s>>>(W, ldw, k, skel, 0, n);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_w_identity_rows(double* W, long long ldw, long long k, const long long* skel, long long r0,
+                                   long long r1, cudaStream_t s) {
+  if (k <= 0 || r1 <= r0) return cudaSuccess;
+  k_w_identity<<<grid_for(k * k), 256, 0, s>>>(W, ldw, k, skel, r0, r1);
   return counted(cudaGetLastError());
 }
 

@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(128) k_wsolve_g(const double* __restrict__ L1,
 template <bool L64>
 cudaError_t wsolve_all(const void* L, long long ldl, float* Wh, float* Wl, long long ldw32, double* W64,
                        long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl, long long ldt,
-                       long long n, long long k, State* st, cudaStream_t s) {
+                       long long r0, long long r1, bool form_g, long long k, State* st, cudaStream_t s) {
   using C = WCfg;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -454,12 +454,22 @@ cudaError_t wsolve_all(const void* L, long long ldl, float* Wh, float* Wl, long 
     if (e != cudaSuccess) return e;
     if (dev < 64) attr_set |= 1ULL << dev;
   }
-  const int nblk = (int)((k + WN - 1) / WN);
-  cudaError_t eg = launch_pdl(k_wsolve_g, dim3((unsigned)((k + 127) / 128), (unsigned)nblk), dim3(128), 0, s, L1, ld1,
-                              (int)k, Gh, Gl, ldt);
-  if (eg != cudaSuccess) return eg;
-  e = counted(cudaGetLastError());
-  if (e != cudaSuccess) return e;
+  if (form_g) {
+    const int nblk = (int)((k + WN - 1) / WN);
+    cudaError_t eg = launch_pdl(k_wsolve_g, dim3((unsigned)((k + 127) / 128), (unsigned)nblk), dim3(128), 0, s, L1,
+                                ld1, (int)k, Gh, Gl, ldt);
+    if (eg != cudaSuccess) return eg;
+    e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+  }
+  if (r1 <= r0) return cudaSuccess;
+  // Rows [r0, r1) only: the maps and W64 start at row r0 (r0 is a multiple of
+  // the tile height, so every base stays 16-byte aligned and tiles line up).
+  const long long n = r1 - r0;
+  L = (const char*)L + r0 * ldl * (L64 ? 8 : 4);
+  Wh += r0 * ldw32;
+  Wl += r0 * ldw32;
+  W64 += r0 * ldw64;
 
   CUtensorMap mL, mWh, mWl, mGh, mGl;
   if (L64) {
@@ -486,11 +496,15 @@ cudaError_t wsolve_all(const void* L, long long ldl, float* Wh, float* Wl, long 
 
 cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* Wh, float* Wl, long long ldw32,
                              double* W64, long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl,
-                             long long ldt, long long n, long long k, State* st, cudaStream_t s) {
+                             long long ldt, long long n, long long r0, long long r1, bool form_g, long long k,
+                             State* st, cudaStream_t s) {
   if (k <= 0 || n <= 0) return cudaSuccess;
+  if (r0 < 0 || r1 > n || r0 % tc::WM != 0) return cudaErrorInvalidValue;
   if (l_is_fp64)
-    return tc::wsolve_all<true>(L, ldl, Wh, Wl, ldw32, W64, ldw64, L1, ld1, Gh, Gl, ldt, n, k, st, s);
-  return tc::wsolve_all<false>(L, ldl, Wh, Wl, ldw32, W64, ldw64, L1, ld1, Gh, Gl, ldt, n, k, st, s);
+    return tc::wsolve_all<true>(L, ldl, Wh, Wl, ldw32, W64, ldw64, L1, ld1, Gh, Gl, ldt, r0, r1, form_g, k, st, s);
+  return tc::wsolve_all<false>(L, ldl, Wh, Wl, ldw32, W64, ldw64, L1, ld1, Gh, Gl, ldt, r0, r1, form_g, k, st, s);
 }
+
+int wsolve_tc_rows_per_tile() { return tc::WM; }
 
 }  // namespace rbrp

@@ -505,9 +505,18 @@ cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// Receiver of finished row ranges of W: after done(r0, r1) is called, rows
+// [r0, r1) of W are final once the work queued on the stream so far completes,
+// so a caller can start copying them while later rows are still being solved.
+struct WSink {
+  long long chunk_rows = 0;  // rows per range (rounded to whole tiles)
+  cudaError_t (*done)(void* ctx, long long r0, long long r1, long long k, cudaStream_t s) = nullptr;
+  void* ctx = nullptr;
+};
+
 // Alg. 3: W(S,:) = I, W(rest,:) = L2 L1^{-1}, blocked right-to-left substitution.
 rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* skel, double* W, long long ldw,
-                    cudaStream_t s) {
+                    cudaStream_t s, const WSink* sink = nullptr) {
   if (k <= 0) return RBRP_OK;
   const long long n = p.n;
   CK(launch_gather_rows_f64(u.L, p.l64, p.ldl, skel, k, u.L1, k, s));
@@ -525,18 +534,34 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
       CK(launch_trsm_cols<double>(W, ldw, n, j0, (int)nb, u.L1, k, s));
     }
     CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));
-  } else {
+    if (sink) CK(sink->done(sink->ctx, 0, n, k, s));
+  } else if (!sink) {
     // FP32 solve on tensor cores (3xTF32): every 64-column block of W is one
     // product with the precomputed block-inverse factor, then W(S, :) = I.
-    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, k, u.st, s));
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, n, true,
+                        k, u.st, s));
     CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));  // W(S, :) = I exactly
+  } else {
+    // The same solve in row ranges (rows are independent once G is formed),
+    // each finished with its skeleton rows set to I and handed to the sink.
+    const long long tile = wsolve_tc_rows_per_tile();
+    const long long chunk = std::max(tile, (sink->chunk_rows + tile - 1) / tile * tile);
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, 0, true,
+                        k, u.st, s));
+    for (long long r0 = 0; r0 < n; r0 += chunk) {
+      const long long r1 = std::min(n, r0 + chunk);
+      CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, r0, r1,
+                          false, k, u.st, s));
+      CK(launch_w_identity_rows(W, ldw, k, skel, r0, r1, s));
+      CK(sink->done(sink->ctx, r0, r1, k, s));
+    }
   }
   return RBRP_OK;
 }
 
 rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long long ldx, double tol,
                 const rbrp_opts* o, void* ws, size_t ws_bytes, long long* skel, double* W, long long ldw,
-                rbrp_result* res, cudaStream_t s) {
+                rbrp_result* res, cudaStream_t s, const WSink* sink = nullptr) {
   Plan p;
   rbrp_status rs = make_plan(n, d, o, &p);
   if (rs != RBRP_OK) return rs;
@@ -598,7 +623,7 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   {
     rbrp_status wrs = RBRP_OK;
     cudaError_t te = timed(g_prof.wsv, s, [&] {
-      wrs = solve_w(p, u, h.k, skel, W, ldw, s);
+      wrs = solve_w(p, u, h.k, skel, W, ldw, s, sink);
       return cudaSuccess;
     });
     if (te != cudaSuccess) {
@@ -985,6 +1010,45 @@ rbrp_status rbrp_host_workspace_size(int64_t n, int64_t d, int x_is_fp64, const 
   return RBRP_OK;
 }
 
+namespace {
+// Device-to-host copy of W by row ranges on its own stream (rbrp_id_host).
+struct HostCopy {
+  const double* Wd = nullptr;
+  double* W_host = nullptr;
+  long long ldw = 0;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaError_t err = cudaSuccess;
+
+  // Rows [r0, r1) are final once the work queued on s so far completes: the
+  // copy stream waits for that point, then copies the k used columns.
+  static cudaError_t done(void* ctx, long long r0, long long r1, long long k, cudaStream_t s) {
+    HostCopy* h = (HostCopy*)ctx;
+    cudaError_t e = cudaEventRecord(h->ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cs, h->ev, 0);
+    if (e == cudaSuccess && k > 0)
+      e = cudaMemcpy2DAsync(h->W_host + r0 * h->ldw, (size_t)h->ldw * 8, h->Wd + r0 * h->ldw, (size_t)h->ldw * 8,
+                            (size_t)k * 8, (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->cs);
+    if (e != cudaSuccess && h->err == cudaSuccess) h->err = e;
+    return e;
+  }
+  // Waits for every queued copy, then frees the stream and the event.
+  cudaError_t release() {
+    cudaError_t e = cudaSuccess;
+    if (cs) {
+      e = cudaStreamSynchronize(cs);
+      cudaStreamDestroy(cs);
+      cs = nullptr;
+    }
+    if (ev) {
+      cudaEventDestroy(ev);
+      ev = nullptr;
+    }
+    return e;
+  }
+};
+}  // namespace
+
 rbrp_status rbrp_id_host(const void* X_host, int x_is_fp64, int64_t n, int64_t d, double tol, const rbrp_opts* o,
                          void* workspace, size_t ws_bytes, int64_t* skel_host, double* W_host, rbrp_result* res,
                          rbrp_stream_t stream) {
@@ -1006,15 +1070,45 @@ rbrp_status rbrp_id_host(const void* X_host, int x_is_fp64, int64_t n, int64_t d
   long long* Sd = (long long*)(base + off);
   const size_t xb = (size_t)n * d * (x_is_fp64 ? 8 : 4);
   CK(cudaMemcpyAsync(Xd, X_host, xb, cudaMemcpyHostToDevice, s));
-  rs = run(Xd, x_is_fp64, n, d, d, tol, o, workspace, p.total, Sd, Wd, p.k_cap, res, s);
-  if (rs != RBRP_OK && rs != RBRP_ENOTCONVERGED) return rs;
-  const long long k = res->k;
-  if (k > 0) {
-    CK(cudaMemcpyAsync(skel_host, Sd, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpy2DAsync(W_host, (size_t)p.k_cap * 8, Wd, (size_t)p.k_cap * 8, (size_t)k * 8, (size_t)n,
-                         cudaMemcpyDeviceToHost, s));
+  // W leaves the device in row ranges on a second stream while the solve of
+  // the later ranges runs (the host link, not the solve, bounds this tail).
+  HostCopy hc;
+  hc.Wd = Wd;
+  hc.W_host = W_host;
+  hc.ldw = p.k_cap;
+  CK(cudaStreamCreateWithFlags(&hc.cs, cudaStreamNonBlocking));
+  cudaError_t ce = cudaEventCreateWithFlags(&hc.ev, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    hc.release();
+    g_last_cuda = (int)ce;
+    return RBRP_ECUDA;
   }
-  CK(cudaStreamSynchronize(s));
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  WSink sink;
+  sink.chunk_rows = (long long)sms * wsolve_tc_rows_per_tile();  // one tile per SM per range
+  sink.done = &HostCopy::done;
+  sink.ctx = &hc;
+  rs = run(Xd, x_is_fp64, n, d, d, tol, o, workspace, p.total, Sd, Wd, p.k_cap, res, s, &sink);
+  if (rs == RBRP_OK || rs == RBRP_ENOTCONVERGED) {
+    if (res->k > 0) {
+      ce = cudaMemcpyAsync(skel_host, Sd, (size_t)res->k * 8, cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) {
+        g_last_cuda = (int)ce;
+        rs = RBRP_ECUDA;
+      }
+    }
+  }
+  if (hc.err != cudaSuccess && (rs == RBRP_OK || rs == RBRP_ENOTCONVERGED)) {
+    g_last_cuda = (int)hc.err;
+    rs = RBRP_ECUDA;
+  }
+  const cudaError_t re = hc.release();
+  if (re != cudaSuccess && (rs == RBRP_OK || rs == RBRP_ENOTCONVERGED)) {
+    g_last_cuda = (int)re;
+    rs = RBRP_ECUDA;
+  }
   return rs;
 }
 

@@ -270,6 +270,9 @@ cudaError_t launch_trsm_cols(T* W, long long ldw, long long n, long long j0, int
                              long long ld1, cudaStream_t s);
 cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long long ldw32, long long n,
                             long long k, const long long* skel, cudaStream_t s);
+// W(S, :) = I restricted to the skeleton rows that fall in [r0, r1).
+cudaError_t launch_w_identity_rows(double* W, long long ldw, long long k, const long long* skel, long long r0,
+                                   long long r1, cudaStream_t s);
 
 // Small products (k_sgemm.cu).  TS: element type in memory.  TACC = float:
 // FP32 products, 64 x 64 tiles; double: FP64 products, 32 x 32 tiles.  BKC
@@ -302,9 +305,14 @@ int update_tf32_max_block(int split);
 // Wh/Wl (n x ldw32 FP32 scratch) receive W split into TF32 hi/lo; Gh/Gl
 // (k x ldt FP32 scratch) the transposed block-inverse factor G.  W64 (n x k
 // FP64, leading dimension ldw64) receives the result; rows of S are not set.
+// form_g launches the G factor first; rows [r0, r1) of W are then solved
+// (r0 a multiple of wsolve_tc_rows_per_tile(); r1 <= r0 solves none), so the
+// rows can be produced in several launches after one G.
 cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* Wh, float* Wl, long long ldw32,
                              double* W64, long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl,
-                             long long ldt, long long n, long long k, State* st, cudaStream_t s);
+                             long long ldt, long long n, long long r0, long long r1, bool form_g, long long k,
+                             State* st, cudaStream_t s);
+int wsolve_tc_rows_per_tile();
 
 // Batched form (k_batched.cu): one persistent launch over P small problems.
 constexpr long long kBatchMaxRows = 4096;
