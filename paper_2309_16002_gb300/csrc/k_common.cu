@@ -666,13 +666,6 @@ template cudaError_t launch_trsm_cols<float>(float*, long long, long long, long 
                                              cudaStream_t);
 
 // W(S, :) = I_k exactly; with W32 set, the FP32 solve result is first widened into W.
-__global__ void k_w_finish(double* __restrict__ W, long long ldw, const float* __restrict__ W32, long long ldw32,
-                           long long n, long long k, const long long* __restrict__ skel) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e / k, j = e % k;
-    if (W32) W[i * ldw + j] = (double)W32[i * ldw32 + j];
-  }
-}
 __global__ void k_w_identity(double* __restrict__ W, long long ldw, long long k, const long long* __restrict__ skel,
                              long long r0, long long r1) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (long long)gridDim.x * blockDim.x) {
@@ -680,18 +673,6 @@ __global__ void k_w_identity(double* __restrict__ W, long long ldw, long long k,
     const long long r = skel[i];
     if (r >= r0 && r < r1) W[r * ldw + j] = (i == j) ? 1.0 : 0.0;
   }
-}
-
-cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long long ldw32, long long n, long long k,
-                            const long long* skel, cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
-  if (W32) {
-    k_w_finish<<<grid_for(n * k), 256, 0, s>>>(W, ldw, W32, ldw32, n, k, skel);
-    cudaError_t e = counted(cudaGetLastError());
-    if (e != cudaSuccess) return e;
-  }
-  k_w_identity<<<grid_for(k * k), 256, 0, s>>>(W, ldw, k, skel, 0, n);
-  return counted(cudaGetLastError());
 }
 
 cudaError_t launch_w_identity_rows(double* W, long long ldw, long long k, const long long* skel, long long r0,

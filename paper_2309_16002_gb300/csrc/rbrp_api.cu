@@ -533,14 +533,14 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
       }
       CK(launch_trsm_cols<double>(W, ldw, n, j0, (int)nb, u.L1, k, s));
     }
-    CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));
+    CK(launch_w_identity_rows(W, ldw, k, skel, 0, n, s));  // W(S, :) = I exactly
     if (sink) CK(sink->done(sink->ctx, 0, n, k, s));
   } else if (!sink) {
     // FP32 solve on tensor cores (3xTF32): every 64-column block of W is one
     // product with the precomputed block-inverse factor, then W(S, :) = I.
     CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, n, true,
                         k, u.st, s));
-    CK(launch_w_finish(W, ldw, nullptr, 0, n, k, skel, s));  // W(S, :) = I exactly
+    CK(launch_w_identity_rows(W, ldw, k, skel, 0, n, s));  // W(S, :) = I exactly
   } else {
     // The same solve in row ranges (rows are independent once G is formed),
     // each finished with its skeleton rows set to I and handed to the sink.

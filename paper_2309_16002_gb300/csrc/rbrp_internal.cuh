@@ -268,8 +268,6 @@ cudaError_t launch_gather_rows_f64(const void* L, int l_is_fp64, long long ldl, 
 template <typename T>
 cudaError_t launch_trsm_cols(T* W, long long ldw, long long n, long long j0, int nb, const double* L1,
                              long long ld1, cudaStream_t s);
-cudaError_t launch_w_finish(double* W, long long ldw, const float* W32, long long ldw32, long long n,
-                            long long k, const long long* skel, cudaStream_t s);
 // W(S, :) = I restricted to the skeleton rows that fall in [r0, r1).
 cudaError_t launch_w_identity_rows(double* W, long long ldw, long long k, const long long* skel, long long r0,
                                    long long r1, cudaStream_t s);
