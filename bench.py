@@ -29,9 +29,12 @@ METRIC = "ID time-to-tol (ms) at 1e5×1e3, rel err ≤1e-4; % of HBM/TC roofline
 # DRAM bytes (read + write) per launch of the persistent tensor-core update, per
 # row of R, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # caches left as the preceding kernels leave them) of the 40000 x 1000 zipf_gmm
-# workload at b = 64 (profiles/k_update_tf32p_*.md).
+# workload at b = 64 (profiles/k_update_tf32p_*.md).  The kernel has changed
+# since (a programmatic-dependent-launch wait at entry; loads and stores are the
+# same), so the figure is reported as the last capture, not as current traffic.
 UPD_TRAFFIC_PER_ROW = (196233472 + 132443136) / 40000
 UPD_TRAFFIC_D = 1000
+UPD_TRAFFIC_CURRENT = False
 FALLBACK_HBM = 6800.0
 
 
@@ -264,13 +267,18 @@ def run_ours(a):
                "other_ms_per_step": ms - (upd_ms + w_ms) / a.steps}
     persistent = a.precision == "tf32" and a.block <= 64
     kname = ("k_update_tf32p" if persistent else "k_update_tf32") if a.precision.startswith("tf32") else "update_simt"
-    traffic = UPD_TRAFFIC_PER_ROW * n if (persistent and d == UPD_TRAFFIC_D) else None
+    captured = UPD_TRAFFIC_PER_ROW * n if (persistent and d == UPD_TRAFFIC_D) else None
+    traffic = captured if UPD_TRAFFIC_CURRENT else None
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
                 "peak_kind": peak_kind, "traffic": traffic,
+                "traffic_last_capture": captured,
                 "traffic_note": ("DRAM read+write bytes per launch from one ncu capture of the 40000 x 1000 "
                                  "workload (L2 as the preceding kernels leave it), scaled by rows"
-                                 if traffic else None),
+                                 + ("" if UPD_TRAFFIC_CURRENT else "; taken before the kernel gained its "
+                                    "programmatic-dependent-launch wait at entry (its loads and stores are "
+                                    "unchanged), so traffic is null until the next capture")
+                                 if captured else None),
                 "bytes_per_launch": upd_bytes / max(1, blocks),
                 "note": "achieved = (2 n d s + 16 n) per block + n k s for Lhat, over CUDA-event time of all "
                         "update launches in the timed region (including no-op launches queued after the stop)"}
