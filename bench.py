@@ -164,6 +164,61 @@ def cpu_oracle_leg(a, X, rows, reps=1):
     return ms * scale, info
 
 
+def cpu_batched_leg(P_all, tol, block, budget_s=15.0, max_problems=256):
+    """The FP64 oracle as it stands on a strided sample of the kernel-block list (same shapes,
+    seeds, tol, b and Philox problem ids as the GPU run), stopped after about budget_s seconds;
+    the mean time per problem is scaled to all P_all problems.  Returns (ms_scaled, info)."""
+    import numpy as np
+    from oracle import rbrp as O
+    from paper_2309_16002_gb300 import workloads as WL
+    stride = max(1, P_all // max_problems)
+    spent, done, ks = 0.0, 0, []
+    for p in range(0, P_all, stride):
+        X = WL.kernel_blocks(P=P_all, seed=4, lo=p, hi=p + 1)[0].astype(np.float64)
+        t0 = time.perf_counter()
+        out = O.rbrp_id(X, tau=tol, b=block, seed=0, problem=p)
+        spent += time.perf_counter() - t0
+        done += 1
+        ks.append(len(out["S"]))
+        if done >= max_problems or (done >= 8 and spent >= budget_s):
+            break
+    ms = 1e3 * spent / done * P_all
+    info = {"sample": ("%d of %d kernel blocks (every %d-th problem of the list, same shapes, seeds, tol %g, b %d "
+                       "and problem ids), full Alg. 2 + Alg. 3 in FP64 one problem at a time; mean time per "
+                       "problem scaled x%d" % (done, P_all, stride, tol, block, P_all)),
+            "sample_ms": 1e3 * spent, "sample_problems": done, "sample_k_mean": sum(ks) / len(ks),
+            "cores": os.cpu_count()}
+    return ms, info
+
+
+def run_reference_batched(a):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    P_all = a.batch * ws
+    tol = 1e-5 if a.tol == 1e-4 else a.tol
+    block = 16 if a.block == 64 else a.block
+    budget = 15.0
+    for _ in range(a.warmup):
+        cpu_batched_leg(P_all, tol, block, budget_s=budget / 4, max_problems=8)
+    vals, info = [], None
+    for _ in range(a.steps):
+        v, info = cpu_batched_leg(P_all, tol, block, budget_s=budget)
+        vals.append(v)
+    ms = sum(vals) / len(vals)
+    line = {"impl": "reference",
+            "metric": "batched ID time (ms) for %d kernel blocks per GPU, tol %g, b %d" % (a.batch, tol, block),
+            "value": ms, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "kernel_blocks", "P": P_all, "P_per_gpu": a.batch, "m": [64, 2048],
+                       "n": [32, 256], "h": 0.5, "gap": 2.0, "dtype_in": "fp32", "tol_sq_rel": tol, "block": block,
+                       "seed": 4},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(a):
     ws, rank, _ = dist_init()
     if rank != 0:
@@ -451,6 +506,10 @@ def run_batched(a):
             "speedup_vs_per_matrix": single_ms / ms if ms > 0 else None,
             "gpu_launches": int(launches) * a.steps, "graph": True, "schedule": tuned,
             "fp64_form": fp64_form}
+    if ws_n == 1 and not a.no_cpu_baseline:
+        v, info = cpu_batched_leg(P_all, tol, block)
+        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": info["cores"], "kind": "oracle",
+                                "sample": info["sample"]}
     print(json.dumps(line), flush=True)
     if ws_n > 1:
         torch.distributed.destroy_process_group()
@@ -514,7 +573,10 @@ def run_fixed_rank(a):
 def main():
     a = parse()
     if a.workload == "kernel_blocks":
-        run_batched(a)
+        if a.impl == "reference":
+            run_reference_batched(a)
+        else:
+            run_batched(a)
         return
     if a.workload == "gmm_fixed_rank":
         run_fixed_rank(a)
