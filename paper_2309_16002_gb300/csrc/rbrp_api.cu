@@ -939,9 +939,16 @@ rbrp_status rbrp_batch_run(rbrp_batch h, double tol, rbrp_stream_t stream) {
 rbrp_status rbrp_batch_autotune(rbrp_batch h, double tol, int32_t reps, rbrp_stream_t stream, float* best_ms) {
   if (!h || reps < 1) return RBRP_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  {
+    const cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+      cudaEventDestroy(e0);
+      g_last_cuda = (int)ce;
+      return RBRP_ECUDA;
+    }
+  }
   int best_t = h->threads, best_p = h->per_sm;
   float best = -1.f;
   rbrp_status rs = RBRP_OK;
