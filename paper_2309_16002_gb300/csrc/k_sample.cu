@@ -21,6 +21,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "rbrp_internal.cuh"
 #include "sample_common.cuh"
 
@@ -476,7 +478,7 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
   const int want = b + kMargin;
   {
     // one cooperative launch, one CTA per SM, when the device allows it (asked once per device)
-    static int coop_sms[64] = {0};  // 0: not asked, -1: not available, else the SM count
+    static std::atomic<int> coop_sms[64];  // 0: not asked, -1: not available, else the SM count
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (coop_sms[dev] == 0) {
@@ -494,7 +496,7 @@ cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, u
       int cap = kSampCap;
       // cooperative, and allowed to be scheduled as the previous kernel drains
       // (programmatic dependent launch; the kernel starts with pdl_wait())
-      static int pdl_ok = 1;
+      static std::atomic<int> pdl_ok{1};
       if (pdl_ok) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)sms);

@@ -17,6 +17,8 @@
 
 #include <algorithm>
 
+#include <atomic>
+
 #include "rbrp_internal.cuh"
 
 namespace rbrp {
@@ -333,7 +335,7 @@ cudaError_t launch_sgemm_cluster(const SgemmArgs& g, long long Mmax, long long N
     // 16 CTAs per cluster is beyond the portable size: use it only where the
     // device can hold such a cluster (asked once per process), else two
     // splits per CTA
-    static int ok16 = -1;
+    static std::atomic<int> ok16{-1};
     if (ok16 < 0) {
       int nclusters = 0;
       ok16 = (cudaOccupancyMaxActiveClusters(&nclusters, k_sgemm_cl<TS, BKC>, &cfg) == cudaSuccess && nclusters >= 1);

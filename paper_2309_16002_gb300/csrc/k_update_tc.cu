@@ -27,6 +27,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 #include "rbrp_internal.cuh"
 #include "tc_common.cuh"
 
@@ -748,11 +750,11 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  static unsigned long long attr_set = 0;  // one bit per device
-  if (dev >= 64 || !(attr_set >> dev & 1ULL)) {
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
+  if (dev >= 64 || !(attr_set.load() >> dev & 1ULL)) {
     e = cudaFuncSetAttribute(k_update_tf32p<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    if (dev < 64) attr_set |= 1ULL << dev;
+    if (dev < 64) attr_set.fetch_or(1ULL << dev);
   }
   CUtensorMap mR, mQ, mQT;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, PROWS)) return cudaErrorInvalidValue;
@@ -768,16 +770,16 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
 
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once (a function-local static is initialised exactly once, also
+  // under concurrent first calls)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+      return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -800,15 +802,15 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
                        long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L, long long ldl,
                        const int* mark, double* dvec, double* partials, const State* st, cudaStream_t s) {
   using C = Cfg<BMAX, SPLIT>;
-  static unsigned long long attr_set = 0;  // one bit per device
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(attr_set >> dev & 1ULL)) {
+    if (dev >= 64 || !(attr_set.load() >> dev & 1ULL)) {
       e = cudaFuncSetAttribute(k_update_tf32<BMAX, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
       if (e != cudaSuccess) return e;
-      if (dev < 64) attr_set |= 1ULL << dev;
+      if (dev < 64) attr_set.fetch_or(1ULL << dev);
     }
   }
   CUtensorMap mR, mQ, mQlo, mQT, mQTlo;

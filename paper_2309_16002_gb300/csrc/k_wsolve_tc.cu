@@ -30,6 +30,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 #include "rbrp_internal.cuh"
 #include "tc_common.cuh"
 
@@ -448,11 +450,11 @@ cudaError_t wsolve_all(const void* L, long long ldl, float* Wh, float* Wl, long 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  static unsigned long long attr_set = 0;  // one bit per device
-  if (dev >= 64 || !(attr_set >> dev & 1ULL)) {
+  static std::atomic<unsigned long long> attr_set{0};  // one bit per device
+  if (dev >= 64 || !(attr_set.load() >> dev & 1ULL)) {
     e = cudaFuncSetAttribute(k_wsolve_rows<L64>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    if (dev < 64) attr_set |= 1ULL << dev;
+    if (dev < 64) attr_set.fetch_or(1ULL << dev);
   }
   if (form_g) {
     const int nblk = (int)((k + WN - 1) / WN);

@@ -17,7 +17,7 @@
 
 namespace rbrp {
 
-long long g_kernel_launches = 0;
+std::atomic<long long> g_kernel_launches{0};
 
 namespace {
 
@@ -1155,7 +1155,7 @@ rbrp_status rbrp_id_noalloc(const void* X, int x_is_fp64, int64_t n, int64_t d, 
 
 void rbrp_profile_begin(void) {
   g_prof.on = true;
-  g_prof.launches0 = g_kernel_launches;
+  g_prof.launches0 = g_kernel_launches.load();
   g_prof.upd.used = 0;
   g_prof.wsv.used = 0;
   g_prof.blocks = 0;
@@ -1165,7 +1165,7 @@ void rbrp_profile_begin(void) {
 rbrp_status rbrp_profile_end(rbrp_profile* out) {
   if (!out) return RBRP_EINVAL;
   memset(out, 0, sizeof(*out));
-  out->launches = g_kernel_launches - g_prof.launches0;
+  out->launches = g_kernel_launches.load() - g_prof.launches0;
   out->blocks = g_prof.blocks;
   out->skeletons = g_prof.skel;
   EventPool* pools[2] = {&g_prof.upd, &g_prof.wsv};

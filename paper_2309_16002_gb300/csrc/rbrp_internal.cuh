@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/rbrp.h"
 
 namespace rbrp {
@@ -193,9 +195,9 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 
 // ---------------------------------------------------------------- instrumentation
 // Number of kernels the library has launched (read by rbrp_profile_end).
-extern long long g_kernel_launches;
+extern std::atomic<long long> g_kernel_launches;
 inline cudaError_t counted(cudaError_t e) {
-  ++g_kernel_launches;
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
 }
 
