@@ -112,7 +112,9 @@ typedef struct {
 void rbrp_default_opts(rbrp_opts *o);
 
 /* Bytes of device workspace rbrp_id needs for an n x d problem with options o
- * (residual copy of X, L, Q, the norms d and the per-block buffers). */
+ * (residual copy of X, L, Q, the norms d and the per-block buffers).
+ * RBRP_EINVAL for n < 1, d < 1, n or d >= 2^31, n d > 2^48 (no byte count can
+ * then overflow), a null o or bytes, or an option out of range. */
 rbrp_status rbrp_workspace_size(int64_t n, int64_t d, const rbrp_opts *o, size_t *bytes);
 
 /*

@@ -98,6 +98,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   if (o->form != RBRP_FORM_RESIDUAL && o->form != RBRP_FORM_DOWNDATE) return RBRP_EINVAL;
   if (o->form == RBRP_FORM_DOWNDATE && o->precision != RBRP_FP64) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
+  if (n > (1LL << 48) / d) return RBRP_EINVAL;  // n d elements: every byte count below stays far from overflow
   // the tensor-core update keeps Lhat (128 x b'_pad) in shared memory: b <= 128
   if (o->precision == RBRP_TF32 && o->block > update_tf32_max_block(0)) return RBRP_EINVAL;
   if (o->precision == RBRP_TF32X3 && o->block > update_tf32_max_block(1)) return RBRP_EINVAL;

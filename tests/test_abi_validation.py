@@ -90,6 +90,11 @@ def test_sizes_out_of_range(L, R):
     assert L.rbrp_workspace_size(1 << 31, 20, ctypes.byref(o), ctypes.byref(out)) == EINVAL
     assert L.rbrp_workspace_size(100, 1 << 31, ctypes.byref(o), ctypes.byref(out)) == EINVAL
     assert L.rbrp_workspace_size(100, 0, ctypes.byref(o), ctypes.byref(out)) == EINVAL
+    # shapes whose byte counts would overflow 64 bits are refused, not wrapped
+    assert L.rbrp_workspace_size(1 << 30, 1 << 30, ctypes.byref(o), ctypes.byref(out)) == EINVAL
+    assert L.rbrp_workspace_size((1 << 31) - 1, (1 << 31) - 1, ctypes.byref(o), ctypes.byref(out)) == EINVAL
+    assert L.rbrp_workspace_size((1 << 31) - 1, 4096, ctypes.byref(o), ctypes.byref(out)) == OK
+    assert out.value > ((1 << 31) - 1) * 4096 * 8
     assert L.rbrp_workspace_size(100, 20, ctypes.byref(o), None) == EINVAL
 
 
