@@ -184,6 +184,38 @@ def _result_dict(res, status):
                 converged=(status == 0))
 
 
+# The C ABI receives plain pointers and sizes, so the binding checks every buffer it
+# passes (dtype, device, shape, layout) before the call: a wrong one would otherwise
+# be read or written out of bounds.
+def _check_x(X, cuda):
+    import torch
+    if X.dim() != 2 or X.stride(1) != 1 or X.is_cuda != cuda:
+        raise ValueError("X must be a 2-D %s tensor with unit column stride" % ("CUDA" if cuda else "host"))
+    if X.dtype not in (torch.float32, torch.float64):
+        raise ValueError("X must be float32 or float64")
+    if X.shape[0] < 1 or X.shape[1] < 1:
+        raise ValueError("X must have at least one row and one column")
+
+
+def _check_outputs(skel, W, n, kc, device=None, exact_host_shape=False):
+    """skel: int64[>= kc]; W: FP64 n x (>= kc) rows with unit column stride, row stride >= kc
+    (host outputs of rbrp_id_host: exactly n x kc, C-contiguous, since the copy assumes that pitch)."""
+    import torch
+    cuda = device is not None
+    for name, t in (("skel", skel), ("W", W)):
+        if t.is_cuda != cuda or (cuda and t.device != device):
+            raise ValueError("%s must be a %s tensor" % (name, "CUDA tensor on %s" % device if cuda else "host"))
+    if skel.dtype != torch.int64 or not skel.is_contiguous() or skel.numel() < kc:
+        raise ValueError("skel must be a contiguous int64 tensor of at least k_cap = %d entries" % kc)
+    if W.dtype != torch.float64 or W.dim() != 2 or W.stride(1) != 1:
+        raise ValueError("W must be a 2-D float64 tensor with unit column stride")
+    if exact_host_shape:
+        if tuple(W.shape) != (n, kc) or not W.is_contiguous():
+            raise ValueError("W must be a C-contiguous float64 host tensor of shape (%d, %d)" % (n, kc))
+    elif W.shape[0] < n or W.shape[1] < kc or W.stride(0) < kc:
+        raise ValueError("W must hold n = %d rows of k_cap = %d columns" % (n, kc))
+
+
 class Workspace:
     """Device buffers for repeated rbrp_id calls of one shape (allocated once by PyTorch)."""
 
@@ -213,13 +245,14 @@ def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, pro
     rel_err_sq (= ||d||_1 / ||d0||_1), d0, d_final, converged).
     """
     import torch
-    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
-        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
-    if X.dtype not in (torch.float32, torch.float64):
-        raise ValueError("X must be float32 or float64")
+    _check_x(X, cuda=True)
     n, d = X.shape
     opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form)
+    if workspace is not None and ((workspace.n, workspace.d) != (n, d) or workspace.kc < k_cap(n, d, k_max)):
+        raise ValueError("workspace was made for %d x %d, k_cap %d" % (workspace.n, workspace.d, workspace.kc))
     ws = workspace if workspace is not None else Workspace(n, d, opts, X.device)
+    if ws.ws.device != X.device:
+        raise ValueError("workspace and X are on different devices")
     res = Result()
     s = stream if stream is not None else torch.cuda.current_stream(X.device)
     st = load().rbrp_id(ctypes.c_void_p(X.data_ptr()), int(X.dtype == torch.float64), n, d, X.stride(0), float(tol),
@@ -240,9 +273,9 @@ def rbrp_id_noalloc(X, tol, skel_out, W_out, block=64, seed=0, precision="tf32",
     fixed device array (RBRP_NOALLOC_SCRATCH_BYTES).  For callers that cannot allocate; the
     outputs skel_out (int64[k_cap]) and W_out (FP64 n x k_cap) are the caller's CUDA tensors."""
     import torch
-    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
-        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
+    _check_x(X, cuda=True)
     n, d = X.shape
+    _check_outputs(skel_out, W_out, n, k_cap(n, d, k_max), device=X.device)
     opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
     res = Result()
     s = stream if stream is not None else torch.cuda.current_stream(X.device)
@@ -282,15 +315,19 @@ def rbrp_id_host(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0
     """
     import torch
     Xt = torch.as_tensor(X)
-    if Xt.is_cuda or Xt.dim() != 2 or not Xt.is_contiguous():
+    if not Xt.is_contiguous():
         raise ValueError("X must be a C-contiguous 2-D host array")
+    _check_x(Xt, cuda=False)
     n, d = Xt.shape
     fp64 = int(Xt.dtype == torch.float64)
     opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form)
     kc = k_cap(n, d, k_max)
-    ws = workspace if workspace is not None else HostWorkspace(n, d, fp64, opts)
     skel = skel_out if skel_out is not None else torch.empty(kc, dtype=torch.int64)
     W = W_out if W_out is not None else torch.empty((n, kc), dtype=torch.float64)
+    _check_outputs(skel, W, n, kc, exact_host_shape=True)
+    if workspace is not None and workspace.nbytes() < rbrp_host_workspace_size(n, d, fp64, opts):
+        raise ValueError("workspace too small for this problem")
+    ws = workspace if workspace is not None else HostWorkspace(n, d, fp64, opts)
     res = Result()
     s = stream if stream is not None else torch.cuda.current_stream()
     st = load().rbrp_id_host(ctypes.c_void_p(Xt.data_ptr()), fp64, n, d, float(tol), ctypes.byref(opts),
@@ -329,9 +366,11 @@ class Batch:
             raise ValueError("empty batch")
         dt = Xs[0].dtype
         dev = Xs[0].device
+        if dt not in (torch.float32, torch.float64):
+            raise ValueError("Xs must be float32 or float64")
         for X in Xs:
-            if not X.is_cuda or X.dim() != 2 or X.dtype != dt or not X.is_contiguous():
-                raise ValueError("Xs must be contiguous 2-D CUDA tensors of one dtype")
+            if not X.is_cuda or X.dim() != 2 or X.dtype != dt or not X.is_contiguous() or X.device != dev:
+                raise ValueError("Xs must be contiguous 2-D CUDA tensors of one dtype on one device")
         self.Xs = Xs
         self.fp64_in = int(dt == torch.float64)
         self.opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, "fp64")
