@@ -521,6 +521,44 @@ def run_batched(a):
 PAPER_GPU_RBRP_S = {52: 4.448e-2, 100: 7.231e-2, 220: 1.073e-1, 346: 1.336e-1, 472: 1.596e-1}
 
 
+def run_reference_fixed_rank(a):
+    """The FP64 oracle at each fixed rank k on the first --ref-rows rows of the same adversarial
+    GMM (same seed, b), time scaled linearly to all rows; rank 0 only."""
+    import numpy as np
+    from oracle import rbrp as O
+    from paper_2309_16002_gb300 import workloads as WL
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    X = WL.gmm_pitfall(n=a.n, d=a.d, k=100, seed=6, dtype=np.float32)
+    ns = min(a.ref_rows, a.n) if a.ref_rows > 0 else a.n
+    Xs = np.ascontiguousarray(X[:ns].astype(np.float64))
+    ks = [int(x) for x in a.ranks.split(",") if x]
+    for _ in range(a.warmup):
+        O.rbrp_id(Xs[: max(1, ns // 4)], k=ks[0], b=a.block, seed=0)
+    rows = []
+    for k in ks:
+        times, k_out = [], 0
+        for _ in range(a.steps):
+            t0 = time.perf_counter()
+            out = O.rbrp_id(Xs, k=k, b=a.block, seed=0)
+            times.append(time.perf_counter() - t0)
+            k_out = len(out["S"])
+        rows.append({"precision": "fp64", "k": k, "k_out": k_out, "ms": 1e3 * sum(times) / len(times) * a.n / ns})
+    ms = rows[0]["ms"]
+    sample = ("first %d of %d rows of the same GMM (seed 6, b %d), Alg. 2 at fixed k + Alg. 3 in FP64, time "
+              "scaled x%.2f to all rows" % (ns, a.n, a.block, a.n / ns))
+    line = {"impl": "reference", "metric": "ID time at fixed rank (ms), adversarial GMM 1e5 x 1e3", "unit": "ms",
+            "value": ms, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "gmm_fixed_rank", "n": a.n, "d": a.d, "clusters": 100, "means": "10 j e_j",
+                       "block": a.block, "seed": 0},
+            "ranks": rows,
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_fixed_rank(a):
     """The adversarial GMM of Sec. 4 (means 10 j e_j, identity covariance, 100 clusters of
     1000 points, 1e5 x 1e3, FP32 storage) at fixed ranks k (tol < 0, k_max = k), TF32 and
@@ -579,7 +617,10 @@ def main():
             run_batched(a)
         return
     if a.workload == "gmm_fixed_rank":
-        run_fixed_rank(a)
+        if a.impl == "reference":
+            run_reference_fixed_rank(a)
+        else:
+            run_fixed_rank(a)
         return
     if a.impl == "reference":
         run_reference(a)

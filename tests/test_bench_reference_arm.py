@@ -43,6 +43,15 @@ def test_reference_arm_batched_workload_small():
     assert j["config"]["P"] == 24 and "24 of 24 kernel blocks" in j["cpu_baseline"]["sample"]
 
 
+def test_reference_arm_fixed_rank_workload_small():
+    lines = _bench(["--workload", "gmm_fixed_rank", "--n", "2000", "--d", "120", "--ref-rows", "1000",
+                    "--block", "8", "--ranks", "10,20", "--steps", "1", "--warmup", "0"])
+    assert len(lines) == 1
+    j = _check_line(lines[0], "gmm_fixed_rank")
+    assert [r["k"] for r in j["ranks"]] == [10, 20] and [r["k_out"] for r in j["ranks"]] == [10, 20]
+    assert j["value"] == j["ranks"][0]["ms"]
+
+
 def test_reference_arm_other_ranks_print_nothing():
     env = {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}
     assert _bench(["--steps", "1", "--warmup", "0", "--n", "2000", "--d", "50"], env) == []
