@@ -46,8 +46,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "tf32x3", "fp32", "fp64"])
     ap.add_argument("--w-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--chain", default="default", choices=["default", "fp64"],
+                    help="precision of the per-block chain (fp64: CGS2, Gram, filter and Q' in FP64)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other precision forms timed after the headline (outside its timed region)")
+    ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--form", default="residual", choices=["residual", "downdate"],
-                    help="update form of Alg. 2 lines 12/16 (downdate: as printed, FP64 only)")
+                    help="update form of Alg. 2's update step (downdate: as printed, FP64 only)")
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--n", type=int, default=100000)
@@ -72,9 +77,23 @@ def parse():
 def workload_config(a):
     return {"workload": "zipf_gmm_near_duplicates", "n": a.n, "d": a.d, "dtype_in": "fp32", "clusters": 100,
             "zipf_s": 1.5, "within_var": 1e-6, "extra_rows": 0.05, "extra_var": 0.01, "tol_sq_rel": a.tol,
-            "block": a.block, "seed": 0, "update": a.precision, "form": a.form, "w_solve": a.w_precision,
+            "block": a.block, "seed": 0, "update": a.precision, "chain": chain_label(a), "form": a.form,
+            "w_solve": a.w_precision,
             "l2": "inputs larger than L2 (X is %.0f MB, residual copy %.0f MB per step)" % (a.n * a.d * 4 / 1e6,
                                                                                             a.n * a.d * 4 / 1e6)}
+
+
+def chain_label(a):
+    """Arithmetic of the per-block chain (sampler keys and norm sums are FP64 in every form)."""
+    if a.precision == "fp64" or a.chain == "fp64":
+        return "f64"
+    return "f32" if a.precision == "tf32" else "f64 storage, f32 products"
+
+
+def dtype_label(a):
+    upd = {"tf32": "tf32", "tf32x3": "3xtf32", "fp32": "f32", "fp64": "f64"}[a.precision]
+    return "%s update, %s chain, %s W" % (upd, chain_label(a).split(",")[0], {"fp32": "f32", "fp64": "f64"}[
+        a.w_precision])
 
 
 def measured_peaks():
@@ -242,6 +261,50 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def true_err_sq(Xd, S, W):
+    """||X - W X_S||_F^2 / ||X||_F^2 in FP64 on the device from the returned S and W (outside any
+    timed region): the error the metric asks for, not the device's ||d||_1 / ||d0||_1."""
+    import torch
+    X64 = Xd.to(torch.float64)
+    E = X64 - W.to(torch.float64) @ X64[S]
+    return float(torch.sum(E * E) / torch.sum(X64 * X64))
+
+
+def time_forms(a, G, Xd, stream, pid):
+    """The same ID in the other precision forms, each against the plain FP64 GPU form at the same
+    tolerance: time per call (CUDA events, --form-steps calls after one warm-up), k and the true
+    FP64 error of the returned S and W.  Timed after, and outside, the headline's timed region."""
+    import torch
+    forms = [("tf32", "fp64", "fp64"), ("tf32", "fp64", "fp32"), ("tf32", "default", "fp32"),
+             ("tf32x3", "default", "fp32"), ("fp64", "default", "fp64")]
+    res = {}
+    for prec, chain, wprec in forms:
+        kw = dict(block=a.block, seed=0, precision=prec, w_precision=wprec, problem=pid, chain=chain)
+        ws = G.Workspace(a.n, a.d, G.make_opts(a.block, prec, -1.0, 0, 0, pid, "random", wprec, "residual", chain),
+                         Xd.device)
+        out = G.rbrp_id(Xd, a.tol, workspace=ws, stream=stream, **kw)
+        torch.cuda.synchronize()
+        G.rbrp_profile_begin()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.form_steps):
+            out = G.rbrp_id(Xd, a.tol, workspace=ws, stream=stream, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = G.rbrp_profile_end()
+        key = "%s update, %s chain, %s W" % ({"tf32": "tf32", "tf32x3": "3xtf32", "fp64": "f64"}[prec],
+                                              "f64" if (chain == "fp64" or prec == "fp64") else
+                                              ("f32" if prec == "tf32" else "f64 storage/f32 products"),
+                                              "f64" if wprec == "fp64" else "f32")
+        res[key] = {"ms": e0.elapsed_time(e1) / a.form_steps, "k": out["k"],
+                    "rel_err_sq_device": out["rel_err_sq"],
+                    "rel_err_sq_true": true_err_sq(Xd, out["S"], out["W"]),
+                    "update_ms": prof["update_ms"] / a.form_steps, "w_solve_ms": prof["wsolve_ms"] / a.form_steps}
+        del ws, out
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -267,8 +330,9 @@ def run_ours(a):
     Xd = torch.from_numpy(X).to(dev)
     from paper_2309_16002_gb300 import shard
     pid = shard.replica_problem_id(rank)
-    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=pid, form=a.form)
-    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, pid, "random", a.w_precision, a.form)
+    kw = dict(block=a.block, seed=0, precision=a.precision, w_precision=a.w_precision, problem=pid, form=a.form,
+              chain=a.chain)
+    opts = G.make_opts(a.block, a.precision, -1.0, 0, 0, pid, "random", a.w_precision, a.form, a.chain)
     wsp = G.Workspace(a.n, a.d, opts, dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -303,7 +367,7 @@ def run_ours(a):
     elapsed = shard.max_over_ranks(ev0.elapsed_time(ev1), dev)
     ms = elapsed / a.steps
 
-    # roofline of the fused residual update (Alg. 2 lines 12/16), events on the launch stream
+    # roofline of the fused residual update (Alg. 2, update step), events on the launch stream
     n, d = a.n, a.d
     blocks = prof["blocks"]
     k_tot = prof["skeletons"]
@@ -342,11 +406,13 @@ def run_ours(a):
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws_n, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"tf32": "tf32+f64", "tf32x3": "3xtf32+f64", "fp32": "f32+f64", "fp64": "f64"}[a.precision],
+                "dtype": dtype_label(a),
                 "data": "synthetic",
                 "config": workload_config(a), "k": ks[-1], "blocks_per_step": blocks / max(1, a.steps),
-                "rel_err_sq": out["rel_err_sq"], "roofline": roofline, "kernels": kernels,
+                "rel_err_sq": out["rel_err_sq"], "rel_err_sq_true": true_err_sq(Xd, out["S"], out["W"]),
+                "roofline": roofline, "kernels": kernels,
                 "gpu_launches": prof["launches"], "clocks": clk}
+
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
     if not a.no_e2e:
@@ -372,6 +438,10 @@ def run_ours(a):
             line["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": a.n * a.d * 4,
                            "d2h_bytes_per_step": o2["k"] * 8 + a.n * o2["k"] * 8}
 
+    if line is not None and ws_n == 1 and not a.no_forms:
+        wsp = None
+        torch.cuda.empty_cache()
+        line["forms"] = time_forms(a, G, Xd, stream, pid)
     if line is not None and ws_n == 1 and not a.no_cpu_baseline:
         v, info = cpu_oracle_leg(a, X, a.cpu_rows)
         line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": info["cores"], "kind": "oracle",

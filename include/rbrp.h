@@ -47,19 +47,38 @@ typedef enum {
   RBRP_EWORKSPACE = 7       /* workspace pointer misaligned or too small          */
 } rbrp_status;
 
-/* Arithmetic of the residual-update contraction (the O(n d b') step). */
+/* Arithmetic of the residual-update contraction (the O(n d b') step).  The
+ * per-block chain around it (the rows drawn, the projection against Q, the
+ * Gram matrix, the pivoted filter and Q') runs in the precision's default
+ * chain unless rbrp_opts.chain asks for the FP64 chain (rbrp_chain).  The
+ * sampling keys and the sums of the row norms are FP64 in every form. */
 typedef enum {
   RBRP_FP64 = 0,   /* residual R and every step in FP64 (CUDA-core DFMA)          */
   RBRP_TF32 = 1,   /* R in FP32, update on tcgen05 tensor cores (TF32 in, FP32    */
-                   /* accumulate); sampler keys, CGS2 Gram corrections, the b x b */
-                   /* filter and Q' stay FP64                                     */
-  RBRP_FP32 = 2,   /* R in FP32, update on CUDA cores in FP32 (same FP64 parts)   */
+                   /* accumulate).  Default chain: FP32 throughout -- FP32 copies */
+                   /* of the drawn rows and of Q, ONE projection pass against Q   */
+                   /* with FP32 products, FP32 Gram matrix and FP32 pivoted       */
+                   /* Cholesky filter, Q' = Lc^{-1} V_perm in FP32.               */
+  RBRP_FP32 = 2,   /* R in FP32, update on CUDA cores in FP32.  Default chain:    */
+                   /* FP64 storage of V and Q, two projection passes (CGS2) with  */
+                   /* FP32 products, FP64 Gram and filter, one FP64 CholQR pass   */
   RBRP_TF32X3 = 3  /* as RBRP_TF32 with every operand split into TF32 hi + lo and */
-                   /* three products per step (~FP32-accurate update); b <= 64    */
+                   /* three products per step (~FP32-accurate update); b <= 64;   */
+                   /* default chain as RBRP_FP32                                  */
 } rbrp_precision;
 
+/* Precision of the per-block chain (rbrp_opts.chain). */
 typedef enum {
-  RBRP_SAMPLER_RANDOM = 0,  /* Alg. 2 line 5: sample ~ d/||d||_1 without replacement */
+  RBRP_CHAIN_DEFAULT = 0,   /* the chain listed with each rbrp_precision            */
+  RBRP_CHAIN_FP64 = 1       /* FP64 storage and FP64 products for every small step:
+                               CGS2 against Q (two passes), the Gram matrix and the
+                               pivoted filter, Q' by two CholQR passes; combined with
+                               RBRP_TF32 this keeps tensor cores for the update only
+                               (RBRP_FP64 always runs this chain)                   */
+} rbrp_chain;
+
+typedef enum {
+  RBRP_SAMPLER_RANDOM = 0,  /* Alg. 2 sampling step: ~ d/||d||_1 without replacement */
   RBRP_SAMPLER_GREEDY = 1,  /* blockwise greedy remark (Sec. 4): top-b of d          */
   /* The same draws as RANDOM / GREEDY (identical S_t), always computed by the
    * single-stage exact sampler (FP64 keys of every eligible row, ranked in full)
@@ -69,7 +88,7 @@ typedef enum {
   RBRP_SAMPLER_GREEDY_EXACT = 3
 } rbrp_sampler;
 
-/* How lines 12 and 16 of Alg. 2 are carried out. */
+/* How the update step of Alg. 2 (coefficients and new residual norms) is carried out. */
 typedef enum {
   RBRP_FORM_RESIDUAL = 0,   /* R <- R - (R Q'^T) Q' in a residual copy of X, d_i =
                                ||R_i||^2 recomputed (robust at any precision)       */
@@ -96,7 +115,7 @@ typedef struct {
   int32_t sampler;      /* rbrp_sampler                                           */
   int32_t w_precision;  /* rbrp_w_precision                                       */
   int32_t form;         /* rbrp_form (rbrp_id only; the batched call ignores it)  */
-  int32_t reserved;     /* must be 0                                              */
+  int32_t chain;        /* rbrp_chain (rbrp_id only; the batched call ignores it) */
 } rbrp_opts;
 
 typedef struct {
@@ -108,7 +127,7 @@ typedef struct {
 } rbrp_result;
 
 /* Fill *o with the defaults: TF32, b = 64, tau_b = 1/b_t, k_max = min(n, d),
- * seed 0, problem 0, random sampler, W in FP64, residual form. */
+ * seed 0, problem 0, random sampler, W in FP64, residual form, default chain. */
 void rbrp_default_opts(rbrp_opts *o);
 
 /* Bytes of device workspace rbrp_id needs for an n x d problem with options o
@@ -163,7 +182,7 @@ rbrp_status rbrp_id_host(const void *X_host, int x_is_fp64, int64_t n, int64_t d
 /*
  * Profiling counters (instrumentation; no counterpart in the paper).  Between
  * rbrp_profile_begin() and rbrp_profile_end() the library counts every kernel
- * it launches and brackets each residual-update launch (Alg. 2 lines 12/16)
+ * it launches and brackets each residual-update launch (Alg. 2, update step)
  * and each W solve (Alg. 3) with CUDA events recorded on the caller's stream.
  * rbrp_profile_end synchronises those events, fills *out and stops counting.
  * Process-wide; not thread-safe; calls outside a begin/end pair cost nothing.
@@ -192,15 +211,23 @@ rbrp_status rbrp_profile_end(rbrp_profile *out);
  * and res exactly as documented there) but uses, instead of a caller
  * workspace, one fixed array of RBRP_NOALLOC_SCRATCH_BYTES bytes that lives in
  * the library's device image: it calls no cudaMalloc, no cudaFree and no
- * allocating library routine.  Every GPU that loads the library holds that
- * array until the process exits.
+ * allocating library routine.  Every GPU on which the library's module is
+ * loaded holds that array until the process exits.
  *
  * Limits and behaviour:
  *  - a problem whose rbrp_workspace_size exceeds RBRP_NOALLOC_SCRATCH_BYTES is
  *    rejected with RBRP_EWORKSPACE before anything is launched;
  *  - the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    before any stream capture.  Under CUDA's lazy module loading (the
+ *    default) this lookup is also what loads the module and commits the
+ *    array's memory on that device, so the first call can fail with
+ *    RBRP_ECUDA if the device is short of memory then: callers that must not
+ *    fail later should make one small call at start-up (or load modules
+ *    eagerly, CUDA_MODULE_LOADING=EAGER);
+ *  - the address is remembered per device index for the primary context (the
+ *    one the CUDA runtime uses); after cudaDeviceReset, or from a thread
+ *    bound to another context of the same device, it is not valid;
  *  - all calls on a device share the one array and it keeps the previous
  *    call's contents (each call rewrites what it reads), so calls whose work
  *    overlaps on the GPU (different streams, different host threads) race and
@@ -301,6 +328,25 @@ const char *rbrp_status_string(rbrp_status s);
 
 /* The cudaError_t value behind the last RBRP_ECUDA returned on this thread. */
 int rbrp_last_cuda_error(void);
+
+/*
+ * Bounded device waits (failure detection; no counterpart in the paper).  Every
+ * wait of the library's kernels on another part of the same launch -- the
+ * mbarrier waits between the roles of the tensor-core kernels (fused update,
+ * W solve) and the grid barriers of the cooperative sampler -- gives up after
+ * a number of polls.  The kernel then records RBRP_ETIMEOUT in the call's
+ * device state, stops issuing work, waits for the copies and tensor-core
+ * operations it has already issued, releases its tensor memory and returns;
+ * every later kernel of the call returns at once and the call returns
+ * RBRP_ETIMEOUT with its outputs unspecified.  The workspace stays usable: the
+ * next call starts from a fresh state.
+ * rbrp_set_wait_limits sets the poll limits of the calls started after it
+ * (process-wide; 0 restores the default of 2^24 mbarrier polls and 2^25 grid
+ * barrier polls, about a second each, far above any wait of a healthy run).  A
+ * small limit makes the waits of a healthy run give up: that is how the
+ * failure path is tested without hanging or faulting a GPU.
+ */
+void rbrp_set_wait_limits(uint32_t mbarrier_polls, uint32_t barrier_polls);
 
 #ifdef __cplusplus
 }

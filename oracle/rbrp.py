@@ -24,7 +24,8 @@ Everything is FP64 (FP32 inputs are upcast exactly).  Library primitives
 no blocking or fusion beyond what the algorithms state.
 
 Readings of points where the paper is silent:
-  R1  tau bounds the squared relative residual ||d||_1 / ||d0||_1 (Alg. 2 line 3).
+  R1  tau bounds the squared relative residual ||d||_1 / ||d0||_1 (the stopping
+      test of Alg. 2).
   R2  "sample without replacement" is realised as an exponential race: keys
       kappa_i = -log(u_i) / d_i over eligible rows, the b_t smallest in
       ascending (kappa, i) order.  This is sequential sampling proportional to
@@ -34,7 +35,7 @@ Readings of points where the paper is silent:
   R3  tau_b defaults to 1/b_t where b_t = min(b, #eligible, k_cap - |S|) is the
       block actually drawn, so b_t = 1 gives b' = 1 (Alg. 1 behaviour).
   R4  b' = max{ i : ||R_V(i:b_t, i:b_t)||_F^2 >= tau_b ||R_V||_F^2 and the
-      trailing mass is > 0 } (Alg. 2 line 8, 1-based i; the "> 0" guard only
+      trailing mass is > 0 } (the truncation of Alg. 2, 1-based i; the "> 0" guard only
       matters for tau_b = 0 on rank-deficient blocks).
   R5  eligible rows are E = { i not in S : d_i > 0 }; accepted rows get d = 0
       and R(i,:) = 0 exactly; rejected candidates stay eligible.
@@ -46,7 +47,7 @@ Readings of points where the paper is silent:
   R8  residual form (the GPU form): R starts as X; V = R(S_t,:)^T projected
       twice against Q (CGS2); the update applies R <- R - (R Q') Q'^T to the
       active rows and recomputes d_i = ||R(i,:)||^2.  form="downdate" follows
-      Alg. 2 lines 12 and 16 literally (X read-only, d downdated).
+      the update step of Alg. 2 as printed (X read-only, d downdated).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -55,16 +56,16 @@ from . import philox
 
 
 # ---------------------------------------------------------------------------
-# Alg. 2 line 2: squared row norms
+# Alg. 2, initial norms: squared row norms
 # ---------------------------------------------------------------------------
 def row_sq_norms(X):
-    """d_i = ||x_i||_2^2 for every row (Alg. 2 line 2; Eq. (2.2) numerators)."""
+    """d_i = ||x_i||_2^2 for every row (Alg. 2, initial norms; Eq. (2.2) numerators)."""
     X = np.asarray(X, dtype=np.float64)
     return np.einsum("ij,ij->i", X, X)
 
 
 # ---------------------------------------------------------------------------
-# Alg. 2 line 5: sample b_t rows ~ d / ||d||_1 without replacement (reading R2)
+# Alg. 2, sampling step: b_t rows ~ d / ||d||_1 without replacement (reading R2)
 # ---------------------------------------------------------------------------
 def race_keys(d, eligible, t, seed, problem=0):
     """Exponential-race keys kappa_i = -log(u_i)/d_i; +inf for ineligible rows."""
@@ -100,7 +101,7 @@ def greedy_block(d, eligible, b_t):
 
 
 # ---------------------------------------------------------------------------
-# Alg. 2 line 7: column-pivoted Householder QR of V (d x b_t)
+# Alg. 2, local CPQR: column-pivoted Householder QR of V (d x b_t)
 # ---------------------------------------------------------------------------
 def cpqr(V):
     """V(:, piv) = Q_V R_V by Householder QR with column pivoting (reading R7).
@@ -149,7 +150,7 @@ def cpqr(V):
 
 
 def filter_rank(R_V, tau_b):
-    """Alg. 2 line 8: b' = max{ i : ||R_V(i:, i:)||_F^2 >= tau_b ||R_V||_F^2 } (reading R4)."""
+    """Truncation of Alg. 2: b' = max{ i : ||R_V(i:, i:)||_F^2 >= tau_b ||R_V||_F^2 } (reading R4)."""
     m = R_V.shape[0]
     total = float(np.sum(R_V * R_V))
     tails = np.array([np.sum(R_V[i:, i:] * R_V[i:, i:]) for i in range(m)])
@@ -159,20 +160,38 @@ def filter_rank(R_V, tau_b):
 
 
 # ---------------------------------------------------------------------------
-# Alg. 2: RBRP skeleton selection
+# Alg. 2: RBRP skeleton selection, organised by the method's steps
 # ---------------------------------------------------------------------------
+def project_out(V, Q, passes):
+    """Projection step: remove from the columns of V their components in span(Q),
+    V <- V - Q (Q^T V), `passes` times (two = CGS2; the second pass only repairs
+    rounding, in exact arithmetic it changes nothing)."""
+    for _ in range(passes):
+        V = V - Q @ (Q.T @ V)
+    return V
+
+
+def truncation_gap(tails, bp, tb):
+    """How far the truncation of the filter sits from its threshold tau_b ||R_V||_F^2,
+    relative to ||R_V||_F^2 (smallest distance of the last kept and the first dropped
+    tail mass); a near-tie there can flip b' under rounding.  Logged, not used."""
+    thr = tb * tails[0]
+    near = [abs(tails[bp - 1] - thr)] + ([abs(tails[bp] - thr)] if bp < len(tails) else [])
+    return min(near) / tails[0] if tails[0] > 0 else np.inf
+
+
 def rbrp(X, tau=None, b=16, seed=0, problem=0, k=None, k_max=None, tau_b=None,
          sampler="random", form="residual"):
-    """Robust blockwise random pivoting (Alg. 2).
+    """Robust blockwise random pivoting (Alg. 2, Sec. 4).
 
     X: n x dim array (any real dtype; upcast to FP64).
     tau: tolerance on ||d||_1 / ||d0||_1 (reading R1); k: fixed-rank mode
     ("or k" in Alg. 2).  b: block size.  tau_b: filter tolerance (None -> 1/b_t,
     0 -> plain BRP).  sampler: "random" (RBRP/BRP) or "greedy" (RBGP/BGP).
-    form: "residual" (R8) or "downdate" (Alg. 2 lines 12 and 16 as printed).
+    form: "residual" (R8) or "downdate" (Alg. 2's update step as printed).
 
     Returns a dict with S (acceptance order), L (n x k), Q (dim x k), d, D0, D,
-    per-block records (t, b_t, b', sample gap, CPQR gap) and k_cap.
+    per-block records (t, b_t, b', sampling / CPQR / truncation gaps, D) and k_cap.
     """
     X = np.asarray(X, dtype=np.float64)
     n, dim = X.shape
@@ -184,69 +203,79 @@ def rbrp(X, tau=None, b=16, seed=0, problem=0, k=None, k_max=None, tau_b=None,
     if tau is None and k is None:
         raise ValueError("give tau or k")
 
-    # line 1
+    # Start: no skeletons, empty basis and coefficient matrix; the residual form
+    # keeps its own copy R of X, and d holds the initial squared row norms.
     L = np.zeros((n, 0))
     Q = np.zeros((dim, 0))
     S = []
     in_S = np.zeros(n, dtype=bool)
     t = 0
     R = X.copy() if form == "residual" else None
-    # line 2
     d = row_sq_norms(X)
     D0 = float(d.sum())
     blocks = []
 
     def keep_going():
+        # stopping test (reading R1), with the guard of reading R6
         if len(S) >= k_cap:
             return False
         if k is not None:
             return True
         return float(d.sum()) > tau * D0
 
-    # line 3
     while keep_going():
         eligible = (~in_S) & (d > 0)
         b_t = min(b, int(eligible.sum()), k_cap - len(S))
         if b_t <= 0:
             break
-        # line 4
         t += 1
-        # line 5
+
+        # Sampling step: b_t candidate rows, drawn ~ d without replacement
+        # (or the b_t largest d for the greedy variant).
         if sampler == "random":
             S_t, sgap = sample_block(d, eligible, b_t, t, seed, problem)
         else:
             S_t, sgap = greedy_block(d, eligible, b_t)
-        # line 6: V = X(S_t,:)^T - Q (Q^T X(S_t,:)^T); residual form starts from R(S_t,:)
+
+        # Projection step: the candidates' rows with span(Q) taken out.  The
+        # residual rows already are orthogonal to Q (up to rounding), so two
+        # cheap passes suffice; the printed form projects the rows of X once.
         if form == "residual":
-            V = R[S_t].T.copy()
-            for _ in range(2):
-                V = V - Q @ (Q.T @ V)
+            V = project_out(R[S_t].T.copy(), Q, 2)
         else:
             V = X[S_t].T - Q @ (Q.T @ X[S_t].T)
-        # line 7
+
+        # Local CPQR of the projected candidates and the robust truncation:
+        # keep the leading b' pivots whose trailing mass stays above tau_b.
         QV, RV, piv, qgap = cpqr(V)
-        # line 8
         tb = (1.0 / b_t) if tau_b is None else float(tau_b)
         bp, tails = filter_rank(RV, tb)
         if bp == 0:
             break
-        # line 9
+        fgap = truncation_gap(tails, bp, tb)
+
+        # Acceptance: the first b' pivots become skeletons (in pivot order) and
+        # their orthonormal directions extend the basis.
         Sp_t = S_t[piv[:bp]]
         Qp = QV[:, :bp]
-        # line 10: Q <- [Q, Q'_V]
         Q = np.concatenate([Q, Qp], axis=1)
-        # line 11-12: pi_a = rows not in the previous S (the new skeletons are in pi_a)
+
+        # Update step: coefficients of every row not yet a skeleton along the
+        # new directions (rows accepted earlier have a zero residual and keep
+        # zero coefficients), appended to L.
         active = ~in_S
         Lhat = np.zeros((n, bp))
         if form == "residual":
             Lhat[active] = R[active] @ Qp
         else:
             Lhat[active] = X[active] @ Qp
-        # line 14-15
         S.extend(int(s) for s in Sp_t)
         in_S[Sp_t] = True
         L = np.concatenate([L, Lhat], axis=1)
-        # line 16
+
+        # New squared residual norms: recomputed from the updated residual
+        # (residual form) or downdated by the new coefficients (printed form);
+        # skeletons have none left.
         if form == "residual":
             R[active] -= Lhat[active] @ Qp.T
             R[Sp_t] = 0.0
@@ -255,7 +284,7 @@ def rbrp(X, tau=None, b=16, seed=0, problem=0, k=None, k_max=None, tau_b=None,
             d = d - np.einsum("ij,ij->i", Lhat, Lhat)
         d[in_S] = 0.0
         blocks.append(dict(t=t, b_t=b_t, bp=bp, sample_gap=float(sgap), cpqr_gap=float(qgap),
-                           D=float(d.sum())))
+                           filter_gap=float(fgap), D=float(d.sum())))
 
     return dict(S=np.array(S, dtype=np.int64), L=L, Q=Q, d=d, D0=D0, D=float(d.sum()),
                 blocks=blocks, k_cap=k_cap, R=R)

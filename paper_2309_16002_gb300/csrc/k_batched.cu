@@ -26,7 +26,7 @@
 // CTA size, a schedule parameter chosen by the host (autotuned per batch).
 // Results do not depend on NT: sums over rows use a fixed 256-way partition
 // and every other reduction is per warp.  Sampling keys are the exact FP64
-// keys of Alg. 2 line 5 as in the single-problem sampler: FP32 log-domain
+// keys of Alg. 2's sampling step as in the single-problem sampler: FP32 log-domain
 // keys choose >= b_t + 32 candidates, their FP64 keys are ranked, and a margin
 // check against the FP32 error bound proves that no other row could be drawn
 // (else every eligible row is keyed in FP64).  Problem p uses Philox problem
@@ -170,7 +170,7 @@ __device__ int find_bin_cta(Smem& sm, unsigned int want, unsigned int* below) {
   return bin;
 }
 
-// Exact FP64 key of row i (as ordered bits) and its logarithm (Alg. 2 line 5).
+// Exact FP64 key of row i (as ordered bits) and its logarithm (Alg. 2, sampling step).
 __device__ __forceinline__ void exact_key(double di, long long i, unsigned long long t, unsigned long long seed,
                                           unsigned long long p, int greedy, unsigned long long* key, double* lg) {
   if (greedy) {
@@ -376,7 +376,7 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
   }
 }
 
-// The residual update of the FP32 form (Alg. 2 lines 12 and 16), with a row
+// The residual update of the FP32 form (Alg. 2, update step), with a row
 // spread over eight lanes instead of 32: lanes 8g .. 8g + 7 of a warp hold row
 // i0 + g (four rows a warp), lane q of the octet the float4 at columns
 // 4q + 32u .. 4q + 32u + 3 for u < 8, so that the octet reads 128 contiguous
@@ -655,7 +655,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
   T* Wt = (T*)(slotp + so.Wt);  // column-major
   long long* skel = a.skel[p];
 
-  // Alg. 2 lines 1-2: R = X and d_i = ||X_i||^2 in one pass over X
+  // Alg. 2, start and initial norms: R = X and d_i = ||X_i||^2 in one pass over X
   if (a.x_is_fp64)
     project_rows<NT, RPW0, false, false, true, T, double, true>((const double*)a.X[p], n, nullptr, R, ldr, m, n,
                                                                 (const T*)nullptr, 0, nullptr, 0, d, nullptr);
@@ -671,7 +671,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
   int status = isfinite(D0) ? RBRP_OK : RBRP_ENONFINITE;
 
   while (status == RBRP_OK) {
-    // Alg. 2 line 3
+    // Alg. 2, stopping test
     if (a.tau >= 0.0 && !(D > a.tau * D0)) break;
     if (k >= kc) {
       if (a.tau >= 0.0) status = RBRP_ENOTCONVERGED;
@@ -684,9 +684,9 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     if (kc - k < btl) btl = kc - k;
     const int bt = (int)btl;
     ++t;
-    // line 5
+    // sampling step
     sample_cta<NT>(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
-    // line 6: V = R(S_t, :) projected against Q twice (CGS2)
+    // projection step: V = R(S_t, :) projected against Q twice (CGS2)
     project_rows<NT, RPW, true, false, false, T, T>(R, ldr, sm.St, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
                                                     nullptr);
     __syncthreads();
@@ -695,14 +695,14 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
                                                       nullptr);
       __syncthreads();
     }
-    // lines 7-8: G = V V^T, pivoted Cholesky with the tail-mass truncation
+    // local CPQR and truncation: G = V V^T, pivoted Cholesky with the tail-mass truncation
     gram_rows<NT, T>(V, bt, n, sm);
     __syncthreads();
     const double tau_b = a.tau_b >= 0.0 ? a.tau_b : 1.0 / (double)bt;
     chol_warp<T>(sm, bt, tau_b, 1);
     const int bp = sm.bp;
     if (bp == 0) break;
-    // lines 9-10, 13: Q'_V by CholQR of V(perm), a CGS pass against Q, a second CholQR
+    // acceptance: Q'_V by CholQR of V(perm), a CGS pass against Q, a second CholQR
     trsm_cols<NT, T>(sm, V, sm.perm, Y, bp, n);
     for (int i = tid; i < bp; i += NT) {
       const long long row = sm.St[sm.perm[i]];
@@ -730,7 +730,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
       for (long long e = tid; e < bp * n; e += NT) sQp[e] = Q[k * n + e];
     }
     __syncthreads();
-    // lines 12, 16 (residual form): Lhat = R Q'^T into L(:, k : k + b'), R -= Lhat Q',
+    // update step (residual form): Lhat = R Q'^T into L(:, k : k + b'), R -= Lhat Q',
     // d_i = ||R_i||^2, rows accepted so far zeroed
     if constexpr (sizeof(T) == 4)
       update_rows_oct<NT>(R, ldr, m, sQp, bp, L + k * m, m, d, mark);

@@ -15,7 +15,7 @@
 namespace rbrp {
 
 // ============================================================================
-// Alg. 2 line 2: d0(i) = ||x_i||^2, copy of X into the residual R.
+// Alg. 2, initial norms: d0(i) = ||x_i||^2, copy of X into the residual R.
 // One warp per row; per-CTA partial sums in a fixed order (deterministic).
 // ============================================================================
 template <typename TX, typename TR>
@@ -89,9 +89,11 @@ __device__ __forceinline__ void stop_test(State* st) {
 }
 
 __global__ void k_finish_init(const double* __restrict__ partials, int np, State* st, double tau, double tau_b,
-                              long long k_cap) {
+                              long long k_cap, unsigned spin_mbar, unsigned spin_grid) {
   const double D0 = fixed_sum_partials<kFixedSumThreads>(partials, np);
   if (threadIdx.x == 0) {
+    st->spin_mbar = spin_mbar;
+    st->spin_grid = spin_grid;
     st->tau = tau;
     st->tau_b = tau_b;
     st->k_cap = k_cap;
@@ -115,12 +117,14 @@ __global__ void k_finish_init(const double* __restrict__ partials, int np, State
 
 cudaError_t launch_finish_init(const double* partials, int nparts, State* st, double tau, double tau_b,
                                long long k_cap, cudaStream_t s) {
-  k_finish_init<<<1, kFixedSumThreads, 0, s>>>(partials, nparts, st, tau, tau_b, k_cap);
+  unsigned spin_mbar = kDefaultSpinMbar, spin_grid = kDefaultSpinGrid;
+  wait_limits(&spin_mbar, &spin_grid);
+  k_finish_init<<<1, kFixedSumThreads, 0, s>>>(partials, nparts, st, tau, tau_b, k_cap, spin_mbar, spin_grid);
   return counted(cudaGetLastError());
 }
 
 // ============================================================================
-// Alg. 2 line 5: S_t ~ d / ||d||_1 without replacement, as an exponential race:
+// Alg. 2, sampling step: S_t ~ d / ||d||_1 without replacement, as an exponential race:
 // key kappa_i = -log(u_i) / d_i over eligible rows (d_i > 0; accepted rows
 // have d_i = 0), the b_t smallest in ascending (kappa, i) order.  The greedy
 // sampler (blockwise greedy remark) uses key -d_i.  Selection is a tree of
@@ -241,7 +245,7 @@ cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, un
 }
 
 // ============================================================================
-// Alg. 2 line 6 (first half): V = R(S_t, :) (FP64, or FP32 on the plain TF32 path).
+// Alg. 2, projection step (first half): V = R(S_t, :) (FP64, or FP32 on the plain TF32 path).
 // ============================================================================
 template <typename TR, typename TV>
 __global__ void k_gather(const TR* __restrict__ R, long long ldr, const long long* __restrict__ S_t,
@@ -452,7 +456,7 @@ cudaError_t launch_qp_lowp(const void* Qt, int q_is_fp64, long long ldq, float* 
 }
 
 // ============================================================================
-// Alg. 2 line 16 (residual form): d_i = ||R_i||^2; rows accepted in this block
+// Alg. 2, new residual norms (residual form): d_i = ||R_i||^2; rows accepted in this block
 // are zeroed (R_i = 0, d_i = 0).  One warp per row, fixed-order partials.
 // ============================================================================
 template <typename TR>
@@ -498,7 +502,7 @@ cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n
   return counted(cudaGetLastError());
 }
 
-// Alg. 2 line 16 as printed (downdate form): with Lhat = X Q'^T in columns
+// Alg. 2, new residual norms as printed (downdate form): with Lhat = X Q'^T in columns
 // k .. k + b' - 1 of L, d_i -= ||Lhat_i||^2 for the rows not yet in S, d_i = 0
 // for the rows accepted in this block (their Lhat row is kept), and Lhat_i = 0
 // for rows accepted in earlier blocks (their residual is zero, so their Lhat
@@ -544,7 +548,7 @@ cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* ma
   return counted(cudaGetLastError());
 }
 
-// Alg. 2 line 3 after a block: D = ||d||_1, k += b', t += 1, stopping test.
+// Alg. 2, stopping test after a block: D = ||d||_1, k += b', t += 1.
 __global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st) {
   pdl_wait();
   if (st->done) return;

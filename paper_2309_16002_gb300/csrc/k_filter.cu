@@ -1,6 +1,6 @@
 // The robust blockwise filter and the new basis Q' of one RBRP block.
 //
-// Alg. 2 lines 7-9 and the robust blockwise filtering remark (Sec. 4): the
+// Alg. 2's local CPQR, truncation and acceptance with the robust blockwise filtering remark (Sec. 4): the
 // candidates V (b_t rows) are pivoted like a column-pivoted QR of V^T and the
 // factorisation is truncated at the first step i where the trailing mass
 // ||R_V(i:, i:)||_F^2 drops below tau_b ||R_V||_F^2.  On the GPU this is the
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
 // index: redux.sync max over the FP32 bit patterns, which order like the
 // values for d_r >= 0, then min over the indices of the maxima) per warp,
 // combines the two warps through shared memory, and stops at the first step
-// whose trailing mass fails the test of Alg. 2 line 8; the pivot's owner then
+// whose trailing mass fails the truncation test of Alg. 2; the pivot's owner then
 // publishes its scaled column l = S(:, p) / sqrt(d_p) and every thread applies
 // the rank-1 update S(:, r) -= l l_r to its column.  The kernel writes the
 // pivot-order factor Lc; Q'_V = Lc^{-1} V_perm follows as a column-parallel
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
   }
 }
 
-// Q'_V = Lc^{-1} V(perm, :) on the plain TF32 path (Alg. 2 lines 9-10): rows by
+// Q'_V = Lc^{-1} V(perm, :) on the plain TF32 path (Alg. 2, acceptance): rows by
 // forward substitution, Y(i, :) = (V(perm[i], :) - sum_{l<i} Lc(i, l) Y(l, :)) / Lc(i, i)
 // for i < b' <= 64, FP32.  32 columns per CTA, one octet of lanes per column;
 // lane q of the octet holds rows q, q + 8, ... of its column in registers and,

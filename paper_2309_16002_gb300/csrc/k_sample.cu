@@ -1,4 +1,4 @@
-// Alg. 2 line 5 on the GPU: S_t ~ d / ||d||_1 without replacement (reading of
+// Alg. 2's sampling step on the GPU: S_t ~ d / ||d||_1 without replacement (reading of
 // the sampling step as an exponential race: keys kappa_i = -log(u_i) / d_i over
 // eligible rows, the b_t smallest in ascending (kappa, i) order; the greedy
 // variant of the blockwise greedy remark uses -d_i).
@@ -59,9 +59,11 @@ __global__ void __launch_bounds__(kSampThreads) k_samp_keys(const double* __rest
 // kSampThreads threads each sum eight bins and take an exclusive scan of those
 // sums; the one thread whose range contains the want-th count walks its bins.
 // Callable from any block size >= kSampThreads (the other threads only take
-// part in the barriers).
-__device__ int find_bin(const unsigned int* __restrict__ hist, unsigned int want, unsigned int* below,
-                        unsigned int* total) {
+// part in the barriers).  The bins are read through L2 (__ldcg): in the
+// cooperative sampler they were filled by other CTAs' atomics earlier in the
+// same launch, and every CTA must see the same counts to take the same branch
+// at the next grid barrier (a non-coherent or L1-cached read could be stale).
+__device__ int find_bin(const unsigned int* hist, unsigned int want, unsigned int* below, unsigned int* total) {
   __shared__ unsigned int wsum[kSampThreads / 32];
   __shared__ int s_bin;
   __shared__ unsigned int s_below, s_total;
@@ -71,7 +73,7 @@ __device__ int find_bin(const unsigned int* __restrict__ hist, unsigned int want
   if (t < kSampThreads) {
 #pragma unroll
     for (int q = 0; q < per; ++q) {
-      c[q] = hist[t * per + q];
+      c[q] = __ldcg(hist + t * per + q);
       sum += c[q];
     }
     incl = sum;
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(1024) k_samp_final(long long n, unsigned int* 
   unsigned int below1, total1;
   find_bin(hist1, (unsigned int)want, &below1, &total1);  // total1 = number of eligible rows
   const unsigned int c22 = cut22(hist1, hist2, want);
-  const int nc = (int)*ncand;
+  const int nc = (int)__ldcg(ncand);  // counted by every CTA's atomics
   const bool overflow = nc > cap;
   const int m = overflow ? 0 : nc;
   for (int e = threadIdx.x; e < m; e += blockDim.x) {
@@ -281,13 +283,14 @@ __global__ void k_samp_clear(unsigned int* __restrict__ hist1, unsigned int* __r
 // exact keys | ranking, margin check and S_t by CTA 0.  Results are those of
 // the four kernels above (same keys, cut, candidates and ranking).
 constexpr int kCoopThreads = 512;
-constexpr unsigned kBarSpins = 1u << 25;  // ~1-2 s of polls, then the barrier gives up
-
 // Grid barrier over gridDim.x CTAs: arrival counter bar[0] (reset by the last
-// arriver) and generation bar[1].  The wait is bounded: on timeout the CTA
-// records RBRP_ETIMEOUT in the State and carries on (every CTA still passes
-// every barrier, so no CTA is left waiting).
-__device__ __forceinline__ void grid_barrier(unsigned int* bar, State* st) {
+// arriver) and generation bar[1].  The wait is bounded (`limit` polls, by
+// default ~1-2 s): on timeout the CTA records RBRP_ETIMEOUT in the State and
+// carries on (every CTA still passes every barrier, so no CTA is left
+// waiting; the results of that block are then void, every later kernel of the
+// call sees the State's done flag, and the next call clears the barrier
+// words before its first launch of this kernel).
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, State* st, unsigned limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = bar + 1;
@@ -301,7 +304,7 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, State* st) {
     } else {
       unsigned int spins = 0;
       while (*vgen == gen0) {
-        if (++spins > kBarSpins) {
+        if (++spins > limit) {
           st->status = RBRP_ETIMEOUT;
           st->done = 1;
           break;
@@ -329,6 +332,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
   if (st->done) return;  // read before any CTA writes the State: the same for every CTA
   __shared__ unsigned int h[kBins];
   unsigned int* bar = ncand + 2;
+  const unsigned glim = st->spin_grid;
   const unsigned long long block_no = (unsigned long long)st->t + 1ULL;
   const long long gstride = (long long)gridDim.x * kCoopThreads;
   const long long g0 = (long long)blockIdx.x * kCoopThreads + threadIdx.x;
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
   __syncthreads();
   for (int j = threadIdx.x; j < kBins; j += kCoopThreads)
     if (h[j]) atomicAdd(&hist1[j], h[j]);
-  grid_barrier(bar, st);
+  grid_barrier(bar, st, glim);
   // pass 2: histogram of the next 11 bits inside the cut bin -- skipped (with
   // its barrier) when the whole cut bin adds few candidates (the final ranking
   // is quadratic in their number), which every CTA decides alike from the
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
     for (int j = threadIdx.x; j < kBins; j += kCoopThreads)
       if (h[j]) atomicAdd(&hist2[j], h[j]);
   }
-  if (!one_level) grid_barrier(bar, st);
+  if (!one_level) grid_barrier(bar, st, glim);
   // pass 3: candidates with their exact FP64 keys
   unsigned int c22 = 0x3FFFFFu;
   if (one_level) {
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
       }
     }
   }
-  grid_barrier(bar, st);
+  grid_barrier(bar, st, glim);
   if (blockIdx.x != 0) return;
   // pass 4 (CTA 0): rank the candidates, check the margin, write S_t and b_t
   __shared__ unsigned long long ek[kSampCap];
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_sample_coop(const double* __re
   __shared__ double elog[kSampCap];
   __shared__ long long sorted_idx[kMaxBlock];
   __shared__ double sorted_log[kMaxBlock];
-  const int nc = (int)*ncand;
+  const int nc = (int)__ldcg(ncand);  // counted by every CTA's atomics
   const bool overflow = nc > cap;
   const int m = overflow ? 0 : nc;
   for (int e = threadIdx.x; e < m; e += kCoopThreads) {  // written by other CTAs: read from L2

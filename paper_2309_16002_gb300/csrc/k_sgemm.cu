@@ -1,4 +1,4 @@
-// Small dense products of the per-block chain (Alg. 2 lines 6-11): the CGS2
+// Small dense products of the per-block chain (Alg. 2, projection to acceptance): the CGS2
 // coefficients V Q^T, the corrections V -= C Q, and the Gram matrix V V^T.
 // M is a block of b <= 256 rows, N and K are up to k_cap or d; too small for
 // tensor-core tiles to pay, so these run on CUDA cores.

@@ -1,6 +1,6 @@
 // Fused residual update of RBRP on Blackwell tensor cores (sm_103a).
 //
-// Alg. 2 lines 12 and 16 in the residual form: for every 128-row tile of R,
+// Alg. 2's update step in the residual form: for every 128-row tile of R,
 //   Lhat = R_tile Q'^T            (GEMM 1, K = d, N = b'_pad)
 //   R_tile <- R_tile - Lhat Q'    (GEMM 2, K = b'_pad, N = d in 32-column chunks)
 //   d_i = ||R_i||^2, rows accepted in this block set to 0,
@@ -65,7 +65,7 @@ struct Cfg {
   static constexpr int BAR_OFF = P + NOP * A2;
   // the BM-row A reads of GEMM 1 (last stage, lo copy) end inside the Lhat buffers
   static_assert((S1 - 1) * ST1 + (NOP - 1) * (A1 + B1) + BM * BK1 * 4 <= P + NOP * A2, "A over-read");
-  static constexpr int BAR_BYTES = 256;
+  static constexpr int BAR_BYTES = 320;
   static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
   static constexpr uint32_t D2COL = BMAX;              // D2 double buffer after D1
   static constexpr uint32_t TMEM_COLS = (BMAX + 2 * NB2 <= 128) ? 128 : 256;
@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
   auto d2_empty = [&](int b) { return a2_ready + 24u + 8u * b; };
   const uint32_t red_bar = a2_ready + 40u;
   uint32_t* tmem_slot = (uint32_t*)(smem + C::BAR_OFF + 8 * (3 * S1 + 3 * S3 + 7));
+  const uint32_t drain = sBar + 8u * (3 * S1 + 3 * S3 + 8);  // abort path: MMA drain
+  static_assert(8 * (3 * S1 + 3 * S3 + 9) <= C::BAR_BYTES, "barrier area");
 
   __shared__ int s_abort;
   __shared__ double s_red[4];
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       mbar_init(d2_empty(b), 128);
     }
     mbar_init(red_bar, 128);
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -146,6 +149,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
   tc_after();
   const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
   volatile int* abort = &s_abort;
+  const uint32_t lim = st->spin_mbar;
+  uint32_t fills1 = 0, fills3 = 0;  // TMA fills issued into ring 1 / ring 3 (for the abort drain)
 
   if (warp == 0) {
     if (lane == 0) {
@@ -156,21 +161,22 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       for (int kc = 0; kc < nK1; ++kc) {
         const int s = kc % S1;
         const uint32_t ph = (uint32_t)(kc / S1) & 1u;
-        if (!mbar_wait(empty1(s), ph ^ 1u, abort)) break;
+        if (!mbar_wait(empty1(s), ph ^ 1u, abort, lim)) break;
         mbar_expect_tx(full1(s), (uint32_t)((C::A1 + C::B1) + (SPLIT ? C::B1 : 0)));
         const uint32_t base = sb + s * C::ST1;
         tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)row0, keep);
         tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
         if (SPLIT) tma_load_2d(base + 2 * C::A1 + C::B1, &tmQlo, full1(s), kc * BK1, 0);
+        ++fills1;
       }
       // phase-3 buffers alias the phase-1 ring: reuse only after GEMM 1 has drained it.
       // Chunks are taken last-to-first so the most recently loaded columns are re-read first.
-      if (mbar_wait(d1_full, 0, abort)) {
+      if (mbar_wait(d1_full, 0, abort, lim)) {
         for (int c = 0; c < nC; ++c) {
           const int s = c % S3;
           const uint32_t ph = (uint32_t)(c / S3) & 1u;
           const int col = (nC - 1 - c) * NB2;
-          if (!mbar_wait(empty3(s), ph ^ 1u, abort)) break;
+          if (!mbar_wait(empty3(s), ph ^ 1u, abort, lim)) break;
           mbar_expect_tx(full3(s), (uint32_t)C::ST3);
           const uint32_t base = sb + s * C::ST3;
           tma_load_2d_hint(base, &tmR, full3(s), col, (int)row0, drop);
@@ -179,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
             tma_load_2d(base + C::R3 + a * C::B2A, &tmQT, full3(s), a * 32, col);
             if (SPLIT) tma_load_2d(base + C::R3 + C::B2 + a * C::B2A, &tmQTlo, full3(s), a * 32, col);
           }
+          ++fills3;
         }
       }
     }
@@ -189,8 +196,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       for (int kc = 0; kc < nK1; ++kc) {
         const int s = kc % S1;
         const uint32_t ph = (uint32_t)(kc / S1) & 1u;
-        if (!mbar_wait(full1(s), ph, abort)) break;
-        if (SPLIT && !mbar_wait(conv1(s), ph, abort)) break;
+        if (!mbar_wait(full1(s), ph, abort, lim)) break;
+        if (SPLIT && !mbar_wait(conv1(s), ph, abort, lim)) break;
         tc_after();
         const uint32_t a = sb + s * C::ST1, b = a + C::A1;
         const uint32_t alo = a + C::A1 + C::B1, blo = alo + C::A1;
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
         mma_commit(empty1(s));
       }
       mma_commit(d1_full);
-      if (mbar_wait(a2_ready, 0, abort)) {
+      if (mbar_wait(a2_ready, 0, abort, lim)) {
         tc_after();
         const uint32_t id2 = idesc_tf32(BM, NB2);
         const int nk2 = N1 / 8;
@@ -214,8 +221,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
           const uint32_t ph = (uint32_t)(c / S3) & 1u;
           const int buf = c & 1;
           const uint32_t bph = (uint32_t)(c >> 1) & 1u;
-          if (!mbar_wait(full3(s), ph, abort)) break;
-          if (!mbar_wait(d2_empty(buf), bph ^ 1u, abort)) break;
+          if (!mbar_wait(full3(s), ph, abort, lim)) break;
+          if (!mbar_wait(d2_empty(buf), bph ^ 1u, abort, lim)) break;
           tc_after();
           const uint32_t dt = tmem + C::D2COL + (uint32_t)(buf * NB2);
           const uint32_t b2 = sb + s * C::ST3 + C::R3;
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       for (int kc = 0; kc < nK1; ++kc) {
         const int s = kc % S1;
         const uint32_t ph = (uint32_t)(kc / S1) & 1u;
-        if (!mbar_wait(full1(s), ph, abort)) break;
+        if (!mbar_wait(full1(s), ph, abort, lim)) break;
         if (!own) {
           mbar_arrive(conv1(s));
           continue;
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       }
     }
     double nrm = 0.0;
-    if (mbar_wait(d1_full, 0, abort)) {
+    if (mbar_wait(d1_full, 0, abort, lim)) {
       tc_after();
       for (int cb = 0; own && cb * 32 < N1; ++cb) {
         uint32_t v[32];
@@ -303,8 +310,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       const uint32_t ph = (uint32_t)(c / S3) & 1u;
       const int buf = c & 1;
       const uint32_t bph = (uint32_t)(c >> 1) & 1u;
-      if (!mbar_wait(full3(s), ph, abort)) break;
-      if (!mbar_wait(d2_full(buf), bph, abort)) break;
+      if (!mbar_wait(full3(s), ph, abort, lim)) break;
+      if (!mbar_wait(d2_full(buf), bph, abort, lim)) break;
       tc_after();
       uint32_t u[32];
       if (own) {
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       mbar_arrive(epi_done(s));
       if (et == 0) {
         // every epilogue thread has written its row of this chunk (bounded wait)
-        if (!mbar_wait(epi_done(s), ph, abort)) break;
+        if (!mbar_wait(epi_done(s), ph, abort, lim)) break;
         tma_store_2d_hint(&tmR, sb + s * C::ST3, (nC - 1 - c) * NB2, (int)row0, drop);
         tma_commit();
         // with at most this store pending, the previous chunk's stage has been read out
@@ -352,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     if (lane == 0) s_red[q] = t;
     mbar_arrive(red_bar);
     if (et == 0) {
-      if (mbar_wait(red_bar, 0, abort)) {
+      if (mbar_wait(red_bar, 0, abort, lim)) {
         partials[2 * blockIdx.x] = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
         partials[2 * blockIdx.x + 1] = 0.0;
       }
@@ -363,8 +370,16 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
   tc_before();
   __syncthreads();
   if (s_abort) {
-    // let copies already in flight land before the shared memory is released
-    for (int i = 0; i < 64; ++i) __nanosleep(1000);
+    // every role has left its loop: the producer waits for the fills it issued
+    // into both rings and the MMA issuer for its MMAs before the memory is
+    // released (the epilogue's stores were waited for above)
+    if (threadIdx.x == 0) {
+      drain_ring(full1(0), S1, fills1);
+      drain_ring(full3(0), S3, fills3);
+    }
+    if (warp == 1 && lane == 0) drain_mma(drain);
+    tc_before();
+    __syncthreads();
     if (threadIdx.x == 0) {
       st->status = RBRP_ETIMEOUT;
       st->done = 1;
@@ -443,6 +458,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   auto d2_full = [&](int b) { return x0 + 32u + 8u * b; };
   auto d2_empty = [&](int b) { return x0 + 48u + 8u * b; };
   uint32_t* tmem_slot = (uint32_t*)(smem + (x0 + 64u - sb));
+  const uint32_t drain1 = x0 + 72u, drain3 = x0 + 80u;  // abort path: MMA drains of GEMM 1 / GEMM 2
 
   __shared__ int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -484,6 +500,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
       mbar_init(d2_full(b), 1);
       mbar_init(d2_empty(b), 128);
     }
+    mbar_init(drain1, 1);
+    mbar_init(drain3, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -497,6 +515,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
   tc_after();
   const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
   volatile int* abort = &s_abort;
+  const uint32_t lim = st->spin_mbar;
+  uint32_t fills = 0;  // TMA fills issued by this thread's ring (for the abort drain)
 
   if (warp == 0) {
     // ---------------- ring 1: R and Q' chunks for GEMM 1 (R asked to stay in L2)
@@ -507,7 +527,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         for (int kc = 0; kc < nK1; ++kc, ++g) {
           const int s = (int)(g % PS1);
-          if (!mbar_wait(empty1(s), ((g / PS1) & 1u) ^ 1u, abort)) {
+          if (!mbar_wait(empty1(s), ((g / PS1) & 1u) ^ 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -517,6 +537,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
         }
       }
+      fills = g;
     }
   } else if (warp == 1) {
     // ---------------- GEMM 1: D1[it & 1] = R_tile Q'^T
@@ -526,12 +547,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
       bool ok = true;
       for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int buf = it & 1;
-        if (!mbar_wait(d1_empty(buf), ((it >> 1) & 1u) ^ 1u, abort)) break;
+        if (!mbar_wait(d1_empty(buf), ((it >> 1) & 1u) ^ 1u, abort, lim)) break;
         tc_after();
         const uint32_t dt = tmem + (uint32_t)(buf * BMAX);
         for (int kc = 0; kc < nK1; ++kc, ++g) {
           const int s = (int)(g % PS1);
-          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort)) {
+          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -557,7 +578,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           const int j = nJ - 1 - jj;
           for (int pc = 0; pc < npieces(j); ++pc, ++g) {
             const int s = (int)(g % PS3);
-            if (!mbar_wait(empty3(s), ((g / PS3) & 1u) ^ 1u, abort)) {
+            if (!mbar_wait(empty3(s), ((g / PS3) & 1u) ^ 1u, abort, lim)) {
               ok = false;
               break;
             }
@@ -567,6 +588,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
         }
       }
+      fills = g;
     }
   } else if (warp == 9) {
     // ---------------- Q'^T chunks of GEMM 2, for the MMA
@@ -577,7 +599,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         for (int jj = 0; jj < nJ; ++jj, ++g) {
           const int j = nJ - 1 - jj;
           const int s = (int)(g % PSB);
-          if (!mbar_wait(emptyb(s), ((g / PSB) & 1u) ^ 1u, abort)) {
+          if (!mbar_wait(emptyb(s), ((g / PSB) & 1u) ^ 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -587,6 +609,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           for (int a = 0; a < BMAX / 32; ++a) tma_load_2d(base + a * C::B2A, &tmQT, fullb(s), a * 32, j * PNB);
         }
       }
+      fills = g;
     }
   } else if (warp == 3) {
     // ---------------- GEMM 2: D2[g & 1] = Lhat Q'(:, chunk), Lhat = D1[it & 1] in TMEM
@@ -597,13 +620,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
       bool ok = true;
       for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int dbuf = it & 1;
-        if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort)) break;
+        if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort, lim)) break;
         tc_after();
         const uint32_t a1 = tmem + (uint32_t)(dbuf * BMAX);
         for (int jj = 0; jj < nJ; ++jj, ++g) {
           const int s = (int)(g % PSB);
           const int buf = g & 1;
-          if (!mbar_wait(fullb(s), (g / PSB) & 1u, abort) || !mbar_wait(d2_empty(buf), ((g >> 1) & 1u) ^ 1u, abort)) {
+          if (!mbar_wait(fullb(s), (g / PSB) & 1u, abort, lim) || !mbar_wait(d2_empty(buf), ((g >> 1) & 1u) ^ 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -634,7 +657,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       const bool marked = in && (mark[row] == tno);
       // Lhat: TMEM -> registers -> L (GEMM 2 reads it from TMEM itself)
       const int dbuf = it & 1;
-      if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort)) break;
+      if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort, lim)) break;
       tc_after();
       uint32_t v[BMAX];
       tmem_ld32(tmem + lane_base + (uint32_t)(dbuf * BMAX), *(uint32_t(*)[32])&v[0]);
@@ -653,14 +676,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
       for (int jj = 0; jj < nJ && ok; ++jj, ++gj) {
         const int j = nJ - 1 - jj;
         const int b2 = gj & 1;
-        if (!mbar_wait(d2_full(b2), (gj >> 1) & 1u, abort)) {
+        if (!mbar_wait(d2_full(b2), (gj >> 1) & 1u, abort, lim)) {
           ok = false;
           break;
         }
         tc_after();
         for (int pc = 0; pc < npieces(j); ++pc, ++g) {
           const int s = (int)(g % PS3);
-          if (!mbar_wait(full3(s), (g / PS3) & 1u, abort)) {
+          if (!mbar_wait(full3(s), (g / PS3) & 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -712,7 +735,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           const int j = nJ - 1 - jj;
           for (int pc = 0; pc < npieces(j); ++pc, ++g) {
             const int s = (int)(g % PS3);
-            if (!mbar_wait(epi_done(s), (g / PS3) & 1u, abort)) {
+            if (!mbar_wait(epi_done(s), (g / PS3) & 1u, abort, lim)) {
               ok = false;
               break;
             }
@@ -730,7 +753,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
   tc_before();
   __syncthreads();
   if (s_abort) {
-    for (int i = 0; i < 64; ++i) __nanosleep(1000);
+    // Every role has left its loop.  Before the shared and tensor memory are
+    // released, each producer waits for the fills it issued and each MMA issuer
+    // for the MMAs it issued (the R stores were waited for by warp 8 above).
+    if (lane == 0) {
+      if (warp == 0) drain_ring(full1(0), PS1, fills);
+      else if (warp == 2) drain_ring(full3(0), PS3, fills);
+      else if (warp == 9) drain_ring(fullb(0), PSB, fills);
+      else if (warp == 1) drain_mma(drain1);
+      else if (warp == 3) drain_mma(drain3);
+    }
+    tc_before();
+    __syncthreads();
     if (threadIdx.x == 0) {
       st->status = RBRP_ETIMEOUT;
       st->done = 1;

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const uint32_t f_full = sBar + 8u * (3 * WS + 4);  // epilogue -> MMA, producer: newest block written
   const uint32_t f_free = sBar + 8u * (3 * WS + 5);  // producer -> epilogue: its TMA store has read it
   uint32_t* tmem_slot = (uint32_t*)(smem + C::BAR_OFF + 8 * (3 * WS + 6));
+  const uint32_t drain = sBar + 8u * (3 * WS + 7);  // abort path: MMA drain
 
   __shared__ int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
     }
     mbar_init(f_full, 128);
     mbar_init(f_free, 1);
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -127,6 +129,8 @@ __global__ void __launch_bounds__(kWThreads, 1)
   tc_after();
   const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
   volatile int* abort = &s_abort;
+  const uint32_t lim = st->spin_mbar;
+  uint32_t fills = 0;  // TMA fills issued by the producer (for the abort drain)
 
   if (warp == 0) {
     // ---------------- TMA producer
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
             if (kind == 1 && i == q.nL) tma_wait_all0();  // the stores of W(tile, J+2 ...) are complete
             const int s = (int)(g % WS);
             const uint32_t ph = (g / WS) & 1u;
-            if (!mbar_wait(empty(s), ph ^ 1u, abort)) {
+            if (!mbar_wait(empty(s), ph ^ 1u, abort, lim)) {
               ok = false;
               break;
             }
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
           }
           if (!ok || q.nF == 0) continue;
           // W(tile, J+1) for the blocks left of J (none after J = 0)
-          if (!mbar_wait(f_full, f & 1u, abort)) {
+          if (!mbar_wait(f_full, f & 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
           ++f;
         }
       }
+      fills = g;
       tma_wait_all0();
     }
   } else if (warp == 1) {
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
         for (int J = nblk - 1; J >= 0; --J, ++it) {
           const WSeq q(J, k);
           const int buf = it & 1;
-          if (!mbar_wait(d_empty(buf), ((it >> 1) & 1u) ^ 1u, abort)) {
+          if (!mbar_wait(d_empty(buf), ((it >> 1) & 1u) ^ 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -201,18 +206,18 @@ __global__ void __launch_bounds__(kWThreads, 1)
             const int kind = q.kind(i);
             const int s = (int)(g % WS);
             const uint32_t ph = (g / WS) & 1u;
-            if (!mbar_wait(full(s), ph, abort)) {
+            if (!mbar_wait(full(s), ph, abort, lim)) {
               ok = false;
               break;
             }
             // every chunk passes the converters (which split the L chunks), so
             // none of them can fall a whole ring behind
-            if (!mbar_wait(conv(s), ph, abort)) {
+            if (!mbar_wait(conv(s), ph, abort, lim)) {
               ok = false;
               break;
             }
             if (kind == 2 && i == q.nL + q.nW) {
-              if (!mbar_wait(f_full, f & 1u, abort)) {
+              if (!mbar_wait(f_full, f & 1u, abort, lim)) {
                 ok = false;
                 break;
               }
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
         const WSeq q(J, k);
         for (int i = 0; i < q.n(); ++i, ++g) {
           const int s = (int)(g % WS);
-          if (!mbar_wait(full(s), (g / WS) & 1u, abort)) {
+          if (!mbar_wait(full(s), (g / WS) & 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
       const long long row = (long long)tile * WM + r;
       for (int J = nblk - 1; J >= 0; --J, ++it) {
         const int buf = it & 1;
-        if (!mbar_wait(d_full(buf), (it >> 1) & 1u, abort)) {
+        if (!mbar_wait(d_full(buf), (it >> 1) & 1u, abort, lim)) {
           ok = false;
           break;
         }
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
         mbar_arrive(d_empty(buf));
         if (J > 0) {
           // W(tile, J) as the MMA operand of block J-1 (hi/lo, 128-byte swizzle)
-          if (f > 0 && !mbar_wait(f_free, (f - 1) & 1u, abort)) {
+          if (f > 0 && !mbar_wait(f_free, (f - 1) & 1u, abort, lim)) {
             ok = false;
             break;
           }
@@ -372,7 +377,13 @@ __global__ void __launch_bounds__(kWThreads, 1)
   tc_before();
   __syncthreads();
   if (s_abort) {
-    for (int i = 0; i < 64; ++i) __nanosleep(1000);
+    // every role has left its loop: the producer waits for the fills it issued
+    // and the MMA issuer for its MMAs before the memory is released (the
+    // producer's stores were waited for above)
+    if (lane == 0 && warp == 0) drain_ring(full(0), WS, fills);
+    if (lane == 0 && warp == 1) drain_mma(drain);
+    tc_before();
+    __syncthreads();
     if (threadIdx.x == 0) {
       st->status = RBRP_ETIMEOUT;
       st->done = 1;

@@ -19,6 +19,14 @@ namespace rbrp {
 
 std::atomic<long long> g_kernel_launches{0};
 
+// Poll limits of the bounded device waits (rbrp_set_wait_limits).
+std::atomic<unsigned> g_spin_mbar{kDefaultSpinMbar};
+std::atomic<unsigned> g_spin_grid{kDefaultSpinGrid};
+void wait_limits(unsigned* mbar, unsigned* grid) {
+  *mbar = g_spin_mbar.load();
+  *grid = g_spin_grid.load();
+}
+
 namespace {
 
 thread_local int g_last_cuda = 0;
@@ -64,6 +72,7 @@ cudaError_t timed(EventPool& pool, cudaStream_t s, F&& body) {
 struct Plan {
   long long n, d, k_cap;
   int b, prec, r64, l64, w32, greedy, f32, exact_sampler, downdate;
+  int chain64;  // FP64 storage and FP64 products for every step of the per-block chain
   long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32, ldt;
   int nparts;
   int s_upd1, s_upd2;
@@ -97,6 +106,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   if (o->tau_b > 1.0) return RBRP_EINVAL;
   if (o->form != RBRP_FORM_RESIDUAL && o->form != RBRP_FORM_DOWNDATE) return RBRP_EINVAL;
   if (o->form == RBRP_FORM_DOWNDATE && o->precision != RBRP_FP64) return RBRP_EINVAL;
+  if (o->chain != RBRP_CHAIN_DEFAULT && o->chain != RBRP_CHAIN_FP64) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
   if (n > (1LL << 48) / d) return RBRP_EINVAL;  // n d elements: every byte count below stays far from overflow
   // the tensor-core update keeps Lhat (128 x b'_pad) in shared memory: b <= 128
@@ -113,7 +123,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->r64 = (o->precision == RBRP_FP64);
   p->l64 = p->r64;
   p->w32 = (o->w_precision == RBRP_W_FP32);
-  p->f32 = (o->precision == RBRP_TF32);  // FP32 storage for the per-block chain
+  p->chain64 = (o->precision == RBRP_FP64 || o->chain == RBRP_CHAIN_FP64);
+  p->f32 = (o->precision == RBRP_TF32 && !p->chain64);  // FP32 storage for the per-block chain
   p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
   p->exact_sampler = (o->sampler == RBRP_SAMPLER_RANDOM_EXACT || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
   p->downdate = (o->form == RBRP_FORM_DOWNDATE);
@@ -142,7 +153,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   need = std::max<size_t>(need, (size_t)splits_for(n, 64, kc) * n * 64);
   {
     // small products (k_sgemm.cu): splits x tiles x tile^2 FP64 partials
-    const int cgs64 = (p->prec == RBRP_FP64), gram64 = (p->prec != RBRP_TF32);
+    const int cgs64 = p->chain64, gram64 = !p->f32;
     auto sg_need = [&](long long M, long long N, long long K, int acc64) {
       const int tile = sgemm_tile(acc64);
       int sp = 1, kcs = 0;
@@ -353,7 +364,8 @@ cudaError_t sgemm(const Plan& p, const Bufs& u, const void* A, DimRef a_off, lon
 // the rows of V come from a residual that is already orthogonal to Q up to the
 // update's rounding, so the coefficients are small and each pass shrinks the
 // component in span(Q) by the FP32 product accuracy (~1e-7); two passes leave
-// it at FP64 level.  The FP64 path keeps FP64 products throughout.
+// it at FP64 level.  The FP64 path, and any path with the FP64 chain
+// (RBRP_CHAIN_FP64), keeps FP64 products throughout.
 template <typename TS, typename TACC>
 cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, void* V, DimRef voff, DimRef rows, cudaStream_t s) {
   const State* st = u.st;
@@ -373,13 +385,13 @@ cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, void* V, DimRef voff, DimRe
 cudaError_t cgs_pass(const Plan& p, const Bufs& u, void* V, DimRef rows, cudaStream_t s,
                      DimRef voff = dim_const(0)) {
   if (p.f32) return cgs_pass_t<float, float>(p, u, V, voff, rows, s);
-  if (p.prec == RBRP_FP64) return cgs_pass_t<double, double>(p, u, V, voff, rows, s);
+  if (p.chain64) return cgs_pass_t<double, double>(p, u, V, voff, rows, s);
   return cgs_pass_t<double, float>(p, u, V, voff, rows, s);
 }
 
 cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s);
 
-// One block of Alg. 2 (lines 4-16), all sizes on the device.
+// One block of Alg. 2 (sampling through the new residual norms), all sizes on the device.
 cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cudaStream_t s) {
   State* st = u.st;
   const long long n = p.n, d = p.d, b = p.b;
@@ -389,11 +401,11 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     e = (call);                      \
     if (e != cudaSuccess) return e;  \
   } while (0)
-  // line 5: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it)
+  // sampling step: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it)
   if (!p.exact_sampler) LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
   LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, p.exact_sampler, s));
-  // line 6: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
-  if (p.downdate)  // Alg. 2 line 6 as printed: V = X(S_t, :), projected below
+  // projection step: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
+  if (p.downdate)  // projection step as printed: V = X(S_t, :), projected below
     LK(launch_gather(const_cast<void*>(u.X), u.x64, u.ldx, u.S_t, u.V, 1, p.ldq, d, p.b, st, s));
   else
     LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
@@ -402,7 +414,7 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   // that to the FP32 floor, which a second FP32 pass cannot lower)
   LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
   if (!p.f32) LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
-  // lines 7-9: G = V V^T, pivoted Cholesky with the tail-mass truncation
+  // local CPQR and truncation: G = V V^T, pivoted Cholesky with the tail-mass truncation
   if (p.f32) {
     // FP32 chain: Gram, filter with Lc^{-1}, Q'_V = Lc^{-1} V_perm as one
     // product.  Q'_V is a combination of rows already projected off Q, so its
@@ -422,12 +434,13 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     LK((sgemm<double, double, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0),
                                     p.ldg, dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
     LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
-    // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 path
-    // adds a second CholQR pass (orthogonality to FP64 rounding); on the mixed
-    // paths one FP64 CholQR already leaves ~u64 * cond^2 <= ~1e-8, far below
+    // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 chain
+    // adds a second CholQR pass (orthogonality to FP64 rounding); with the
+    // default chain of the mixed paths one FP64 CholQR already leaves
+    // ~u64 * cond^2 <= ~1e-8, far below
     // the rounding of their residual update, so Q' is written in place and only
     // re-projected.
-    if (p.prec == RBRP_FP64) {
+    if (p.chain64) {
       LK(launch_trsm_rows(u.Lc, p.ldlc, u.perm, u.V, p.ldq, u.Y, dim_const(0), p.ldq, d, p.b, st, s));
       LK(cgs_pass(p, u, u.Y, dim_dev(&st->bp), s));
       LK((sgemm<double, double, true>(p, u, u.Y, dim_const(0), p.ldq, u.Y, dim_const(0), p.ldq, u.G, dim_const(0),
@@ -439,7 +452,7 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
       LK(cgs_pass(p, u, u.Qt, dim_dev(&st->bp), s, dim_dev(&st->k, p.ldq)));
     }
   }
-  // lines 12 and 16 (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
+  // update step (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
   if (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) {
     const int split = (p.prec == RBRP_TF32X3);
     if (!(p.f32 && filter_f32_writes_factor((int)p.b)))  // else the Q' substitution wrote them
@@ -468,7 +481,7 @@ cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s) {
     if (e != cudaSuccess) return e;  \
   } while (0)
   if (p.downdate) {
-    // Alg. 2 lines 12 and 16 as printed: Lhat = X Q'^T into L(:, k : k + b'), d_i -= ||Lhat_i||^2
+    // update step as printed: Lhat = X Q'^T into L(:, k : k + b'), d_i -= ||Lhat_i||^2
     if (u.x64)
       LK((gemm<double, double, double, double>(
           p, u, mat(const_cast<void*>(u.X), dim_const(0), u.ldx, 1), mat(u.Qt, dim_dev(&st->k, p.ldq), 1, p.ldq),
@@ -577,13 +590,13 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   u.x64 = x_is_fp64 ? 1 : 0;
   u.ldx = ldx;
   State* st = u.st;
-  // Alg. 2 lines 1-2 (the residual form also copies X into R)
+  // Alg. 2, start and initial norms (the residual form also copies X into R)
   CK(launch_init_norms(X, x_is_fp64, n, d, ldx, p.downdate ? nullptr : u.R, p.r64, p.ldr, u.dvec, u.mark, u.part,
                        p.nparts, st, s));
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
   CK(launch_sample_clear(u.samp2, n, s));
   CK(cudaMemsetAsync(u.cnt, 0, (size_t)kSgemmCounters * 4, s));
-  // Alg. 2 lines 3-16: blocks are queued in groups and the State is read back
+  // Alg. 2's loop: blocks are queued in groups and the State is read back
   // after each group.  The group size is the number of blocks still expected,
   // extrapolated from the observed per-block decay of ||d||_1 (or of the rank
   // gap in fixed-rank mode), so that few blocks are queued past the stop
@@ -1135,6 +1148,11 @@ const char* rbrp_status_string(rbrp_status s) {
 }
 
 int rbrp_last_cuda_error(void) { return g_last_cuda; }
+
+void rbrp_set_wait_limits(uint32_t mbarrier_polls, uint32_t barrier_polls) {
+  g_spin_mbar = mbarrier_polls ? mbarrier_polls : kDefaultSpinMbar;
+  g_spin_grid = barrier_polls ? barrier_polls : kDefaultSpinGrid;
+}
 
 // rbrp_id with the workspace taken from the fixed device array above: no
 // cudaMalloc, no cudaFree, no allocating library call.  The run writes every

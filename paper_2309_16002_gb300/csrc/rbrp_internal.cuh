@@ -22,11 +22,12 @@ struct State {
   long long b_t;     // rows drawn in the current block
   long long bp;      // rows accepted in the current block (b')
   long long k_cap;   // min(n, d, k_max)
-  long long done;    // 1 once the stopping test (Alg. 2 line 3) fails
+  long long done;    // 1 once the stopping test of Alg. 2 ends the loop
   long long status;  // rbrp_status raised on the device (0 = ok)
   long long bp_pad;  // b' rounded up to a multiple of 16 (tensor-core N)
   long long sample_fallback;  // 1: the exact FP64 tree sampler must draw this block
-  long long pad_;
+  unsigned int spin_mbar;     // polls of one bounded mbarrier wait (tensor-core kernels)
+  unsigned int spin_grid;     // polls of one bounded grid barrier (cooperative sampler)
   double D0;         // ||d0||_1
   double D;          // ||d||_1 after the last block
   double tau;        // tolerance (< 0: fixed-rank mode)
@@ -153,7 +154,7 @@ __device__ __forceinline__ double fixed_sum_partials(const double* partials, int
   return t;
 }
 
-// Alg. 2 line 3 after a block: D = ||d||_1, k += b', t += 1, stopping test.
+// Alg. 2, stopping test after a block: D = ||d||_1, k += b', t += 1.
 __device__ __forceinline__ void finish_block(State* st, double D) {
   st->D = D;
   st->k += st->bp;
@@ -215,6 +216,11 @@ cudaError_t launch_init_norms(const void* X, int x_is_fp64, long long n, long lo
                               double* partials, int nparts, State* st, cudaStream_t s);
 cudaError_t launch_finish_init(const double* partials, int nparts, State* st, double tau, double tau_b,
                                long long k_cap, cudaStream_t s);
+// Poll limits of the bounded device waits, copied into the State of every call
+// (rbrp_set_wait_limits; the defaults are far above any wait a healthy run needs).
+constexpr unsigned kDefaultSpinMbar = 1u << 24;
+constexpr unsigned kDefaultSpinGrid = 1u << 25;
+void wait_limits(unsigned* mbar, unsigned* grid);
 cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
                           unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
                           State* st, int force, cudaStream_t s);

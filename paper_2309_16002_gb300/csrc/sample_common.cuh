@@ -1,4 +1,4 @@
-// Device helpers of the exact two-stage sampler (Alg. 2 line 5 as an
+// Device helpers of the exact two-stage sampler (Alg. 2's sampling step as an
 // exponential race), shared by the single-problem sampler (k_sample.cu) and
 // the batched kernel (k_batched.cu): the FP32 log-domain key of a row and the
 // constants of the cut.

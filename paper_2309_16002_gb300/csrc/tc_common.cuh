@@ -9,7 +9,9 @@
 namespace rbrp {
 namespace tc {
 
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Polls of a drain wait (an abort path waiting for its own copies and MMAs in
+// flight): independent of the run's wait limit, since those always complete.
+constexpr uint32_t kDrainSpins = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -31,14 +33,30 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; on timeout raises the CTA-wide abort flag.  Returns false once aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+// Bounded wait (`limit` polls, State::spin_mbar); on timeout raises the CTA-wide
+// abort flag.  Returns false once aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (*abort) return false;
   }
   *abort = 1;
   return false;
+}
+
+// Abort path of a TMA producer: waits (at most kDrainSpins polls per stage,
+// ignoring the abort flag) until the last fill issued into each stage of a
+// ring of `stages` full-barriers (8 bytes apart from bar0) has landed, so no
+// copy still writes the CTA's shared memory or signals its barriers after the
+// CTA has exited.  `issued` = number of fills issued (fill f uses stage
+// f % stages, phase f / stages; a stage holds at most one fill in flight).
+__device__ __forceinline__ void drain_ring(uint32_t bar0, uint32_t stages, uint32_t issued) {
+  const uint32_t first = issued > stages ? issued - stages : 0u;
+  for (uint32_t f = first; f < issued; ++f) {
+    const uint32_t bar = bar0 + 8u * (f % stages);
+    for (uint32_t it = 0; it < kDrainSpins && !mbar_try(bar, (f / stages) & 1u); ++it) {
+    }
+  }
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -120,6 +138,14 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// Abort path of an MMA issuer: commits every tcgen05 operation this thread
+// has issued to `bar` (a fresh barrier of count 1) and waits until they have
+// completed, so tensor memory is not released under an MMA still writing it.
+__device__ __forceinline__ void drain_mma(uint32_t bar) {
+  mma_commit(bar);
+  for (uint32_t it = 0; it < kDrainSpins && !mbar_try(bar, 0u); ++it) {
+  }
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(

@@ -29,14 +29,14 @@ EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_wor
            "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
            "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched", "rbrp_batch_create",
            "rbrp_batch_run", "rbrp_batch_autotune", "rbrp_batch_set_schedule", "rbrp_batch_get_schedule",
-           "rbrp_batch_destroy"]
+           "rbrp_batch_destroy", "rbrp_set_wait_limits"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("block", ctypes.c_int32), ("tau_b", ctypes.c_double),
                 ("k_max", ctypes.c_int64), ("seed", ctypes.c_uint64), ("problem", ctypes.c_uint64),
                 ("sampler", ctypes.c_int32), ("w_precision", ctypes.c_int32), ("form", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("chain", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -113,12 +113,19 @@ def load():
     L.rbrp_batch_get_schedule.restype = ctypes.c_int
     L.rbrp_batch_destroy.argtypes = [vp]
     L.rbrp_batch_destroy.restype = None
+    L.rbrp_set_wait_limits.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+    L.rbrp_set_wait_limits.restype = None
     L.rbrp_profile_begin.argtypes = []
     L.rbrp_profile_begin.restype = None
     L.rbrp_profile_end.argtypes = [ctypes.POINTER(Profile)]
     L.rbrp_profile_end.restype = ctypes.c_int
     _lib = L
     return L
+
+
+def set_wait_limits(mbarrier_polls=0, barrier_polls=0):
+    """Poll limits of the library's bounded device waits for later calls (0: the default)."""
+    load().rbrp_set_wait_limits(int(mbarrier_polls), int(barrier_polls))
 
 
 def rbrp_profile_begin():
@@ -134,10 +141,11 @@ def rbrp_profile_end():
 
 
 FORMS = {"residual": 0, "downdate": 1}
+CHAINS = {"default": 0, "fp64": 1}
 
 
 def make_opts(block=64, precision="tf32", tau_b=-1.0, k_max=0, seed=0, problem=0, sampler="random",
-              w_precision="fp64", form="residual"):
+              w_precision="fp64", form="residual", chain="default"):
     o = Opts()
     load().rbrp_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -149,6 +157,7 @@ def make_opts(block=64, precision="tf32", tau_b=-1.0, k_max=0, seed=0, problem=0
     o.sampler = SAMPLERS[sampler]
     o.w_precision = W_PRECISIONS[w_precision]
     o.form = FORMS[form]
+    o.chain = CHAINS[chain]
     return o
 
 
@@ -238,7 +247,7 @@ class Workspace:
 
 
 def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0, sampler="random",
-            w_precision="fp64", workspace=None, stream=None, form="residual"):
+            w_precision="fp64", workspace=None, stream=None, form="residual", chain="default"):
     """Row ID of a CUDA tensor X (n x d, FP32/FP64, row-major rows) by RBRP (Alg. 2) and Alg. 3.
 
     Returns dict(S (int64 CUDA tensor, acceptance order), W (n x k FP64 CUDA tensor), k, blocks,
@@ -247,7 +256,7 @@ def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, pro
     import torch
     _check_x(X, cuda=True)
     n, d = X.shape
-    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form)
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form, chain)
     if workspace is not None and ((workspace.n, workspace.d) != (n, d) or workspace.kc < k_cap(n, d, k_max)):
         raise ValueError("workspace was made for %d x %d, k_cap %d" % (workspace.n, workspace.d, workspace.kc))
     ws = workspace if workspace is not None else Workspace(n, d, opts, X.device)
@@ -268,15 +277,16 @@ def rbrp_id(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, pro
 
 
 def rbrp_id_noalloc(X, tol, skel_out, W_out, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0,
-                    sampler="random", w_precision="fp64", stream=None):
+                    sampler="random", w_precision="fp64", stream=None, form="residual", chain="default"):
     """rbrp_id without any device allocation by the library: the workspace is the library's
     fixed device array (RBRP_NOALLOC_SCRATCH_BYTES).  For callers that cannot allocate; the
-    outputs skel_out (int64[k_cap]) and W_out (FP64 n x k_cap) are the caller's CUDA tensors."""
+    outputs skel_out (int64[k_cap]) and W_out (FP64 n x k_cap) are the caller's CUDA tensors.
+    The first call on a device commits the array (see include/rbrp.h): make it at start-up."""
     import torch
     _check_x(X, cuda=True)
     n, d = X.shape
     _check_outputs(skel_out, W_out, n, k_cap(n, d, k_max), device=X.device)
-    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision)
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form, chain)
     res = Result()
     s = stream if stream is not None else torch.cuda.current_stream(X.device)
     st = load().rbrp_id_noalloc(ctypes.c_void_p(X.data_ptr()), int(X.dtype == torch.float64), n, d, X.stride(0),
@@ -307,7 +317,8 @@ class HostWorkspace:
 
 
 def rbrp_id_host(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0, problem=0, sampler="random",
-                 w_precision="fp64", workspace=None, skel_out=None, W_out=None, stream=None, form="residual"):
+                 w_precision="fp64", workspace=None, skel_out=None, W_out=None, stream=None, form="residual",
+                 chain="default"):
     """rbrp_id on host buffers: X (numpy array or CPU tensor, C-contiguous FP32/FP64).
 
     skel_out / W_out: optional preallocated host outputs (int64[k_cap], FP64 n x k_cap, pinned
@@ -320,7 +331,7 @@ def rbrp_id_host(X, tol, block=64, seed=0, precision="tf32", tau_b=-1.0, k_max=0
     _check_x(Xt, cuda=False)
     n, d = Xt.shape
     fp64 = int(Xt.dtype == torch.float64)
-    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form)
+    opts = make_opts(block, precision, tau_b, k_max, seed, problem, sampler, w_precision, form, chain)
     kc = k_cap(n, d, k_max)
     skel = skel_out if skel_out is not None else torch.empty(kc, dtype=torch.int64)
     W = W_out if W_out is not None else torch.empty((n, kc), dtype=torch.float64)

@@ -72,6 +72,13 @@ def test_workspace_size_and_validation_on_host(libpath):
     assert res - dd >= 100000 * 1000 * 8
     with pytest.raises(rbrp.RBRPError):
         rbrp.rbrp_workspace_size(0, 10, o)
+    # the FP64 chain beside the TF32 update: accepted, and it needs no less than the FP32 chain
+    c64 = rbrp.rbrp_workspace_size(100000, 1000, rbrp.make_opts(block=64, precision="tf32", chain="fp64"))
+    assert c64 >= ws
+    bad = rbrp.make_opts(block=64, precision="tf32")
+    bad.chain = 2
+    with pytest.raises(rbrp.RBRPError):
+        rbrp.rbrp_workspace_size(100, 10, bad)
     assert rbrp.rbrp_host_workspace_size(1000, 50, 0, o) > rbrp.rbrp_workspace_size(1000, 50, o)
 
 
@@ -120,4 +127,4 @@ def test_opts_layout_matches_the_header(libpath):
     ctypes.memset(ctypes.byref(o), 0xAB, ctypes.sizeof(o))
     rbrp.load().rbrp_default_opts(ctypes.byref(o))
     assert (o.precision, o.block, o.tau_b, o.k_max, o.seed, o.problem) == (1, 64, -1.0, 0, 0, 0)
-    assert (o.sampler, o.w_precision, o.form, o.reserved) == (0, 0, 0, 0)
+    assert (o.sampler, o.w_precision, o.form, o.chain) == (0, 0, 0, 0)

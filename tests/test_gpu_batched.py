@@ -2,21 +2,30 @@
 
 Problem p of a batch uses Philox problem id (base + p), base 0 unless given, so it must
 reproduce the single-problem oracle run with that problem id.  Bars, problem by problem (as in test_gpu_parity):
-  FP64  skeleton indices identical to the oracle's (or a near-tie the oracle logged) and
-        |e_gpu - e_oracle| <= 1e-10, e = ||X - W X_S||_F / ||X||_F;
-  FP32  e_gpu <= max(1.05 e_same, e_same + 1e-5) with e_same the oracle's exact error for
-        the same skeletons (W = X X_S^+), e_gpu^2 <= 1.05 tol, k <= 1.1 k_oracle + b.
+  FP64  skeleton indices identical to the oracle's (or a near-tie the oracle logged at the
+        first block where the runs part, oracle/parity.py) and |e_gpu - e_oracle| <= 1e-10,
+        e = ||X - W X_S||_F / ||X||_F;
+  FP32  e_gpu <= max(1.05 e_oracle, e_oracle + 1e-5) against the oracle's own run of the
+        problem, the same bar against the exact error of the GPU's skeletons (W = X X_S^+),
+        e_gpu^2 <= 1.05 tol, k <= 1.1 k_oracle + b.
 W(S, :) = I exactly in both.
 """
 import numpy as np
 import pytest
 
+from oracle import parity as P
 from oracle import rbrp as O
 from paper_2309_16002_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
-NEAR_TIE = 1e-12
+
+def _skeletons_ok(ref, S, tau, where):
+    ok, note = P.fp64_skeleton_check(ref, S, tau)
+    assert ok, (where, note)
+    if note:
+        print("near-tie excuse (%s): %s" % (where, note))
+    return not note
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +65,7 @@ def _run(G, Xs, tol, **kw):
 
 
 def _e(X, S, W):
-    return float(np.sqrt(O.id_error_sq(X, S, W)))
+    return P.id_error(X, S, W)
 
 
 @pytest.mark.parametrize("tol,b", [(1e-5, 16), (1e-9, 8)])
@@ -65,11 +74,9 @@ def test_batched_fp64_matches_oracle(G, tol, b):
     outs = _run(G, Xs, tol, block=b, seed=7, precision="fp64")
     for p, (X, out) in enumerate(zip(Xs, outs)):
         ref = O.rbrp_id(X, tau=tol, b=b, seed=7, problem=p)
-        S, S_ref = out["S"].tolist(), ref["S"].tolist()
+        S = out["S"].tolist()
         assert out["status"] in (0, 5), (p, out["status"])
-        if S != S_ref:
-            gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
-            assert gaps and min(gaps) < NEAR_TIE, (p, S[:10], S_ref[:10])
+        if not _skeletons_ok(ref, S, tol, p):
             continue
         k = len(S)
         assert np.array_equal(out["W"][out["S"]], np.eye(k)), p
@@ -93,8 +100,10 @@ def test_batched_fp32_bar(G, tol, b):
             continue
         ref = O.rbrp_id(X64, tau=tol, b=b, seed=3, problem=p)
         e_gpu = _e(X64, out["S"], out["W"])
+        e_ref = _e(X64, ref["S"], ref["W"])
+        assert P.mixed_bar(e_gpu, e_ref), (p, e_gpu, e_ref)
         e_same = float(np.sqrt(O.skeleton_error_sq(X64, out["S"])))
-        assert e_gpu <= max(1.05 * e_same, e_same + 1e-5), (p, e_gpu, e_same)
+        assert P.mixed_bar(e_gpu, e_same), (p, e_gpu, e_same)
         if out["status"] == 0:
             assert e_gpu ** 2 <= 1.05 * tol + 1e-10, (p, e_gpu ** 2, tol)
         assert k <= 1.1 * len(ref["S"]) + b, (p, k, len(ref["S"]))
@@ -107,16 +116,12 @@ def test_batched_fixed_rank_and_options(G):
         outs = _run(G, Xs, 1e-7, block=8, seed=1, precision="fp64", **kw)
         for p, (X, out) in enumerate(zip(Xs, outs)):
             ref = O.rbrp_id(X, tau=1e-7, b=8, seed=1, problem=p, **okw)
-            if out["S"].tolist() != ref["S"].tolist():
-                gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
-                assert gaps and min(gaps) < NEAR_TIE, (kw, p)
+            _skeletons_ok(ref, out["S"], 1e-7, (kw, p))
     outs = _run(G, Xs, -1.0, block=4, seed=2, precision="fp64", k_max=10)
     for p, (X, out) in enumerate(zip(Xs, outs)):
         ref = O.rbrp_id(X, b=4, seed=2, problem=p, k=10)
         assert out["k"] == len(ref["S"]), p
-        if out["S"].tolist() != ref["S"].tolist():
-            gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
-            assert gaps and min(gaps) < NEAR_TIE, p
+        _skeletons_ok(ref, out["S"], None, p)
 
 
 def test_batched_same_as_single_problem_calls(G):
@@ -205,9 +210,7 @@ def test_batched_exact_sampler_and_tie_fallback(G, sampler):
     base = sampler.replace("_exact", "")
     for p, (X, out) in enumerate(zip(Xs, outs)):
         ref = O.rbrp_id(X, tau=1e-6, b=8, seed=2, problem=p, sampler=base)
-        if out["S"].tolist() != ref["S"].tolist():
-            gaps = [min(bl["sample_gap"], bl["cpqr_gap"]) for bl in ref["blocks"]]
-            assert gaps and min(gaps) < NEAR_TIE, (p, out["S"][:10], ref["S"][:10])
+        _skeletons_ok(ref, out["S"], 1e-6, p)
 
 
 def test_batched_nonfinite_and_limits(G):
@@ -251,7 +254,9 @@ def test_batched_full_workload_sampled(G):
         assert np.array_equal(W[S], np.eye(k)), p
         ref = O.rbrp_id(X64, tau=tol, b=b, seed=0, problem=p)
         e_gpu = _e(X64, S, W)
+        e_ref = _e(X64, ref["S"], ref["W"])
+        assert P.mixed_bar(e_gpu, e_ref), (p, e_gpu, e_ref)
         e_same = float(np.sqrt(O.skeleton_error_sq(X64, S)))
-        assert e_gpu <= max(1.05 * e_same, e_same + 1e-5), (p, e_gpu, e_same)
+        assert P.mixed_bar(e_gpu, e_same), (p, e_gpu, e_same)
         assert e_gpu ** 2 <= 1.05 * tol + 1e-10, (p, e_gpu ** 2)
         assert k <= 1.1 * len(ref["S"]) + b, (p, k, len(ref["S"]))

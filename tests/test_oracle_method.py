@@ -16,7 +16,7 @@ from paper_2309_16002_gb300 import workloads as WL
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-# ---------------------------------------------------------------- sampler (Alg. 2 line 5)
+# ---------------------------------------------------------------- sampler (Alg. 2, sampling step)
 def test_race_sampler_plackett_luce_law():
     """Ordered pair (S_t[0], S_t[1]) ~ p_i p_j / (1 - p_i): sequential sampling without replacement."""
     d = np.array([5.0, 1.0, 3.0, 0.5, 2.5])
@@ -49,7 +49,7 @@ def test_greedy_block_is_topb():
     assert S_t.tolist() == [1, 3, 2]
 
 
-# ---------------------------------------------------------------- CPQR filter (Alg. 2 lines 7-8)
+# ---------------------------------------------------------------- CPQR filter (Alg. 2, local CPQR and truncation)
 def test_cpqr_factorisation_and_lapack_pivots():
     rng = np.random.default_rng(3)
     for trial in range(5):
