@@ -94,10 +94,17 @@ def sample_block(d, eligible, b_t, t, seed, problem=0):
 
 
 def greedy_block(d, eligible, b_t):
-    """RBGP/BGP: indices of the b_t largest d among eligible rows, descending, ties to smaller row."""
+    """RBGP/BGP: indices of the b_t largest d among eligible rows, descending, ties to smaller row.
+
+    Returns (S_t, gap) with gap the relative gap between the b_t-th and (b_t+1)-th largest
+    d (inf if there is no (b_t+1)-th eligible row), the boundary rounding can flip."""
     key = np.where(eligible, -d, np.inf)
     order = np.lexsort((np.arange(d.shape[0]), key))
-    return order[:b_t].copy(), np.inf
+    gap = np.inf
+    if b_t < int(eligible.sum()):
+        a, c = d[order[b_t - 1]], d[order[b_t]]
+        gap = (a - c) / a if a > 0 else np.inf
+    return order[:b_t].copy(), gap
 
 
 # ---------------------------------------------------------------------------
