@@ -25,6 +25,7 @@ same structure):
   gmm_pitfall   the adversarial GMM of Sec. 4 (means 10 j e_j, covariance I,
                 n/k points per cluster)
   low_rank      an exactly rank-r Gaussian product
+  gaussian_embedding  the d x l N(0, 1/l) embedding of sketchy pivoting
 """
 import numpy as np
 
@@ -166,6 +167,13 @@ def gmm_pitfall(n=2000, d=500, k=100, seed=6, dtype=np.float64):
     for j in range(k):
         X[j * m:(j + 1) * m, j] += 10.0 * (j + 1)
     return X.astype(dtype)
+
+
+def gaussian_embedding(d, l, seed=11, dtype=np.float64):
+    """Gaussian embedding Omega (d x l) with i.i.d. N(0, 1/l) entries, the random input of
+    sketchy pivoting (drawn here so that the GPU path and the oracle use the same one)."""
+    rng = _rng(seed)
+    return (rng.standard_normal((d, l)) / np.sqrt(l)).astype(dtype)
 
 
 def low_rank(n=500, d=100, r=20, seed=7, dtype=np.float64):
