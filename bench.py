@@ -589,6 +589,8 @@ def run_batched(a):
 # stated, block size not stated) on the 1e5 x 1e3 adversarial GMM, in seconds,
 # by fixed rank: context only (other hardware, other precision).
 PAPER_GPU_RBRP_S = {52: 4.448e-2, 100: 7.231e-2, 220: 1.073e-1, 346: 1.336e-1, 472: 1.596e-1}
+# the same table's SkLUPP-OSID row (sketchy pivoting with LUPP, W by Alg. 4 with l = 3k)
+PAPER_GPU_SKLUPP_OSID_S = {52: 1.204e-2, 100: 2.233e-2, 220: 4.835e-2, 346: 8.254e-2, 472: 1.189e-1}
 
 
 def run_reference_fixed_rank(a):
@@ -668,11 +670,42 @@ def run_fixed_rank(a):
                          "paper_v100_ms": paper * 1e3 if paper else None})
         del wsp
         torch.cuda.empty_cache()
+    # sketchy pivoting with LUPP + OSID (Sec. 3.2, Alg. 4), l = 3k, the paper's GPU comparator:
+    # FP32 sketch and LUPP with the TF32 W pass, and the FP64 form
+    sk_rows = []
+    for prec, wprec in (("tf32", "fp32"), ("fp64", "fp64")):
+        Xs = Xd if prec != "fp64" else Xd.to(torch.float64)
+        for k in ks:
+            l = 3 * k
+            Om = torch.from_numpy(WL.gaussian_embedding(a.d, l, seed=k,
+                                                        dtype=np.float64 if prec == "fp64" else np.float32)).to(dev)
+            opts = G.sketch_opts(prec, a.block if prec != "tf32" else min(a.block, 128), wprec)
+            ws = G.SketchWorkspace(a.n, a.d, l, k, opts, dev)
+            kw = dict(precision=prec, w_precision=wprec, block=opts.block, workspace=ws, stream=s)
+            steps = max(1, a.steps if prec == "tf32" else min(a.steps, 2))
+            for _ in range(max(1, min(a.warmup, 2))):
+                out = G.rbrp_sketch_id(Xs, Om, k, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                out = G.rbrp_sketch_id(Xs, Om, k, **kw)
+            e1.record(s)
+            torch.cuda.synchronize()
+            Xe = Xd.to(torch.float64)
+            E = Xe - out["W"] @ Xe[out["S"]]
+            paper = PAPER_GPU_SKLUPP_OSID_S.get(k)
+            sk_rows.append({"precision": prec, "k": k, "l": l, "k_out": out["k"], "ms": e0.elapsed_time(e1) / steps,
+                            "rel_err_sq_true": float(torch.sum(E * E) / torch.sum(Xe * Xe)),
+                            "paper_v100_ms": paper * 1e3 if paper else None})
+            del ws, Om, Xe, E
+            torch.cuda.empty_cache()
     line = {"metric": "ID time at fixed rank (ms), adversarial GMM 1e5 x 1e3", "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "tf32+f64 / f64",
             "config": {"workload": "gmm_fixed_rank", "n": a.n, "d": a.d, "clusters": 100, "means": "10 j e_j",
                        "block": a.block, "seed": 0},
             "value": next(r["ms"] for r in rows if r["precision"] == "tf32"), "ranks": rows,
+            "sklupp_osid": sk_rows,
             "note": "paper_v100_ms: the paper's RBRP-ID GPU times (V100, cuBLAS + MAGMA), other hardware and "
                     "precision; context, not a target"}
     print(json.dumps(line), flush=True)

@@ -323,6 +323,53 @@ rbrp_status rbrp_batch_set_schedule(rbrp_batch h, int32_t threads, int32_t ctas_
 rbrp_status rbrp_batch_get_schedule(rbrp_batch h, int32_t *threads, int32_t *ctas_per_sm, int32_t *ctas);
 void rbrp_batch_destroy(rbrp_batch h);
 
+/*
+ * Sketchy pivoting with LU partial pivoting and the oversampled sketchy ID
+ * (SkLUPP-OSID): the comparison method of Sec. 3.2 and Alg. 4, not rank-adaptive.
+ *
+ *   Y = X Omega (n x l): the sketching step of Sec. 3.2;
+ *   S = the k pivot rows of LU with partial (row) pivoting of Y(:, 0:k), in pivot
+ *       order (largest |Schur complement entry|, ties to the smaller row; a zero
+ *       pivot ends the selection, so |S| < k when Y(:, 0:k) has rank below k);
+ *   W = Y_c Y_{S,c}^+ with Y_c = Y(:, 0:c), c = osid_cols: Alg. 4 (OSID, c = l,
+ *       the paper uses l = 3k) or Eq. (5.2) (c = k).  W(S,:) = I.
+ *
+ * W is built by the block loop of rbrp_id run on Y_c with S forced in order (no
+ * sampling, no pivoting, no truncation: Sec. 5.1's identity L2 L1^{-1} = Y_c Y_{S,c}^+
+ * for the accepted rows), so its update, chain and W solve are those of rbrp_id.
+ *
+ * X          device, row-major n x d, leading dimension ldx >= d; FP64 or FP32
+ *            (x_is_fp64).  Read only.
+ * Omega      device, row-major d x l: the embedding, drawn by the caller (the paper:
+ *            i.i.d. N(0, 1/l) entries); FP64 when o->precision == RBRP_FP64, else FP32
+ *            (then X must be FP32 too).  Read only.
+ * k          skeletons wanted, 1 <= k <= min(n, l); osid_cols in [k, l] (0 = l).
+ * o          precision: RBRP_FP64 runs the sketch, LUPP and the W pass in FP64; any
+ *            other value runs the sketch and LUPP in FP32 and the W pass's update in
+ *            that precision (its per-block chain always FP64); block: rows accepted
+ *            per block of the W pass (as rbrp_opts.block); w_precision: the final solve.
+ * skel       device int64[k]: S in pivot order.
+ * W          device FP64 n x k, leading dimension ldw >= k; columns < |S| written.
+ * res        host: k = |S|, blocks of the W pass, d0 and d_final of the W pass on Y_c
+ *            (so rel_err_sq = ||Y_c - W Y_{S,c}||_F^2 / ||Y_c||_F^2, the sketched error).
+ * workspace  device, 256-byte aligned, >= rbrp_sketch_workspace_size bytes.
+ * Returns RBRP_ENOTCONVERGED when the W pass accepted fewer rows than LUPP chose (a
+ * chosen row without residual left in Y_c); RBRP_ETIMEOUT when a bounded grid
+ * barrier of the LUPP kernel gave up; otherwise as rbrp_id.  The call synchronises
+ * the stream once after LUPP (to size the W pass) and returns after the work ends.
+ */
+typedef struct {
+  int32_t precision;    /* rbrp_precision (see above)                              */
+  int32_t block;        /* rows per block of the W pass, as rbrp_opts.block          */
+  int32_t w_precision;  /* rbrp_w_precision                                         */
+  int32_t osid_cols;    /* 0: all l columns (OSID, Alg. 4); k: Eq. (5.2)             */
+} rbrp_sketch_opts;
+rbrp_status rbrp_sketch_workspace_size(int64_t n, int64_t d, int64_t l, int64_t k, const rbrp_sketch_opts *o,
+                                       size_t *bytes);
+rbrp_status rbrp_sketch_id(const void *X, int x_is_fp64, int64_t n, int64_t d, int64_t ldx, const void *Omega,
+                           int64_t l, int64_t k, const rbrp_sketch_opts *o, void *workspace, size_t ws_bytes,
+                           int64_t *skel, double *W, int64_t ldw, rbrp_result *res, rbrp_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *rbrp_status_string(rbrp_status s);
 

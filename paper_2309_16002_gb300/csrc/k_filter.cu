@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kRegCholThreads) k_pchol_reg(const double* __r
         if (!alive[j]) continue;
         const double dj = diag[j];
         msum += dj;
-        const unsigned long long kj = pivoted ? orderable(dj) : (j == i ? ~0ULL : 0ULL);
+        const unsigned long long kj = (pivoted == 1) ? orderable(dj) : (j == i ? ~0ULL : 0ULL);
         if (kj > key || (kj == key && j < vi)) {
           key = kj;
           vi = j;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kRegCholThreads) k_pchol_reg(const double* __r
       if (tid == 0) {
         const double v = (vi == INT_MAX) ? 0.0 : diag[vi];
         int stop = 0;
-        if (pivoted && !(msum >= tau_b * total && msum > 0.0)) stop = 1;
+        if (pivoted == 1 && !(msum >= tau_b * total && msum > 0.0)) stop = 1;
         if (vi == INT_MAX || !(v > 0.0)) stop = 1;
         s_stop = stop;
         s_piv = vi;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_pchol_global(const double* __restrict__
       for (int j = tid; j < m; j += 32) {
         if (!alive[j]) continue;
         msum += diag[j];
-        const bool better = pivoted ? (diag[j] > v || (diag[j] == v && j < vi)) : (j == i);
+        const bool better = (pivoted == 1) ? (diag[j] > v || (diag[j] == v && j < vi)) : (j == i);
         if (better) { v = diag[j]; vi = j; }
       }
 #pragma unroll
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_pchol_global(const double* __restrict__
         s_piv = vi;
         s_pv = v;
         int stop = 0;
-        if (pivoted && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
+        if (pivoted == 1 && !(msum >= tau_b * s_total && msum > 0.0)) stop = 1;
         if (vi == INT_MAX || !(v > 0.0)) stop = 1;
         s_stop = stop;
       }
@@ -723,6 +723,14 @@ static cudaError_t launch_pchol_any(const double* G, long long ldg, double* Lc, 
 cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
                           int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
   return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 1, s);
+}
+
+// Forced acceptance (sketchy pivoting's OSID on the sketch): the b_t candidates are
+// taken in the order given, with no pivoting and no truncation; only a candidate
+// that has no residual left (Gram matrix not positive definite) ends the block.
+cudaError_t launch_filter_forced(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
+                                 int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+  return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 2, s);
 }
 
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b, State* st,

@@ -73,6 +73,7 @@ struct Plan {
   long long n, d, k_cap;
   int b, prec, r64, l64, w32, greedy, f32, exact_sampler, downdate;
   int chain64;  // FP64 storage and FP64 products for every step of the per-block chain
+  int forced;   // skeletons taken from a given list (the OSID pass of sketchy pivoting)
   long long ldr, ldl, ldq, ldp, ldpt, ldc, ldg, ldlc, ldw32, ldt;
   int nparts;
   int s_upd1, s_upd2;
@@ -97,7 +98,7 @@ int splits_for(long long M, long long N, long long K, int tile = kGemmTile, long
   return (int)s;
 }
 
-rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
+rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int forced = 0) {
   if (!o || n <= 0 || d <= 0) return RBRP_EINVAL;
   if (o->block < 1 || o->block > kMaxBlock) return RBRP_EINVAL;
   if (o->precision < RBRP_FP64 || o->precision > RBRP_TF32X3) return RBRP_EINVAL;
@@ -123,7 +124,9 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p) {
   p->r64 = (o->precision == RBRP_FP64);
   p->l64 = p->r64;
   p->w32 = (o->w_precision == RBRP_W_FP32);
-  p->chain64 = (o->precision == RBRP_FP64 || o->chain == RBRP_CHAIN_FP64);
+  p->forced = forced;
+  // the forced pass runs the FP64 chain: its filter is the FP64 Cholesky in the given order
+  p->chain64 = (o->precision == RBRP_FP64 || o->chain == RBRP_CHAIN_FP64 || forced);
   p->f32 = (o->precision == RBRP_TF32 && !p->chain64);  // FP32 storage for the per-block chain
   p->greedy = (o->sampler == RBRP_SAMPLER_GREEDY || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
   p->exact_sampler = (o->sampler == RBRP_SAMPLER_RANDOM_EXACT || o->sampler == RBRP_SAMPLER_GREEDY_EXACT);
@@ -250,6 +253,8 @@ struct Bufs {
   void* samp2;
   unsigned* cnt;
   long long* skel;
+  const long long* forced_list;  // forced pass: the skeletons in order
+  const int* forced_count;       // forced pass: their number (device)
 };
 
 Bufs carve(const Plan& p, void* ws) {
@@ -284,6 +289,8 @@ Bufs carve(const Plan& p, void* ws) {
   u.samp2 = b + p.off_samp2;
   u.cnt = (unsigned*)(b + p.off_cnt);
   u.skel = nullptr;
+  u.forced_list = nullptr;
+  u.forced_count = nullptr;
   return u;
 }
 
@@ -401,9 +408,14 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     e = (call);                      \
     if (e != cudaSuccess) return e;  \
   } while (0)
-  // sampling step: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it)
-  if (!p.exact_sampler) LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
-  LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, p.exact_sampler, s));
+  // sampling step: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it),
+  // or, in the forced pass, the next rows of the given skeleton list
+  if (p.forced) {
+    LK(launch_forced_take(u.forced_list, u.forced_count, u.S_t, st, p.b, s));
+  } else {
+    if (!p.exact_sampler) LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
+    LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, p.exact_sampler, s));
+  }
   // projection step: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
   if (p.downdate)  // projection step as printed: V = X(S_t, :), projected below
     LK(launch_gather(const_cast<void*>(u.X), u.x64, u.ldx, u.S_t, u.V, 1, p.ldq, d, p.b, st, s));
@@ -433,7 +445,10 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   } else {
     LK((sgemm<double, double, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0),
                                     p.ldg, dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
-    LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+    if (p.forced)
+      LK(launch_filter_forced(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+    else
+      LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
     // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 chain
     // adds a second CholQR pass (orthogonality to FP64 rounding); with the
     // default chain of the mixed paths one FP64 CholQR already leaves
@@ -573,11 +588,17 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
   return RBRP_OK;
 }
 
+// Forced skeletons for run(): the list (device, in acceptance order) and its length (device).
+struct Forced {
+  const long long* list;
+  const int* count;
+};
+
 rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long long ldx, double tol,
                 const rbrp_opts* o, void* ws, size_t ws_bytes, long long* skel, double* W, long long ldw,
-                rbrp_result* res, cudaStream_t s, const WSink* sink = nullptr) {
+                rbrp_result* res, cudaStream_t s, const WSink* sink = nullptr, const Forced* forced = nullptr) {
   Plan p;
-  rbrp_status rs = make_plan(n, d, o, &p);
+  rbrp_status rs = make_plan(n, d, o, &p, forced ? 1 : 0);
   if (rs != RBRP_OK) return rs;
   if (!X || !skel || !W || !res || !ws) return RBRP_EINVAL;
   if (ldx < d || ldw < p.k_cap) return RBRP_EINVAL;
@@ -586,6 +607,10 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   memset(res, 0, sizeof(*res));
   Bufs u = carve(p, ws);
   u.skel = skel;
+  if (forced) {
+    u.forced_list = forced->list;
+    u.forced_count = forced->count;
+  }
   u.X = X;
   u.x64 = x_is_fp64 ? 1 : 0;
   u.ldx = ldx;
@@ -1170,6 +1195,145 @@ rbrp_status rbrp_id_noalloc(const void* X, int x_is_fp64, int64_t n, int64_t d, 
   CK(noalloc_scratch(&ws));
   return run(X, x_is_fp64, n, d, ldx, tol, o, ws, (size_t)RBRP_NOALLOC_SCRATCH_BYTES, (long long*)skel, W, ldw, res,
              (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- sketchy pivoting + OSID
+}  // extern "C"
+
+namespace {
+
+struct SketchPlan {
+  Plan rp;                 // the forced block loop on Y(:, 0:ocols)
+  long long l, k, ocols;
+  int sk64, sms;
+  size_t off_Y, off_A, off_U, off_lu, off_piv, off_rs, off_mark, total;
+};
+
+rbrp_status sketch_plan(long long n, long long d, long long l, long long k, const rbrp_sketch_opts* so,
+                        rbrp_opts* ro, SketchPlan* sp, bool need_grid) {
+  if (!so || !ro || !sp) return RBRP_EINVAL;
+  if (n < 1 || d < 1 || l < 1 || k < 1 || k > l || k > n || l >= (1LL << 31)) return RBRP_EINVAL;
+  if (so->precision < RBRP_FP64 || so->precision > RBRP_TF32X3) return RBRP_EINVAL;
+  const long long ocols = so->osid_cols == 0 ? l : (long long)so->osid_cols;
+  if (ocols < k || ocols > l) return RBRP_EINVAL;
+  memset(sp, 0, sizeof(*sp));
+  rbrp_default_opts(ro);
+  ro->precision = so->precision;
+  ro->block = so->block;
+  ro->w_precision = so->w_precision;
+  ro->k_max = k;
+  ro->chain = RBRP_CHAIN_FP64;
+  rbrp_status rs = make_plan(n, ocols, ro, &sp->rp, 1);
+  if (rs != RBRP_OK) return rs;
+  if (n > (1LL << 48) / l) return RBRP_EINVAL;
+  sp->l = l;
+  sp->k = k;
+  sp->ocols = ocols;
+  sp->sk64 = (so->precision == RBRP_FP64);
+  sp->sms = 152;
+  if (need_grid) {
+    cudaError_t e = lupp_grid(&sp->sms);
+    if (e != cudaSuccess) {
+      g_last_cuda = (int)e;
+      return RBRP_ECUDA;
+    }
+  }
+  const size_t ts = sp->sk64 ? 8 : 4;
+  size_t off = (size_t)round_up((long long)sp->rp.total, 256);
+  auto take = [&](size_t bytes) {
+    const size_t o2 = off;
+    off = (size_t)round_up((long long)(off + bytes), 256);
+    return o2;
+  };
+  sp->off_Y = take((size_t)n * l * ts);
+  sp->off_A = take((size_t)n * k * ts);
+  sp->off_U = take((size_t)lupp_panel_width() * k * ts);
+  sp->off_lu = take(lupp_scratch_bytes(std::max(sp->sms, 152)));
+  sp->off_piv = take((size_t)k * 8);
+  sp->off_rs = take(8);
+  sp->off_mark = take((size_t)n * 4);
+  sp->total = off;
+  return RBRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rbrp_status rbrp_sketch_workspace_size(int64_t n, int64_t d, int64_t l, int64_t k, const rbrp_sketch_opts* o,
+                                       size_t* bytes) {
+  if (!bytes) return RBRP_EINVAL;
+  rbrp_opts ro;
+  SketchPlan sp;
+  rbrp_status rs = sketch_plan(n, d, l, k, o, &ro, &sp, false);
+  if (rs != RBRP_OK) return rs;
+  *bytes = sp.total;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_sketch_id(const void* X, int x_is_fp64, int64_t n, int64_t d, int64_t ldx, const void* Omega,
+                           int64_t l, int64_t k, const rbrp_sketch_opts* o, void* workspace, size_t ws_bytes,
+                           int64_t* skel, double* W, int64_t ldw, rbrp_result* res, rbrp_stream_t stream) {
+  rbrp_opts ro;
+  SketchPlan sp;
+  rbrp_status rs = sketch_plan(n, d, l, k, o, &ro, &sp, true);
+  if (rs != RBRP_OK) return rs;
+  if (!X || !Omega || !workspace || !skel || !W || !res) return RBRP_EINVAL;
+  if (ldx < d || ldw < k) return RBRP_EINVAL;
+  if (x_is_fp64 && !sp.sk64) return RBRP_EINVAL;  // the FP32 sketch takes FP32 input
+  if (((uintptr_t)workspace & 255) != 0 || ws_bytes < sp.total) return RBRP_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  memset(res, 0, sizeof(*res));
+  char* base = (char*)workspace;
+  void* Y = base + sp.off_Y;
+  void* A = base + sp.off_A;
+  void* U = base + sp.off_U;
+  long long* piv = (long long*)(base + sp.off_piv);
+  int* rstat = (int*)(base + sp.off_rs);
+  int* mark = (int*)(base + sp.off_mark);
+  // sketching step (Sec. 3.2): Y = X Omega, n x l row-major
+  GemmArgs g;
+  g.A = MatRef{const_cast<void*>(X), dim_const(0), ldx, 1};
+  g.B = MatRef{const_cast<void*>(Omega), dim_const(0), l, 1};
+  g.C = MatRef{Y, dim_const(0), l, 1};
+  g.M = dim_const(n);
+  g.N = dim_const(l);
+  g.K = dim_const(d);
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  g.partial = nullptr;
+  g.pm = n;
+  g.pn = l;
+  g.st = nullptr;
+  if (sp.sk64 && x_is_fp64)
+    CK((launch_gemm<double, double, double, double>(g, n, l, 1, kGemmTile, s)));
+  else if (sp.sk64)
+    CK((launch_gemm<float, double, double, double>(g, n, l, 1, kGemmTile, s)));
+  else
+    CK((launch_gemm<float, float, float, float>(g, n, l, 1, kGemmTile, s)));
+  // skeleton selection: LU with partial pivoting of Y(:, 0:k)
+  unsigned mlim = kDefaultSpinMbar, glim = kDefaultSpinGrid;
+  wait_limits(&mlim, &glim);
+  if (sp.sk64)
+    CK(launch_lupp<double>((const double*)Y, l, n, (int)k, (double*)A, (double*)U, mark, piv, rstat,
+                           base + sp.off_lu, sp.sms, glim, s));
+  else
+    CK(launch_lupp<float>((const float*)Y, l, n, (int)k, (float*)A, (float*)U, mark, piv, rstat, base + sp.off_lu,
+                          sp.sms, glim, s));
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, rstat, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h[1] != 0) return RBRP_ETIMEOUT;
+  const long long r = h[0];
+  if (r == 0) return RBRP_OK;  // Y(:, 0:k) is zero: no skeleton
+  // interpolation matrix (Alg. 4): the block loop on Y(:, 0:ocols) with the
+  // pivots as forced skeletons gives W = Y Y_S^+ (W(S,:) = I, W(rest,:) = L2 L1^{-1})
+  ro.k_max = r;
+  Forced f{piv, rstat};
+  rs = run(Y, sp.sk64, n, sp.ocols, l, -1.0, &ro, workspace, sp.rp.total, (long long*)skel, W, ldw, res, s,
+           nullptr, &f);
+  if (rs == RBRP_OK && res->k < r) return RBRP_ENOTCONVERGED;
+  return rs;
 }
 
 void rbrp_profile_begin(void) {

@@ -252,6 +252,23 @@ cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_
                               int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
                         State* st, cudaStream_t s);
+// Forced acceptance: the b_t candidates in the given order, no pivoting, no truncation.
+cudaError_t launch_filter_forced(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
+                                 int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
+
+// Sketchy pivoting (k_lupp.cu): LU with partial pivoting of Y(:, 0:k) (row-major n x
+// ldy) into the column-major scratch A (n x k); pivots to piv, their number to
+// rank_status[0], a timed-out grid barrier to rank_status[1].  U12: 32 x k scratch;
+// mark: n ints; scratch: lupp_scratch_bytes(sms).  sms from lupp_grid.
+template <typename T>
+cudaError_t launch_lupp(const T* Y, long long ldy, long long n, int k, T* A, T* U12, int* mark, long long* piv,
+                        int* rank_status, void* scratch, int sms, unsigned limit, cudaStream_t s);
+size_t lupp_scratch_bytes(int sms);
+cudaError_t lupp_grid(int* sms);
+int lupp_panel_width();
+// Forced sampling step: S_t = list[k .. k + b_t), b_t = min(b, *count - k, k_cap - k).
+cudaError_t launch_forced_take(const long long* list, const int* count, long long* S_t, State* st, int b,
+                               cudaStream_t s);
 cudaError_t launch_trsm_rows(const double* Lc, long long ldl, const int* perm, const double* V,
                              long long ldv, double* Y, DimRef y_off, long long ldy, long long d, int b,
                              const State* st, cudaStream_t s);

@@ -29,7 +29,7 @@ EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_wor
            "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
            "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched", "rbrp_batch_create",
            "rbrp_batch_run", "rbrp_batch_autotune", "rbrp_batch_set_schedule", "rbrp_batch_get_schedule",
-           "rbrp_batch_destroy", "rbrp_set_wait_limits"]
+           "rbrp_batch_destroy", "rbrp_set_wait_limits", "rbrp_sketch_workspace_size", "rbrp_sketch_id"]
 
 
 class Opts(ctypes.Structure):
@@ -37,6 +37,11 @@ class Opts(ctypes.Structure):
                 ("k_max", ctypes.c_int64), ("seed", ctypes.c_uint64), ("problem", ctypes.c_uint64),
                 ("sampler", ctypes.c_int32), ("w_precision", ctypes.c_int32), ("form", ctypes.c_int32),
                 ("chain", ctypes.c_int32)]
+
+
+class SketchOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("block", ctypes.c_int32), ("w_precision", ctypes.c_int32),
+                ("osid_cols", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -113,6 +118,11 @@ def load():
     L.rbrp_batch_get_schedule.restype = ctypes.c_int
     L.rbrp_batch_destroy.argtypes = [vp]
     L.rbrp_batch_destroy.restype = None
+    L.rbrp_sketch_workspace_size.argtypes = [i64, i64, i64, i64, ctypes.POINTER(SketchOpts), ctypes.POINTER(sz)]
+    L.rbrp_sketch_workspace_size.restype = ctypes.c_int
+    L.rbrp_sketch_id.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, i64, i64, ctypes.POINTER(SketchOpts), vp, sz,
+                                 vp, vp, i64, ctypes.POINTER(Result), vp]
+    L.rbrp_sketch_id.restype = ctypes.c_int
     L.rbrp_set_wait_limits.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
     L.rbrp_set_wait_limits.restype = None
     L.rbrp_profile_begin.argtypes = []
@@ -502,3 +512,74 @@ def rbrp_id_batched(Xs, tol, block=16, seed=0, precision="fp32", tau_b=-1.0, k_m
     b.run_once(tol, s)
     s.synchronize()
     return b.results()
+
+
+# ---------------------------------------------------------------- sketchy pivoting + OSID
+def sketch_opts(precision="fp64", block=64, w_precision="fp64", osid_cols=0):
+    o = SketchOpts()
+    o.precision = PRECISIONS[precision]
+    o.block = int(block)
+    o.w_precision = W_PRECISIONS[w_precision]
+    o.osid_cols = int(osid_cols)
+    return o
+
+
+def rbrp_sketch_workspace_size(n, d, l, k, opts):
+    out = ctypes.c_size_t(0)
+    st = load().rbrp_sketch_workspace_size(int(n), int(d), int(l), int(k), ctypes.byref(opts), ctypes.byref(out))
+    if st != 0:
+        raise RBRPError(st, "rbrp_sketch_workspace_size")
+    return out.value
+
+
+class SketchWorkspace:
+    """Device buffers for repeated rbrp_sketch_id calls of one shape (allocated once by PyTorch)."""
+
+    def __init__(self, n, d, l, k, opts, device=None):
+        import torch
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.shape = (int(n), int(d), int(l), int(k))
+        self.ws = torch.empty(rbrp_sketch_workspace_size(n, d, l, k, opts) + 256, dtype=torch.uint8, device=dev)
+        self.skel = torch.empty(int(k), dtype=torch.int64, device=dev)
+        self.W = torch.empty((int(n), int(k)), dtype=torch.float64, device=dev)
+
+    def ptr(self):
+        return (self.ws.data_ptr() + 255) // 256 * 256
+
+    def nbytes(self):
+        return self.ws.numel() - (self.ptr() - self.ws.data_ptr())
+
+
+def rbrp_sketch_id(X, Omega, k, precision="fp64", block=64, w_precision="fp64", osid_cols=0, workspace=None,
+                   stream=None):
+    """SkLUPP skeletons and the OSID interpolation matrix (Sec. 3.2, Alg. 4) of a CUDA tensor X
+    (n x d) with the caller's embedding Omega (CUDA tensor, d x l: FP64 for precision "fp64",
+    else FP32).  Returns dict(S, W (n x |S| FP64), k, blocks, rel_err_sq (sketched), converged)."""
+    import torch
+    _check_x(X, cuda=True)
+    n, d = X.shape
+    if Omega.dim() != 2 or not Omega.is_cuda or Omega.device != X.device or not Omega.is_contiguous():
+        raise ValueError("Omega must be a contiguous 2-D CUDA tensor on X's device")
+    if Omega.shape[0] != d:
+        raise ValueError("Omega must have d = %d rows" % d)
+    want = torch.float64 if precision == "fp64" else torch.float32
+    if Omega.dtype != want:
+        raise ValueError("Omega must be %s for precision %s" % (want, precision))
+    l = Omega.shape[1]
+    opts = sketch_opts(precision, block, w_precision, osid_cols)
+    ws = workspace if workspace is not None else SketchWorkspace(n, d, l, k, opts, X.device)
+    if ws.shape != (n, d, l, int(k)) or ws.ws.device != X.device:
+        raise ValueError("workspace was made for another shape or device")
+    res = Result()
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    st = load().rbrp_sketch_id(ctypes.c_void_p(X.data_ptr()), int(X.dtype == torch.float64), n, d, X.stride(0),
+                               ctypes.c_void_p(Omega.data_ptr()), l, int(k), ctypes.byref(opts),
+                               ctypes.c_void_p(ws.ptr()), ws.nbytes(), ctypes.c_void_p(ws.skel.data_ptr()),
+                               ctypes.c_void_p(ws.W.data_ptr()), int(k), ctypes.byref(res),
+                               ctypes.c_void_p(s.cuda_stream))
+    _check(st, "rbrp_sketch_id")
+    out = _result_dict(res, st)
+    kk = out["k"]
+    out["S"] = ws.skel[:kk]
+    out["W"] = ws.W[:, :kk]
+    return out

@@ -128,3 +128,22 @@ def test_opts_layout_matches_the_header(libpath):
     rbrp.load().rbrp_default_opts(ctypes.byref(o))
     assert (o.precision, o.block, o.tau_b, o.k_max, o.seed, o.problem) == (1, 64, -1.0, 0, 0, 0)
     assert (o.sampler, o.w_precision, o.form, o.chain) == (0, 0, 0, 0)
+
+
+def test_sketch_workspace_validation_on_host(libpath):
+    """Host logic of rbrp_sketch_workspace_size: sizes, limits and options, no GPU needed."""
+    from paper_2309_16002_gb300 import rbrp
+    o = rbrp.sketch_opts(precision="tf32", block=64)
+    a = rbrp.rbrp_sketch_workspace_size(100000, 1000, 300, 100, o)
+    # at least the sketch Y (FP32, n x l) and the LUPP copy of its first k columns
+    assert a >= 100000 * 300 * 4 + 100000 * 100 * 4
+    b = rbrp.rbrp_sketch_workspace_size(100000, 1000, 300, 100, rbrp.sketch_opts(precision="fp64", block=64))
+    assert b > a
+    for bad in [(100, 10, 5, 6), (100, 10, 0, 1), (5, 10, 8, 6), (0, 10, 5, 2)]:  # k > l, l < 1, k > n, n < 1
+        with pytest.raises(rbrp.RBRPError):
+            rbrp.rbrp_sketch_workspace_size(*bad, o)
+    with pytest.raises(rbrp.RBRPError):   # osid_cols outside [k, l]
+        rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(osid_cols=5))
+    with pytest.raises(rbrp.RBRPError):   # the TF32 W pass takes b <= 128
+        rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(precision="tf32", block=256))
+    assert rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(osid_cols=10)) > 0
