@@ -29,12 +29,11 @@ METRIC = "ID time-to-tol (ms) at 1e5×1e3, rel err ≤1e-4; % of HBM/TC roofline
 # DRAM bytes (read + write) per launch of the persistent tensor-core update, per
 # row of R, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # caches left as the preceding kernels leave them) of the 40000 x 1000 zipf_gmm
-# workload at b = 64 (profiles/k_update_tf32p_*.md).  The kernel has changed
-# since (a programmatic-dependent-launch wait at entry; loads and stores are the
-# same), so the figure is reported as the last capture, not as current traffic.
-UPD_TRAFFIC_PER_ROW = (196233472 + 132443136) / 40000
+# workload at b = 64 (profiles/k_update_tf32p_zipf_gmm_40000x1000.md), taken on
+# the kernel as it is now.
+UPD_TRAFFIC_PER_ROW = (194578176 + 132194304) / 40000
 UPD_TRAFFIC_D = 1000
-UPD_TRAFFIC_CURRENT = False
+UPD_TRAFFIC_CURRENT = True
 FALLBACK_HBM = 6800.0
 
 
@@ -393,10 +392,9 @@ def run_ours(a):
                 "peak_kind": peak_kind, "traffic": traffic,
                 "traffic_last_capture": captured,
                 "traffic_note": ("DRAM read+write bytes per launch from one ncu capture of the 40000 x 1000 "
-                                 "workload (L2 as the preceding kernels leave it), scaled by rows"
-                                 + ("" if UPD_TRAFFIC_CURRENT else "; taken before the kernel gained its "
-                                    "programmatic-dependent-launch wait at entry (its loads and stores are "
-                                    "unchanged), so traffic is null until the next capture")
+                                 "workload (L2 as the preceding kernels leave it), scaled by rows to this n"
+                                 + ("" if UPD_TRAFFIC_CURRENT else "; taken on an earlier build of the kernel, "
+                                    "so traffic is null until the next capture")
                                  if captured else None),
                 "bytes_per_launch": upd_bytes / max(1, blocks),
                 "note": "achieved = (2 n d s + 16 n) per block + n k s for Lhat, over CUDA-event time of all "
