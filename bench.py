@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU baseline run (0: all rows)")
     ap.add_argument("--ref-rows", type=int, default=20000, help="row sample per step of the reference arm")
-    ap.add_argument("--workload", default="zipf_gmm", choices=["zipf_gmm", "kernel_blocks", "gmm_fixed_rank"],
+    ap.add_argument("--workload", default="zipf_gmm",
+                    choices=["zipf_gmm", "kernel_blocks", "gmm_fixed_rank", "spectral", "random_features"],
                     help="kernel_blocks: the batched workload (one rbrp_id_batched launch per step); "
                          "gmm_fixed_rank: the adversarial GMM of Sec. 4 at fixed ranks (context for the "
                          "paper's GPU table)")
@@ -73,7 +74,43 @@ def parse():
     return ap.parse_args()
 
 
+# The two large single-ID configurations (their own n, d, b and tol; the split update
+# against the FP64 GPU form), used when the zipf_gmm defaults were left unchanged.
+LARGE = {"spectral": dict(n=200000, d=2000, block=128, tol=1e-4, precision="tf32x3"),
+         "random_features": dict(n=1000000, d=512, block=256, tol=1e-2, precision="tf32x3")}
+
+
+def apply_workload_defaults(a):
+    if a.workload in LARGE:
+        w = LARGE[a.workload]
+        for key, zipf_default in (("n", 100000), ("d", 1000), ("block", 64), ("tol", 1e-4), ("precision", "tf32")):
+            if getattr(a, key) == zipf_default:
+                setattr(a, key, w[key])
+
+
+def make_input(a):
+    """The single-ID workload's X (FP32), drawn by the seeded generators."""
+    import numpy as np
+    from paper_2309_16002_gb300 import workloads as WL
+    if a.workload == "spectral":
+        return WL.spectral(n=a.n, d=a.d, decay="power", rate=1.5, seed=3, dtype=np.float32,
+                           haar_block=4000 if a.n % 4000 == 0 and 4000 >= min(a.n, a.d) else None)[0]
+    if a.workload == "random_features":
+        return WL.random_features(n=a.n, d=a.d, seed=5)
+    return WL.zipf_gmm(n=a.n, d=a.d)
+
+
 def workload_config(a):
+    if a.workload == "spectral":
+        return {"workload": "spectral_decay_power", "n": a.n, "d": a.d, "dtype_in": "fp32", "sigma": "i^-1.5",
+                "U": "Haar, built blockwise (4000-row blocks)", "tol_sq_rel": a.tol, "block": a.block, "seed": 0,
+                "update": a.precision, "chain": chain_label(a), "w_solve": a.w_precision,
+                "l2": "inputs larger than L2 (X is %.1f GB)" % (a.n * a.d * 4 / 1e9)}
+    if a.workload == "random_features":
+        return {"workload": "random_features_relu", "n": a.n, "d": a.d, "dtype_in": "fp32", "latent": 64,
+                "gmm_components": 20, "tol_sq_rel": a.tol, "block": a.block, "seed": 0, "update": a.precision,
+                "chain": chain_label(a), "w_solve": a.w_precision,
+                "l2": "inputs larger than L2 (X is %.1f GB)" % (a.n * a.d * 4 / 1e9)}
     return {"workload": "zipf_gmm_near_duplicates", "n": a.n, "d": a.d, "dtype_in": "fp32", "clusters": 100,
             "zipf_s": 1.5, "within_var": 1e-6, "extra_rows": 0.05, "extra_var": 0.01, "tol_sq_rel": a.tol,
             "block": a.block, "seed": 0, "update": a.precision, "chain": chain_label(a), "form": a.form,
@@ -242,7 +279,7 @@ def run_reference(a):
     if rank != 0:
         return
     from paper_2309_16002_gb300 import workloads as WL
-    X = WL.zipf_gmm(n=a.n, d=a.d)
+    X = make_input(a)
     for _ in range(a.warmup):
         cpu_oracle_leg(a, X, a.ref_rows)
     vals = []
@@ -258,6 +295,19 @@ def run_reference(a):
                              "sample": info["sample"]},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def tensor_roofline(a, k_tot, upd_ms, peaks, peak_kind):
+    """Tensor-pipe view of the update: MMA flops issued (4 n d b' per block, three times that for
+    the 3xTF32 split) over the update's CUDA-event time, against the TF32 rate taken as half the
+    measured dense BF16 rate (the nominal TF32:BF16 ratio)."""
+    if a.precision not in ("tf32", "tf32x3") or upd_ms <= 0:
+        return None
+    flops = (3 if a.precision == "tf32x3" else 1) * 4.0 * a.n * a.d * k_tot
+    tflops = flops / (upd_ms / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))) / 2
+    return {"achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+            "peak_kind": peak_kind + " sustained bf16 x 1/2"}
 
 
 def true_err_sq(Xd, S, W):
@@ -279,8 +329,11 @@ def time_forms(a, G, Xd, stream, pid):
     res = {}
     for prec, chain, wprec in forms:
         kw = dict(block=a.block, seed=0, precision=prec, w_precision=wprec, problem=pid, chain=chain)
-        ws = G.Workspace(a.n, a.d, G.make_opts(a.block, prec, -1.0, 0, 0, pid, "random", wprec, "residual", chain),
-                         Xd.device)
+        try:
+            ws = G.Workspace(a.n, a.d, G.make_opts(a.block, prec, -1.0, 0, 0, pid, "random", wprec, "residual",
+                                                   chain), Xd.device)
+        except G.RBRPError:
+            continue  # the form does not take this block size (the FP32 chain: b <= 128)
         out = G.rbrp_id(Xd, a.tol, workspace=ws, stream=stream, **kw)
         torch.cuda.synchronize()
         G.rbrp_profile_begin()
@@ -325,7 +378,7 @@ def run_ours(a):
     from paper_2309_16002_gb300 import rbrp as G
     from paper_2309_16002_gb300 import workloads as WL
 
-    X = WL.zipf_gmm(n=a.n, d=a.d)
+    X = make_input(a)
     Xd = torch.from_numpy(X).to(dev)
     from paper_2309_16002_gb300 import shard
     pid = shard.replica_problem_id(rank)
@@ -397,6 +450,7 @@ def run_ours(a):
                                     "so traffic is null until the next capture")
                                  if captured else None),
                 "bytes_per_launch": upd_bytes / max(1, blocks),
+                "tensor": tensor_roofline(a, k_tot, upd_ms, peaks, peak_kind),
                 "note": "achieved = (2 n d s + 16 n) per block + n k s for Lhat, over CUDA-event time of all "
                         "update launches in the timed region (including no-op launches queued after the stop)"}
 
@@ -711,6 +765,7 @@ def run_fixed_rank(a):
 
 def main():
     a = parse()
+    apply_workload_defaults(a)
     if a.workload == "kernel_blocks":
         if a.impl == "reference":
             run_reference_batched(a)

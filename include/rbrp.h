@@ -58,13 +58,15 @@ typedef enum {
                    /* accumulate).  Default chain: FP32 throughout -- FP32 copies */
                    /* of the drawn rows and of Q, ONE projection pass against Q   */
                    /* with FP32 products, FP32 Gram matrix and FP32 pivoted       */
-                   /* Cholesky filter, Q' = Lc^{-1} V_perm in FP32.               */
+                   /* Cholesky filter, Q' = Lc^{-1} V_perm in FP32 (b <= 128; the */
+                   /* FP64 chain takes b <= 256, in 128-column chunks of Q').     */
   RBRP_FP32 = 2,   /* R in FP32, update on CUDA cores in FP32.  Default chain:    */
                    /* FP64 storage of V and Q, two projection passes (CGS2) with  */
                    /* FP32 products, FP64 Gram and filter, one FP64 CholQR pass   */
   RBRP_TF32X3 = 3  /* as RBRP_TF32 with every operand split into TF32 hi + lo and */
-                   /* three products per step (~FP32-accurate update); b <= 64;   */
-                   /* default chain as RBRP_FP32                                  */
+                   /* three products per step (~FP32-accurate update); blocks     */
+                   /* wider than 64 run as 64-column chunks of Q' (each chunk one */
+                   /* pass over R); default chain as RBRP_FP32                    */
 } rbrp_precision;
 
 /* Precision of the per-block chain (rbrp_opts.chain). */

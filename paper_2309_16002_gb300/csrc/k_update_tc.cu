@@ -79,10 +79,13 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
                   const __grid_constant__ CUtensorMap tmQlo, const __grid_constant__ CUtensorMap tmQT,
                   const __grid_constant__ CUtensorMap tmQTlo, float* __restrict__ L, long long ldl, long long n,
                   long long d, const int* __restrict__ mark, double* __restrict__ dvec,
-                  double* __restrict__ partials, State* st) {
+                  double* __restrict__ partials, State* st, int c0) {
   using C = Cfg<BMAX, SPLIT>;
   constexpr int S1 = C::S1, S3 = C::S3;
   if (st->done) return;
+  // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block)
+  const int bp = min((int)st->bp - c0, BMAX);
+  if (bp <= 0) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -109,9 +112,8 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long row0 = (long long)blockIdx.x * ROWS;
-  const long long kcol = st->k;
-  const int bp = (int)st->bp;
-  const int N1 = (int)st->bp_pad;
+  const long long kcol = st->k + c0;
+  const int N1 = (bp + 15) / 16 * 16;
   const int tno = (int)(st->t + 1);
   const int nK1 = (int)((d + BK1 - 1) / BK1);
   const int nC = (int)((d + NB2 - 1) / NB2);
@@ -437,10 +439,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
     k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
                    const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
                    long long d, const int* __restrict__ mark, double* __restrict__ dvec,
-                   double* __restrict__ partials, State* st) {
+                   double* __restrict__ partials, State* st, int c0) {
   using C = PCfg<BMAX>;
   pdl_wait();
   if (st->done) return;
+  // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block)
+  const int bp = min((int)st->bp - c0, BMAX);
+  if (bp <= 0) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -462,9 +467,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
 
   __shared__ int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long kcol = st->k;
-  const int bp = (int)st->bp;
-  const int N1 = (int)st->bp_pad;
+  const long long kcol = st->k + c0;
+  const int N1 = (bp + 15) / 16 * 16;
   const int tno = (int)(st->t + 1);
   const int nK1 = (int)((d + BK1 - 1) / BK1);  // 32-column chunks of GEMM 1 (and epilogue pieces)
   const int nJ = (int)((d + PNB - 1) / PNB);   // GEMM-2 chunks
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   // previous block wrote last, which are still in L2 (the residual is larger
   // than L2, so a fixed order would always start on the least recent tiles).
   // Partial sums stay indexed by the tile's position, so their order is fixed.
-  const bool rev = (st->t & 1) != 0;
+  const bool rev = ((st->t + c0 / BMAX) & 1) != 0;  // successive chunks of a block alternate too
   auto ptile = [&](long long tl) { return rev ? ntiles - 1 - tl : tl; };
   // GEMM 2 walks its chunks from the last (the most recently read columns
   // first); a chunk j covers pieces 4j .. min(4j + 4, nK1) - 1.
@@ -725,7 +729,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
       if (lane == 0) partials[4 * ptile(tile) + q] = t;
     }
   } else if (warp == 8) {
-    // ---------------- stores of finished R pieces; a stage is released once its store has read it
+    // ---------------- stores of finished R pieces; one bulk store is kept reading while the
+    // next is issued, and a stage is released once the store after it has been issued
     if (lane == 0) {
       const uint64_t drop = l2_policy_evict_first();
       uint32_t g = 0;
@@ -741,11 +746,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             tma_store_2d_hint(&tmR, sb + C::OFF3 + s * C::R3, (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS), drop);
             tma_commit();
-            tma_wait_read<0>();
-            mbar_arrive(empty3(s));
+            if (g > 0) {
+              tma_wait_read<1>();  // the previous piece's store has read its stage
+              mbar_arrive(empty3((int)((g - 1) % PS3)));
+            }
           }
         }
       }
+      tma_wait_read<0>();
+      if (g > 0) mbar_arrive(empty3((int)((g - 1) % PS3)));
       tma_wait_all0();
     }
   }
@@ -777,9 +786,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
 }
 
 template <int BMAX>
-cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long ldp,
-                        const float* QpT, long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
-                        double* partials, const State* st, cudaStream_t s) {
+cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long qrows,
+                        long long ldp, const float* QpT, long long qtcols, long long ldpt, float* L, long long ldl,
+                        const int* mark, double* dvec, double* partials, const State* st, int c0, cudaStream_t s) {
   using C = PCfg<BMAX>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -792,14 +801,14 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
   }
   CUtensorMap mR, mQ, mQT;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, PROWS)) return cudaErrorInvalidValue;
-  if (!make_map(&mQ, Qp, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
-  if (!make_map(&mQT, QpT, ldpt, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
+  if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+  if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (n + PROWS - 1) / PROWS;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
   return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mQ, mQT, L,
-                            ldl, n, d, mark, dvec, partials, const_cast<State*>(st)));
+                            ldl, n, d, mark, dvec, partials, const_cast<State*>(st), c0));
 }
 
 // ------------------------------------------------------------------ host side
@@ -833,8 +842,9 @@ bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer,
 
 template <int BMAX, bool SPLIT>
 cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
-                       long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L, long long ldl,
-                       const int* mark, double* dvec, double* partials, const State* st, cudaStream_t s) {
+                       long long qrows, long long ldp, const float* QpT, const float* QpT_lo, long long qtcols,
+                       long long ldpt, float* L, long long ldl, const int* mark, double* dvec, double* partials,
+                       const State* st, int c0, cudaStream_t s) {
   using C = Cfg<BMAX, SPLIT>;
   static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   {
@@ -849,18 +859,18 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
   }
   CUtensorMap mR, mQ, mQlo, mQT, mQTlo;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, ROWS)) return cudaErrorInvalidValue;
-  if (!make_map(&mQ, Qp, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
-  if (!make_map(&mQT, QpT, ldpt, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
+  if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+  if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
   if (SPLIT) {
-    if (!make_map(&mQlo, Qp_lo, d, ldpt, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
-    if (!make_map(&mQTlo, QpT_lo, ldpt, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
+    if (!make_map(&mQlo, Qp_lo, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+    if (!make_map(&mQTlo, QpT_lo, qtcols, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
   } else {
     mQlo = mQ;
     mQTlo = mQT;
   }
   const unsigned grid = (unsigned)((n + ROWS - 1) / ROWS);
   k_update_tf32<BMAX, SPLIT><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark, dvec,
-                                                             partials, const_cast<State*>(st));
+                                                             partials, const_cast<State*>(st), c0);
   return counted(cudaGetLastError());
 }
 
@@ -873,22 +883,35 @@ int update_tf32_parts(long long n, int bmax, int split) {
   return 2 * (int)((n + tc::ROWS - 1) / tc::ROWS);
 }
 
-int update_tf32_max_block(int split) { return split ? 64 : 128; }
+int update_tf32_chunk(int ldpt, int split) {
+  if (split) return ldpt < 64 ? ldpt : 64;
+  return ldpt <= 64 ? ldpt : 128;
+}
 
 cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
                                long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L,
                                long long ldl, const int* mark, double* dvec, double* partials, const State* st,
-                               int bmax, int split, cudaStream_t s) {
-#define RBRP_TC_ARGS R, ldr, n, d, Qp, Qp_lo, ldp, QpT, QpT_lo, ldpt, L, ldl, mark, dvec, partials, st, s
+                               int bmax, int split, int c0, cudaStream_t s) {
+  // columns c0 .. of Q': rows c0.. of the Qp copies, columns c0.. of the QpT copies (c0 is a
+  // multiple of 64, so the bases stay 256-byte aligned for the tensor maps)
+  if (c0 < 0 || c0 % 64 != 0 || c0 >= ldpt) return cudaErrorInvalidValue;
+  const float* Qc = Qp + (long long)c0 * ldp;
+  const float* Qlc = Qp_lo ? Qp_lo + (long long)c0 * ldp : nullptr;
+  const float* QTc = QpT + c0;
+  const float* QTlc = QpT_lo ? QpT_lo + c0 : nullptr;
+  const long long qrows = ldpt - c0, qtcols = ldpt - c0;
+#define RBRP_TC_ARGS R, ldr, n, d, Qc, Qlc, qrows, ldp, QTc, QTlc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0, s
   if (split) {
     if (bmax <= 32) return tc::launch_cfg<32, true>(RBRP_TC_ARGS);
     if (bmax <= 64) return tc::launch_cfg<64, true>(RBRP_TC_ARGS);
     return cudaErrorInvalidValue;
   }
   if (bmax <= 32)
-    return tc::launch_pcfg<32>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+    return tc::launch_pcfg<32>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
+                               s);
   if (bmax <= 64)
-    return tc::launch_pcfg<64>(R, ldr, n, d, Qp, ldp, QpT, ldpt, L, ldl, mark, dvec, partials, st, s);
+    return tc::launch_pcfg<64>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
+                               s);
   if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
 #undef RBRP_TC_ARGS
   return cudaErrorInvalidValue;

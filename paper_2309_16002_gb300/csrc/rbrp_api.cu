@@ -110,9 +110,9 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int
   if (o->chain != RBRP_CHAIN_DEFAULT && o->chain != RBRP_CHAIN_FP64) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
   if (n > (1LL << 48) / d) return RBRP_EINVAL;  // n d elements: every byte count below stays far from overflow
-  // the tensor-core update keeps Lhat (128 x b'_pad) in shared memory: b <= 128
-  if (o->precision == RBRP_TF32 && o->block > update_tf32_max_block(0)) return RBRP_EINVAL;
-  if (o->precision == RBRP_TF32X3 && o->block > update_tf32_max_block(1)) return RBRP_EINVAL;
+  // the FP32 filter of the plain TF32 chain takes b <= 128 candidates (the tensor-core
+  // update itself takes any b <= 256, in column chunks of Q')
+  if (o->precision == RBRP_TF32 && o->chain != RBRP_CHAIN_FP64 && !forced && o->block > 128) return RBRP_EINVAL;
   memset(p, 0, sizeof(*p));
   p->n = n;
   p->d = d;
@@ -472,11 +472,17 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     const int split = (p.prec == RBRP_TF32X3);
     if (!(p.f32 && filter_f32_writes_factor((int)p.b)))  // else the Q' substitution wrote them
       LK(launch_qp_lowp(u.Qt, !p.f32, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
+    // blocks wider than one launch (3xTF32 above 64 columns, TF32 above 128) run as
+    // successive column chunks of Q'
+    const int cw = update_tf32_chunk((int)p.ldpt, split);
     LK(timed(g_prof.upd, s, [&] {
-      return launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, (float*)u.L,
-                                p.ldl, u.mark, u.dvec, u.part, st, (int)p.ldpt, split, s);
+      cudaError_t ce = cudaSuccess;
+      for (int c0 = 0; c0 < (int)p.ldpt && ce == cudaSuccess; c0 += cw)
+        ce = launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt,
+                                (float*)u.L, p.ldl, u.mark, u.dvec, u.part, st, cw, split, c0, s);
+      return ce;
     }));
-    LK(launch_finalize_block(u.part, update_tf32_parts(n, (int)p.ldpt, split), st, s));
+    LK(launch_finalize_block(u.part, update_tf32_parts(n, cw, split), st, s));
     return cudaSuccess;
   }
   LK(timed(g_prof.upd, s, [&] { return enqueue_update_simt(p, u, s); }));

@@ -315,13 +315,18 @@ constexpr int kSgemmCounters = 4096;
 // tcgen05 fused residual update (k_update_tc.cu): per 128-row tile,
 // Lhat = R Q'^T (TF32 in, FP32 accumulate in TMEM), R -= Lhat Q', d_i = ||R_i||^2,
 // rows accepted in this block zeroed; Lhat stored to L(:, k : k + b').
-// split = 1: 3xTF32 (Qp_lo / QpT_lo hold the low parts of Q').
+// split = 1: 3xTF32 (Qp_lo / QpT_lo hold the low parts of Q').  One launch applies
+// the columns c0 .. c0 + bmax - 1 of Q' (c0 a multiple of 64): the rows of Q' are
+// orthonormal, so R - (R Q'^T) Q' is the same as applying its column chunks one
+// after the other, and a block wider than one launch takes several (the last
+// launch's norms and partial sums are the block's; launches past b' return at once).
 cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp,
                                const float* Qp_lo, long long ldp, const float* QpT, const float* QpT_lo,
                                long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
-                               double* partials, const State* st, int bmax, int split, cudaStream_t s);
+                               double* partials, const State* st, int bmax, int split, int c0, cudaStream_t s);
 int update_tf32_parts(long long n, int bmax, int split);
-int update_tf32_max_block(int split);
+// Columns of Q' per launch for a block of b'_pad <= ldpt columns.
+int update_tf32_chunk(int ldpt, int split);
 
 // Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k) from
 // L (FP32 or FP64, leading dimension ldl) and L1 = L(S, :) (FP64, k x k, ld1).

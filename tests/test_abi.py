@@ -62,8 +62,11 @@ def test_workspace_size_and_validation_on_host(libpath):
         rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=0))
     with pytest.raises(rbrp.RBRPError):
         rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=300, precision="fp64"))
-    with pytest.raises(rbrp.RBRPError):
+    with pytest.raises(rbrp.RBRPError):   # the FP32 filter of the plain TF32 chain: b <= 128
         rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=256, precision="tf32"))
+    # wider blocks run as column chunks of Q': 3xTF32 and the FP64 chain take b <= 256
+    assert rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=256, precision="tf32x3")) > 0
+    assert rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(block=256, precision="tf32", chain="fp64")) > 0
     # the downdate form: FP64 only, and it keeps no residual copy of X
     with pytest.raises(rbrp.RBRPError):
         rbrp.rbrp_workspace_size(100, 10, rbrp.make_opts(precision="tf32", form="downdate"))
@@ -144,6 +147,6 @@ def test_sketch_workspace_validation_on_host(libpath):
             rbrp.rbrp_sketch_workspace_size(*bad, o)
     with pytest.raises(rbrp.RBRPError):   # osid_cols outside [k, l]
         rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(osid_cols=5))
-    with pytest.raises(rbrp.RBRPError):   # the TF32 W pass takes b <= 128
-        rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(precision="tf32", block=256))
+    with pytest.raises(rbrp.RBRPError):   # b <= 256
+        rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(precision="tf32", block=300))
     assert rbrp.rbrp_sketch_workspace_size(1000, 50, 30, 10, rbrp.sketch_opts(osid_cols=10)) > 0

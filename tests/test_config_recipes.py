@@ -91,12 +91,13 @@ def test_spectral_recipe_fp64_b128(G, spectral_2000):
     _fp64_parity(X, ref, out, 1e-4)
 
 
-@pytest.mark.parametrize("prec,b", [("tf32", 128), ("tf32x3", 64)])
-def test_spectral_recipe_mixed(G, spectral_2000, prec, b):
+@pytest.mark.parametrize("prec,b,chain", [("tf32", 128, "default"), ("tf32x3", 64, "default"),
+                                          ("tf32x3", 128, "default"), ("tf32", 128, "fp64")])
+def test_spectral_recipe_mixed(G, spectral_2000, prec, b, chain):
     X = spectral_2000.astype(np.float64)
     ref = O.rbrp_id(X, tau=1e-4, b=b, seed=0)
-    out = _run(G, spectral_2000, 1e-4, block=b, seed=0, precision=prec)
-    _mixed_bar(X, ref, out, 1e-4, b, "spectral %s b=%d" % (prec, b))
+    out = _run(G, spectral_2000, 1e-4, block=b, seed=0, precision=prec, chain=chain)
+    _mixed_bar(X, ref, out, 1e-4, b, "spectral %s b=%d chain %s" % (prec, b, chain))
 
 
 def test_features_recipe_fp64_b256(G, features_512):
@@ -106,19 +107,40 @@ def test_features_recipe_fp64_b256(G, features_512):
     _fp64_parity(X, ref, out, 1e-2)
 
 
-def test_features_recipe_tf32_b128(G, features_512):
+@pytest.mark.parametrize("prec,b,chain", [("tf32", 128, "default"), ("tf32x3", 256, "default"),
+                                          ("tf32", 256, "fp64")])
+def test_features_recipe_mixed(G, features_512, prec, b, chain):
     X = features_512.astype(np.float64)
-    ref = O.rbrp_id(X, tau=1e-2, b=128, seed=0)
-    out = _run(G, features_512, 1e-2, block=128, seed=0, precision="tf32")
-    _mixed_bar(X, ref, out, 1e-2, 128, "features tf32 b=128")
+    ref = O.rbrp_id(X, tau=1e-2, b=b, seed=0)
+    out = _run(G, features_512, 1e-2, block=b, seed=0, precision=prec, chain=chain)
+    _mixed_bar(X, ref, out, 1e-2, b, "features %s b=%d chain %s" % (prec, b, chain))
 
 
-def _full_size_fp64(G, X32, tol, b):
+@pytest.fixture(scope="module")
+def spectral_full():
+    """200000 x 2000, sigma_i = i^-1.5 (U Haar, built blockwise), FP32, and its oracle run at b = 128."""
+    X32, _ = WL.spectral(n=200000, d=2000, decay="power", rate=1.5, seed=3, dtype=np.float32, haar_block=4000)
+    return X32, O.rbrp_id(X32.astype(np.float64), tau=1e-4, b=128, seed=0), 1e-4, 128
+
+
+@pytest.fixture(scope="module")
+def features_full():
+    """10^6 x 512 random features, FP32, and its oracle run at b = 256."""
+    X32 = WL.random_features(n=1000000, d=512, seed=5)
+    return X32, O.rbrp_id(X32.astype(np.float64), tau=1e-2, b=256, seed=0), 1e-2, 256
+
+
+def _e_dev(Xd, S, W):
+    import torch
+    S_t = torch.as_tensor(S, device="cuda:0")
+    return float(torch.linalg.norm(Xd - torch.as_tensor(W, device="cuda:0") @ Xd[S_t]) / torch.linalg.norm(Xd))
+
+
+def _full_size_fp64(G, cfg):
     """The FP64 path at a configuration's full size against the oracle run on the same input;
     the errors are recomputed in FP64 on the device (the oracle's S and W, then the GPU's)."""
     import torch
-    X = X32.astype(np.float64)
-    ref = O.rbrp_id(X, tau=tol, b=b, seed=0)
+    X32, ref, tol, b = cfg
     out = _run(G, X32, tol, block=b, seed=0, precision="fp64")
     ok, note = P.fp64_skeleton_check(ref, out["S"], tol)
     assert ok, note
@@ -126,26 +148,48 @@ def _full_size_fp64(G, X32, tol, b):
     if note:
         print("near-tie excuse: " + note)
         return
-    Xd = torch.from_numpy(X).to("cuda:0")
-    nx = torch.linalg.norm(Xd)
-
-    def e(S, W):
-        S_t = torch.as_tensor(S, device="cuda:0")
-        return float(torch.linalg.norm(Xd - torch.as_tensor(W, device="cuda:0") @ Xd[S_t]) / nx)
-
-    e_ref, e_gpu = e(ref["S"], ref["W"]), e(out["S"], out["W"])
-    print("full size %s b=%d: k %d, e %.12e (oracle %.12e)" % (X.shape, b, out["k"], e_gpu, e_ref))
+    Xd = torch.from_numpy(X32).to("cuda:0", dtype=torch.float64)
+    e_ref, e_gpu = _e_dev(Xd, ref["S"], ref["W"]), _e_dev(Xd, out["S"], out["W"])
+    print("full size %s b=%d: k %d, e %.12e (oracle %.12e)" % (X32.shape, b, out["k"], e_gpu, e_ref))
     assert abs(e_gpu - e_ref) <= 1e-10
     assert abs(out["rel_err_sq"] - ref["rel_err_sq"]) <= 1e-10 * ref["rel_err_sq"]
 
 
-def test_spectral_full_size_fp64_b128(G):
+def _full_size_mixed(G, cfg, prec, chain="default", w_prec="fp32"):
+    """A mixed form at the configuration's full size and block: the literal bar against the
+    oracle's own error, the tolerance itself (true FP64 error), W(S,:) = I."""
+    import torch
+    X32, ref, tol, b = cfg
+    out = _run(G, X32, tol, block=b, seed=0, precision=prec, chain=chain, w_precision=w_prec)
+    Xd = torch.from_numpy(X32).to("cuda:0", dtype=torch.float64)
+    e_ref, e_gpu = _e_dev(Xd, ref["S"], ref["W"]), _e_dev(Xd, out["S"], out["W"])
+    note = "full size %s b=%d %s chain %s: k %d (oracle %d), e %.6e (oracle %.6e)" % (
+        X32.shape, b, prec, chain, out["k"], len(ref["S"]), e_gpu, e_ref)
+    print(note)
+    assert P.mixed_bar(e_gpu, e_ref), note
+    assert e_gpu ** 2 <= tol, note
+    assert np.array_equal(out["W"][out["S"]], np.eye(out["k"]))
+
+
+def test_spectral_full_size_fp64_b128(G, spectral_full):
     """200000 x 2000, sigma_i = i^-1.5, b = 128, tol 1e-4: the configuration's full size."""
-    X, _ = WL.spectral(n=200000, d=2000, decay="power", rate=1.5, seed=3, dtype=np.float32, haar_block=4000)
-    _full_size_fp64(G, X, 1e-4, 128)
+    _full_size_fp64(G, spectral_full)
 
 
-def test_features_full_size_fp64_b256(G):
+@pytest.mark.parametrize("prec,chain", [("tf32x3", "default"), ("tf32", "fp64")])
+def test_spectral_full_size_mixed_b128(G, spectral_full, prec, chain):
+    """The three-term split update (3xTF32, two 64-column chunks per block) and the TF32 update
+    with the FP64 chain at the configuration's own b = 128."""
+    _full_size_mixed(G, spectral_full, prec, chain)
+
+
+def test_features_full_size_fp64_b256(G, features_full):
     """10^6 x 512 random features, b = 256, tol 1e-2: the configuration's full size."""
-    X = WL.random_features(n=1000000, d=512, seed=5)
-    _full_size_fp64(G, X, 1e-2, 256)
+    _full_size_fp64(G, features_full)
+
+
+@pytest.mark.parametrize("prec,chain", [("tf32x3", "default"), ("tf32", "fp64")])
+def test_features_full_size_mixed_b256(G, features_full, prec, chain):
+    """3xTF32 (four 64-column chunks per block) and TF32 with the FP64 chain (two 128-column
+    chunks) at the configuration's own b = 256."""
+    _full_size_mixed(G, features_full, prec, chain)
