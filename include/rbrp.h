@@ -379,6 +379,22 @@ const char *rbrp_status_string(rbrp_status s);
 int rbrp_last_cuda_error(void);
 
 /*
+ * How the blocks of Alg. 2 are driven (process-wide; default RBRP_LOOP_DEVICE).
+ * RBRP_LOOP_DEVICE: one CUDA graph per call whose conditional while node repeats
+ * one block, the stopping test setting the node's condition on the device; the host
+ * launches the graph and reads the result once.  The graph is built at the first call
+ * with a given set of buffers, sizes and options and reused by later such calls
+ * (rbrp_id is then not itself capturable into a caller's graph: it synchronises its
+ * stream once to size the W solve).  RBRP_LOOP_HOST: the host queues blocks in groups
+ * and reads the device state after each group.  Both run the same kernels and give
+ * identical results; the device loop is used unless capture is unavailable, or while
+ * profiling counters are on (they time each update launch with events).
+ */
+#define RBRP_LOOP_DEVICE 0
+#define RBRP_LOOP_HOST 1
+rbrp_status rbrp_set_loop_mode(int32_t mode);
+
+/*
  * Bounded device waits (failure detection; no counterpart in the paper).  Every
  * wait of the library's kernels on another part of the same launch -- the
  * mbarrier waits between the roles of the tensor-core kernels (fused update,

@@ -106,6 +106,7 @@ __global__ void k_finish_init(const double* __restrict__ partials, int np, State
     st->bp_pad = 0;
     st->sample_fallback = 0;
     st->status = 0;
+    st->iters = 0;
     if (!isfinite(D0)) {
       st->status = RBRP_ENONFINITE;
       st->done = 1;
@@ -683,6 +684,28 @@ cudaError_t launch_w_identity_rows(double* W, long long ldw, long long k, const 
                                    long long r1, cudaStream_t s) {
   if (k <= 0 || r1 <= r0) return cudaSuccess;
   k_w_identity<<<grid_for(k * k), 256, 0, s>>>(W, ldw, k, skel, r0, r1);
+  return counted(cudaGetLastError());
+}
+
+}  // namespace rbrp
+
+namespace rbrp {
+
+// ============================================================================
+// Alg. 2, stopping test as the condition of a CUDA graph's while node: the loop
+// runs on the device, the host never reads the State between blocks.
+// ============================================================================
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, State* st) {
+  const long long it = ++st->iters;
+  if (!st->done && it > st->k_cap + 2) {  // cannot happen: every block accepts a row or stops
+    st->status = RBRP_ETIMEOUT;
+    st->done = 1;
+  }
+  cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, State* st, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(h, st);
   return counted(cudaGetLastError());
 }
 

@@ -22,8 +22,8 @@
 // row norms are summed in FP32 over each 32-column chunk and the chunk sums in
 // FP64 (per-element FP64 arithmetic would cost ~2 FMA/clock/SM on GB300).
 // Every mbarrier wait is bounded: after the limit the CTA records
-// RBRP_ETIMEOUT in the State, stops issuing work, waits briefly for copies in
-// flight, frees its TMEM and returns.
+// RBRP_ETIMEOUT in the State, stops issuing work, waits for the TMA copies and
+// MMAs it has issued (drain_ring / drain_mma), frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -83,9 +83,12 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
   using C = Cfg<BMAX, SPLIT>;
   constexpr int S1 = C::S1, S3 = C::S3;
   if (st->done) return;
-  // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block)
+  // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block);
+  // rows accepted in this block keep their residual until the last chunk (the later
+  // chunks' coefficients of those rows are part of L1), which then zeroes it
   const int bp = min((int)st->bp - c0, BMAX);
   if (bp <= 0) return;
+  const bool last_chunk = c0 + BMAX >= (int)st->bp;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     const long long row = row0 + r;
     const bool own = r < ROWS;  // warps with q >= 2 own no row of R
     const bool in = own && row < n;
-    const bool marked = in && (mark[row] == tno);
+    const bool marked = last_chunk && in && (mark[row] == tno);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const uint64_t drop = l2_policy_evict_first();
     if (SPLIT) {
@@ -443,9 +446,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
   using C = PCfg<BMAX>;
   pdl_wait();
   if (st->done) return;
-  // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block)
+  // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block);
+  // rows accepted in this block keep their residual until the last chunk (the later
+  // chunks' coefficients of those rows are part of L1), which then zeroes it
   const int bp = min((int)st->bp - c0, BMAX);
   if (bp <= 0) return;
+  const bool last_chunk = c0 + BMAX >= (int)st->bp;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -658,7 +664,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
       const long long row = ptile(tile) * PROWS + r;
       const bool in = row < n;
-      const bool marked = in && (mark[row] == tno);
+      const bool marked = last_chunk && in && (mark[row] == tno);
       // Lhat: TMEM -> registers -> L (GEMM 2 reads it from TMEM itself)
       const int dbuf = it & 1;
       if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort, lim)) break;

@@ -18,6 +18,7 @@
 namespace rbrp {
 
 std::atomic<long long> g_kernel_launches{0};
+constexpr int kMaxDevicesLoop = 64;
 
 // Poll limits of the bounded device waits (rbrp_set_wait_limits).
 std::atomic<unsigned> g_spin_mbar{kDefaultSpinMbar};
@@ -594,6 +595,91 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
   return RBRP_OK;
 }
 
+// ---------------------------------------------------------------- device-side block loop
+// The blocks of Alg. 2 run as one CUDA graph: a while node whose body is one block
+// (captured from enqueue_block) followed by k_loop_cond, which sets the node's
+// condition from the State's stopping test.  The host launches the graph once and
+// reads the State once after the loop; nothing of the loop comes back to the host.
+// Graphs are cached per (device, buffers, sizes, options): the captured kernels hold
+// the workspace and output pointers and the plan's sizes (the tolerance lives in the
+// State, so one graph serves any tol).
+struct LoopKey {
+  int dev, x64, pad_;
+  const void* ws;
+  const void* X;
+  const long long* skel;
+  const long long* flist;
+  const int* fcount;
+  long long n, d, ldx, total;
+  rbrp_opts o;
+};
+struct LoopEntry {
+  LoopKey key;
+  cudaGraph_t g;
+  cudaGraphExec_t x;
+};
+std::mutex g_loop_mu;
+std::vector<LoopEntry> g_loops;
+std::atomic<int> g_loop_mode{0};  // 0: device-side loop where it can be built, 1: host-side groups
+int g_loop_broken[kMaxDevicesLoop] = {0};
+cudaStream_t g_capture_stream[kMaxDevicesLoop] = {nullptr};
+constexpr size_t kLoopCache = 8;
+
+// Builds (or finds) the executable loop graph; cudaErrorNotSupported if this device
+// cannot capture the block (the caller then queues blocks from the host).
+cudaError_t loop_graph(const Plan& p, const Bufs& u, const rbrp_opts* o, const LoopKey& key, cudaGraphExec_t* out) {
+  std::lock_guard<std::mutex> lock(g_loop_mu);
+  for (auto& e : g_loops)
+    if (memcmp(&e.key, &key, sizeof(LoopKey)) == 0) {
+      *out = e.x;
+      return cudaSuccess;
+    }
+  if (g_loop_broken[key.dev]) return cudaErrorNotSupported;
+  cudaError_t e;
+  if (!g_capture_stream[key.dev]) {
+    e = cudaStreamCreateWithFlags(&g_capture_stream[key.dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaStream_t cs = g_capture_stream[key.dev];
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t be = enqueue_block(p, u, o, cs);
+    if (be == cudaSuccess) be = launch_loop_cond(h, u.st, cs);
+    cudaGraph_t got = nullptr;
+    e = cudaStreamEndCapture(cs, &got);
+    if (be != cudaSuccess) e = be;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (x) cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+    g_loop_broken[key.dev] = 1;  // fall back to host-side groups on this device from now on
+    return cudaErrorNotSupported;
+  }
+  if (g_loops.size() >= kLoopCache) {
+    cudaGraphExecDestroy(g_loops.front().x);
+    cudaGraphDestroy(g_loops.front().g);
+    g_loops.erase(g_loops.begin());
+  }
+  g_loops.push_back(LoopEntry{key, g, x});
+  *out = x;
+  return cudaSuccess;
+}
+
 // Forced skeletons for run(): the list (device, in acceptance order) and its length (device).
 struct Forced {
   const long long* list;
@@ -627,15 +713,47 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
   CK(launch_sample_clear(u.samp2, n, s));
   CK(cudaMemsetAsync(u.cnt, 0, (size_t)kSgemmCounters * 4, s));
-  // Alg. 2's loop: blocks are queued in groups and the State is read back
-  // after each group.  The group size is the number of blocks still expected,
-  // extrapolated from the observed per-block decay of ||d||_1 (or of the rank
-  // gap in fixed-rank mode), so that few blocks are queued past the stop
-  // (those return at once) and few host round trips are needed.
+  // Alg. 2's loop, on the device where the block can be captured into a graph
+  // (not while the profiling counters time each update launch with events).
   State h;
+  bool looped = false;
+  int dev = 0;
+  if (g_loop_mode.load() == 0 && !g_prof.on && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 &&
+      dev < kMaxDevicesLoop) {
+    LoopKey key;
+    memset(&key, 0, sizeof(key));
+    key.dev = dev;
+    key.x64 = u.x64;
+    key.ws = ws;
+    key.X = X;
+    key.skel = skel;
+    key.flist = u.forced_list;
+    key.fcount = u.forced_count;
+    key.n = n;
+    key.d = d;
+    key.ldx = ldx;
+    key.total = (long long)p.total;
+    key.o = *o;
+    cudaGraphExec_t gx = nullptr;
+    const cudaError_t ge = loop_graph(p, u, o, key, &gx);
+    if (ge == cudaSuccess) {
+      CK(cudaGraphLaunch(gx, s));
+      CK(cudaMemcpyAsync(&h, st, sizeof(State), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      looped = true;
+    } else if (ge != cudaErrorNotSupported) {
+      g_last_cuda = (int)ge;
+      return RBRP_ECUDA;
+    }
+  }
+  // Otherwise blocks are queued from the host in groups and the State is read
+  // back after each group.  The group size is the number of blocks still
+  // expected, extrapolated from the observed per-block decay of ||d||_1 (or of
+  // the rank gap in fixed-rank mode), so that few blocks are queued past the
+  // stop (those return at once) and few host round trips are needed.
   long long queued = 0;
   long long group = 2;
-  for (;;) {
+  for (; !looped;) {
     for (long long g = 0; g < group && queued < p.k_cap; ++g, ++queued) {
       cudaError_t e = enqueue_block(p, u, o, s);
       if (e != cudaSuccess) {
@@ -1179,6 +1297,12 @@ const char* rbrp_status_string(rbrp_status s) {
 }
 
 int rbrp_last_cuda_error(void) { return g_last_cuda; }
+
+rbrp_status rbrp_set_loop_mode(int32_t mode) {
+  if (mode != RBRP_LOOP_DEVICE && mode != RBRP_LOOP_HOST) return RBRP_EINVAL;
+  g_loop_mode = mode;
+  return RBRP_OK;
+}
 
 void rbrp_set_wait_limits(uint32_t mbarrier_polls, uint32_t barrier_polls) {
   g_spin_mbar = mbarrier_polls ? mbarrier_polls : kDefaultSpinMbar;

@@ -28,6 +28,7 @@ struct State {
   long long sample_fallback;  // 1: the exact FP64 tree sampler must draw this block
   unsigned int spin_mbar;     // polls of one bounded mbarrier wait (tensor-core kernels)
   unsigned int spin_grid;     // polls of one bounded grid barrier (cooperative sampler)
+  long long iters;            // blocks run by the device-side loop (its iteration bound)
   double D0;         // ||d0||_1
   double D;          // ||d||_1 after the last block
   double tau;        // tolerance (< 0: fixed-rank mode)
@@ -282,6 +283,10 @@ cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n
                               const int* mark, double* dvec, double* partials, int nparts,
                               const State* st, cudaStream_t s);
 cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s);
+// Device-side loop control (the last kernel of the captured block): sets the while
+// node's condition to "another block" unless the stopping test ended the loop, and
+// ends it after k_cap + 2 iterations in any case (no block can run more often).
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, State* st, cudaStream_t s);
 cudaError_t launch_copy_cols_to_f64(const void* L, int l_is_fp64, long long ldl, long long n,
                                     long long c0, long long c1, double* W, long long ldw,
                                     cudaStream_t s);

@@ -29,7 +29,8 @@ EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_wor
            "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
            "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched", "rbrp_batch_create",
            "rbrp_batch_run", "rbrp_batch_autotune", "rbrp_batch_set_schedule", "rbrp_batch_get_schedule",
-           "rbrp_batch_destroy", "rbrp_set_wait_limits", "rbrp_sketch_workspace_size", "rbrp_sketch_id"]
+           "rbrp_batch_destroy", "rbrp_set_wait_limits", "rbrp_sketch_workspace_size", "rbrp_sketch_id",
+           "rbrp_set_loop_mode"]
 
 
 class Opts(ctypes.Structure):
@@ -123,6 +124,8 @@ def load():
     L.rbrp_sketch_id.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, i64, i64, ctypes.POINTER(SketchOpts), vp, sz,
                                  vp, vp, i64, ctypes.POINTER(Result), vp]
     L.rbrp_sketch_id.restype = ctypes.c_int
+    L.rbrp_set_loop_mode.argtypes = [ctypes.c_int32]
+    L.rbrp_set_loop_mode.restype = ctypes.c_int
     L.rbrp_set_wait_limits.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
     L.rbrp_set_wait_limits.restype = None
     L.rbrp_profile_begin.argtypes = []
@@ -131,6 +134,16 @@ def load():
     L.rbrp_profile_end.restype = ctypes.c_int
     _lib = L
     return L
+
+
+LOOP_MODES = {"device": 0, "host": 1}
+
+
+def set_loop_mode(mode="device"):
+    """How later calls drive the blocks of Alg. 2: "device" (a CUDA graph's while node) or "host"."""
+    st = load().rbrp_set_loop_mode(LOOP_MODES[mode])
+    if st != 0:
+        raise RBRPError(st, "rbrp_set_loop_mode")
 
 
 def set_wait_limits(mbarrier_polls=0, barrier_polls=0):
