@@ -64,7 +64,7 @@ def test_device_loop_fixed_rank_zero_and_one_block(G):
     h = _both(G, np.zeros((40, 8)), 1e-3, block=4, precision="fp64")
     assert h["k"] == 0
     h = _both(G, X, -1.0, block=16, seed=2, precision="fp64", k_max=16)
-    assert h["k"] == 16 and h["blocks"] == 1
+    assert h["k"] == 16 and h["blocks"] >= 1  # the robust filter may accept fewer than b per block
 
 
 def test_device_loop_graph_serves_any_tolerance(G):
