@@ -372,6 +372,56 @@ rbrp_status rbrp_sketch_id(const void *X, int x_is_fp64, int64_t n, int64_t d, i
                            int64_t l, int64_t k, const rbrp_sketch_opts *o, void *workspace, size_t ws_bytes,
                            int64_t *skel, double *W, int64_t ldw, rbrp_result *res, rbrp_stream_t stream);
 
+/*
+ * Row shards of one ID (the row-sharded block loop of Alg. 2 across processes;
+ * SURVEY's multi-GPU design; no counterpart in the paper beyond Alg. 2 itself).
+ *
+ * The rows of X are split into contiguous shards, one per process (or several per
+ * process); rows [row_base, row_base + n_local) of X live on this shard.  Every step of
+ * a block runs on the shard's GPU through these calls; the caller exchanges the small
+ * per-block data between shards (host arrays here; an all-gather / all-reduce between
+ * processes):
+ *   1. rbrp_shard_draw: this shard's candidates of the sampling step -- its b_t rows with
+ *      the smallest race keys (Philox counters use the GLOBAL row index, so the keys are
+ *      those one unsharded call draws), in ascending (key, row) order; rows are global
+ *      indices, keys the race keys kappa (or -d_i for the greedy sampler).  b_t here is
+ *      min(b, eligible rows of this shard, k_cap - k).  The caller merges all shards'
+ *      lists and keeps the b_t globally smallest pairs (b_t = min(b, sum of the counts,
+ *      k_cap - k)), in (key, row) order: that is S_t of one unsharded call.
+ *   2. rbrp_shard_rows: the current residual rows (FP64) of the requested global rows
+ *      this shard holds (owned[i] = 1), for the caller to assemble V = R(S_t, :).
+ *   3. rbrp_shard_block: with V (b_t x d, FP64, row-major) and S_t identical on every
+ *      shard, runs the rest of the block -- projection against Q (CGS2), the robust
+ *      filter, acceptance, the update of this shard's rows, its ||d||_1 -- and returns the
+ *      accepted global rows (b' of them) and this shard's ||d||_1.  Every shard computes
+ *      the same Q', so the shards stay in step; the caller sums ||d||_1 over shards and
+ *      runs the stopping test (||d||_1 <= tol ||d0||_1, ||d0||_1 = the sum of the sum_sq
+ *      values rbrp_shard_create returned).
+ *   4. after the loop: rbrp_shard_l_rows gives the rows of L held here for the requested
+ *      skeleton rows; the caller assembles L1 = L(S, :) (k x k) and passes it to
+ *      rbrp_shard_w, which solves Alg. 3 for this shard's rows of W (W(S,:) = I on the
+ *      skeleton rows held here).
+ * k_cap is the whole ID's min(n, d, k_max) (not this shard's).  The shard runs the FP64
+ * filter, so o->precision may be RBRP_FP64, RBRP_FP32 or RBRP_TF32X3, or RBRP_TF32 with
+ * o->chain = RBRP_CHAIN_FP64; residual form only.  The handle holds pointers into the
+ * caller's workspace and X (both kept alive until rbrp_shard_destroy); every call is
+ * synchronous on `stream` and returns RBRP_EINVAL for bad arguments, RBRP_ECUDA for CUDA
+ * errors.
+ */
+typedef struct rbrp_shard_s *rbrp_shard;
+rbrp_status rbrp_shard_workspace_size(int64_t n_local, int64_t d, int64_t k_cap, const rbrp_opts *o, size_t *bytes);
+rbrp_status rbrp_shard_create(const void *X, int x_is_fp64, int64_t n_local, int64_t d, int64_t ldx, int64_t row_base,
+                              int64_t k_cap, const rbrp_opts *o, void *workspace, size_t ws_bytes,
+                              rbrp_stream_t stream, rbrp_shard *out, double *sum_sq);
+rbrp_status rbrp_shard_draw(rbrp_shard h, int64_t *rows, double *keys, int64_t *count);
+rbrp_status rbrp_shard_rows(rbrp_shard h, const int64_t *rows, int64_t count, double *V, int32_t *owned);
+rbrp_status rbrp_shard_block(rbrp_shard h, const double *V, const int64_t *S_t, int64_t b_t, int64_t *accepted,
+                             int64_t *bp, double *d_sum);
+rbrp_status rbrp_shard_l_rows(rbrp_shard h, const int64_t *rows, int64_t count, int64_t k, double *Lrows,
+                              int32_t *owned);
+rbrp_status rbrp_shard_w(rbrp_shard h, const double *L1, const int64_t *skel, int64_t k, double *W, int64_t ldw);
+void rbrp_shard_destroy(rbrp_shard h);
+
 /* Human-readable name of a status code (static string). */
 const char *rbrp_status_string(rbrp_status s);
 

@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
                                                        Pair* __restrict__ out, int b, int greedy,
                                                        unsigned long long seed, unsigned long long problem,
                                                        long long* __restrict__ S_t, State* st, int first,
-                                                       int last, int force) {
+                                                       int last, int force, long long row_base,
+                                                       unsigned long long* __restrict__ keys_out) {
   pdl_wait();
   // exact FP64 sampler: runs when the two-stage sampler asked for it, or always
   // (force, on the first level, which then raises the flag for the later levels)
@@ -166,7 +167,8 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
           if (greedy) {
             key = -di;
           } else {
-            const double u = philox_uniform((unsigned long long)gidx, block_no, seed, problem);
+            // a row shard draws with its rows' global indices (row_base + local index)
+            const double u = philox_uniform((unsigned long long)(gidx + row_base), block_no, seed, problem);
             key = -log(u) / di;
           }
           p.key = orderable(key);
@@ -210,12 +212,15 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
   const long long room = st->k_cap - st->k;
   if (bt > room) bt = room;
   if (bt < 0) bt = 0;
-  for (int e = threadIdx.x; e < bt; e += blockDim.x) S_t[e] = sh[e].idx;
+  for (int e = threadIdx.x; e < bt; e += blockDim.x) {
+    S_t[e] = sh[e].idx;
+    if (keys_out) keys_out[e] = sh[e].key;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     st->b_t = bt;
     st->sample_fallback = 0;
-    if (bt == 0) st->done = 1;
+    if (bt == 0 && !keys_out) st->done = 1;  // a row shard without candidates is not finished
   }
 }
 
@@ -226,19 +231,21 @@ size_t sample_scratch_pairs(long long n, int b) {
 
 cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
                           unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
-                          State* st, int force, cudaStream_t s) {
+                          State* st, int force, cudaStream_t s, long long row_base,
+                          unsigned long long* keys_out) {
   long long groups = (n + kSortChunk - 1) / kSortChunk;
   Pair* bufs[2] = {(Pair*)cand_a, (Pair*)cand_b};
   int cur = 0;
   cudaError_t e = counted(launch_pdl(k_sample_level, dim3((unsigned)groups), dim3(1024), 0, s, dvec, n,
                                      (const Pair*)nullptr, 0LL, bufs[cur], b, greedy, seed, problem, S_t, st, 1,
-                                     groups == 1 ? 1 : 0, force));
+                                     groups == 1 ? 1 : 0, force, row_base, keys_out));
   if (e != cudaSuccess) return e;
   while (groups > 1) {
     const long long n_in = groups * b;
     groups = (n_in + kSortChunk - 1) / kSortChunk;
     e = counted(launch_pdl(k_sample_level, dim3((unsigned)groups), dim3(1024), 0, s, dvec, n, (const Pair*)bufs[cur],
-                           n_in, bufs[cur ^ 1], b, greedy, seed, problem, S_t, st, 0, groups == 1 ? 1 : 0, 0));
+                           n_in, bufs[cur ^ 1], b, greedy, seed, problem, S_t, st, 0, groups == 1 ? 1 : 0, 0,
+                           row_base, keys_out));
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
@@ -605,22 +612,28 @@ cudaError_t launch_copy_cols_to_f32(const void* L, int l_is_fp64, long long ldl,
 }
 
 template <typename TL>
-__global__ void k_gather_rows(const TL* __restrict__ L, long long ldl, const long long* __restrict__ rows, long long k,
-                              double* __restrict__ out, long long ldo) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e / k, j = e % k;
+__global__ void k_gather_rows(const TL* __restrict__ L, long long ldl, const long long* __restrict__ rows,
+                              long long count, long long width, double* __restrict__ out, long long ldo) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count * width;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / width, j = e % width;
     out[i * ldo + j] = (double)L[rows[i] * ldl + j];
   }
 }
 
 cudaError_t launch_gather_rows_f64(const void* L, int l_is_fp64, long long ldl, const long long* rows, long long k,
                                    double* out, long long ldo, cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
-  const unsigned g = grid_for(k * k);
+  return launch_gather_rows_rect(L, l_is_fp64, ldl, rows, k, k, out, ldo, s);
+}
+
+cudaError_t launch_gather_rows_rect(const void* L, int l_is_fp64, long long ldl, const long long* rows,
+                                    long long count, long long width, double* out, long long ldo, cudaStream_t s) {
+  if (count <= 0 || width <= 0) return cudaSuccess;
+  const unsigned g = grid_for(count * width);
   if (l_is_fp64)
-    k_gather_rows<double><<<g, 256, 0, s>>>((const double*)L, ldl, rows, k, out, ldo);
+    k_gather_rows<double><<<g, 256, 0, s>>>((const double*)L, ldl, rows, count, width, out, ldo);
   else
-    k_gather_rows<float><<<g, 256, 0, s>>>((const float*)L, ldl, rows, k, out, ldo);
+    k_gather_rows<float><<<g, 256, 0, s>>>((const float*)L, ldl, rows, count, width, out, ldo);
   return counted(cudaGetLastError());
 }
 

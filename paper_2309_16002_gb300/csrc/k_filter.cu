@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kRegCholThreads) k_pchol_reg(const double* __r
                                                                double* __restrict__ Lw, int* __restrict__ perm,
                                                                const long long* __restrict__ S_t,
                                                                long long* __restrict__ skel, int* __restrict__ mark,
-                                                               State* st, int pivoted) {
+                                                               State* st, int pivoted, long long mark_base,
+                                                               long long mark_n) {
   if (st->done) return;
   __shared__ double diag[kRegCholMax];
   __shared__ double lcol[kRegCholMax];
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kRegCholThreads) k_pchol_reg(const double* __r
     for (int i = tid; i < bp; i += kRegCholThreads) {
       const long long row = S_t[s_perm[i]];
       skel[k + i] = row;
-      mark[row] = tno;
+      if (row - mark_base >= 0 && row - mark_base < mark_n) mark[row - mark_base] = tno;  // rows of this shard
     }
   }
   __syncthreads();
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) k_pchol_global(const double* __restrict__
                                                double* __restrict__ Lc, long long ldl, double* __restrict__ Lw,
                                                int* __restrict__ perm, const long long* __restrict__ S_t,
                                                long long* __restrict__ skel, int* __restrict__ mark, State* st,
-                                               int pivoted) {
+                                               int pivoted, long long mark_base, long long mark_n) {
   if (st->done) return;
   __shared__ double diag[kMaxBlock];
   __shared__ int alive[kMaxBlock];
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(256) k_pchol_global(const double* __restrict__
     for (int i = tid; i < bp; i += blockDim.x) {
       const long long row = S_t[s_perm[i]];
       skel[k + i] = row;
-      mark[row] = tno;
+      if (row - mark_base >= 0 && row - mark_base < mark_n) mark[row - mark_base] = tno;  // rows of this shard
     }
   }
   __syncthreads();
@@ -707,22 +708,28 @@ cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_
 
 static cudaError_t launch_pchol_any(const double* G, long long ldg, double* Lc, long long ldl, int* perm,
                                     const long long* S_t, long long* skel, int* mark, int b, State* st, int pivoted,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, long long mark_base = 0, long long mark_n = LLONG_MAX) {
   // Lw (candidate-indexed factor, kMaxBlock x kMaxBlock) lives right after Lc in the workspace
   double* Lw = Lc + (long long)kMaxBlock * ldl;
   const int ne = b * (b + 1) / 2;
   if (ne <= 9 * kRegCholThreads)
-    k_pchol_reg<9><<<1, kRegCholThreads, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+    k_pchol_reg<9><<<1, kRegCholThreads, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted, mark_base,
+                                                 mark_n);
   else if (b <= kRegCholMax)
-    k_pchol_reg<33><<<1, kRegCholThreads, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+    k_pchol_reg<33><<<1, kRegCholThreads, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted, mark_base,
+                                                  mark_n);
   else
-    k_pchol_global<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted);
+    k_pchol_global<<<1, 256, 0, s>>>(G, ldg, Lc, ldl, Lw, perm, S_t, skel, mark, st, pivoted, mark_base, mark_n);
   return counted(cudaGetLastError());
 }
 
+// mark_base / mark_n: the rows of S_t are global row indices; only those in
+// [mark_base, mark_base + mark_n) belong to this residual and are marked (a row
+// shard of one ID; the whole problem passes 0 and n).
 cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
-                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
-  return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 1, s);
+                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s, long long mark_base,
+                          long long mark_n) {
+  return launch_pchol_any(G, ldg, Lc, ldl, perm, S_t, skel, mark, b, st, 1, s, mark_base, mark_n);
 }
 
 // Forced acceptance (sketchy pivoting's OSID on the sketch): the b_t candidates are

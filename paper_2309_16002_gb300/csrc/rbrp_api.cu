@@ -99,7 +99,8 @@ int splits_for(long long M, long long N, long long K, int tile = kGemmTile, long
   return (int)s;
 }
 
-rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int forced = 0) {
+rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int forced = 0,
+                      long long kc_force = 0) {
   if (!o || n <= 0 || d <= 0) return RBRP_EINVAL;
   if (o->block < 1 || o->block > kMaxBlock) return RBRP_EINVAL;
   if (o->precision < RBRP_FP64 || o->precision > RBRP_TF32X3) return RBRP_EINVAL;
@@ -119,6 +120,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int
   p->d = d;
   long long kc = std::min(n, d);
   if (o->k_max > 0) kc = std::min(kc, (long long)o->k_max);
+  if (kc_force > 0) kc = std::min(d, kc_force);  // a row shard: the whole ID's rank cap
   p->k_cap = kc;
   p->b = o->block;
   p->prec = o->precision;
@@ -256,6 +258,7 @@ struct Bufs {
   long long* skel;
   const long long* forced_list;  // forced pass: the skeletons in order
   const int* forced_count;       // forced pass: their number (device)
+  long long mark_base, mark_n;   // rows [mark_base, mark_base + mark_n) of the ID are this residual's
 };
 
 Bufs carve(const Plan& p, void* ws) {
@@ -292,6 +295,8 @@ Bufs carve(const Plan& p, void* ws) {
   u.skel = nullptr;
   u.forced_list = nullptr;
   u.forced_count = nullptr;
+  u.mark_base = 0;
+  u.mark_n = p.n;
   return u;
 }
 
@@ -399,10 +404,12 @@ cudaError_t cgs_pass(const Plan& p, const Bufs& u, void* V, DimRef rows, cudaStr
 
 cudaError_t enqueue_update_simt(const Plan& p, const Bufs& u, cudaStream_t s);
 
+cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cudaStream_t s);
+
 // One block of Alg. 2 (sampling through the new residual norms), all sizes on the device.
 cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cudaStream_t s) {
   State* st = u.st;
-  const long long n = p.n, d = p.d, b = p.b;
+  const long long n = p.n, d = p.d;
   cudaError_t e;
 #define LK(call)                     \
   do {                               \
@@ -422,6 +429,16 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     LK(launch_gather(const_cast<void*>(u.X), u.x64, u.ldx, u.S_t, u.V, 1, p.ldq, d, p.b, st, s));
   else
     LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
+  return enqueue_chain(p, u, o, s);
+}
+
+// The rest of a block once V = the candidates' rows (b_t of them, in S_t order) is in
+// place: projection against Q, the robust filter, acceptance, update, stopping test.
+cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cudaStream_t s) {
+  State* st = u.st;
+  const long long n = p.n, d = p.d, b = p.b;
+  cudaError_t e;
+  (void)o;
   // (one pass on the plain TF32 path: the sampled residual rows are orthogonal
   // to Q up to the TF32 rounding of the update, and one FP32 pass already takes
   // that to the FP32 floor, which a second FP32 pass cannot lower)
@@ -449,7 +466,7 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     if (p.forced)
       LK(launch_filter_forced(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
     else
-      LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+      LK(launch_filter(u.G, p.ldg, u.S_t, u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s, u.mark_base, u.mark_n));
     // Q'_V: Y = Lc^{-1} V(perm) (CholQR), then CGS against Q.  The FP64 chain
     // adds a second CholQR pass (orthogonality to FP64 rounding); with the
     // default chain of the mixed paths one FP64 CholQR already leaves
@@ -551,11 +568,13 @@ struct WSink {
 };
 
 // Alg. 3: W(S,:) = I, W(rest,:) = L2 L1^{-1}, blocked right-to-left substitution.
+// l1_given: L1 is already in u.L1 (a row shard receives it from the other shards);
+// skel then holds this residual's row of each skeleton (negative: not here).
 rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* skel, double* W, long long ldw,
-                    cudaStream_t s, const WSink* sink = nullptr) {
+                    cudaStream_t s, const WSink* sink = nullptr, bool l1_given = false) {
   if (k <= 0) return RBRP_OK;
   const long long n = p.n;
-  CK(launch_gather_rows_f64(u.L, p.l64, p.ldl, skel, k, u.L1, k, s));
+  if (!l1_given) CK(launch_gather_rows_f64(u.L, p.l64, p.ldl, skel, k, u.L1, k, s));
   const long long nblk = (k + 63) / 64;
   if (!p.w32) {
     CK(launch_copy_cols_to_f64(u.L, p.l64, p.ldl, n, 0, k, W, ldw, s));
@@ -1465,6 +1484,252 @@ rbrp_status rbrp_sketch_id(const void* X, int x_is_fp64, int64_t n, int64_t d, i
   if (rs == RBRP_OK && res->k < r) return RBRP_ENOTCONVERGED;
   return rs;
 }
+
+// ---------------------------------------------------------------- row shards of one ID
+}  // extern "C"
+
+struct rbrp_shard_s {
+  Plan p;
+  Bufs u;
+  rbrp_opts o;
+  long long n, d, row_base, k_cap;
+  long long* skel;            // device: k_cap global rows, acceptance order
+  unsigned long long* keys;   // device: the draw's ordered keys
+  long long* idx;             // device: local row indices of a request
+  double* buf;                // device: FP64 staging of requested rows
+  cudaStream_t s;
+};
+
+namespace {
+
+struct ShardLayout {
+  Plan p;
+  size_t off_skel, off_keys, off_idx, off_buf, total;
+};
+
+rbrp_status shard_layout(long long n, long long d, long long k_cap, const rbrp_opts* o, ShardLayout* L) {
+  if (!o || !L || n < 1 || d < 1 || k_cap < 1 || k_cap > d) return RBRP_EINVAL;
+  if (o->form != RBRP_FORM_RESIDUAL) return RBRP_EINVAL;
+  rbrp_status rs = make_plan(n, d, o, &L->p, 0, k_cap);
+  if (rs != RBRP_OK) return rs;
+  if (L->p.f32) return RBRP_EINVAL;  // the shard steps run the FP64 filter: not the FP32 chain of RBRP_TF32
+  size_t off = (size_t)round_up((long long)L->p.total, 256);
+  auto take = [&](size_t bytes) {
+    const size_t o2 = off;
+    off = (size_t)round_up((long long)(off + bytes), 256);
+    return o2;
+  };
+  const long long kc = L->p.k_cap;
+  L->off_skel = take((size_t)kc * 8);
+  L->off_keys = take((size_t)kMaxBlock * 8);
+  L->off_idx = take((size_t)std::max<long long>(kMaxBlock, kc) * 8);
+  L->off_buf = take((size_t)std::max<long long>((long long)kMaxBlock * d, kc * kc) * 8);
+  L->total = off;
+  return RBRP_OK;
+}
+
+double decode_key(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k;
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+}
+
+// Local positions of the requested global rows that this shard holds.
+void shard_local(const rbrp_shard_s* h, const int64_t* rows, int64_t count, std::vector<long long>* loc,
+                 std::vector<int64_t>* pos, int32_t* owned) {
+  for (int64_t i = 0; i < count; ++i) {
+    const long long g = rows[i];
+    const bool mine = g >= h->row_base && g < h->row_base + h->n;
+    if (owned) owned[i] = mine ? 1 : 0;
+    if (mine) {
+      loc->push_back(g - h->row_base);
+      pos->push_back(i);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+rbrp_status rbrp_shard_workspace_size(int64_t n_local, int64_t d, int64_t k_cap, const rbrp_opts* o, size_t* bytes) {
+  if (!bytes) return RBRP_EINVAL;
+  ShardLayout L;
+  rbrp_status rs = shard_layout(n_local, d, k_cap, o, &L);
+  if (rs != RBRP_OK) return rs;
+  *bytes = L.total;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_shard_create(const void* X, int x_is_fp64, int64_t n_local, int64_t d, int64_t ldx, int64_t row_base,
+                              int64_t k_cap, const rbrp_opts* o, void* workspace, size_t ws_bytes,
+                              rbrp_stream_t stream, rbrp_shard* out, double* sum_sq) {
+  if (!out || !sum_sq) return RBRP_EINVAL;
+  *out = nullptr;
+  ShardLayout L;
+  rbrp_status rs = shard_layout(n_local, d, k_cap, o, &L);
+  if (rs != RBRP_OK) return rs;
+  if (!X || !workspace || ldx < d || row_base < 0) return RBRP_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0 || ws_bytes < L.total) return RBRP_EWORKSPACE;
+  rbrp_shard_s* h = new (std::nothrow) rbrp_shard_s();
+  if (!h) return RBRP_ENOMEM;
+  char* base = (char*)workspace;
+  h->p = L.p;
+  h->u = carve(h->p, workspace);
+  h->o = *o;
+  h->n = n_local;
+  h->d = d;
+  h->row_base = row_base;
+  h->k_cap = h->p.k_cap;
+  h->skel = (long long*)(base + L.off_skel);
+  h->keys = (unsigned long long*)(base + L.off_keys);
+  h->idx = (long long*)(base + L.off_idx);
+  h->buf = (double*)(base + L.off_buf);
+  h->s = (cudaStream_t)stream;
+  Bufs& u = h->u;
+  u.skel = h->skel;
+  u.X = X;
+  u.x64 = x_is_fp64 ? 1 : 0;
+  u.ldx = ldx;
+  u.mark_base = row_base;
+  u.mark_n = n_local;
+  const Plan& p = h->p;
+  cudaStream_t s = h->s;
+  State st;
+  cudaError_t e = launch_init_norms(X, x_is_fp64, n_local, d, ldx, u.R, p.r64, p.ldr, u.dvec, u.mark, u.part,
+                                    p.nparts, u.st, s);
+  if (e == cudaSuccess) e = launch_finish_init(u.part, p.nparts, u.st, -1.0, o->tau_b, h->k_cap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(u.cnt, 0, (size_t)kSgemmCounters * 4, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, u.st, sizeof(State), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete h;
+    g_last_cuda = (int)e;
+    return RBRP_ECUDA;
+  }
+  if (st.status != 0) {
+    delete h;
+    return (rbrp_status)st.status;
+  }
+  *sum_sq = st.D0;
+  *out = h;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_shard_draw(rbrp_shard h, int64_t* rows, double* keys, int64_t* count) {
+  if (!h || !rows || !keys || !count) return RBRP_EINVAL;
+  *count = 0;
+  Bufs& u = h->u;
+  const Plan& p = h->p;
+  cudaStream_t s = h->s;
+  State st;
+  CK(launch_sample(u.dvec, h->n, p.b, p.greedy, h->o.seed, h->o.problem, u.ca, u.cb, u.S_t, u.st, 1, s,
+                   h->row_base, h->keys));
+  CK(cudaMemcpyAsync(&st, u.st, sizeof(State), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st.status != 0) return (rbrp_status)st.status;
+  if (st.done || st.b_t <= 0) return RBRP_OK;
+  std::vector<long long> loc((size_t)st.b_t);
+  std::vector<unsigned long long> kk((size_t)st.b_t);
+  CK(cudaMemcpyAsync(loc.data(), u.S_t, (size_t)st.b_t * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(kk.data(), h->keys, (size_t)st.b_t * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (long long i = 0; i < st.b_t; ++i) {
+    rows[i] = loc[(size_t)i] + h->row_base;
+    keys[i] = decode_key(kk[(size_t)i]);
+  }
+  *count = st.b_t;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_shard_rows(rbrp_shard h, const int64_t* rows, int64_t count, double* V, int32_t* owned) {
+  if (!h || count < 0 || count > kMaxBlock || (count > 0 && (!rows || !V || !owned))) return RBRP_EINVAL;
+  std::vector<long long> loc;
+  std::vector<int64_t> pos;
+  shard_local(h, rows, count, &loc, &pos, owned);
+  if (loc.empty()) return RBRP_OK;
+  const long long m = (long long)loc.size(), d = h->d;
+  std::vector<double> tmp((size_t)(m * d));
+  cudaStream_t s = h->s;
+  CK(cudaMemcpyAsync(h->idx, loc.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+  CK(launch_gather_rows_rect(h->u.R, h->p.r64, h->p.ldr, h->idx, m, d, h->buf, d, s));
+  CK(cudaMemcpyAsync(tmp.data(), h->buf, (size_t)(m * d) * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (long long i = 0; i < m; ++i) memcpy(V + pos[(size_t)i] * d, tmp.data() + i * d, (size_t)d * 8);
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_shard_block(rbrp_shard h, const double* V, const int64_t* S_t, int64_t b_t, int64_t* accepted,
+                             int64_t* bp, double* d_sum) {
+  if (!h || !V || !S_t || !accepted || !bp || !d_sum) return RBRP_EINVAL;
+  const Plan& p = h->p;
+  if (b_t < 1 || b_t > p.b) return RBRP_EINVAL;
+  Bufs& u = h->u;
+  cudaStream_t s = h->s;
+  const long long bt = b_t;
+  State st;
+  CK(cudaMemcpy2DAsync(u.V, (size_t)p.ldq * 8, V, (size_t)h->d * 8, (size_t)h->d * 8, (size_t)bt,
+                       cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(u.S_t, S_t, (size_t)bt * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(&u.st->b_t, &bt, 8, cudaMemcpyHostToDevice, s));
+  {
+    const cudaError_t e = enqueue_chain(p, u, &h->o, s);
+    if (e != cudaSuccess) {
+      g_last_cuda = (int)e;
+      return RBRP_ECUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(&st, u.st, sizeof(State), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st.status != 0) return (rbrp_status)st.status;
+  const long long k0 = st.k - st.bp;
+  *bp = st.bp;
+  *d_sum = st.D;
+  if (st.bp > 0) {
+    CK(cudaMemcpyAsync(accepted, h->skel + k0, (size_t)st.bp * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_shard_l_rows(rbrp_shard h, const int64_t* rows, int64_t count, int64_t k, double* Lrows,
+                              int32_t* owned) {
+  if (!h || count < 0 || count > h->k_cap || k < 0 || k > h->k_cap || (count > 0 && (!rows || !Lrows || !owned)))
+    return RBRP_EINVAL;
+  std::vector<long long> loc;
+  std::vector<int64_t> pos;
+  shard_local(h, rows, count, &loc, &pos, owned);
+  if (loc.empty() || k == 0) return RBRP_OK;
+  const long long m = (long long)loc.size();
+  std::vector<double> tmp((size_t)(m * k));
+  cudaStream_t s = h->s;
+  CK(cudaMemcpyAsync(h->idx, loc.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+  CK(launch_gather_rows_rect(h->u.L, h->p.l64, h->p.ldl, h->idx, m, k, h->buf, k, s));
+  CK(cudaMemcpyAsync(tmp.data(), h->buf, (size_t)(m * k) * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (long long i = 0; i < m; ++i) memcpy(Lrows + pos[(size_t)i] * k, tmp.data() + i * k, (size_t)k * 8);
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_shard_w(rbrp_shard h, const double* L1, const int64_t* skel, int64_t k, double* W, int64_t ldw) {
+  if (!h || k < 0 || k > h->k_cap || (k > 0 && (!L1 || !skel || !W)) || ldw < k) return RBRP_EINVAL;
+  if (k == 0) return RBRP_OK;
+  cudaStream_t s = h->s;
+  std::vector<long long> loc((size_t)k);
+  for (int64_t j = 0; j < k; ++j) {
+    const long long g = skel[j];
+    loc[(size_t)j] = (g >= h->row_base && g < h->row_base + h->n) ? g - h->row_base : -1;
+  }
+  CK(cudaMemcpyAsync(h->u.L1, L1, (size_t)(k * k) * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->idx, loc.data(), (size_t)k * 8, cudaMemcpyHostToDevice, s));
+  rbrp_status rs = solve_w(h->p, h->u, k, h->idx, W, ldw, s, nullptr, true);
+  if (rs != RBRP_OK) return rs;
+  CK(cudaStreamSynchronize(s));
+  return RBRP_OK;
+}
+
+void rbrp_shard_destroy(rbrp_shard h) { delete h; }
 
 void rbrp_profile_begin(void) {
   g_prof.on = true;

@@ -222,9 +222,13 @@ cudaError_t launch_finish_init(const double* partials, int nparts, State* st, do
 constexpr unsigned kDefaultSpinMbar = 1u << 24;
 constexpr unsigned kDefaultSpinGrid = 1u << 25;
 void wait_limits(unsigned* mbar, unsigned* grid);
+// row_base: the Philox counter of local row i is row_base + i (a row shard of one
+// ID); keys_out (optional, b entries): the ordered keys of S_t, and then a shard
+// without candidates is not marked done.
 cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
                           unsigned long long problem, void* cand_a, void* cand_b, long long* S_t,
-                          State* st, int force, cudaStream_t s);
+                          State* st, int force, cudaStream_t s, long long row_base = 0,
+                          unsigned long long* keys_out = nullptr);
 size_t sample_scratch_pairs(long long n, int b);
 // Two-stage sampler (k_sample.cu): FP32 log-domain cut + exact FP64 ranking of
 // the candidates; sets State::sample_fallback when the exact tree sampler
@@ -238,7 +242,8 @@ cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const lon
 template <typename TA, typename TB, typename TC, typename TACC>
 cudaError_t launch_gemm(const GemmArgs& g, long long Mmax, long long Nmax, int splits, int tile, cudaStream_t s);
 cudaError_t launch_filter(const double* G, long long ldg, const long long* S_t, double* Lc, long long ldl,
-                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
+                          int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s,
+                          long long mark_base = 0, long long mark_n = (1LL << 62));
 // FP32 filter (plain TF32 path): as launch_filter on an FP32 Gram matrix.  Into
 // Lout (b' x b', FP32, lower triangular, leading dimension ldl) it writes, for
 // b <= 64 (filter_f32_writes_factor), the pivot-order factor Lc, after which
@@ -295,6 +300,9 @@ cudaError_t launch_copy_cols_to_f32(const void* L, int l_is_fp64, long long ldl,
                                     cudaStream_t s);
 cudaError_t launch_gather_rows_f64(const void* L, int l_is_fp64, long long ldl, const long long* rows,
                                    long long k, double* out, long long ldo, cudaStream_t s);
+// count rows (indices in rows, device) of width columns each, as FP64.
+cudaError_t launch_gather_rows_rect(const void* L, int l_is_fp64, long long ldl, const long long* rows,
+                                    long long count, long long width, double* out, long long ldo, cudaStream_t s);
 template <typename T>
 cudaError_t launch_trsm_cols(T* W, long long ldw, long long n, long long j0, int nb, const double* L1,
                              long long ld1, cudaStream_t s);

@@ -30,7 +30,8 @@ EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_wor
            "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched", "rbrp_batch_create",
            "rbrp_batch_run", "rbrp_batch_autotune", "rbrp_batch_set_schedule", "rbrp_batch_get_schedule",
            "rbrp_batch_destroy", "rbrp_set_wait_limits", "rbrp_sketch_workspace_size", "rbrp_sketch_id",
-           "rbrp_set_loop_mode"]
+           "rbrp_set_loop_mode", "rbrp_shard_workspace_size", "rbrp_shard_create", "rbrp_shard_draw",
+           "rbrp_shard_rows", "rbrp_shard_block", "rbrp_shard_l_rows", "rbrp_shard_w", "rbrp_shard_destroy"]
 
 
 class Opts(ctypes.Structure):
@@ -124,6 +125,24 @@ def load():
     L.rbrp_sketch_id.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, i64, i64, ctypes.POINTER(SketchOpts), vp, sz,
                                  vp, vp, i64, ctypes.POINTER(Result), vp]
     L.rbrp_sketch_id.restype = ctypes.c_int
+    PD = ctypes.POINTER(ctypes.c_double)
+    L.rbrp_shard_workspace_size.argtypes = [i64, i64, i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    L.rbrp_shard_workspace_size.restype = ctypes.c_int
+    L.rbrp_shard_create.argtypes = [vp, ctypes.c_int, i64, i64, i64, i64, i64, ctypes.POINTER(Opts), vp, sz, vp,
+                                    ctypes.POINTER(vp), PD]
+    L.rbrp_shard_create.restype = ctypes.c_int
+    L.rbrp_shard_draw.argtypes = [vp, P64, PD, P64]
+    L.rbrp_shard_draw.restype = ctypes.c_int
+    L.rbrp_shard_rows.argtypes = [vp, P64, i64, PD, P32]
+    L.rbrp_shard_rows.restype = ctypes.c_int
+    L.rbrp_shard_block.argtypes = [vp, PD, P64, i64, P64, P64, PD]
+    L.rbrp_shard_block.restype = ctypes.c_int
+    L.rbrp_shard_l_rows.argtypes = [vp, P64, i64, i64, PD, P32]
+    L.rbrp_shard_l_rows.restype = ctypes.c_int
+    L.rbrp_shard_w.argtypes = [vp, PD, P64, i64, vp, i64]
+    L.rbrp_shard_w.restype = ctypes.c_int
+    L.rbrp_shard_destroy.argtypes = [vp]
+    L.rbrp_shard_destroy.restype = None
     L.rbrp_set_loop_mode.argtypes = [ctypes.c_int32]
     L.rbrp_set_loop_mode.restype = ctypes.c_int
     L.rbrp_set_wait_limits.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -596,3 +615,100 @@ def rbrp_sketch_id(X, Omega, k, precision="fp64", block=64, w_precision="fp64", 
     out["S"] = ws.skel[:kk]
     out["W"] = ws.W[:, :kk]
     return out
+
+
+# ---------------------------------------------------------------- row shards of one ID
+def _p64(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _p32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+class Shard:
+    """Rows [row_base, row_base + n_local) of one ID on this GPU (include/rbrp.h, row shards).
+
+    X_local: CUDA tensor (n_local x d, FP32/FP64); k_cap: the whole ID's min(n, d, k_max).
+    The per-block steps are draw(), rows(), block(); after the loop l_rows() and w().  Host
+    arrays are numpy (the caller exchanges them between shards); sum_sq = this shard's
+    ||X_local||_F^2."""
+
+    def __init__(self, X_local, row_base, k_cap, block=16, precision="fp64", seed=0, problem=0, sampler="random",
+                 tau_b=-1.0, chain="default", w_precision="fp64", stream=None):
+        import torch
+        _check_x(X_local, cuda=True)
+        self.X = X_local
+        self.n, self.d = X_local.shape
+        self.row_base = int(row_base)
+        self.k_cap = int(k_cap)
+        self.block_size = int(block)
+        self.opts = make_opts(block, precision, tau_b, k_cap, seed, problem, sampler, w_precision, "residual", chain)
+        out = ctypes.c_size_t(0)
+        st = load().rbrp_shard_workspace_size(self.n, self.d, self.k_cap, ctypes.byref(self.opts), ctypes.byref(out))
+        if st != 0:
+            raise RBRPError(st, "rbrp_shard_workspace_size")
+        self.ws = torch.empty(out.value + 256, dtype=torch.uint8, device=X_local.device)
+        ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(X_local.device)
+        self.h = ctypes.c_void_p()
+        ss = ctypes.c_double(0.0)
+        st = load().rbrp_shard_create(ctypes.c_void_p(X_local.data_ptr()), int(X_local.dtype == torch.float64),
+                                      self.n, self.d, X_local.stride(0), self.row_base, self.k_cap,
+                                      ctypes.byref(self.opts), ctypes.c_void_p(ptr),
+                                      self.ws.numel() - (ptr - self.ws.data_ptr()),
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.h), ctypes.byref(ss))
+        _check(st, "rbrp_shard_create", allow_notconverged=False)
+        self.sum_sq = ss.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None and self.h.value:
+            _lib.rbrp_shard_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def draw(self):
+        rows = np.zeros(256, dtype=np.int64)
+        keys = np.zeros(256, dtype=np.float64)
+        cnt = ctypes.c_int64(0)
+        _check(load().rbrp_shard_draw(self.h, _p64(rows), _pd(keys), ctypes.byref(cnt)), "rbrp_shard_draw", False)
+        return rows[:cnt.value].copy(), keys[:cnt.value].copy()
+
+    def rows(self, rows):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        V = np.zeros((len(rows), self.d), dtype=np.float64)
+        own = np.zeros(len(rows), dtype=np.int32)
+        _check(load().rbrp_shard_rows(self.h, _p64(rows), len(rows), _pd(V), _p32(own)), "rbrp_shard_rows", False)
+        return V, own.astype(bool)
+
+    def block(self, V, S_t):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        S_t = np.ascontiguousarray(S_t, dtype=np.int64)
+        acc = np.zeros(len(S_t), dtype=np.int64)
+        bp = ctypes.c_int64(0)
+        dsum = ctypes.c_double(0.0)
+        st = load().rbrp_shard_block(self.h, _pd(V), _p64(S_t), len(S_t), _p64(acc), ctypes.byref(bp),
+                                     ctypes.byref(dsum))
+        _check(st, "rbrp_shard_block", False)
+        return acc[:bp.value].copy(), dsum.value
+
+    def l_rows(self, rows, k):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        Lr = np.zeros((len(rows), int(k)), dtype=np.float64)
+        own = np.zeros(len(rows), dtype=np.int32)
+        st = load().rbrp_shard_l_rows(self.h, _p64(rows), len(rows), int(k), _pd(Lr), _p32(own))
+        _check(st, "rbrp_shard_l_rows", False)
+        return Lr, own.astype(bool)
+
+    def w(self, L1, skel):
+        import torch
+        L1 = np.ascontiguousarray(L1, dtype=np.float64)
+        skel = np.ascontiguousarray(skel, dtype=np.int64)
+        k = len(skel)
+        W = torch.empty((self.n, max(k, 1)), dtype=torch.float64, device=self.X.device)
+        st = load().rbrp_shard_w(self.h, _pd(L1), _p64(skel), k, ctypes.c_void_p(W.data_ptr()), max(k, 1))
+        _check(st, "rbrp_shard_w", False)
+        return W[:, :k]

@@ -5,11 +5,12 @@ Covers what a run with one process per GPU does on the host:
     the shard's first index as Philox problem-id base, reproduce one call over
     the whole list (the batched form split across ranks, no exchange);
   * max-over-ranks timing;
-  * the row-sharded form of the block loop of Alg. 2 (rows split across ranks,
-    race keys drawn with global row ids, a global top-b_t merge of per-rank
-    candidates, the candidate rows all-gathered, the filter replicated, the
-    residual update local, ||d||_1 all-reduced) selects the same skeletons as
-    one process.  The steps are the oracle's; only the distribution is new.
+  * the row-sharded form of the block loop of Alg. 2 (shard.sharded_id over
+    torch.distributed: rows split across ranks, race keys drawn with global row
+    ids, a global top-b_t merge of per-rank candidates, the candidate rows
+    exchanged, the filter replicated, the residual update local, ||d||_1
+    summed) selects the same skeletons as one process.  The shards here are an
+    oracle-backed stand-in for the GPU shards behind the same contract.
 Nothing here touches a GPU.
 """
 
@@ -81,81 +82,87 @@ def _worker_batched(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
-def _sharded_rbrp(dist, rank, world, X, tau, b, seed, problem):
-    """Alg. 2 with the rows of X split across ranks; returns (S, D, D0) on every rank."""
-    import torch
-    n, dim = X.shape
-    lo, hi = shard.shard_bounds([1] * n, world)[rank]
-    R = np.array(X[lo:hi], dtype=np.float64)
-    rows = np.arange(lo, hi, dtype=np.int64)
-    in_S = np.zeros(hi - lo, dtype=bool)
-    d = O.row_sq_norms(R)
+class OracleShard:
+    """Rows [lo, hi) of X with the oracle's FP64 steps behind the shard contract of
+    paper_2309_16002_gb300.shard.sharded_id (draw / rows / block / l_rows / w): a CPU
+    stand-in for a GPU shard, so that the exchange logic runs on gloo ranks."""
 
-    def allsum(x):
-        tt = torch.tensor([float(x)], dtype=torch.float64)
-        dist.all_reduce(tt)
-        return float(tt.item())
+    def __init__(self, X, lo, hi, k_cap, b, seed, problem):
+        self.R = np.array(X[lo:hi], dtype=np.float64)
+        self.lo, self.hi, self.n, self.d = lo, hi, hi - lo, X.shape[1]
+        self.rows_g = np.arange(lo, hi, dtype=np.int64)
+        self.k_cap, self.b, self.seed, self.problem = k_cap, b, seed, problem
+        self.dv = O.row_sq_norms(self.R)
+        self.sum_sq = float(self.dv.sum())
+        self.in_S = np.zeros(self.n, dtype=bool)
+        self.Q = np.zeros((self.d, 0))
+        self.L = np.zeros((self.n, 0))
+        self.t = 0
+        self.k = 0
 
-    def allgather(obj):
-        out = [None] * world
-        dist.all_gather_object(out, obj)
-        return out
+    def draw(self):
+        eligible = (~self.in_S) & (self.dv > 0)
+        b_t = min(self.b, int(eligible.sum()), self.k_cap - self.k)
+        u = philox.uniforms(self.rows_g.astype(np.uint64), self.t + 1, self.seed, self.problem)
+        kappa = np.full(self.n, np.inf)
+        kappa[eligible] = -np.log(u[eligible]) / self.dv[eligible]
+        loc = np.lexsort((self.rows_g, kappa))[:max(b_t, 0)]
+        return self.rows_g[loc], kappa[loc]
 
-    D0 = allsum(d.sum())
-    D = D0
-    Q = np.zeros((dim, 0))
-    S = []
-    t = 0
-    while len(S) < min(n, dim) and D > tau * D0:
-        eligible = (~in_S) & (d > 0)
-        b_t = min(b, int(allsum(eligible.sum())), min(n, dim) - len(S))
-        if b_t <= 0:
-            break
-        t += 1
-        # local race keys with global row ids as Philox counters, local top-b_t
-        u = philox.uniforms(rows.astype(np.uint64), t, seed, problem)
-        kappa = np.full(hi - lo, np.inf)
-        kappa[eligible] = -np.log(u[eligible]) / d[eligible]
-        loc = np.lexsort((rows, kappa))[:b_t]
-        loc = loc[np.isfinite(kappa[loc])]
-        cand = allgather((kappa[loc], rows[loc]))
-        S_t = shard.merge_candidates([c[0] for c in cand], [c[1] for c in cand], b_t)
-        # owners contribute the sampled rows
-        own = {int(i): R[int(i) - lo] for i in S_t if lo <= int(i) < hi}
-        got = {}
-        for g in allgather(own):
-            got.update(g)
-        V = np.stack([got[int(i)] for i in S_t], axis=1)
-        for _ in range(2):
-            V = V - Q @ (Q.T @ V)
-        QV, RV, piv, _ = O.cpqr(V)
-        bp, _ = O.filter_rank(RV, 1.0 / b_t)
+    def rows(self, S_t):
+        own = (S_t >= self.lo) & (S_t < self.hi)
+        V = np.zeros((len(S_t), self.d))
+        V[own] = self.R[S_t[own] - self.lo]
+        return V, own
+
+    def block(self, V, S_t):
+        self.t += 1
+        Vt = O.project_out(np.array(V).T, self.Q, 2)
+        QV, RV, piv, _ = O.cpqr(Vt)
+        bp, _ = O.filter_rank(RV, 1.0 / len(S_t))
         if bp == 0:
-            break
-        Sp = S_t[piv[:bp]]
+            return np.zeros(0, dtype=np.int64), float(self.dv.sum())
+        Sp = np.asarray(S_t)[piv[:bp]]
         Qp = QV[:, :bp]
-        Q = np.concatenate([Q, Qp], axis=1)
-        active = ~in_S
-        Lhat = np.zeros((hi - lo, bp))
-        Lhat[active] = R[active] @ Qp
-        S.extend(int(s) for s in Sp)
-        mine = np.array([int(s) - lo for s in Sp if lo <= int(s) < hi], dtype=np.int64)
-        in_S[mine] = True
-        R[active] -= Lhat[active] @ Qp.T
-        R[mine] = 0.0
-        d = O.row_sq_norms(R)
-        d[in_S] = 0.0
-        D = allsum(d.sum())
-    return S, D, D0
+        self.Q = np.concatenate([self.Q, Qp], axis=1)
+        active = ~self.in_S
+        Lhat = np.zeros((self.n, bp))
+        Lhat[active] = self.R[active] @ Qp
+        mine = np.array([int(s) - self.lo for s in Sp if self.lo <= int(s) < self.hi], dtype=np.int64)
+        self.in_S[mine] = True
+        self.L = np.concatenate([self.L, Lhat], axis=1)
+        self.R[active] -= Lhat[active] @ Qp.T
+        self.R[mine] = 0.0
+        self.dv = O.row_sq_norms(self.R)
+        self.dv[self.in_S] = 0.0
+        self.k += bp
+        return Sp.astype(np.int64), float(self.dv.sum())
+
+    def l_rows(self, S, k):
+        own = (S >= self.lo) & (S < self.hi)
+        out = np.zeros((len(S), k))
+        out[own] = self.L[S[own] - self.lo, :k]
+        return out, own
+
+    def w(self, L1, S):
+        import scipy.linalg as sla
+        W = sla.solve_triangular(L1.T, self.L[:, :len(S)].T, lower=False).T if len(S) else np.zeros((self.n, 0))
+        for j, s in enumerate(S):
+            if self.lo <= s < self.hi:
+                W[s - self.lo] = 0.0
+                W[s - self.lo, j] = 1.0
+        return W
 
 
 def _worker_rows(rank, world, port, out_dir):
     dist = _init(rank, world, port)
     try:
         X = WL.gmm_pitfall(n=312, d=60, k=12, seed=6)
-        S, D, D0 = _sharded_rbrp(dist, rank, world, X, 1e-3, 8, 0, 2)
+        lo, hi = shard.shard_bounds([1] * X.shape[0], world)[rank]
+        sh = OracleShard(X, lo, hi, min(X.shape), 8, 0, 2)
+        out = shard.sharded_id([sh], 1e-3, 8, min(X.shape), comm=shard.DistComm())
         res = [None] * world
-        dist.all_gather_object(res, (S, D, D0))
+        dist.all_gather_object(res, (out["S"].tolist(), out["d_final"], out["d0"], lo, out["W"][0]))
         if rank == 0:
             np.save(os.path.join(out_dir, "rows.npy"), np.array(res, dtype=object), allow_pickle=True)
     finally:
@@ -212,13 +219,18 @@ def test_gloo_batched_shards_match_one_call(tmp_path):
 
 
 def test_gloo_row_sharded_block_loop_matches_one_process(tmp_path):
+    """The product's row-sharded driver (shard.sharded_id over torch.distributed) on two gloo
+    ranks, each holding half of the rows behind the shard contract, selects the skeletons of
+    one unsharded oracle run; each rank's rows of W are those of the unsharded W."""
     _spawn(_worker_rows, tmp_path)
     res = np.load(tmp_path / "rows.npy", allow_pickle=True)
-    S0, D0_, Dinit = res[0]
-    for S, D, Di in res[1:]:
+    S0, D0_, Dinit = res[0][0], res[0][1], res[0][2]
+    for S, D, Di, _, _ in res[1:]:
         assert S == S0 and D == D0_ and Di == Dinit  # every rank holds the same result
     X = WL.gmm_pitfall(n=312, d=60, k=12, seed=6)
-    ref = O.rbrp(X, tau=1e-3, b=8, seed=0, problem=2)
+    ref = O.rbrp_id(X, tau=1e-3, b=8, seed=0, problem=2)
     assert S0 == ref["S"].tolist()
     assert abs(D0_ - ref["D"]) <= 1e-9 * ref["D0"]
     assert abs(Dinit - ref["D0"]) <= 1e-12 * ref["D0"]
+    W = np.concatenate([r[4] for r in sorted(res, key=lambda r: r[3])], axis=0)
+    assert np.allclose(W, ref["W"], atol=1e-10)
