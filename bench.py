@@ -639,7 +639,8 @@ def run_batched(a):
     line = {"metric": "batched ID time (ms) for %d kernel blocks per GPU, tol %g, b %d" % (a.batch, tol, block),
             "value": ms, "unit": "ms", "n_gpus": ws_n, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32+f64", "fp64": "f64"}[prec], "data": "synthetic",
+            "dtype": {"fp32": "f32 residual and products, f64 norms and keys", "fp64": "f64"}[prec],
+            "data": "synthetic",
             "config": {"workload": "kernel_blocks", "P": P_all, "P_per_gpu": a.batch, "m": [64, 2048],
                        "n": [32, 256], "h": 0.5,
                        "gap": 2.0, "dtype_in": "fp32", "tol_sq_rel": tol, "block": block, "seed": 4,
@@ -775,7 +776,7 @@ def run_fixed_rank(a):
             del ws, Om, Xe, E
             torch.cuda.empty_cache()
     line = {"metric": "ID time at fixed rank (ms), adversarial GMM 1e5 x 1e3", "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "tf32+f64 / f64",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "tf32 update, f32 chain, f32 W (value); f64 rows listed beside",
             "config": {"workload": "gmm_fixed_rank", "n": a.n, "d": a.d, "clusters": 100, "means": "10 j e_j",
                        "block": a.block, "seed": 0},
             "value": next(r["ms"] for r in rows if r["precision"] == "tf32"), "ranks": rows,
