@@ -473,22 +473,21 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
   }
 }
 
-// The same filter for blocks of at most 64 candidates, built around latency.
-// Right-looking: thread r holds column r of the Schur complement (the Gram
-// matrix minus the factor so far) in registers.  Each step takes the trailing
-// mass and the pivot (the largest remaining d_r > 0, ties to the smaller
-// index: redux.sync max over the FP32 bit patterns, which order like the
-// values for d_r >= 0, then min over the indices of the maxima) per warp,
-// combines the two warps through shared memory, and stops at the first step
-// whose trailing mass fails the truncation test of Alg. 2; the pivot's owner then
-// publishes its scaled column l = S(:, p) / sqrt(d_p) and every thread applies
-// the rank-1 update S(:, r) -= l l_r to its column.  The kernel writes the
+// The same filter for blocks of at most 64 candidates, built around latency:
+// one warp, no block-wide barrier.  Right-looking: lane l holds columns l and
+// l + 32 of the Schur complement (the Gram matrix minus the factor so far) in
+// registers.  Each step takes the trailing mass (a warp sum) and the pivot (the
+// largest remaining d_r > 0, ties to the smaller index: redux.sync max over the
+// FP32 bit patterns, which order like the values for d_r >= 0, then min over the
+// indices of the maxima), and stops at the first step whose trailing mass fails
+// the truncation test of Alg. 2; the pivot's owner then publishes its scaled
+// column l = S(:, p) / sqrt(d_p) through shared memory and every lane applies
+// the rank-1 update S(:, r) -= l l_r to its two columns.  The kernel writes the
 // pivot-order factor Lc; Q'_V = Lc^{-1} V_perm follows as a column-parallel
 // substitution (k_trsm_rows_f32).
 constexpr int kPchol64 = 64;
-constexpr int kPchol64Threads = 64;
+constexpr int kPchol64Threads = 32;
 constexpr int kPchol64LDF = 68;  // factor rows: float4 steps over t
-constexpr int kPchol64LDG = 65;  // G rows: odd stride, conflict-free column reads
 
 __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* __restrict__ G, long long ldg,
                                                                   float* __restrict__ Lc_out, long long ldl,
@@ -498,100 +497,96 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
                                                                   int* __restrict__ mark, State* st) {
   pdl_wait();
   if (st->done) return;
-  __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];   // Lw[j * LDF + t]: candidate j, step t
+  __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];  // Lw[j * LDF + t]: candidate j, step t
   __shared__ int s_perm[kPchol64];
-  __shared__ int s_bp;
-  const int m = (int)st->b_t;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   __shared__ __align__(16) float lv[kPchol64];  // the pivot's factor column, published each step
-  __shared__ float s_ms[2][2];
-  __shared__ unsigned s_mx[2][2], s_ix[2][2];
-  // thread r holds column r of the Schur complement (= row r) in registers
-  float col[kPchol64];
-  float dr = 0.f;
+  const int m = (int)st->b_t;
+  const int lane = threadIdx.x;
+  const int c0 = lane, c1 = lane + 32;
+  // lane l holds columns l and l + 32 of the Schur complement (= rows, by symmetry)
+  float col0[kPchol64], col1[kPchol64];
 #pragma unroll
   for (int j = 0; j < kPchol64; ++j) {
-    col[j] = (j < m && tid < m) ? G[(long long)j * ldg + tid] : 0.f;
-    if (j == tid) dr = col[j];
+    col0[j] = (j < m && c0 < m) ? G[(long long)j * ldg + c0] : 0.f;
+    col1[j] = (j < m && c1 < m) ? G[(long long)j * ldg + c1] : 0.f;
   }
-  for (int e = tid; e < kPchol64 * kPchol64LDF; e += kPchol64Threads) Lw[e] = 0.f;
+  // the diagonal entries, read directly (a lane-dependent index into col0 / col1
+  // would move those arrays out of registers)
+  float d0 = (c0 < m) ? G[(long long)c0 * ldg + c0] : 0.f;
+  float d1 = (c1 < m) ? G[(long long)c1 * ldg + c1] : 0.f;
+  for (int e = lane; e < kPchol64 * kPchol64LDF; e += kPchol64Threads) Lw[e] = 0.f;
   double tau_b = st->tau_b;
   if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
   const float tb = (float)tau_b;
-  bool alive = tid < m;
-  {
-    float t = alive ? dr : 0.f;
+  bool a0 = c0 < m, a1 = c1 < m;
+  float total = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) s_ms[1][w] = t;
-  }
-  __syncthreads();
-  const float total = s_ms[1][0] + s_ms[1][1];
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  __syncwarp();
   int steps = 0;
   for (int i = 0; i < m; ++i) {
-    const int sl = i & 1;
-    // trailing mass and pivot (largest remaining d_r > 0, ties to the smaller index),
-    // per warp, then the two warps combined through shared memory
-    float ms = alive ? dr : 0.f;
+    float ms = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, o);
-    const unsigned bits = (alive && dr > 0.f) ? __float_as_uint(dr) : 0u;
-    const unsigned mxw = __reduce_max_sync(0xffffffffu, bits);
-    const unsigned ixw = __reduce_min_sync(0xffffffffu, (bits == mxw && mxw != 0u) ? (unsigned)tid : 0xffffffffu);
-    if (lane == 0) {
-      s_ms[sl][w] = ms;
-      s_mx[sl][w] = mxw;
-      s_ix[sl][w] = ixw;
-    }
-    __syncthreads();
-    const float msum = s_ms[sl][0] + s_ms[sl][1];
-    unsigned mx = s_mx[sl][0], p = s_ix[sl][0];
-    if (s_mx[sl][1] > mx || (s_mx[sl][1] == mx && s_ix[sl][1] < p)) {
-      mx = s_mx[sl][1];
-      p = s_ix[sl][1];
-    }
-    if (mx == 0u || !(msum >= tb * total && msum > 0.f)) break;  // the same on every thread; b' = i
+    const unsigned b0 = (a0 && d0 > 0.f) ? __float_as_uint(d0) : 0u;
+    const unsigned b1 = (a1 && d1 > 0.f) ? __float_as_uint(d1) : 0u;
+    const unsigned bl = b1 > b0 ? b1 : b0;          // this lane's better column (ties: the smaller index c0)
+    const unsigned il = b1 > b0 ? (unsigned)c1 : (unsigned)c0;
+    const unsigned mx = __reduce_max_sync(0xffffffffu, bl);
+    const unsigned p = __reduce_min_sync(0xffffffffu, (bl == mx && mx != 0u) ? il : 0xffffffffu);
+    if (mx == 0u || !(ms >= tb * total && ms > 0.f)) break;  // the same on every lane; b' = i
     const float rinv = rsqrtf(__uint_as_float(mx));
-    if (tid == (int)p) {  // the pivot's owner publishes l = S(:, p) / sqrt(d_p)
+    if (lane == (int)(p & 31u)) {  // the pivot's owner publishes l = S(:, p) / sqrt(d_p)
+      if (p < 32u) {
 #pragma unroll
-      for (int j = 0; j < kPchol64; j += 4)
-        *(float4*)(lv + j) = make_float4(col[j] * rinv, col[j + 1] * rinv, col[j + 2] * rinv, col[j + 3] * rinv);
+        for (int j = 0; j < kPchol64; j += 4)
+          *(float4*)(lv + j) = make_float4(col0[j] * rinv, col0[j + 1] * rinv, col0[j + 2] * rinv, col0[j + 3] * rinv);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kPchol64; j += 4)
+          *(float4*)(lv + j) = make_float4(col1[j] * rinv, col1[j + 1] * rinv, col1[j + 2] * rinv, col1[j + 3] * rinv);
+      }
     }
-    __syncthreads();
-    const float lr = lv[tid];
-    if (alive) Lw[tid * kPchol64LDF + i] = lr;
-    if (tid == (int)p) alive = false;
-    dr -= lr * lr;
-    // rank-1 update of this column: S(j, r) -= l_j l_r
+    __syncwarp();
+    const float l0 = lv[c0], l1 = lv[c1];
+    if (a0) Lw[c0 * kPchol64LDF + i] = l0;
+    if (a1) Lw[c1 * kPchol64LDF + i] = l1;
+    if ((unsigned)c0 == p) a0 = false;
+    if ((unsigned)c1 == p) a1 = false;
+    d0 -= l0 * l0;
+    d1 -= l1 * l1;
+    // rank-1 update of both columns: S(j, r) -= l_j l_r
 #pragma unroll
     for (int j = 0; j < kPchol64; j += 4) {
       const float4 l4 = *(const float4*)(lv + j);
-      col[j] = fmaf(-l4.x, lr, col[j]);
-      col[j + 1] = fmaf(-l4.y, lr, col[j + 1]);
-      col[j + 2] = fmaf(-l4.z, lr, col[j + 2]);
-      col[j + 3] = fmaf(-l4.w, lr, col[j + 3]);
+      col0[j] = fmaf(-l4.x, l0, col0[j]);
+      col0[j + 1] = fmaf(-l4.y, l0, col0[j + 1]);
+      col0[j + 2] = fmaf(-l4.z, l0, col0[j + 2]);
+      col0[j + 3] = fmaf(-l4.w, l0, col0[j + 3]);
+      col1[j] = fmaf(-l4.x, l1, col1[j]);
+      col1[j + 1] = fmaf(-l4.y, l1, col1[j + 1]);
+      col1[j + 2] = fmaf(-l4.z, l1, col1[j + 2]);
+      col1[j + 3] = fmaf(-l4.w, l1, col1[j + 3]);
     }
-    if (tid == 0) s_perm[i] = (int)p;
+    if (lane == 0) s_perm[i] = (int)p;
     steps = i + 1;
+    __syncwarp();  // every lane has read lv before the next pivot's owner overwrites it
   }
-  if (tid == 0) s_bp = steps;
-  __syncthreads();
-  const int bp = s_bp;
+  const int bp = steps;
+  __syncwarp();
   // the pivot-order factor Lc(i, l) = Lw[perm[i]][l] for l <= i < b' (zero
-  // elsewhere) to Lc_out, one column per thread (coalesced across threads);
+  // elsewhere) to Lc_out, two columns per lane (coalesced across lanes);
   // Q'_V = Lc^{-1} V_perm is then a column-parallel substitution (k_trsm_rows_f32)
-  {
-    const int c = tid;
-#pragma unroll 8
-    for (int i = 0; i < kPchol64; ++i) {
-      const float v = (c <= i && i < bp) ? Lw[s_perm[i] * kPchol64LDF + c] : 0.f;
-      Lc_out[(long long)i * ldl + c] = v;
-    }
+#pragma unroll 4
+  for (int i = 0; i < kPchol64; ++i) {
+    const int pi = i < bp ? s_perm[i] : 0;
+    Lc_out[(long long)i * ldl + c0] = (c0 <= i && i < bp) ? Lw[pi * kPchol64LDF + c0] : 0.f;
+    Lc_out[(long long)i * ldl + c1] = (c1 <= i && i < bp) ? Lw[pi * kPchol64LDF + c1] : 0.f;
   }
   {
     const long long k = st->k;
     const int tno = (int)(st->t + 1);
-    for (int i = tid; i < bp; i += kPchol64Threads) {
+    for (int i = lane; i < bp; i += kPchol64Threads) {
       const int pi = s_perm[i];
       if (perm) perm[i] = pi;
       const long long row = S_t[pi];
@@ -599,8 +594,8 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
       mark[row] = tno;
     }
   }
-  __syncthreads();
-  if (tid == 0) {
+  __syncwarp();
+  if (lane == 0) {
     st->bp = bp;
     st->bp_pad = (bp + 15) / 16 * 16;
     if (bp == 0) st->done = 1;
