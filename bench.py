@@ -324,13 +324,15 @@ def time_forms(a, G, Xd, stream, pid):
     tolerance: time per call (CUDA events, --form-steps calls after one warm-up), k and the true
     FP64 error of the returned S and W.  Timed after, and outside, the headline's timed region."""
     import torch
-    forms = [("tf32", "fp64", "fp64"), ("tf32", "fp64", "fp32"), ("tf32", "default", "fp32"),
-             ("tf32x3", "default", "fp32"), ("fp64", "default", "fp64")]
+    forms = [("tf32", "fp64", "fp64", "residual"), ("tf32", "fp64", "fp32", "residual"),
+             ("tf32", "default", "fp32", "residual"), ("tf32x3", "default", "fp32", "residual"),
+             ("tf32x3", "default", "fp32", "downdate"), ("fp64", "default", "fp64", "residual"),
+             ("fp64", "default", "fp64", "downdate")]
     res = {}
-    for prec, chain, wprec in forms:
-        kw = dict(block=a.block, seed=0, precision=prec, w_precision=wprec, problem=pid, chain=chain)
+    for prec, chain, wprec, form in forms:
+        kw = dict(block=a.block, seed=0, precision=prec, w_precision=wprec, problem=pid, chain=chain, form=form)
         try:
-            ws = G.Workspace(a.n, a.d, G.make_opts(a.block, prec, -1.0, 0, 0, pid, "random", wprec, "residual",
+            ws = G.Workspace(a.n, a.d, G.make_opts(a.block, prec, -1.0, 0, 0, pid, "random", wprec, form,
                                                    chain), Xd.device)
         except G.RBRPError:
             continue  # the form does not take this block size (the FP32 chain: b <= 128)
@@ -351,6 +353,8 @@ def time_forms(a, G, Xd, stream, pid):
                                               "f64" if (chain == "fp64" or prec == "fp64") else
                                               ("f32" if prec == "tf32" else "f64 storage/f32 products"),
                                               "f64" if wprec == "fp64" else "f32")
+        if form == "downdate":
+            key += ", downdate form"
         res[key] = {"ms": e0.elapsed_time(e1) / a.form_steps, "k": out["k"],
                     "rel_err_sq_device": out["rel_err_sq"],
                     "rel_err_sq_true": true_err_sq(Xd, out["S"], out["W"]),

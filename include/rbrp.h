@@ -96,8 +96,10 @@ typedef enum {
                                ||R_i||^2 recomputed (robust at any precision)       */
   RBRP_FORM_DOWNDATE = 1    /* as printed: X read-only, Lhat = X Q'^T, d_i -=
                                ||Lhat_i||^2; half the memory traffic of the residual
-                               form and no residual copy, FP64 only (the downdate
-                               cancels: it needs FP64 to stay accurate)           */
+                               form and no residual copy.  The downdate cancels, so
+                               it runs in RBRP_FP64 or in RBRP_TF32X3 (Lhat from the
+                               3xTF32 split, ~FP32-accurate, d in FP64; X must then
+                               be FP32 with ldx a multiple of 4 and a 16-byte base) */
 } rbrp_form;
 
 typedef enum {

@@ -515,7 +515,8 @@ cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n
 // for the rows accepted in this block (their Lhat row is kept), and Lhat_i = 0
 // for rows accepted in earlier blocks (their residual is zero, so their Lhat
 // row is, and L(S, :) stays lower triangular).  FP64; one warp per row.
-__global__ void __launch_bounds__(256) k_downdate(double* __restrict__ L, long long ldl, long long n,
+template <typename TL>
+__global__ void __launch_bounds__(256) k_downdate(TL* __restrict__ L, long long ldl, long long n,
                                                   const int* __restrict__ mark, double* __restrict__ dvec,
                                                   double* __restrict__ partials, const State* st) {
   if (st->done) return;
@@ -526,14 +527,14 @@ __global__ void __launch_bounds__(256) k_downdate(double* __restrict__ L, long l
   __shared__ double wsum[8];
   double mine = 0.0;
   for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
-    double* l = L + i * ldl + k;
+    TL* l = L + i * ldl + k;
     const int mk = mark[i];
     double di = 0.0;
     if (mk != 0 && mk != tno) {
-      for (int j = lane; j < bp; j += 32) l[j] = 0.0;
+      for (int j = lane; j < bp; j += 32) l[j] = (TL)0;
     } else if (mk == 0) {
       double s = 0.0;
-      for (int j = lane; j < bp; j += 32) s = fma(l[j], l[j], s);
+      for (int j = lane; j < bp; j += 32) s = fma((double)l[j], (double)l[j], s);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       di = dvec[i] - s;  // may round below zero for an exhausted row: d_i <= 0 is not eligible
@@ -552,7 +553,13 @@ __global__ void __launch_bounds__(256) k_downdate(double* __restrict__ L, long l
 
 cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* mark, double* dvec, double* partials,
                             int nparts, const State* st, cudaStream_t s) {
-  k_downdate<<<nparts, 256, 0, s>>>(L, ldl, n, mark, dvec, partials, st);
+  k_downdate<double><<<nparts, 256, 0, s>>>(L, ldl, n, mark, dvec, partials, st);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_downdate_f32(float* L, long long ldl, long long n, const int* mark, double* dvec, double* partials,
+                                int nparts, const State* st, cudaStream_t s) {
+  k_downdate<float><<<nparts, 256, 0, s>>>(L, ldl, n, mark, dvec, partials, st);
   return counted(cudaGetLastError());
 }
 

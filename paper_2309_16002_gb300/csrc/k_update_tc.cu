@@ -73,7 +73,10 @@ struct Cfg {
 };
 
 // ------------------------------------------------------------------ kernel
-template <int BMAX, bool SPLIT>
+// G1 = true runs GEMM 1 only: Lhat = A Q'^T into L(:, k + c0 ...) for every row of
+// A (the downdate form of the update step: A = X, read only; d is downdated by
+// launch_downdate afterwards), with no subtraction, no norms and no stores of A.
+template <int BMAX, bool SPLIT, bool G1 = false>
 __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     k_update_tf32(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
                   const __grid_constant__ CUtensorMap tmQlo, const __grid_constant__ CUtensorMap tmQT,
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
       }
       // phase-3 buffers alias the phase-1 ring: reuse only after GEMM 1 has drained it.
       // Chunks are taken last-to-first so the most recently loaded columns are re-read first.
-      if (mbar_wait(d1_full, 0, abort, lim)) {
+      if (!G1 && mbar_wait(d1_full, 0, abort, lim)) {
         for (int c = 0; c < nC; ++c) {
           const int s = c % S3;
           const uint32_t ph = (uint32_t)(c / S3) & 1u;
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
         mma_commit(empty1(s));
       }
       mma_commit(d1_full);
-      if (mbar_wait(a2_ready, 0, abort, lim)) {
+      if (!G1 && mbar_wait(a2_ready, 0, abort, lim)) {
         tc_after();
         const uint32_t id2 = idesc_tf32(BM, NB2);
         const int nk2 = N1 / 8;
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     const long long row = row0 + r;
     const bool own = r < ROWS;  // warps with q >= 2 own no row of R
     const bool in = own && row < n;
-    const bool marked = last_chunk && in && (mark[row] == tno);
+    const bool marked = !G1 && last_chunk && in && (mark[row] == tno);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const uint64_t drop = l2_policy_evict_first();
     if (SPLIT) {
@@ -292,6 +295,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
           for (int j = 0; j < 32; ++j)
             if (cb * 32 + j < bp) lrow[j] = __uint_as_float(v[j]);
         }
+        if (G1) continue;
         uint8_t* a2 = smem + C::P + cb * C::A2A;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
@@ -310,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
     fence_async_smem();
     tc_before();
     mbar_arrive(a2_ready);
-    for (int c = 0; c < nC; ++c) {
+    for (int c = 0; c < nC && !G1; ++c) {
       const int s = c % S3;
       const uint32_t ph = (uint32_t)(c / S3) & 1u;
       const int buf = c & 1;
@@ -357,14 +361,14 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
         }
       }
     }
-    if (in) dvec[row] = marked ? 0.0 : nrm;
+    if (in && !G1) dvec[row] = marked ? 0.0 : nrm;
     double t = in ? nrm : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) s_red[q] = t;
     mbar_arrive(red_bar);
     if (et == 0) {
-      if (mbar_wait(red_bar, 0, abort, lim)) {
+      if (mbar_wait(red_bar, 0, abort, lim) && !G1) {
         partials[2 * blockIdx.x] = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
         partials[2 * blockIdx.x + 1] = 0.0;
       }
@@ -846,7 +850,7 @@ bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer,
   return r == CUDA_SUCCESS;
 }
 
-template <int BMAX, bool SPLIT>
+template <int BMAX, bool SPLIT, bool G1 = false>
 cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
                        long long qrows, long long ldp, const float* QpT, const float* QpT_lo, long long qtcols,
                        long long ldpt, float* L, long long ldl, const int* mark, double* dvec, double* partials,
@@ -858,7 +862,7 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !(attr_set.load() >> dev & 1ULL)) {
-      e = cudaFuncSetAttribute(k_update_tf32<BMAX, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      e = cudaFuncSetAttribute(k_update_tf32<BMAX, SPLIT, G1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
       if (e != cudaSuccess) return e;
       if (dev < 64) attr_set.fetch_or(1ULL << dev);
     }
@@ -875,8 +879,8 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
     mQTlo = mQT;
   }
   const unsigned grid = (unsigned)((n + ROWS - 1) / ROWS);
-  k_update_tf32<BMAX, SPLIT><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark, dvec,
-                                                             partials, const_cast<State*>(st), c0);
+  k_update_tf32<BMAX, SPLIT, G1><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark,
+                                                                 dvec, partials, const_cast<State*>(st), c0);
   return counted(cudaGetLastError());
 }
 
@@ -920,6 +924,27 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
                                s);
   if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
 #undef RBRP_TC_ARGS
+  return cudaErrorInvalidValue;
+}
+
+// Downdate form in 3xTF32: Lhat = X Q'^T (columns c0 .. of Q') into L for every row
+// of X (FP32, read only; ldx a multiple of 4 and X 16-byte aligned for the tensor map).
+cudaError_t launch_lhat_tf32x3(const float* X, long long ldx, long long n, long long d, const float* Qp,
+                               const float* Qp_lo, long long ldp, const float* QpT, const float* QpT_lo,
+                               long long ldpt, float* L, long long ldl, const State* st, int bmax, int c0,
+                               cudaStream_t s) {
+  if (c0 < 0 || c0 % 64 != 0 || c0 >= ldpt) return cudaErrorInvalidValue;
+  if ((ldx & 3) != 0 || ((uintptr_t)X & 15) != 0) return cudaErrorInvalidValue;
+  const float* Qc = Qp + (long long)c0 * ldp;
+  const float* Qlc = Qp_lo + (long long)c0 * ldp;
+  const long long qrows = ldpt - c0;
+  float* Xw = const_cast<float*>(X);  // GEMM 1 only reads it
+  // (the Q'^T maps are encoded but not read by GEMM 1)
+#define RBRP_G1_ARGS Xw, ldx, n, d, Qc, Qlc, qrows, ldp, QpT + c0, QpT_lo + c0, qrows, ldpt, L, ldl, nullptr, nullptr, \
+                     nullptr, st, c0, s
+  if (bmax <= 32) return tc::launch_cfg<32, true, true>(RBRP_G1_ARGS);
+  if (bmax <= 64) return tc::launch_cfg<64, true, true>(RBRP_G1_ARGS);
+#undef RBRP_G1_ARGS
   return cudaErrorInvalidValue;
 }
 

@@ -108,7 +108,8 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int
   if (o->w_precision != RBRP_W_FP64 && o->w_precision != RBRP_W_FP32) return RBRP_EINVAL;
   if (o->tau_b > 1.0) return RBRP_EINVAL;
   if (o->form != RBRP_FORM_RESIDUAL && o->form != RBRP_FORM_DOWNDATE) return RBRP_EINVAL;
-  if (o->form == RBRP_FORM_DOWNDATE && o->precision != RBRP_FP64) return RBRP_EINVAL;
+  // the downdate cancels: FP64, or the 3xTF32 split (FP32-accurate coefficients, FP64 d)
+  if (o->form == RBRP_FORM_DOWNDATE && o->precision != RBRP_FP64 && o->precision != RBRP_TF32X3) return RBRP_EINVAL;
   if (o->chain != RBRP_CHAIN_DEFAULT && o->chain != RBRP_CHAIN_FP64) return RBRP_EINVAL;
   if (n >= (1LL << 31) || d >= (1LL << 31)) return RBRP_EINVAL;
   if (n > (1LL << 48) / d) return RBRP_EINVAL;  // n d elements: every byte count below stays far from overflow
@@ -485,6 +486,22 @@ cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
       LK(cgs_pass(p, u, u.Qt, dim_dev(&st->bp), s, dim_dev(&st->k, p.ldq)));
     }
   }
+  // update step as printed, in 3xTF32: Lhat = X Q'^T on tensor cores, d_i -= ||Lhat_i||^2 in FP64
+  if (p.downdate && p.prec == RBRP_TF32X3) {
+    LK(launch_qp_lowp(u.Qt, 1, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
+    const int cw = update_tf32_chunk((int)p.ldpt, 1);
+    LK(timed(g_prof.upd, s, [&] {
+      cudaError_t ce = cudaSuccess;
+      for (int c0 = 0; c0 < (int)p.ldpt && ce == cudaSuccess; c0 += cw)
+        ce = launch_lhat_tf32x3((const float*)u.X, u.ldx, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt,
+                                (float*)u.L, p.ldl, st, cw, c0, s);
+      if (ce == cudaSuccess)
+        ce = launch_downdate_f32((float*)u.L, p.ldl, n, u.mark, u.dvec, u.part, p.nparts, st, s);
+      return ce;
+    }));
+    LK(launch_finalize_block(u.part, p.nparts, st, s));
+    return cudaSuccess;
+  }
   // update step (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
   if (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) {
     const int split = (p.prec == RBRP_TF32X3);
@@ -713,6 +730,9 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   if (rs != RBRP_OK) return rs;
   if (!X || !skel || !W || !res || !ws) return RBRP_EINVAL;
   if (ldx < d || ldw < p.k_cap) return RBRP_EINVAL;
+  // the 3xTF32 downdate reads X itself with a tensor map: FP32, 16-byte rows and base
+  if (p.downdate && p.prec == RBRP_TF32X3 && (x_is_fp64 || (ldx & 3) != 0 || ((uintptr_t)X & 15) != 0))
+    return RBRP_EINVAL;
   if (((uintptr_t)ws & 255) != 0 || ws_bytes < p.total) return RBRP_EWORKSPACE;
   if (!(tol < 1.0)) return RBRP_EINVAL;
   memset(res, 0, sizeof(*res));

@@ -284,6 +284,9 @@ cudaError_t launch_qp_lowp(const void* Qt, int q_is_fp64, long long ldq, float* 
                            cudaStream_t s);
 cudaError_t launch_downdate(double* L, long long ldl, long long n, const int* mark, double* dvec, double* partials,
                             int nparts, const State* st, cudaStream_t s);
+// The same with FP32 coefficients (the 3xTF32 downdate form); the sums stay FP64.
+cudaError_t launch_downdate_f32(float* L, long long ldl, long long n, const int* mark, double* dvec, double* partials,
+                                int nparts, const State* st, cudaStream_t s);
 cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d,
                               const int* mark, double* dvec, double* partials, int nparts,
                               const State* st, cudaStream_t s);
@@ -338,6 +341,13 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
                                long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
                                double* partials, const State* st, int bmax, int split, int c0, cudaStream_t s);
 int update_tf32_parts(long long n, int bmax, int split);
+// The downdate form in 3xTF32 (update step as printed): Lhat = X Q'^T for every row
+// of the FP32 input X (read only) into L(:, k + c0 ...), columns c0 .. c0 + bmax - 1
+// of Q'; launch_downdate_f32 then zeroes the rows accepted earlier and downdates d.
+cudaError_t launch_lhat_tf32x3(const float* X, long long ldx, long long n, long long d, const float* Qp,
+                               const float* Qp_lo, long long ldp, const float* QpT, const float* QpT_lo,
+                               long long ldpt, float* L, long long ldl, const State* st, int bmax, int c0,
+                               cudaStream_t s);
 // Columns of Q' per launch for a block of b'_pad <= ldpt columns.
 int update_tf32_chunk(int ldpt, int split);
 

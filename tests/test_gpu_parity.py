@@ -434,8 +434,40 @@ def test_downdate_form_fixed_rank_and_ragged(G):
     _assert_fp64_parity(X, ref, out)
 
 
-def test_downdate_form_needs_fp64(G):
+def test_downdate_form_needs_fp64_or_split(G):
     import torch
     X = torch.zeros((64, 16), dtype=torch.float32, device="cuda:0")
     with pytest.raises(G.RBRPError):
         G.rbrp_id(X, 1e-3, precision="tf32", form="downdate")
+    with pytest.raises(G.RBRPError):  # the 3xTF32 downdate reads X itself: FP32 only
+        G.rbrp_id(X.double(), 1e-3, precision="tf32x3", form="downdate")
+
+
+@pytest.mark.parametrize("n,d,b,tol", [(2000, 200, 16, 1e-6), (3001, 333, 64, 1e-5), (777, 257, 100, 1e-6)])
+def test_tf32x3_downdate_form(G, n, d, b, tol):
+    """The update step as printed in 3xTF32 (Lhat = X Q'^T on tensor cores, d downdated in
+    FP64): the literal mixed bar against the oracle, ragged tiles, b across two chunks."""
+    X, _ = WL.spectral(n=n, d=d, rate=0.93, seed=n + b, dtype=np.float32)
+    ref = O.rbrp_id(X, tau=tol, b=b, seed=4)
+    out = _run(G, X, tol, block=b, seed=4, precision="tf32x3", form="downdate")
+    _assert_mixed(X, ref, out, "tf32x3 downdate n=%d b=%d" % (n, b), tol=tol, b=b)
+
+
+def test_tf32x3_downdate_first_block_matches_fp64(G):
+    X = WL.zipf_gmm(n=5000, d=200, clusters=30, seed=2)
+    a = _run(G, X, -1.0, block=32, seed=0, precision="fp64", form="downdate", k_max=32)
+    t = _run(G, X, -1.0, block=32, seed=0, precision="tf32x3", form="downdate", k_max=32)
+    assert a["S"].tolist() == t["S"].tolist()
+    assert np.max(np.abs(t["W"] - a["W"])) <= 1e-4 * max(1.0, np.max(np.abs(a["W"])))
+
+
+def test_tf32x3_downdate_zipf_gmm_full_size(G, zipf_full):
+    """The headline workload in the 3xTF32 downdate form: true e^2 <= tol and the literal bar."""
+    X, ref, Xd = zipf_full
+    out = _run(G, X, 1e-4, block=64, seed=0, precision="tf32x3", form="downdate", w_precision="fp32")
+    e_gpu = _e_torch(Xd, out["S"], out["W"])
+    note = "tf32x3 downdate: e %.6e oracle %.6e k %d oracle %d" % (e_gpu, ref["e"], out["k"], len(ref["S"]))
+    print(note)
+    assert e_gpu ** 2 <= 1e-4, note
+    assert P.mixed_bar(e_gpu, ref["e"]), note
+    assert np.array_equal(out["W"][out["S"]], np.eye(out["k"]))
