@@ -26,7 +26,8 @@
 // TMEM and lane 0 issues the MMAs, warps 2-5 (one row each) are the epilogue,
 // warps 6-9 split the L chunks into hi/lo in place.  Every mbarrier wait is
 // bounded: after the limit the CTA records RBRP_ETIMEOUT in the State, stops,
-// waits briefly for copies in flight, frees its TMEM and returns.
+// drains the TMA fills and MMAs it issued (each with a bounded wait), frees its
+// TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 

@@ -278,3 +278,31 @@ def test_gmm_pitfall_robust_filter_helps():
     r = O.rbrp(X, tau=0.2, b=20, seed=0)
     p = O.rbrp(X, tau=0.2, b=20, seed=0, tau_b=0.0)
     assert len(r["S"]) < len(p["S"])
+
+
+def test_tsvd_interp_clip_is_relative_to_sigma_max():
+    """Remark on stable evaluation of L2 L1^{-1}: with L1 = U diag(s) V^T built from known factors,
+    the truncated-SVD W is L2 V diag(1/s_kept) U^T, where s_kept are the s_i > 1e-12 s_max.  The
+    spectrum below puts one value at 1e-13 s_max (dropped) and one at 1e-11 s_max (kept), and the
+    whole L is scaled by 1e6, so an absolute clip, a dropped clip or a clip against s_min all fail."""
+    rng = np.random.default_rng(17)
+    k, n = 5, 40
+    U, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    s = np.array([1.0, 1e-3, 1e-6, 1e-11, 1e-13])
+    for scale in (1.0, 1e6):
+        L1 = scale * (U * s) @ V.T
+        L2 = rng.standard_normal((n - k, k))
+        S = np.arange(3, 3 + k)
+        rest = np.setdiff1d(np.arange(n), S)
+        L = np.zeros((n, k))
+        L[S] = L1
+        L[rest] = L2
+        W = O.interp_matrix_tsvd(L, S)
+        keep = s > 1e-12
+        want = L2 @ ((V[:, keep] / (scale * s[keep])) @ U[:, keep].T)
+        assert np.array_equal(W[S], np.eye(k))
+        # the kept 1e-11 direction amplifies rounding by 1e11: compare relative to |want|
+        assert np.max(np.abs(W[rest] - want)) <= 1e-3 * np.max(np.abs(want))
+        # the dropped direction contributes nothing: W is orthogonal to U's last column
+        assert np.max(np.abs(W[rest] @ U[:, ~keep])) <= 1e-4 * np.max(np.abs(want))
