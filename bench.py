@@ -487,8 +487,8 @@ def run_ours(a):
                 "roofline": roofline, "kernels": kernels,
                 "gpu_launches": prof["launches"],
                 "gpu_launches_note": "kernels of the profiled pass (host-queued blocks); the timed region "
-                                     "runs the same kernels per block plus one loop-condition kernel, inside "
-                                     "one graph launch per step",
+                                     "runs the same kernels per block inside one graph launch per step (the "
+                                     "block's finalisation also sets the loop's condition)",
                 "clocks": clk}
 
 

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "rbrp_internal.cuh"
+#include "sample_common.cuh"
 
 namespace rbrp {
 
@@ -66,12 +67,74 @@ __global__ void __launch_bounds__(256) k_init_norms(const TX* __restrict__ X, lo
   }
 }
 
+// FP32 input and FP32 residual (the tensor-core paths), 16-byte rows: the same sums
+// from float4 loads, eight in flight per lane, so the pass over X runs near the HBM
+// rate (one 4-byte load per lane and step leaves too few bytes in flight).
+__global__ void __launch_bounds__(256) k_init_norms_f32v(const float* __restrict__ X, long long n, long long d,
+                                                         long long ldx, float* __restrict__ R, long long ldr,
+                                                         double* __restrict__ dvec, int* __restrict__ mark,
+                                                         double* __restrict__ partials) {
+  constexpr int U = 8;  // float4 loads in flight per lane
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double wsum[8];
+  double mine = 0.0;
+  const long long nv = d / 4;
+  for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
+    const float4* x4 = (const float4*)(X + i * ldx);
+    float4* r4 = R ? (float4*)(R + i * ldr) : nullptr;
+    float sf = 0.f;
+    for (long long v0 = lane; v0 < nv; v0 += 32 * U) {
+      float4 q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long v = v0 + 32 * u;
+        q[u] = (v < nv) ? x4[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long v = v0 + 32 * u;
+        if (r4 && v < nv) r4[v] = q[u];
+        sf = fmaf(q[u].x, q[u].x, sf);
+        sf = fmaf(q[u].y, q[u].y, sf);
+        sf = fmaf(q[u].z, q[u].z, sf);
+        sf = fmaf(q[u].w, q[u].w, sf);
+      }
+    }
+    for (long long j = 4 * nv + lane; j < d; j += 32) {
+      const float v = X[i * ldx + j];
+      if (R) R[i * ldr + j] = v;
+      sf = fmaf(v, v, sf);
+    }
+    if (R)
+      for (long long j = d + lane; j < ldr; j += 32) R[i * ldr + j] = 0.f;
+    double sum = (double)sf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+      dvec[i] = sum;
+      mark[i] = 0;
+    }
+    mine += sum;
+  }
+  if (lane == 0) wsum[warp] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
 cudaError_t launch_init_norms(const void* X, int x_is_fp64, long long n, long long d, long long ldx,
                               void* R, int r_is_fp64, long long ldr, double* dvec, int* mark,
                               double* partials, int nparts, State* st, cudaStream_t s) {
   (void)st;
   dim3 grid(nparts), block(256);
-  if (x_is_fp64 && r_is_fp64)
+  const bool vec = !x_is_fp64 && !r_is_fp64 && (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0 &&
+                   (!R || ((ldr & 3) == 0 && ((uintptr_t)R & 15) == 0));
+  if (vec)
+    k_init_norms_f32v<<<grid, block, 0, s>>>((const float*)X, n, d, ldx, (float*)R, ldr, dvec, mark, partials);
+  else if (x_is_fp64 && r_is_fp64)
     k_init_norms<double, double><<<grid, block, 0, s>>>((const double*)X, n, d, ldx, (double*)R, ldr, dvec, mark, partials);
   else if (x_is_fp64)
     k_init_norms<double, float><<<grid, block, 0, s>>>((const double*)X, n, d, ldx, (float*)R, ldr, dvec, mark, partials);
@@ -132,14 +195,6 @@ cudaError_t launch_finish_init(const double* partials, int nparts, State* st, do
 // CTA-wide bitonic sorts: every CTA sorts 2048 (key, row) pairs and keeps its
 // b smallest, until one CTA is left.
 // ============================================================================
-struct Pair {
-  unsigned long long key;
-  long long idx;
-};
-
-__device__ __forceinline__ bool pair_less(const Pair& a, const Pair& b) {
-  return (a.key < b.key) || (a.key == b.key && a.idx < b.idx);
-}
 
 __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict__ dvec, long long n,
                                                        const Pair* __restrict__ in, long long n_in,
@@ -161,18 +216,8 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
     Pair p{kIneligible, LLONG_MAX};
     if (first) {
       if (gidx < n) {
-        const double di = dvec[gidx];
-        if (di > 0.0) {
-          double key;
-          if (greedy) {
-            key = -di;
-          } else {
-            // a row shard draws with its rows' global indices (row_base + local index)
-            const double u = philox_uniform((unsigned long long)(gidx + row_base), block_no, seed, problem);
-            key = -log(u) / di;
-          }
-          p.key = orderable(key);
-        }
+        // a row shard draws with its rows' global indices (row_base + local index)
+        p.key = exact_key(dvec[gidx], gidx + row_base, block_no, seed, problem, greedy);
         p.idx = gidx;
       }
     } else if (gidx < n_in) {
@@ -180,23 +225,7 @@ __global__ void __launch_bounds__(1024) k_sample_level(const double* __restrict_
     }
     sh[e] = p;
   }
-  __syncthreads();
-  // bitonic sort, ascending by (key, idx); 1024 threads x 1 compare-exchange per stage
-  for (int k = 2; k <= kSortChunk; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int t = threadIdx.x;
-      const int i = (t / j) * 2 * j + (t % j);
-      const int l = i + j;
-      const bool up = ((i & k) == 0);
-      Pair a = sh[i], c = sh[l];
-      const bool swap = up ? pair_less(c, a) : pair_less(a, c);
-      if (swap) {
-        sh[i] = c;
-        sh[l] = a;
-      }
-      __syncthreads();
-    }
-  }
+  sort_chunk(sh);  // ascending by (key, idx)
   if (!last) {
     for (int e = threadIdx.x; e < b; e += blockDim.x) out[(long long)blockIdx.x * b + e] = sh[e];
     return;
@@ -436,10 +465,11 @@ __global__ void k_qp_lowp(const TQ* __restrict__ Qt, long long ldq, float* __res
     const int i = (int)(e / ldp);
     const long long j = e % ldp;
     const TQ q = (i < bp && j < d) ? Qt[(k + i) * ldq + j] : (TQ)0;
-    float hi = (float)q, lo = 0.0f;
+    // nearest TF32 values (the MMA would truncate an FP32 operand): hi, and lo = q - hi
+    const float hi = tf32_rn((float)q);
+    float lo = 0.0f;
     if (Qp_lo) {
-      hi = __uint_as_float(__float_as_uint(hi) & 0xFFFFE000u);
-      lo = (float)(q - (TQ)hi);
+      lo = tf32_rn((float)(q - (TQ)hi));
       Qp_lo[(long long)i * ldp + j] = lo;
     }
     Qp[(long long)i * ldp + j] = hi;
@@ -563,16 +593,33 @@ cudaError_t launch_downdate_f32(float* L, long long ldl, long long n, const int*
   return counted(cudaGetLastError());
 }
 
-// Alg. 2, stopping test after a block: D = ||d||_1, k += b', t += 1.
-__global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st) {
+// Alg. 2, stopping test after a block: D = ||d||_1, k += b', t += 1.  Inside the
+// device-side loop (loop != 0) it also sets the while node's condition from the
+// State, whether or not the block ran, with a guard on the number of iterations.
+__global__ void k_finalize_block(const double* __restrict__ partials, int np, State* st, cudaGraphConditionalHandle h,
+                                 int loop) {
   pdl_wait();
-  if (st->done) return;
-  const double D = fixed_sum_partials<kFixedSumThreads>(partials, np);
-  if (threadIdx.x == 0) finish_block(st, D);
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = st->done;
+  __syncthreads();
+  if (!s_done) {
+    const double D = fixed_sum_partials<kFixedSumThreads>(partials, np);
+    if (threadIdx.x == 0) finish_block(st, D);
+  }
+  if (loop && threadIdx.x == 0) {
+    const long long it = ++st->iters;
+    if (!st->done && it > st->k_cap + 2) {  // cannot happen: every block accepts a row or stops
+      st->status = RBRP_ETIMEOUT;
+      st->done = 1;
+    }
+    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+  }
 }
 
-cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s) {
-  return counted(launch_pdl(k_finalize_block, dim3(1), dim3(kFixedSumThreads), 0, s, partials, nparts, st));
+cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s,
+                                  cudaGraphConditionalHandle h, int loop) {
+  return counted(
+      launch_pdl(k_finalize_block, dim3(1), dim3(kFixedSumThreads), 0, s, partials, nparts, st, h, loop));
 }
 
 // ============================================================================
@@ -711,22 +758,5 @@ cudaError_t launch_w_identity_rows(double* W, long long ldw, long long k, const 
 
 namespace rbrp {
 
-// ============================================================================
-// Alg. 2, stopping test as the condition of a CUDA graph's while node: the loop
-// runs on the device, the host never reads the State between blocks.
-// ============================================================================
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, State* st) {
-  const long long it = ++st->iters;
-  if (!st->done && it > st->k_cap + 2) {  // cannot happen: every block accepts a row or stops
-    st->status = RBRP_ETIMEOUT;
-    st->done = 1;
-  }
-  cudaGraphSetConditional(h, st->done ? 0u : 1u);
-}
-
-cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, State* st, cudaStream_t s) {
-  k_loop_cond<<<1, 1, 0, s>>>(h, st);
-  return counted(cudaGetLastError());
-}
 
 }  // namespace rbrp

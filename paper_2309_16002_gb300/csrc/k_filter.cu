@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(256) k_trsm_rows_f32(const float* __restrict__
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int r = part + 8 * q;
-      const float v = (r < bp && c < d) ? b[q] : 0.f;
+      const float v = (r < bp && c < d) ? tf32_rn(b[q]) : 0.f;  // the nearest TF32 value
       if (r < qrows) Qp[(long long)r * ldp + c] = v;
       if (r < qrows && c < d) QpT[c * ldpt + r] = v;
     }

@@ -78,7 +78,8 @@ struct Cfg {
 // launch_downdate afterwards), with no subtraction, no norms and no stores of A.
 template <int BMAX, bool SPLIT, bool G1 = false>
 __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
-    k_update_tf32(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
+    k_update_tf32(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmX,
+                  const __grid_constant__ CUtensorMap tmQ,
                   const __grid_constant__ CUtensorMap tmQlo, const __grid_constant__ CUtensorMap tmQT,
                   const __grid_constant__ CUtensorMap tmQTlo, float* __restrict__ L, long long ldl, long long n,
                   long long d, const int* __restrict__ mark, double* __restrict__ dvec,
@@ -92,6 +93,9 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
   const int bp = min((int)st->bp - c0, BMAX);
   if (bp <= 0) return;
   const bool last_chunk = c0 + BMAX >= (int)st->bp;
+  // the residual starts as X and is never copied: the first block's first launch
+  // reads X (tmX) and stores R, every later launch reads and stores R
+  const CUtensorMap* tmSrc = (!G1 && st->t == 0 && c0 == 0) ? &tmX : &tmR;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
         if (!mbar_wait(empty1(s), ph ^ 1u, abort, lim)) break;
         mbar_expect_tx(full1(s), (uint32_t)((C::A1 + C::B1) + (SPLIT ? C::B1 : 0)));
         const uint32_t base = sb + s * C::ST1;
-        tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)row0, keep);
+        tma_load_2d_hint(base, tmSrc, full1(s), kc * BK1, (int)row0, keep);
         tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
         if (SPLIT) tma_load_2d(base + 2 * C::A1 + C::B1, &tmQlo, full1(s), kc * BK1, 0);
         ++fills1;
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
           if (!mbar_wait(empty3(s), ph ^ 1u, abort, lim)) break;
           mbar_expect_tx(full3(s), (uint32_t)C::ST3);
           const uint32_t base = sb + s * C::ST3;
-          tma_load_2d_hint(base, &tmR, full3(s), col, (int)row0, drop);
+          tma_load_2d_hint(base, tmSrc, full3(s), col, (int)row0, drop);
 #pragma unroll
           for (int a = 0; a < BMAX / 32; ++a) {
             tma_load_2d(base + C::R3 + a * C::B2A, &tmQT, full3(s), a * 32, col);
@@ -274,9 +278,9 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           float4 x = *(float4*)(a + ch * 16);
-          float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+          float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
           *(float4*)(a + ch * 16) = h;
-          *(float4*)(alo + ch * 16) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          *(float4*)(alo + ch * 16) = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
         }
         fence_async_smem();
         mbar_arrive(conv1(s));
@@ -302,9 +306,10 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
           const float4 x = make_float4(__uint_as_float(v[4 * ch]), __uint_as_float(v[4 * ch + 1]),
                                        __uint_as_float(v[4 * ch + 2]), __uint_as_float(v[4 * ch + 3]));
           if (SPLIT) {
-            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
             *(float4*)(a2 + swz(r, ch)) = h;
-            *(float4*)(a2 + C::A2 + swz(r, ch)) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+            *(float4*)(a2 + C::A2 + swz(r, ch)) =
+                make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
           } else {
             *(float4*)(a2 + swz(r, ch)) = x;
           }
@@ -443,7 +448,8 @@ struct PCfg {
 
 template <int BMAX>
 __global__ void __launch_bounds__(kPThreads, 1)
-    k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ,
+    k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmX,
+                   const __grid_constant__ CUtensorMap tmQ,
                    const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
                    long long d, const int* __restrict__ mark, double* __restrict__ dvec,
                    double* __restrict__ partials, State* st, int c0) {
@@ -456,6 +462,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const int bp = min((int)st->bp - c0, BMAX);
   if (bp <= 0) return;
   const bool last_chunk = c0 + BMAX >= (int)st->bp;
+  // the residual starts as X and is never copied: the first block's first launch
+  // reads X (tmX) and stores R, every later launch reads and stores R
+  const CUtensorMap* tmSrc = (st->t == 0 && c0 == 0) ? &tmX : &tmR;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sb = smem_u32(smem);
@@ -547,7 +556,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
           mbar_expect_tx(full1(s), (uint32_t)(C::A1 + C::B1));
           const uint32_t base = sb + s * C::ST1;
-          tma_load_2d_hint(base, &tmR, full1(s), kc * BK1, (int)(ptile(tile) * PROWS), keep);
+          tma_load_2d_hint(base, tmSrc, full1(s), kc * BK1, (int)(ptile(tile) * PROWS), keep);
           tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
         }
       }
@@ -597,7 +606,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               break;
             }
             mbar_expect_tx(full3(s), (uint32_t)C::R3);
-            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, &tmR, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS),
+            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, tmSrc, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS),
                              drop);
           }
         }
@@ -798,7 +807,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
 template <int BMAX>
 cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long qrows,
                         long long ldp, const float* QpT, long long qtcols, long long ldpt, float* L, long long ldl,
-                        const int* mark, double* dvec, double* partials, const State* st, int c0, cudaStream_t s) {
+                        const int* mark, double* dvec, double* partials, const State* st, int c0, cudaStream_t s,
+                        const float* X0, long long ldx0) {
   using C = PCfg<BMAX>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -809,15 +819,17 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
     if (e != cudaSuccess) return e;
     if (dev < 64) attr_set.fetch_or(1ULL << dev);
   }
-  CUtensorMap mR, mQ, mQT;
+  CUtensorMap mR, mX, mQ, mQT;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, PROWS)) return cudaErrorInvalidValue;
+  if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, PROWS) : false) return cudaErrorInvalidValue;
+  if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (n + PROWS - 1) / PROWS;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mQ, mQT, L,
+  return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT, L,
                             ldl, n, d, mark, dvec, partials, const_cast<State*>(st), c0));
 }
 
@@ -854,7 +866,7 @@ template <int BMAX, bool SPLIT, bool G1 = false>
 cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
                        long long qrows, long long ldp, const float* QpT, const float* QpT_lo, long long qtcols,
                        long long ldpt, float* L, long long ldl, const int* mark, double* dvec, double* partials,
-                       const State* st, int c0, cudaStream_t s) {
+                       const State* st, int c0, cudaStream_t s, const float* X0 = nullptr, long long ldx0 = 0) {
   using C = Cfg<BMAX, SPLIT>;
   static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   {
@@ -867,8 +879,10 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
       if (dev < 64) attr_set.fetch_or(1ULL << dev);
     }
   }
-  CUtensorMap mR, mQ, mQlo, mQT, mQTlo;
+  CUtensorMap mR, mX, mQ, mQlo, mQT, mQTlo;
   if (!make_map(&mR, R, d, n, ldr * 4, 32, ROWS)) return cudaErrorInvalidValue;
+  if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, ROWS) : false) return cudaErrorInvalidValue;
+  if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, NB2)) return cudaErrorInvalidValue;
   if (SPLIT) {
@@ -879,7 +893,7 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
     mQTlo = mQT;
   }
   const unsigned grid = (unsigned)((n + ROWS - 1) / ROWS);
-  k_update_tf32<BMAX, SPLIT, G1><<<grid, kThreads, C::SMEM, s>>>(mR, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark,
+  k_update_tf32<BMAX, SPLIT, G1><<<grid, kThreads, C::SMEM, s>>>(mR, mX, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, mark,
                                                                  dvec, partials, const_cast<State*>(st), c0);
   return counted(cudaGetLastError());
 }
@@ -901,16 +915,18 @@ int update_tf32_chunk(int ldpt, int split) {
 cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
                                long long ldp, const float* QpT, const float* QpT_lo, long long ldpt, float* L,
                                long long ldl, const int* mark, double* dvec, double* partials, const State* st,
-                               int bmax, int split, int c0, cudaStream_t s) {
+                               int bmax, int split, int c0, cudaStream_t s, const float* X0, long long ldx0) {
   // columns c0 .. of Q': rows c0.. of the Qp copies, columns c0.. of the QpT copies (c0 is a
   // multiple of 64, so the bases stay 256-byte aligned for the tensor maps)
   if (c0 < 0 || c0 % 64 != 0 || c0 >= ldpt) return cudaErrorInvalidValue;
+  if (X0 && ((ldx0 & 3) != 0 || ((uintptr_t)X0 & 15) != 0)) return cudaErrorInvalidValue;
   const float* Qc = Qp + (long long)c0 * ldp;
   const float* Qlc = Qp_lo ? Qp_lo + (long long)c0 * ldp : nullptr;
   const float* QTc = QpT + c0;
   const float* QTlc = QpT_lo ? QpT_lo + c0 : nullptr;
   const long long qrows = ldpt - c0, qtcols = ldpt - c0;
-#define RBRP_TC_ARGS R, ldr, n, d, Qc, Qlc, qrows, ldp, QTc, QTlc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0, s
+#define RBRP_TC_ARGS \
+  R, ldr, n, d, Qc, Qlc, qrows, ldp, QTc, QTlc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0, s, X0, ldx0
   if (split) {
     if (bmax <= 32) return tc::launch_cfg<32, true>(RBRP_TC_ARGS);
     if (bmax <= 64) return tc::launch_cfg<64, true>(RBRP_TC_ARGS);
@@ -918,10 +934,10 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
   }
   if (bmax <= 32)
     return tc::launch_pcfg<32>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
-                               s);
+                               s, X0, ldx0);
   if (bmax <= 64)
     return tc::launch_pcfg<64>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
-                               s);
+                               s, X0, ldx0);
   if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
 #undef RBRP_TC_ARGS
   return cudaErrorInvalidValue;

@@ -280,8 +280,8 @@ __global__ void __launch_bounds__(kWThreads, 1)
               float h[4], l[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                h[e] = tf32_hi((float)v[4 * c + e]);
-                l[e] = (float)(v[4 * c + e] - (double)h[e]);
+                h[e] = tf32_rn((float)v[4 * c + e]);
+                l[e] = tf32_rn((float)(v[4 * c + e] - (double)h[e]));
               }
               *(float4*)(a + ((c ^ r7) << 4)) = make_float4(h[0], h[1], h[2], h[3]);
               *(float4*)(alo + ((c ^ r7) << 4)) = make_float4(l[0], l[1], l[2], l[3]);
@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(kWThreads, 1)
             for (int c = 0; c < 8; ++c) {
               const uint32_t o = (uint32_t)((c ^ r7) << 4);  // distinct banks across 8 consecutive rows
               const float4 x = *(const float4*)(a + o);
-              const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+              const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
               *(float4*)(a + o) = h;
-              *(float4*)(alo + o) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+              *(float4*)(alo + o) = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
             }
           }
           fence_async_smem();
@@ -338,12 +338,14 @@ __global__ void __launch_bounds__(kWThreads, 1)
                                           __uint_as_float(v0[4 * c + 2]), __uint_as_float(v0[4 * c + 3]));
             const float4 x1 = make_float4(__uint_as_float(v1[4 * c]), __uint_as_float(v1[4 * c + 1]),
                                           __uint_as_float(v1[4 * c + 2]), __uint_as_float(v1[4 * c + 3]));
-            const float4 h0 = make_float4(tf32_hi(x0.x), tf32_hi(x0.y), tf32_hi(x0.z), tf32_hi(x0.w));
-            const float4 h1 = make_float4(tf32_hi(x1.x), tf32_hi(x1.y), tf32_hi(x1.z), tf32_hi(x1.w));
+            const float4 h0 = make_float4(tf32_rn(x0.x), tf32_rn(x0.y), tf32_rn(x0.z), tf32_rn(x0.w));
+            const float4 h1 = make_float4(tf32_rn(x1.x), tf32_rn(x1.y), tf32_rn(x1.z), tf32_rn(x1.w));
             *(float4*)(fr + o) = h0;
-            *(float4*)(fr + C::A + o) = make_float4(x0.x - h0.x, x0.y - h0.y, x0.z - h0.z, x0.w - h0.w);
+            *(float4*)(fr + C::A + o) =
+                make_float4(tf32_rn(x0.x - h0.x), tf32_rn(x0.y - h0.y), tf32_rn(x0.z - h0.z), tf32_rn(x0.w - h0.w));
             *(float4*)(fr + 2 * C::A + o) = h1;
-            *(float4*)(fr + 3 * C::A + o) = make_float4(x1.x - h1.x, x1.y - h1.y, x1.z - h1.z, x1.w - h1.w);
+            *(float4*)(fr + 3 * C::A + o) =
+                make_float4(tf32_rn(x1.x - h1.x), tf32_rn(x1.y - h1.y), tf32_rn(x1.z - h1.z), tf32_rn(x1.w - h1.w));
           }
           fence_async_smem();
           mbar_arrive(f_full);
@@ -447,9 +449,9 @@ __global__ void __launch_bounds__(128) k_wsolve_g(const double* __restrict__ L1,
   for (int c = 0; c < WN; ++c) {
     if (c < nb) {
       const float v = sg * y[c];
-      const float h = tf32_hi(v);
+      const float h = tf32_rn(v);
       Gh[(long long)(j0 + c) * ldt + r] = h;
-      Gl[(long long)(j0 + c) * ldt + r] = v - h;
+      Gl[(long long)(j0 + c) * ldt + r] = tf32_rn(v - h);
     }
   }
 }

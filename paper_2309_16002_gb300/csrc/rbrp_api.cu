@@ -260,6 +260,9 @@ struct Bufs {
   const long long* forced_list;  // forced pass: the skeletons in order
   const int* forced_count;       // forced pass: their number (device)
   long long mark_base, mark_n;   // rows [mark_base, mark_base + mark_n) of the ID are this residual's
+  int r_from_x = 0;  // R = X is not copied: the first block reads X (FP32 tensor-core update paths)
+  cudaGraphConditionalHandle loop_h = 0;  // the while node's condition, while the loop body is captured
+  int loop = 0;                           // 1 while the loop body is captured
 };
 
 Bufs carve(const Plan& p, void* ws) {
@@ -417,19 +420,40 @@ cudaError_t enqueue_block(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     e = (call);                      \
     if (e != cudaSuccess) return e;  \
   } while (0)
-  // sampling step: S_t (two-stage sampler; the exact tree sampler runs only if it asks for it),
+  // projection step, first half, done by the sampler: V = R(S_t, :), or X(S_t, :) in the
+  // downdate form (the update step as printed; projected in the chain)
+  GatherSpec g;
+  if (p.downdate) {
+    g.src = u.X;
+    g.src64 = u.x64;
+    g.lds = u.ldx;
+    g.v64 = 1;
+  } else {
+    g.src = u.R;
+    g.src64 = p.r64;
+    g.lds = p.ldr;
+    g.v64 = !p.f32;
+  }
+  g.src0 = u.r_from_x ? u.X : nullptr;  // the first block reads X in place of R
+  g.lds0 = u.ldx;
+  g.V = u.V;
+  g.ldv = p.ldq;
+  g.d = d;
+  // sampling step: S_t (two-stage sampler; the exact sampler runs only if it asks for it),
   // or, in the forced pass, the next rows of the given skeleton list
   if (p.forced) {
     LK(launch_forced_take(u.forced_list, u.forced_count, u.S_t, st, p.b, s));
+    if (p.downdate)
+      LK(launch_gather(const_cast<void*>(u.X), u.x64, u.ldx, u.S_t, u.V, 1, p.ldq, d, p.b, st, s));
+    else
+      LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
   } else {
-    if (!p.exact_sampler) LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, s));
-    LK(launch_sample(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.S_t, st, p.exact_sampler, s));
+    int exact_always = p.exact_sampler;
+    if (!exact_always)
+      LK(launch_sample2(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.samp2, u.S_t, st, g, &exact_always, s));
+    LK(launch_sample_exact(u.dvec, n, p.b, p.greedy, o->seed, o->problem, u.ca, u.cb, u.samp2, u.S_t, st,
+                           exact_always, g, s));
   }
-  // projection step: V = R(S_t,:) re-orthogonalised against Q twice (CGS2)
-  if (p.downdate)  // projection step as printed: V = X(S_t, :), projected below
-    LK(launch_gather(const_cast<void*>(u.X), u.x64, u.ldx, u.S_t, u.V, 1, p.ldq, d, p.b, st, s));
-  else
-    LK(launch_gather(u.R, p.r64, p.ldr, u.S_t, u.V, !p.f32, p.ldq, d, p.b, st, s));
   return enqueue_chain(p, u, o, s);
 }
 
@@ -499,7 +523,7 @@ cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
         ce = launch_downdate_f32((float*)u.L, p.ldl, n, u.mark, u.dvec, u.part, p.nparts, st, s);
       return ce;
     }));
-    LK(launch_finalize_block(u.part, p.nparts, st, s));
+    LK(launch_finalize_block(u.part, p.nparts, st, s, u.loop_h, u.loop));
     return cudaSuccess;
   }
   // update step (residual form): Lhat = R Q'^T, R -= Lhat Q', d_i = ||R_i||^2
@@ -514,14 +538,15 @@ cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
       cudaError_t ce = cudaSuccess;
       for (int c0 = 0; c0 < (int)p.ldpt && ce == cudaSuccess; c0 += cw)
         ce = launch_update_tf32((float*)u.R, p.ldr, n, d, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt,
-                                (float*)u.L, p.ldl, u.mark, u.dvec, u.part, st, cw, split, c0, s);
+                                (float*)u.L, p.ldl, u.mark, u.dvec, u.part, st, cw, split, c0, s,
+                                u.r_from_x ? (const float*)u.X : nullptr, u.ldx);
       return ce;
     }));
-    LK(launch_finalize_block(u.part, update_tf32_parts(n, cw, split), st, s));
+    LK(launch_finalize_block(u.part, update_tf32_parts(n, cw, split), st, s, u.loop_h, u.loop));
     return cudaSuccess;
   }
   LK(timed(g_prof.upd, s, [&] { return enqueue_update_simt(p, u, s); }));
-  LK(launch_finalize_block(u.part, p.nparts, st, s));
+  LK(launch_finalize_block(u.part, p.nparts, st, s, u.loop_h, u.loop));
 #undef LK
   return cudaSuccess;
 }
@@ -633,8 +658,8 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
 
 // ---------------------------------------------------------------- device-side block loop
 // The blocks of Alg. 2 run as one CUDA graph: a while node whose body is one block
-// (captured from enqueue_block) followed by k_loop_cond, which sets the node's
-// condition from the State's stopping test.  The host launches the graph once and
+// (captured from enqueue_block), whose last kernel (the block's finalisation) sets
+// the node's condition from the State's stopping test.  The host launches the graph once and
 // reads the State once after the loop; nothing of the loop comes back to the host.
 // Graphs are cached per (device, buffers, sizes, options): the captured kernels hold
 // the workspace and output pointers and the plan's sizes (the tolerance lives in the
@@ -692,8 +717,10 @@ cudaError_t loop_graph(const Plan& p, const Bufs& u, const rbrp_opts* o, const L
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                           cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    cudaError_t be = enqueue_block(p, u, o, cs);
-    if (be == cudaSuccess) be = launch_loop_cond(h, u.st, cs);
+    Bufs ul = u;  // the block's last kernel sets the condition
+    ul.loop_h = h;
+    ul.loop = 1;
+    cudaError_t be = enqueue_block(p, ul, o, cs);
     cudaGraph_t got = nullptr;
     e = cudaStreamEndCapture(cs, &got);
     if (be != cudaSuccess) e = be;
@@ -745,10 +772,16 @@ rbrp_status run(const void* X, int x_is_fp64, long long n, long long d, long lon
   u.X = X;
   u.x64 = x_is_fp64 ? 1 : 0;
   u.ldx = ldx;
+  // Alg. 2's start R = X: on the FP32 tensor-core update paths the first block reads X
+  // itself (sampler gather and update), so no copy of X is made; elsewhere R is a copy
+  u.r_from_x = (!p.downdate && !forced && !p.r64 && !x_is_fp64 && (p.prec == RBRP_TF32 || p.prec == RBRP_TF32X3) &&
+                (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0)
+                   ? 1
+                   : 0;
   State* st = u.st;
-  // Alg. 2, start and initial norms (the residual form also copies X into R)
-  CK(launch_init_norms(X, x_is_fp64, n, d, ldx, p.downdate ? nullptr : u.R, p.r64, p.ldr, u.dvec, u.mark, u.part,
-                       p.nparts, st, s));
+  // Alg. 2, start and initial norms (with the copy of X into R where one is made)
+  CK(launch_init_norms(X, x_is_fp64, n, d, ldx, (p.downdate || u.r_from_x) ? nullptr : u.R, p.r64, p.ldr, u.dvec,
+                       u.mark, u.part, p.nparts, st, s));
   CK(launch_finish_init(u.part, p.nparts, st, tol, o->tau_b, p.k_cap, s));
   CK(launch_sample_clear(u.samp2, n, s));
   CK(cudaMemsetAsync(u.cnt, 0, (size_t)kSgemmCounters * 4, s));

@@ -118,6 +118,19 @@ __device__ __forceinline__ double philox_uniform(unsigned long long row, unsigne
 }
 
 // Order-preserving map of a double to an unsigned 64-bit key.
+// The TF32 value nearest x (ties away from zero), returned as an FP32 value that
+// the MMA reads exactly.  The 3xTF32 splits take hi = tf32_rn(x) and
+// lo = tf32_rn(x - hi): with rounding, lo is signed and centred on zero, so the
+// terms the split drops (lo*lo and the rounding of lo) carry no bias.  A
+// truncating split (low bits cleared) leaves lo with the sign of x and shrinks
+// every product by ~1e-6 relative; the downdate d_i - ||Lhat_i||^2 (Alg. 2,
+// update step as printed) turns that into a one-sided error in d.
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ unsigned long long orderable(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
@@ -230,11 +243,33 @@ cudaError_t launch_sample(const double* dvec, long long n, int b, int greedy, un
                           State* st, int force, cudaStream_t s, long long row_base = 0,
                           unsigned long long* keys_out = nullptr);
 size_t sample_scratch_pairs(long long n, int b);
+// Rows gathered into V once S_t is known (the projection step's V = R(S_t, :), or
+// X(S_t, :) in the downdate form).
+struct GatherSpec {
+  const void* src;  // FP32 or FP64 rows, leading dimension lds
+  long long lds;
+  const void* src0;  // (optional) the rows read by the first block instead (same type), ld lds0
+  long long lds0;
+  void* V;          // FP32 or FP64 rows, leading dimension ldv (nullptr: no gather)
+  long long ldv;
+  long long d;
+  int src64, v64;
+};
 // Two-stage sampler (k_sample.cu): FP32 log-domain cut + exact FP64 ranking of
-// the candidates; sets State::sample_fallback when the exact tree sampler
-// (launch_sample, which then runs) must draw the block instead.
+// the candidates, then the gather of V; sets State::sample_fallback when the
+// exact sampler (launch_sample_exact, always enqueued after it) must draw the
+// block instead.  *exact_always = 1 (and nothing enqueued) when the device has no
+// cooperative launches: the exact sampler then draws every block.
 cudaError_t launch_sample2(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
-                           unsigned long long problem, void* scratch, long long* S_t, State* st, cudaStream_t s);
+                           unsigned long long problem, void* scratch, long long* S_t, State* st,
+                           const GatherSpec& g, int* exact_always, cudaStream_t s);
+// Exact FP64 sampler in one launch (k_sample.cu) with the gather of V; draws the
+// block when force or State::sample_fallback is set, else returns at once.
+// cand_a, cand_b: sample_scratch_pairs(n, b) pairs each; scratch: the two-stage
+// sampler's (its merge counter).
+cudaError_t launch_sample_exact(const double* dvec, long long n, int b, int greedy, unsigned long long seed,
+                                unsigned long long problem, void* cand_a, void* cand_b, void* scratch, long long* S_t,
+                                State* st, int force, const GatherSpec& g, cudaStream_t s);
 cudaError_t launch_sample_clear(void* scratch, long long n, cudaStream_t s);
 size_t sample2_scratch_bytes(long long n);
 cudaError_t launch_gather(const void* R, int r_is_fp64, long long ldr, const long long* S_t, void* V, int v_is_fp64,
@@ -290,11 +325,12 @@ cudaError_t launch_downdate_f32(float* L, long long ldl, long long n, const int*
 cudaError_t launch_norms_zero(void* R, int r_is_fp64, long long ldr, long long n, long long d,
                               const int* mark, double* dvec, double* partials, int nparts,
                               const State* st, cudaStream_t s);
-cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s);
-// Device-side loop control (the last kernel of the captured block): sets the while
-// node's condition to "another block" unless the stopping test ended the loop, and
-// ends it after k_cap + 2 iterations in any case (no block can run more often).
-cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, State* st, cudaStream_t s);
+// loop != 0: inside the device-side block loop (the last kernel of the captured
+// block), also sets the while node's condition h to "another block" unless the
+// stopping test ended the loop, and ends it after k_cap + 2 iterations in any case
+// (no block can run more often).
+cudaError_t launch_finalize_block(const double* partials, int nparts, State* st, cudaStream_t s,
+                                  cudaGraphConditionalHandle h = 0, int loop = 0);
 cudaError_t launch_copy_cols_to_f64(const void* L, int l_is_fp64, long long ldl, long long n,
                                     long long c0, long long c1, double* W, long long ldw,
                                     cudaStream_t s);
@@ -336,10 +372,13 @@ constexpr int kSgemmCounters = 4096;
 // orthonormal, so R - (R Q'^T) Q' is the same as applying its column chunks one
 // after the other, and a block wider than one launch takes several (the last
 // launch's norms and partial sums are the block's; launches past b' return at once).
+// X0 (optional; FP32, ldx0 a multiple of 4, 16-byte aligned): the input, read in
+// place of R by the first block's first launch, so R = X is never copied.
 cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp,
                                const float* Qp_lo, long long ldp, const float* QpT, const float* QpT_lo,
                                long long ldpt, float* L, long long ldl, const int* mark, double* dvec,
-                               double* partials, const State* st, int bmax, int split, int c0, cudaStream_t s);
+                               double* partials, const State* st, int bmax, int split, int c0, cudaStream_t s,
+                               const float* X0 = nullptr, long long ldx0 = 0);
 int update_tf32_parts(long long n, int bmax, int split);
 // The downdate form in 3xTF32 (update step as printed): Lhat = X Q'^T for every row
 // of the FP32 input X (read only) into L(:, k + c0 ...), columns c0 .. c0 + bmax - 1

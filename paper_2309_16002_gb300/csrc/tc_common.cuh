@@ -159,8 +159,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// hi = x with the 13 low mantissa bits cleared (exactly representable in TF32).
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // Offset of the 16-byte chunk `ch` of row `r` inside a 128-byte-swizzled tile.
 __device__ __forceinline__ uint32_t swz(int r, int ch) {
