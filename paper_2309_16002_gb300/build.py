@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "librbrp.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["k_common.cu", "k_filter.cu", "k_sample.cu", "k_sgemm.cu", "k_batched.cu", "k_update_tc.cu", "k_wsolve_tc.cu", "k_lupp.cu", "rbrp_api.cu"]
+SOURCES = ["k_common.cu", "k_filter.cu", "k_sample.cu", "k_sgemm.cu", "k_batched.cu", "k_update_tc.cu", "k_wsolve_tc.cu", "k_wsolve_rl.cu", "k_lupp.cu", "rbrp_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

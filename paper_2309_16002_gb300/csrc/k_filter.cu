@@ -473,47 +473,93 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
   }
 }
 
-// The same filter for blocks of at most 64 candidates, built around latency:
-// one warp, no block-wide barrier.  Right-looking: lane l holds columns l and
-// l + 32 of the Schur complement (the Gram matrix minus the factor so far) in
-// registers.  Each step takes the trailing mass (a warp sum) and the pivot (the
-// largest remaining d_r > 0, ties to the smaller index: redux.sync max over the
-// FP32 bit patterns, which order like the values for d_r >= 0, then min over the
-// indices of the maxima), and stops at the first step whose trailing mass fails
-// the truncation test of Alg. 2; the pivot's owner then publishes its scaled
-// column l = S(:, p) / sqrt(d_p) through shared memory and every lane applies
-// the rank-1 update S(:, r) -= l l_r to its two columns.  The kernel writes the
-// pivot-order factor Lc; Q'_V = Lc^{-1} V_perm follows as a column-parallel
-// substitution (k_trsm_rows_f32).
+// The same filter for blocks of at most 64 candidates, built around latency: the
+// factorisation runs in one warp with no block-wide barrier.  Right-looking: lane l
+// holds columns l and l + 32 of the Schur complement (the Gram matrix minus the factor
+// so far) in registers.  Each step takes the trailing mass (a warp sum) and the pivot
+// (the largest remaining d_r > 0, ties to the smaller index: redux.sync max over the
+// FP32 bit patterns, which order like the values for d_r >= 0, then the lowest set
+// bit of a ballot of the maxima), and stops at the first step whose trailing mass
+// fails the truncation test of Alg. 2; the pivot's owner publishes its column
+// c = S(:, p) through shared memory, every lane forms l_r = c_r / sqrt(d_p) for its
+// two candidates and applies the rank-1 update S(j, r) -= c_j c_r / d_p to its two
+// columns.  The next step's reductions depend only on the downdated diagonal, so
+// they are issued before the 128 multiply-adds of the update and their latency
+// overlaps it.  The kernel writes the pivot-order factor Lc; Q'_V = Lc^{-1} V_perm
+// follows as a column-parallel substitution (k_trsm_rows_f32).
 constexpr int kPchol64 = 64;
-constexpr int kPchol64Threads = 32;
-constexpr int kPchol64LDF = 68;  // factor rows: float4 steps over t
+constexpr int kPchol64Threads = 32;   // the factorisation: one warp
+constexpr int kPchol64Sum = 256;      // the Gram partial sums: the whole CTA
+constexpr int kPchol64LDF = 68;       // factor rows: float4 steps over t
 
-__global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* __restrict__ G, long long ldg,
-                                                                  float* __restrict__ Lc_out, long long ldl,
-                                                                  int* __restrict__ perm,
-                                                                  const long long* __restrict__ S_t,
-                                                                  long long* __restrict__ skel,
-                                                                  int* __restrict__ mark, State* st) {
+__global__ void __launch_bounds__(kPchol64Sum) k_pchol_f32_64(const float* __restrict__ G, long long ldg,
+                                                              const float* __restrict__ gram, int ntn,
+                                                              float* __restrict__ Lc_out, long long ldl,
+                                                              int* __restrict__ perm,
+                                                              const long long* __restrict__ S_t,
+                                                              long long* __restrict__ skel,
+                                                              int* __restrict__ mark, State* st) {
   pdl_wait();
   if (st->done) return;
-  __shared__ __align__(16) float Lw[kPchol64 * kPchol64LDF];  // Lw[j * LDF + t]: candidate j, step t
+  // Gs: the Gram matrix (rows = columns, by symmetry), then the factor L (row j =
+  // candidate j, column t = step t) once the columns are in registers
+  __shared__ __align__(16) float Gs[kPchol64 * kPchol64LDF];
   __shared__ int s_perm[kPchol64];
-  __shared__ __align__(16) float lv[kPchol64];  // the pivot's factor column, published each step
+  __shared__ __align__(16) float lv[kPchol64];  // the pivot's Schur column, published each step
   const int m = (int)st->b_t;
+  // the Gram matrix: the sum of the column-tile partials (in tile order) that the CGS
+  // product left, or G itself; every thread of the CTA takes part, sixteen entries
+  // each, with the loads of four partials of all sixteen in flight together (the
+  // partials come from L2, and a chain of dependent round trips would dominate)
+  {
+    constexpr int E = kPchol64 * kPchol64 / kPchol64Sum;  // entries per thread
+    constexpr int T = 4;                                   // partials per round
+    float v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = 0.f;
+    if (gram) {
+      for (int t0 = 0; t0 < ntn; t0 += T) {
+        float x[T][E];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+          for (int q = 0; q < E; ++q)
+            x[t][q] = (t0 + t < ntn) ? gram[(size_t)(t0 + t) * (kPchol64 * kPchol64) + threadIdx.x + q * kPchol64Sum]
+                                     : 0.f;
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+          for (int q = 0; q < E; ++q) v[q] += x[t][q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int e = threadIdx.x + q * kPchol64Sum, r = e >> 6, c = e & 63;
+      if (!gram) v[q] = (r < m && c < m) ? G[(long long)r * ldg + c] : 0.f;
+      Gs[r * kPchol64LDF + c] = (r < m && c < m) ? v[q] : 0.f;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x >= kPchol64Threads) return;
   const int lane = threadIdx.x;
   const int c0 = lane, c1 = lane + 32;
-  // lane l holds columns l and l + 32 of the Schur complement (= rows, by symmetry)
-  float col0[kPchol64], col1[kPchol64];
+  float col0[kPchol64], col1[kPchol64];  // S(:, c0), S(:, c1) = rows c0, c1 of the symmetric Gram matrix
 #pragma unroll
-  for (int j = 0; j < kPchol64; ++j) {
-    col0[j] = (j < m && c0 < m) ? G[(long long)j * ldg + c0] : 0.f;
-    col1[j] = (j < m && c1 < m) ? G[(long long)j * ldg + c1] : 0.f;
+  for (int j = 0; j < kPchol64; j += 4) {
+    const float4 x = *(const float4*)(Gs + c0 * kPchol64LDF + j);
+    const float4 y = *(const float4*)(Gs + c1 * kPchol64LDF + j);
+    col0[j] = x.x;
+    col0[j + 1] = x.y;
+    col0[j + 2] = x.z;
+    col0[j + 3] = x.w;
+    col1[j] = y.x;
+    col1[j + 1] = y.y;
+    col1[j + 2] = y.z;
+    col1[j + 3] = y.w;
   }
-  // the diagonal entries, read directly (a lane-dependent index into col0 / col1
-  // would move those arrays out of registers)
-  float d0 = (c0 < m) ? G[(long long)c0 * ldg + c0] : 0.f;
-  float d1 = (c1 < m) ? G[(long long)c1 * ldg + c1] : 0.f;
+  float d0 = Gs[c0 * kPchol64LDF + c0], d1 = Gs[c1 * kPchol64LDF + c1];
+  __syncwarp();
+  float* Lw = Gs;  // reused for the factor
   for (int e = lane; e < kPchol64 * kPchol64LDF; e += kPchol64Threads) Lw[e] = 0.f;
   double tau_b = st->tau_b;
   if (tau_b < 0.0) tau_b = (m > 0) ? 1.0 / (double)m : 1.0;
@@ -522,54 +568,62 @@ __global__ void __launch_bounds__(kPchol64Threads) k_pchol_f32_64(const float* _
   float total = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-  __syncwarp();
-  int steps = 0;
-  for (int i = 0; i < m; ++i) {
-    float ms = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
+  // the trailing mass and the pivot of the coming step, from the diagonal alone
+  float ms;
+  unsigned mx, p;
+  auto reduce = [&]() {
+    ms = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, o);
     const unsigned b0 = (a0 && d0 > 0.f) ? __float_as_uint(d0) : 0u;
     const unsigned b1 = (a1 && d1 > 0.f) ? __float_as_uint(d1) : 0u;
-    const unsigned bl = b1 > b0 ? b1 : b0;          // this lane's better column (ties: the smaller index c0)
-    const unsigned il = b1 > b0 ? (unsigned)c1 : (unsigned)c0;
-    const unsigned mx = __reduce_max_sync(0xffffffffu, bl);
-    const unsigned p = __reduce_min_sync(0xffffffffu, (bl == mx && mx != 0u) ? il : 0xffffffffu);
+    mx = __reduce_max_sync(0xffffffffu, b1 > b0 ? b1 : b0);
+    const unsigned lo = __ballot_sync(0xffffffffu, mx != 0u && b0 == mx);  // candidates 0..31 at the maximum
+    const unsigned hi = __ballot_sync(0xffffffffu, mx != 0u && b1 == mx);  // candidates 32..63
+    p = lo ? (unsigned)(__ffs(lo) - 1) : (hi ? (unsigned)(31 + __ffs(hi)) : 0xffffffffu);
+  };
+  __syncwarp();
+  reduce();
+  int steps = 0;
+  for (int i = 0; i < m; ++i) {
     if (mx == 0u || !(ms >= tb * total && ms > 0.f)) break;  // the same on every lane; b' = i
     const float rinv = rsqrtf(__uint_as_float(mx));
-    if (lane == (int)(p & 31u)) {  // the pivot's owner publishes l = S(:, p) / sqrt(d_p)
+    const float rdp = rinv * rinv;
+    if (lane == (int)(p & 31u)) {  // the pivot's owner publishes c = S(:, p)
       if (p < 32u) {
 #pragma unroll
-        for (int j = 0; j < kPchol64; j += 4)
-          *(float4*)(lv + j) = make_float4(col0[j] * rinv, col0[j + 1] * rinv, col0[j + 2] * rinv, col0[j + 3] * rinv);
+        for (int j = 0; j < kPchol64; j += 4) *(float4*)(lv + j) = make_float4(col0[j], col0[j + 1], col0[j + 2], col0[j + 3]);
       } else {
 #pragma unroll
-        for (int j = 0; j < kPchol64; j += 4)
-          *(float4*)(lv + j) = make_float4(col1[j] * rinv, col1[j + 1] * rinv, col1[j + 2] * rinv, col1[j + 3] * rinv);
+        for (int j = 0; j < kPchol64; j += 4) *(float4*)(lv + j) = make_float4(col1[j], col1[j + 1], col1[j + 2], col1[j + 3]);
       }
     }
     __syncwarp();
-    const float l0 = lv[c0], l1 = lv[c1];
+    const float cr0 = lv[c0], cr1 = lv[c1];
+    const float l0 = cr0 * rinv, l1 = cr1 * rinv;
     if (a0) Lw[c0 * kPchol64LDF + i] = l0;
     if (a1) Lw[c1 * kPchol64LDF + i] = l1;
     if ((unsigned)c0 == p) a0 = false;
     if ((unsigned)c1 == p) a1 = false;
     d0 -= l0 * l0;
     d1 -= l1 * l1;
-    // rank-1 update of both columns: S(j, r) -= l_j l_r
+    if (lane == 0) s_perm[i] = (int)p;
+    steps = i + 1;
+    reduce();  // the next step's, overlapping the update below
+    // rank-1 update of both columns: S(j, r) -= c_j c_r / d_p
+    const float f0 = cr0 * rdp, f1 = cr1 * rdp;
 #pragma unroll
     for (int j = 0; j < kPchol64; j += 4) {
       const float4 l4 = *(const float4*)(lv + j);
-      col0[j] = fmaf(-l4.x, l0, col0[j]);
-      col0[j + 1] = fmaf(-l4.y, l0, col0[j + 1]);
-      col0[j + 2] = fmaf(-l4.z, l0, col0[j + 2]);
-      col0[j + 3] = fmaf(-l4.w, l0, col0[j + 3]);
-      col1[j] = fmaf(-l4.x, l1, col1[j]);
-      col1[j + 1] = fmaf(-l4.y, l1, col1[j + 1]);
-      col1[j + 2] = fmaf(-l4.z, l1, col1[j + 2]);
-      col1[j + 3] = fmaf(-l4.w, l1, col1[j + 3]);
+      col0[j] = fmaf(-l4.x, f0, col0[j]);
+      col0[j + 1] = fmaf(-l4.y, f0, col0[j + 1]);
+      col0[j + 2] = fmaf(-l4.z, f0, col0[j + 2]);
+      col0[j + 3] = fmaf(-l4.w, f0, col0[j + 3]);
+      col1[j] = fmaf(-l4.x, f1, col1[j]);
+      col1[j + 1] = fmaf(-l4.y, f1, col1[j + 1]);
+      col1[j + 2] = fmaf(-l4.z, f1, col1[j + 2]);
+      col1[j + 3] = fmaf(-l4.w, f1, col1[j + 3]);
     }
-    if (lane == 0) s_perm[i] = (int)p;
-    steps = i + 1;
     __syncwarp();  // every lane has read lv before the next pivot's owner overwrites it
   }
   const int bp = steps;
@@ -683,14 +737,16 @@ cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm
 
 int filter_f32_writes_factor(int b) { return b <= kPchol64; }
 
-cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Lout, long long ldl,
-                              int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s) {
+cudaError_t launch_filter_f32(const float* G, long long ldg, const float* gram, int ntn, const long long* S_t,
+                              float* Lout, long long ldl, int* perm, long long* skel, int* mark, int b, State* st,
+                              cudaStream_t s) {
   float* Linv = Lout;  // the factor for b <= 64, its inverse above
   if (b > kRegCholMax) return cudaErrorInvalidValue;
   if (b <= kPchol64) {
-    return counted(launch_pdl(k_pchol_f32_64, dim3(1), dim3(kPchol64Threads), 0, s, G, ldg, Linv, ldl, perm, S_t,
-                              skel, mark, st));
+    return counted(launch_pdl(k_pchol_f32_64, dim3(1), dim3(kPchol64Sum), 0, s, G, ldg, gram, ntn, Linv, ldl, perm,
+                              S_t, skel, mark, st));
   }
+  if (gram) return cudaErrorInvalidValue;  // (Gram partials only for b <= 64)
   const int ldf = (b + 4) & ~3;
   const size_t smem = (size_t)2 * b * ldf * sizeof(float);
   if (smem > 48 * 1024) {

@@ -267,12 +267,11 @@ __global__ void __launch_bounds__(256) k_sgemm_cl(SgemmArgs g) {
   TS* C = (TS*)g.C + dim_val(g.c_off);
   const long long kb = (long long)blockIdx.z * g.kc;
   const long long ke = (kb + g.kc < K) ? kb + g.kc : K;
-  __shared__ __align__(16) float As[KS][LD];
-  __shared__ __align__(16) float Bs[KS][LD];
+  __shared__ __align__(16) float AB[2][KS][LD];  // operand stages; then this CTA's rows of the result
   __shared__ float P[TILE * LP];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float acc[R][R];
-  tile_product<TS, float, BKC, TILE>(g, A, B, M, N, m0, n0, kb, ke, As, Bs, acc);
+  tile_product<TS, float, BKC, TILE>(g, A, B, M, N, m0, n0, kb, ke, AB[0], AB[1], acc);
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
@@ -281,19 +280,42 @@ __global__ void __launch_bounds__(256) k_sgemm_cl(SgemmArgs g) {
   const int cs = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int rows = TILE / cs;
   const TS alpha = (TS)g.alpha, beta = (TS)g.beta;
+  float* Vred = &AB[0][0][0];  // rows [rank rows, (rank + 1) rows) of the result tile (Gram form)
   for (int e = tid; e < rows * TILE; e += 256) {
     const int r = rank * rows + e / TILE, c = e % TILE;
     float v = 0.f;
     for (int z = 0; z < cs; ++z) v += cluster.map_shared_rank(P, z)[r * LP + c];
     const long long gm = m0 + r, gn = n0 + c;
+    float out = 0.f;
     if (gm < M && gn < N) {
       TS* cp = C + gm * g.ldc + gn;
       TS w = alpha * (TS)v;
       if (g.beta != 0.0) w += beta * *cp;
       *cp = w;
+      out = (float)w;
     }
+    if (g.gram) Vred[e] = out;
   }
   cluster.sync();
+  if (!g.gram) return;
+  // Gram partial of this column tile: the whole 64 x 64 result tile into P (read from
+  // the cluster's CTAs), then this CTA's rows of T T^T; every row pair is summed over
+  // c in the same order, so the partial is exactly symmetric
+  for (int e = tid; e < TILE * TILE; e += 256) {
+    const int r = e / TILE, c = e % TILE, z = r / rows;
+    P[r * LP + c] = cluster.map_shared_rank(Vred, z)[(r - z * rows) * TILE + c];
+  }
+  cluster.sync();  // every CTA has copied the others' rows
+  float* gt = g.gram + (size_t)blockIdx.x * (TILE * TILE);
+  for (int e = tid; e < rows * TILE; e += 256) {
+    const int i = rank * rows + e / TILE, j = e % TILE;
+    const float* pi = P + i * LP;
+    const float* pj = P + j * LP;
+    float sum = 0.f;
+#pragma unroll 8
+    for (int c = 0; c < TILE; ++c) sum = fmaf(pi[c], pj[c], sum);
+    gt[i * TILE + j] = sum;
+  }
 }
 
 }  // namespace

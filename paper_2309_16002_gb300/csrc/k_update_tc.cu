@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "rbrp_internal.cuh"
@@ -674,6 +675,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     uint32_t g = 0, gj = 0, it = 0;
     bool ok = true;
+    double part = 0.0;  // this warp's rows over the CTA's tiles, in its tile order
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
       const long long row = ptile(tile) * PROWS + r;
       const bool in = row < n;
@@ -745,8 +747,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
       double t = in ? (double)nrm : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) partials[4 * ptile(tile) + q] = t;
+      part += t;
     }
+    // one partial per (CTA, lane quarter): the block's finalisation sums 4 x grid values
+    if (lane == 0) partials[4 * blockIdx.x + q] = part;
   } else if (warp == 8) {
     // ---------------- stores of finished R pieces; one bulk store is kept reading while the
     // next is issued, and a stage is released once the store after it has been issued
@@ -804,6 +808,20 @@ __global__ void __launch_bounds__(kPThreads, 1)
   }
 }
 
+// SM count of the current device (asked once per device): the persistent grid, and
+// with it the number of partial sums the update leaves.
+int device_sms() {
+  static std::atomic<int> sms[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (sms[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 152;
+    sms[dev] = v;
+  }
+  return sms[dev];
+}
+
 template <int BMAX>
 cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long qrows,
                         long long ldp, const float* QpT, long long qtcols, long long ldpt, float* L, long long ldl,
@@ -825,8 +843,7 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
   if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sms();
   const long long ntiles = (n + PROWS - 1) / PROWS;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
   return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT, L,
@@ -900,10 +917,14 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
 
 }  // namespace tc
 
-// Partial sums the update leaves for launch_finalize_block: 4 per 128-row tile
-// (persistent form) or 2 per 64-row tile.
+// Partial sums the update leaves for launch_finalize_block: 4 per CTA of the
+// persistent form (one CTA per SM, at most one per 128-row tile), or 2 per 64-row tile.
 int update_tf32_parts(long long n, int bmax, int split) {
-  if (!split && bmax <= 64) return 4 * (int)((n + tc::PROWS - 1) / tc::PROWS);
+  if (!split && bmax <= 64) {
+    const long long ntiles = (n + tc::PROWS - 1) / tc::PROWS;
+    const long long grid = std::min<long long>(ntiles, tc::device_sms());
+    return 4 * (int)grid;
+  }
   return 2 * (int)((n + tc::ROWS - 1) / tc::ROWS);
 }
 

@@ -81,8 +81,8 @@ struct Plan {
   size_t pm, pn;  // split-K partial buffer extents (elements per split)
   size_t partial_elems;
   size_t off_R, off_L, off_Q, off_d, off_mark, off_part, off_state, off_St, off_ca, off_cb, off_V, off_Y, off_C,
-      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_Wh, off_Wl, off_Gh, off_Gl,
-      off_samp2, off_cnt, total;
+      off_G, off_Lc, off_perm, off_gp, off_Qp, off_QpT, off_Qplo, off_QpTlo, off_L1, off_Wh, off_Gh, off_Gl,
+      off_samp2, off_cnt, off_gram, total;
 };
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -143,7 +143,7 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int
   p->ldc = round_up(kc, 8);
   p->ldg = p->b;
   p->ldlc = kMaxBlock;
-  p->ldw32 = round_up(kc, 32);
+  p->ldw32 = round_up(kc, 64);  // whole 64-column blocks of the read-back copy
   p->ldt = round_up(kc, 32);
   {
     long long np = (n + 7) / 8;
@@ -206,11 +206,11 @@ rbrp_status make_plan(long long n, long long d, const rbrp_opts* o, Plan* p, int
   p->off_QpTlo = take(p->prec == RBRP_TF32X3 ? (size_t)p->ldq * p->ldpt * 4 : 0);
   p->off_L1 = take((size_t)kc * kc * 8);
   p->off_Wh = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
-  p->off_Wl = take(p->w32 ? (size_t)n * p->ldw32 * 4 : 0);
   p->off_Gh = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->off_Gl = take(p->w32 ? (size_t)kc * p->ldt * 4 : 0);
   p->off_samp2 = take(sample2_scratch_bytes(n));
   p->off_cnt = take((size_t)kSgemmCounters * 4);
+  p->off_gram = take((p->f32 && filter_f32_writes_factor(p->b)) ? (size_t)((d + 63) / 64) * 4096 * 4 : 0);
   p->total = off;
   return RBRP_OK;
 }
@@ -251,10 +251,10 @@ struct Bufs {
   float* QpT_lo;
   double* L1;
   float* Wh;
-  float* Wl;
   float* Gh;
   float* Gl;
   void* samp2;
+  float* gram32;  // FP32 path, b <= 64: Gram partials of the CGS product's column tiles
   unsigned* cnt;
   long long* skel;
   const long long* forced_list;  // forced pass: the skeletons in order
@@ -291,10 +291,10 @@ Bufs carve(const Plan& p, void* ws) {
   u.QpT_lo = (p.prec == RBRP_TF32X3) ? (float*)(b + p.off_QpTlo) : nullptr;
   u.L1 = (double*)(b + p.off_L1);
   u.Wh = p.w32 ? (float*)(b + p.off_Wh) : nullptr;
-  u.Wl = p.w32 ? (float*)(b + p.off_Wl) : nullptr;
   u.Gh = p.w32 ? (float*)(b + p.off_Gh) : nullptr;
   u.Gl = p.w32 ? (float*)(b + p.off_Gl) : nullptr;
   u.samp2 = b + p.off_samp2;
+  u.gram32 = (float*)(b + p.off_gram);
   u.cnt = (unsigned*)(b + p.off_cnt);
   u.skel = nullptr;
   u.forced_list = nullptr;
@@ -332,9 +332,10 @@ template <typename TS, typename TACC, bool BKC>
 cudaError_t sgemm(const Plan& p, const Bufs& u, const void* A, DimRef a_off, long long lda, const void* B,
                   DimRef b_off, long long ldb, void* C, DimRef c_off, long long ldc, DimRef M, DimRef N, DimRef K,
                   long long Mmax, long long Nmax, long long Kmax, double alpha, double beta, cudaStream_t s,
-                  const int* b_rows = nullptr) {
+                  const int* b_rows = nullptr, float* gram = nullptr) {
   SgemmArgs g;
   g.b_rows = b_rows;
+  g.gram = gram;
   g.A = A;
   g.a_off = a_off;
   g.lda = lda;
@@ -357,7 +358,7 @@ cudaError_t sgemm(const Plan& p, const Bufs& u, const void* A, DimRef a_off, lon
     // FP32 accumulation: split-K reduced inside a thread-block cluster
     int cs = 1, kcl = 32;
     sgemm_cluster(Mmax, Nmax, Kmax, 160, &cs, &kcl);
-    if (cs > 1) {
+    if (cs > 1 || gram) {  // (the Gram partials come from the cluster form only)
       g.kc = kcl;
       return launch_sgemm_cluster<TS, BKC>(g, Mmax, Nmax, cs, s);
     }
@@ -384,7 +385,8 @@ cudaError_t sgemm(const Plan& p, const Bufs& u, const void* A, DimRef a_off, lon
 // it at FP64 level.  The FP64 path, and any path with the FP64 chain
 // (RBRP_CHAIN_FP64), keeps FP64 products throughout.
 template <typename TS, typename TACC>
-cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, void* V, DimRef voff, DimRef rows, cudaStream_t s) {
+cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, void* V, DimRef voff, DimRef rows, cudaStream_t s,
+                       float* gram = nullptr) {
   const State* st = u.st;
   const long long kc = p.k_cap, b = p.b;
   // C = V Qt^T  (rows x k)
@@ -393,15 +395,16 @@ cudaError_t cgs_pass_t(const Plan& p, const Bufs& u, void* V, DimRef voff, DimRe
   if (e != cudaSuccess) return e;
   // V -= C Qt
   return sgemm<TS, TACC, false>(p, u, u.C, dim_const(0), p.ldc, u.Qt, dim_const(0), p.ldq, V, voff, p.ldq, rows,
-                                dim_const(p.d), dim_dev(&st->k), b, p.d, kc, -1.0, 1.0, s);
+                                dim_const(p.d), dim_dev(&st->k), b, p.d, kc, -1.0, 1.0, s, nullptr, gram);
 }
 
 // V (rows [0, rows) at V + voff, leading dimension ldq) <- V - (V Qt^T) Qt over Qt rows [0, k).
 // FP32 storage and products on the plain TF32 path; FP64 storage with FP32
 // products on the other mixed paths; FP64 throughout on the FP64 path.
+// gram (FP32 path, b <= 64): also the Gram partials of the result's column tiles.
 cudaError_t cgs_pass(const Plan& p, const Bufs& u, void* V, DimRef rows, cudaStream_t s,
-                     DimRef voff = dim_const(0)) {
-  if (p.f32) return cgs_pass_t<float, float>(p, u, V, voff, rows, s);
+                     DimRef voff = dim_const(0), float* gram = nullptr) {
+  if (p.f32) return cgs_pass_t<float, float>(p, u, V, voff, rows, s, gram);
   if (p.chain64) return cgs_pass_t<double, double>(p, u, V, voff, rows, s);
   return cgs_pass_t<double, float>(p, u, V, voff, rows, s);
 }
@@ -467,17 +470,22 @@ cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
   // (one pass on the plain TF32 path: the sampled residual rows are orthogonal
   // to Q up to the TF32 rounding of the update, and one FP32 pass already takes
   // that to the FP32 floor, which a second FP32 pass cannot lower)
-  LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
-  if (!p.f32) LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
   // local CPQR and truncation: G = V V^T, pivoted Cholesky with the tail-mass truncation
+  // (on the FP32 path with b <= 64 the CGS product leaves the Gram partials of its
+  // column tiles, which the filter sums)
+  const bool gram_fused = p.f32 && filter_f32_writes_factor((int)p.b);
+  LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s, dim_const(0), gram_fused ? u.gram32 : nullptr));
+  if (!p.f32) LK(cgs_pass(p, u, u.V, dim_dev(&st->b_t), s));
   if (p.f32) {
     // FP32 chain: Gram, filter with Lc^{-1}, Q'_V = Lc^{-1} V_perm as one
     // product.  Q'_V is a combination of rows already projected off Q, so its
     // component in span(Q) stays ~cond(Lc) times the FP32 floor, far below the
     // TF32 rounding of the update; it is not projected again.
-    LK((sgemm<float, float, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0), p.ldg,
-                                  dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
-    LK(launch_filter_f32((const float*)u.G, p.ldg, u.S_t, (float*)u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
+    if (!gram_fused)
+      LK((sgemm<float, float, true>(p, u, u.V, dim_const(0), p.ldq, u.V, dim_const(0), p.ldq, u.G, dim_const(0),
+                                    p.ldg, dim_dev(&st->b_t), dim_dev(&st->b_t), dim_const(d), b, b, d, 1.0, 0.0, s)));
+    LK(launch_filter_f32((const float*)u.G, p.ldg, gram_fused ? u.gram32 : nullptr, (int)((d + 63) / 64), u.S_t,
+                         (float*)u.Lc, p.ldlc, u.perm, u.skel, u.mark, p.b, st, s));
     if (filter_f32_writes_factor((int)p.b))  // also writes the update's copies of Q' (no k_qp_lowp)
       LK(launch_trsm_rows_f32((const float*)u.Lc, p.ldlc, u.perm, (const float*)u.V, p.ldq, (float*)u.Qt,
                               dim_dev(&st->k, p.ldq), p.ldq, d, u.Qp, p.ldp, u.QpT, p.ldpt, (int)p.ldpt, st, s));
@@ -635,7 +643,7 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
   } else if (!sink) {
     // FP32 solve on tensor cores (3xTF32): every 64-column block of W is one
     // product with the precomputed block-inverse factor, then W(S, :) = I.
-    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, n, true,
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, n, true,
                         k, u.st, s));
     CK(launch_w_identity_rows(W, ldw, k, skel, 0, n, s));  // W(S, :) = I exactly
   } else {
@@ -643,11 +651,11 @@ rbrp_status solve_w(const Plan& p, const Bufs& u, long long k, const long long* 
     // each finished with its skeleton rows set to I and handed to the sink.
     const long long tile = wsolve_tc_rows_per_tile();
     const long long chunk = std::max(tile, (sink->chunk_rows + tile - 1) / tile * tile);
-    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, 0, true,
+    CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, 0, 0, true,
                         k, u.st, s));
     for (long long r0 = 0; r0 < n; r0 += chunk) {
       const long long r1 = std::min(n, r0 + chunk);
-      CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, u.Wl, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, r0, r1,
+      CK(launch_wsolve_tc(u.L, p.l64, p.ldl, u.Wh, p.ldw32, W, ldw, u.L1, k, u.Gh, u.Gl, p.ldt, n, r0, r1,
                           false, k, u.st, s));
       CK(launch_w_identity_rows(W, ldw, k, skel, r0, r1, s));
       CK(sink->done(sink->ctx, r0, r1, k, s));

@@ -86,6 +86,10 @@ struct SgemmArgs {
   const int* b_rows;  // C = A B only: row r of B is row b_rows[r] of the array (null: r)
   int kc;             // K per split, a multiple of 32
   const State* st;    // kernels return at once when st->done (if non-null)
+  // (FP32 cluster form with one M tile of 64 rows, optional) the Gram partial of every
+  // 64-column tile tn of the result: gram[tn * 4096 + i * 64 + j] = sum over the tile's
+  // columns c of C(i, c) C(j, c), rows past M and columns past N as zeros
+  float* gram = nullptr;
 };
 
 // ---------------------------------------------------------------- Philox4x64-10
@@ -289,8 +293,11 @@ int filter_f32_writes_factor(int b);
 cudaError_t launch_trsm_rows_f32(const float* Lc, long long ldl, const int* perm, const float* V, long long ldv,
                                  float* Y, DimRef y_off, long long ldy, long long d, float* Qp, long long ldp,
                                  float* QpT, long long ldpt, int qrows, const State* st, cudaStream_t s);
-cudaError_t launch_filter_f32(const float* G, long long ldg, const long long* S_t, float* Lout, long long ldl,
-                              int* perm, long long* skel, int* mark, int b, State* st, cudaStream_t s);
+// gram (b <= 64, optional): the Gram matrix as ntn partials of 64 x 64 (SgemmArgs::gram),
+// summed in order, in place of G.
+cudaError_t launch_filter_f32(const float* G, long long ldg, const float* gram, int ntn, const long long* S_t,
+                              float* Lout, long long ldl, int* perm, long long* skel, int* mark, int b, State* st,
+                              cudaStream_t s);
 cudaError_t launch_chol(const double* G, long long ldg, double* Lc, long long ldl, int b,
                         State* st, cudaStream_t s);
 // Forced acceptance: the b_t candidates in the given order, no pivoting, no truncation.
@@ -390,18 +397,20 @@ cudaError_t launch_lhat_tf32x3(const float* X, long long ldx, long long n, long 
 // Columns of Q' per launch for a block of b'_pad <= ldpt columns.
 int update_tf32_chunk(int ldpt, int split);
 
-// Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu): W (n x k) from
-// L (FP32 or FP64, leading dimension ldl) and L1 = L(S, :) (FP64, k x k, ld1).
-// Wh/Wl (n x ldw32 FP32 scratch) receive W split into TF32 hi/lo; Gh/Gl
-// (k x ldt FP32 scratch) the transposed block-inverse factor G.  W64 (n x k
-// FP64, leading dimension ldw64) receives the result; rows of S are not set.
-// form_g launches the G factor first; rows [r0, r1) of W are then solved
-// (r0 a multiple of wsolve_tc_rows_per_tile(); r1 <= r0 solves none), so the
-// rows can be produced in several launches after one G.
-cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* Wh, float* Wl, long long ldw32,
-                             double* W64, long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl,
-                             long long ldt, long long n, long long r0, long long r1, bool form_g, long long k,
-                             State* st, cudaStream_t s);
+// Alg. 3 with an FP32 result on tensor cores (k_wsolve_tc.cu, k_wsolve_rl.cu): W
+// (n x k) from L (FP32 or FP64, leading dimension ldl) and L1 = L(S, :) (FP64,
+// k x k, ld1).  Wb (n x ldwb FP32 scratch, ldwb a multiple of 4 and >= k rounded
+// up to 64, 16-byte aligned) receives the exact FP32 W columns that a later panel
+// reads back (k > 512); Gh/Gl (k x ldt FP32 scratch) the transposed block-inverse
+// factor G split into TF32 hi/lo.  W64 (n x k FP64, leading dimension ldw64)
+// receives the result; rows of S are not set.  form_g launches the G factor
+// first; rows [r0, r1) of W are then solved (r0 a multiple of
+// wsolve_tc_rows_per_tile(); r1 <= r0 solves none), so the rows can be produced
+// in several launches after one G.
+cudaError_t launch_wsolve_tc(const void* L, int l_is_fp64, long long ldl, float* Wb, long long ldwb, double* W64,
+                             long long ldw64, const double* L1, long long ld1, float* Gh, float* Gl, long long ldt,
+                             long long n, long long r0, long long r1, bool form_g, long long k, State* st,
+                             cudaStream_t s);
 int wsolve_tc_rows_per_tile();
 
 // Batched form (k_batched.cu): one persistent launch over P small problems.

@@ -170,6 +170,8 @@ __device__ __forceinline__ uint32_t swz(int r, int ch) {
 // encoding failed.
 bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer, long long row_bytes, int box_inner,
               int box_outer, bool f64 = false);
+// Host: SM count of the current device (asked once per device).
+int device_sms();
 
 }  // namespace tc
 }  // namespace rbrp

@@ -76,8 +76,9 @@ def test_workspace_size_and_validation_on_host(libpath):
     with pytest.raises(rbrp.RBRPError):
         rbrp.rbrp_workspace_size(0, 10, o)
     # the FP64 chain beside the TF32 update: accepted, and it needs no less than the FP32 chain
+    # but for the FP32 chain's Gram partials (ceil(d / 64) tiles of 64 x 64 FP32)
     c64 = rbrp.rbrp_workspace_size(100000, 1000, rbrp.make_opts(block=64, precision="tf32", chain="fp64"))
-    assert c64 >= ws
+    assert c64 >= ws - 16 * 64 * 64 * 4
     bad = rbrp.make_opts(block=64, precision="tf32")
     bad.chain = 2
     with pytest.raises(rbrp.RBRPError):

@@ -160,14 +160,23 @@ def test_zero_and_nonfinite(G):
         _run(G, X.astype(np.float32), 1e-3, block=4, precision="tf32")
 
 
-@pytest.mark.parametrize("n,d,rate,tol,b", [(3001, 333, 0.97, 1e-8, 64), (777, 150, 0.9, 1e-8, 32),
-                                           (129, 100, 0.95, 1e-10, 16)])
-def test_w_fp32_tensor_core_solve_matches_fp64_solve(G, n, d, rate, tol, b):
-    """Alg. 3 in FP32 on tensor cores (3xTF32 products, fused triangular solve) against the FP64
-    solve on the same skeletons: k spans several 64-column blocks and n a ragged last tile."""
-    X, _ = WL.spectral(n=n, d=d, rate=rate, seed=n + d)
-    a = _run(G, X, tol, block=b, seed=5, precision="fp64", w_precision="fp64")
-    c = _run(G, X, tol, block=b, seed=5, precision="fp64", w_precision="fp32")
+@pytest.mark.parametrize("n,d,rate,tol,b,prec", [(3001, 333, 0.97, 1e-8, 64, "fp64"), (777, 150, 0.9, 1e-8, 32, "fp64"),
+                                                (129, 100, 0.95, 1e-10, 16, "fp64"),
+                                                (2000, 800, 0.987, 1e-8, 64, "fp64"),
+                                                (1500, 1200, 0.9915, 1e-8, 64, "fp64"),
+                                                (2000, 800, 0.9905, 1e-5, 64, "tf32"),
+                                                (60000, 300, 0.97, 1e-8, 64, "fp64"),
+                                                (40000, 800, 0.987, 1e-8, 64, "fp64"),
+                                                (40000, 800, 0.9905, 1e-5, 64, "tf32")])
+def test_w_fp32_tensor_core_solve_matches_fp64_solve(G, n, d, rate, tol, b, prec):
+    """Alg. 3 in FP32 on tensor cores (3xTF32 products) against the FP64 solve on the same
+    skeletons: k spans several 64-column blocks, one panel of tensor-memory accumulators
+    (k <= 512) or two and three (k ~ 700 and ~ 1100, the later panels reading W back), L in
+    FP64 (FP64 update) or FP32 (TF32 update), n a ragged last tile, and n large enough that a
+    CTA takes several tiles one after the other (the hand-over of shared memory between tiles)."""
+    X, _ = WL.spectral(n=n, d=d, rate=rate, seed=n + d, dtype=np.float64 if prec == "fp64" else np.float32)
+    a = _run(G, X, tol, block=b, seed=5, precision=prec, w_precision="fp64")
+    c = _run(G, X, tol, block=b, seed=5, precision=prec, w_precision="fp32")
     assert a["S"].tolist() == c["S"].tolist()
     assert np.max(np.abs(c["W"] - a["W"])) <= 1e-4 * max(1.0, np.max(np.abs(a["W"])))
     ea, ec = _e(X, a["S"], a["W"]), _e(X, c["S"], c["W"])
