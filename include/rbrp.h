@@ -291,27 +291,41 @@ rbrp_status rbrp_id_batched(int32_t P, const void *const *X, const int64_t *m, c
  * keeps all of them alive and unchanged until rbrp_batch_destroy).  The
  * handle allocates only host memory.
  *
- * rbrp_batch_run queues one solve of every problem to tolerance tol on
- * `stream`: a 4-byte memset of the work counter and one kernel launch, no
- * host synchronisation and no host-to-device copy, so it may be captured in a
- * CUDA graph (the graph then replays the solve with that tol; outputs are
- * rewritten in full on every run).  Runs on one handle must not overlap on
- * the GPU (they share the workspace).
+ * Buckets: the problems are split by shape into at most two buckets, those
+ * with n > 128 columns and those with n <= 128 (empty buckets are dropped,
+ * wide first); each bucket is one persistent launch over its own work queue,
+ * with its own schedule and per-CTA slot size.
  *
- * Schedule: the kernel runs `threads` (256 or 512) threads per CTA with
- * `ctas_per_sm` (1 or 2) CTAs resident on every SM.  Results do not depend
- * on the schedule.  A new handle takes the schedule that rbrp_batch_autotune
- * last chose for a batch of the same shape in this process (same precision,
- * block, P, largest m and n, total elements), else 256 threads, one CTA per
- * SM.  rbrp_batch_autotune times every schedule that fits on the device
- * (one warm-up and `reps` timed runs of rbrp_batch_run each, CUDA events on
- * `stream`, synchronising the stream), keeps the fastest on the handle and
- * in the process-wide table, and returns its time per run in *best_ms (may
- * be NULL); it must not be called while `stream` is being captured, and it
- * overwrites the outputs (with the same values any run produces).
- * rbrp_batch_set_schedule returns RBRP_EINVAL for a schedule the device
- * cannot hold (shared memory or registers); rbrp_batch_get_schedule reports
- * the current one and the number of CTAs launched.
+ * rbrp_batch_run queues one solve of every problem to tolerance tol on
+ * `stream`: per bucket a 4-byte memset of its work counter and one kernel
+ * launch, no host synchronisation and no host-to-device copy, so it may be
+ * captured in a CUDA graph (the graph then replays the solve with that tol;
+ * outputs are rewritten in full on every run).  Runs on one handle must not
+ * overlap on the GPU (they share the workspace).
+ *
+ * Schedule of a bucket: `threads` (256 or 512) threads per CTA, `ctas_per_sm`
+ * (1 or 2) CTAs resident on every SM, and the row width `vec` of the row
+ * passes (the values of a row one lane holds: 8, for n <= 256, or 4, for n <=
+ * 128, half the registers and multiply-adds a row).  Results do not depend on
+ * the schedule.  A new handle takes, per bucket, the schedule that
+ * rbrp_batch_autotune last chose for a bucket of the same shape in this
+ * process (same precision, block, problem count, largest m and n, total
+ * elements), else 256 threads, one CTA per SM and the narrowest row width
+ * that holds the bucket's rows.  rbrp_batch_autotune times, bucket by bucket,
+ * every schedule that fits on the device (one warm-up and `reps` timed
+ * launches each, CUDA events on `stream`, synchronising the stream), keeps
+ * the fastest on the handle and in the process-wide table, and returns the
+ * sum over buckets of their times per run in *best_ms (may be NULL); it must
+ * not be called while `stream` is being captured, and it overwrites the
+ * outputs (with the same values any run produces).
+ * rbrp_batch_set_schedule sets (threads, ctas_per_sm) on every bucket, each
+ * with its narrowest row width; rbrp_batch_set_bucket_schedule sets bucket
+ * i's three values; both return RBRP_EINVAL for a schedule the device cannot
+ * hold (shared memory or registers) or a row width narrower than the
+ * bucket's rows.  rbrp_batch_get_schedule reports bucket 0's schedule and
+ * CTAs launched; rbrp_batch_buckets the number of buckets (0 for NULL);
+ * rbrp_batch_get_bucket bucket i's problem count, largest n, schedule and
+ * CTAs launched (any pointer may be NULL).
  *
  * Errors: as rbrp_id_batched; RBRP_EINVAL for a NULL handle, RBRP_ENOMEM if
  * the host handle cannot be allocated.
@@ -325,6 +339,11 @@ rbrp_status rbrp_batch_run(rbrp_batch h, double tol, rbrp_stream_t stream);
 rbrp_status rbrp_batch_autotune(rbrp_batch h, double tol, int32_t reps, rbrp_stream_t stream, float *best_ms);
 rbrp_status rbrp_batch_set_schedule(rbrp_batch h, int32_t threads, int32_t ctas_per_sm);
 rbrp_status rbrp_batch_get_schedule(rbrp_batch h, int32_t *threads, int32_t *ctas_per_sm, int32_t *ctas);
+int32_t rbrp_batch_buckets(rbrp_batch h);
+rbrp_status rbrp_batch_get_bucket(rbrp_batch h, int32_t i, int32_t *problems, int64_t *n_max, int32_t *threads,
+                                  int32_t *ctas_per_sm, int32_t *vec, int32_t *ctas);
+rbrp_status rbrp_batch_set_bucket_schedule(rbrp_batch h, int32_t i, int32_t threads, int32_t ctas_per_sm,
+                                           int32_t vec);
 void rbrp_batch_destroy(rbrp_batch h);
 
 /*

@@ -47,7 +47,6 @@ namespace bt {
 constexpr int kMaxWarps = kBatchMaxThreads / 32;
 constexpr int kSumLanes = 256;   // fixed partition of sums over rows
 constexpr int kCand = 1024;      // candidates the sampler ranks exactly
-constexpr int kRowVec = 8;       // values of a row per lane (n <= 256)
 
 // Offsets of one slot (bytes), for the batch maxima.
 struct Slot {
@@ -303,13 +302,13 @@ __device__ void sample_cut(const double* d, const int* mark, long long m, int bt
 // completely before it is written).  STREAM: src is read once (the input X),
 // with evict-first loads so that it does not push the residuals of the
 // resident problems out of L2.  No barrier inside; the caller synchronises.
-template <int NT, int RPW, bool BASIS, bool COEF, bool NORM, typename T, typename TS, bool STREAM = false>
+template <int NT, int RPW, int VEC, bool BASIS, bool COEF, bool NORM, typename T, typename TS, bool STREAM = false>
 __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* dst, long long ldd, long long nrows,
                              long long n, const T* B, int nb, T* coef, long long ldc, double* dn, const int* mark) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long long i0 = (long long)w * RPW; i0 < nrows; i0 += (long long)NW * RPW) {
-    T x[RPW][kRowVec], y[RPW][kRowVec];
+    T x[RPW][VEC], y[RPW][VEC];
     bool zero[RPW];
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
@@ -317,7 +316,7 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
       const long long si = (i < nrows) ? (rowmap ? (long long)rowmap[i] : i) : 0;
       zero[r] = mark && i < nrows && mark[i] != 0;  // read with the row, before any store of the group
 #pragma unroll
-      for (int u = 0; u < kRowVec; ++u) {
+      for (int u = 0; u < VEC; ++u) {
         const long long c = lane + 32 * u;
         if (i < nrows && c < n) x[r][u] = STREAM ? (T)__ldcs(src + si * ls + c) : (T)src[si * ls + c];
         else x[r][u] = (T)0;
@@ -326,9 +325,9 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
     }
     if (BASIS) {
       for (int j = 0; j < nb; ++j) {
-        T q[kRowVec];
+        T q[VEC];
 #pragma unroll
-        for (int u = 0; u < kRowVec; ++u) {
+        for (int u = 0; u < VEC; ++u) {
           const long long c = lane + 32 * u;
           q[u] = c < n ? B[(long long)j * n + c] : (T)0;
         }
@@ -337,7 +336,7 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
         for (int r = 0; r < RPW; ++r) {
           T acc = 0;
 #pragma unroll
-          for (int u = 0; u < kRowVec; ++u) acc += x[r][u] * q[u];
+          for (int u = 0; u < VEC; ++u) acc += x[r][u] * q[u];
           s[r] = acc;
         }
 #pragma unroll
@@ -347,7 +346,7 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
 #pragma unroll
         for (int r = 0; r < RPW; ++r) {
 #pragma unroll
-          for (int u = 0; u < kRowVec; ++u) y[r][u] -= s[r] * q[u];
+          for (int u = 0; u < VEC; ++u) y[r][u] -= s[r] * q[u];
           if (COEF && lane == 0 && i0 + r < nrows) coef[(long long)j * ldc + i0 + r] = s[r];
         }
       }
@@ -358,7 +357,7 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
       if (i >= nrows) break;
       T nr = 0;
 #pragma unroll
-      for (int u = 0; u < kRowVec; ++u) {
+      for (int u = 0; u < VEC; ++u) {
         const long long c = lane + 32 * u;
         if (c >= ldd) continue;
         const T v = (zero[r] || c >= n) ? (T)0 : y[r][u];  // columns n .. ldd - 1: zero padding
@@ -386,7 +385,7 @@ __device__ void project_rows(const TS* src, long long ls, const int* rowmap, T* 
 // c_ij = <R_i, Q'_j> from the original row, R_i -= sum_j c_ij Q'_j in
 // ascending j, coef[j * ldc + i] = c_ij, dn[i] = ||R_i||^2; rows with
 // mark[i] != 0 are zeroed (dn = 0).
-template <int NT>
+template <int NT, int VEC>
 __device__ void update_rows_oct(float* R, long long ldr, long long m, const float* Qs, int bp, float* coef,
                                 long long ldc, double* dn, const int* mark) {
   constexpr int NW = NT / 32;
@@ -397,9 +396,9 @@ __device__ void update_rows_oct(float* R, long long ldr, long long m, const floa
     const long long i = i0 + g;
     const bool valid = i < m;
     const bool zero = valid && mark[i] != 0;
-    float4 x[8], y[8];
+    float4 x[VEC], y[VEC];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < VEC; ++u) {
       const long long c = 4 * q + 32 * u;
       x[u] = (valid && c < ldr) ? *(const float4*)(R + i * ldr + c) : z4;
       y[u] = x[u];
@@ -411,7 +410,7 @@ __device__ void update_rows_oct(float* R, long long ldr, long long m, const floa
       // the registers for the row
       float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
+      for (int u = 0; u < VEC; u += 2) {
         const float4 q0 = (u < nu) ? *(const float4*)(qj + 32 * u) : z4;
         const float4 q1 = (u + 1 < nu) ? *(const float4*)(qj + 32 * u + 32) : z4;
         a0 = fmaf(x[u].x, q0.x, a0);
@@ -428,7 +427,7 @@ __device__ void update_rows_oct(float* R, long long ldr, long long m, const floa
       acc += __shfl_xor_sync(0xffffffffu, acc, 2);
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < VEC; ++u) {
         const float4 qv = (u < nu) ? *(const float4*)(qj + 32 * u) : z4;
         y[u].x = fmaf(-acc, qv.x, y[u].x);
         y[u].y = fmaf(-acc, qv.y, y[u].y);
@@ -439,7 +438,7 @@ __device__ void update_rows_oct(float* R, long long ldr, long long m, const floa
     }
     float nr = 0.f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < VEC; ++u) {
       const long long c = 4 * q + 32 * u;
       if (zero) y[u] = z4;
       if (valid && c < ldr) *(float4*)(R + i * ldr + c) = y[u];
@@ -457,21 +456,21 @@ __device__ void update_rows_oct(float* R, long long ldr, long long m, const floa
 
 // sm.G[i][j] = <V_i, V_j> for i, j < rows (V row-major, leading dimension n);
 // row i's values stay in registers while its warp walks j <= i.
-template <int NT, typename T>
+template <int NT, typename T, int VEC>
 __device__ void gram_rows(const T* V, int rows, long long n, Smem& sm) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = w; i < rows; i += NW) {
-    T x[kRowVec];
+    T x[VEC];
 #pragma unroll
-    for (int u = 0; u < kRowVec; ++u) {
+    for (int u = 0; u < VEC; ++u) {
       const long long c = lane + 32 * u;
       x[u] = c < n ? V[(long long)i * n + c] : (T)0;
     }
     for (int j = 0; j <= i; ++j) {
       T acc = 0;
 #pragma unroll
-      for (int u = 0; u < kRowVec; ++u) {
+      for (int u = 0; u < VEC; ++u) {
         const long long c = lane + 32 * u;
         acc += x[u] * (c < n ? V[(long long)j * n + c] : (T)0);
       }
@@ -634,9 +633,9 @@ __device__ double rows_sum(long long m, Smem& sm, F f) {
   return block_sum<NT>(part, sm);
 }
 
-template <int NT, typename T>
+template <int NT, typename T, int VEC>
 __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem& sm, T* sQp) {
-  constexpr int RPW = sizeof(T) == 4 ? 4 : 2;  // rows per warp group in the row passes
+  constexpr int RPW = sizeof(T) == 4 ? 4 : 2;   // rows per warp group in the row passes
   constexpr int RPW0 = sizeof(T) == 4 ? 8 : 4;  // the same for the pass over X (no basis)
   const int tid = threadIdx.x;
   const long long m = a.rows[p], n = a.cols[p];
@@ -657,10 +656,10 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
 
   // Alg. 2, start and initial norms: R = X and d_i = ||X_i||^2 in one pass over X
   if (a.x_is_fp64)
-    project_rows<NT, RPW0, false, false, true, T, double, true>((const double*)a.X[p], n, nullptr, R, ldr, m, n,
+    project_rows<NT, RPW0, VEC, false, false, true, T, double, true>((const double*)a.X[p], n, nullptr, R, ldr, m, n,
                                                                 (const T*)nullptr, 0, nullptr, 0, d, nullptr);
   else
-    project_rows<NT, RPW0, false, false, true, T, float, true>((const float*)a.X[p], n, nullptr, R, ldr, m, n,
+    project_rows<NT, RPW0, VEC, false, false, true, T, float, true>((const float*)a.X[p], n, nullptr, R, ldr, m, n,
                                                                (const T*)nullptr, 0, nullptr, 0, d, nullptr);
   for (long long i = tid; i < m; i += NT) mark[i] = 0;
   __syncthreads();
@@ -687,16 +686,16 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     // sampling step
     sample_cta<NT>(d, mark, m, bt, ne, t, a, a.pbase + (unsigned long long)p, K64, sm);
     // projection step: V = R(S_t, :) projected against Q twice (CGS2)
-    project_rows<NT, RPW, true, false, false, T, T>(R, ldr, sm.St, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
+    project_rows<NT, RPW, VEC, true, false, false, T, T>(R, ldr, sm.St, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
                                                     nullptr);
     __syncthreads();
     if (k > 0) {
-      project_rows<NT, RPW, true, false, false, T, T>(V, n, nullptr, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
+      project_rows<NT, RPW, VEC, true, false, false, T, T>(V, n, nullptr, V, n, bt, n, Q, (int)k, nullptr, 0, nullptr,
                                                       nullptr);
       __syncthreads();
     }
     // local CPQR and truncation: G = V V^T, pivoted Cholesky with the tail-mass truncation
-    gram_rows<NT, T>(V, bt, n, sm);
+    gram_rows<NT, T, VEC>(V, bt, n, sm);
     __syncthreads();
     const double tau_b = a.tau_b >= 0.0 ? a.tau_b : 1.0 / (double)bt;
     chol_warp<T>(sm, bt, tau_b, 1);
@@ -710,10 +709,10 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
       mark[row] = (int)t;
     }
     if (k > 0)
-      project_rows<NT, RPW, true, false, false, T, T>(Y, n, nullptr, Y, n, bp, n, Q, (int)k, nullptr, 0, nullptr,
+      project_rows<NT, RPW, VEC, true, false, false, T, T>(Y, n, nullptr, Y, n, bp, n, Q, (int)k, nullptr, 0, nullptr,
                                                       nullptr);
     __syncthreads();
-    gram_rows<NT, T>(Y, bp, n, sm);
+    gram_rows<NT, T, VEC>(Y, bp, n, sm);
     __syncthreads();
     chol_warp<T>(sm, bp, 0.0, 0);
     if (sm.bp < bp) {
@@ -733,9 +732,9 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
     // update step (residual form): Lhat = R Q'^T into L(:, k : k + b'), R -= Lhat Q',
     // d_i = ||R_i||^2, rows accepted so far zeroed
     if constexpr (sizeof(T) == 4)
-      update_rows_oct<NT>(R, ldr, m, sQp, bp, L + k * m, m, d, mark);
+      update_rows_oct<NT, VEC>(R, ldr, m, sQp, bp, L + k * m, m, d, mark);
     else
-      project_rows<NT, RPW, true, true, true, T, T>(R, ldr, nullptr, R, ldr, m, n, sQp, bp, L + k * m, m, d, mark);
+      project_rows<NT, RPW, VEC, true, true, true, T, T>(R, ldr, nullptr, R, ldr, m, n, sQp, bp, L + k * m, m, d, mark);
     __syncthreads();
     D = rows_sum<NT>(m, sm, [&](long long i) { return d[i]; });
     k += bp;
@@ -787,7 +786,7 @@ __device__ void solve_problem(const BatchedArgs& a, int p, uint8_t* slotp, Smem&
   __syncthreads();
 }
 
-template <int NT, typename T>
+template <int NT, typename T, int VEC>
 __global__ void __launch_bounds__(NT, kBatchMaxThreads / NT) k_batched(BatchedArgs a) {
   extern __shared__ __align__(16) uint8_t dyn[];
   Smem& sm = *(Smem*)dyn;
@@ -803,13 +802,20 @@ __global__ void __launch_bounds__(NT, kBatchMaxThreads / NT) k_batched(BatchedAr
     const int p = s_p;
     __syncthreads();
     if (p < 0) break;
-    solve_problem<NT, T>(a, p, slotp, sm, sQp);
+    solve_problem<NT, T, VEC>(a, p, slotp, sm, sQp);
   }
 }
 
-const void* pick(int threads, int fp64) {
-  if (threads == 256) return fp64 ? (const void*)k_batched<256, double> : (const void*)k_batched<256, float>;
-  if (threads == 512) return fp64 ? (const void*)k_batched<512, double> : (const void*)k_batched<512, float>;
+// The kernel for a schedule: CTA size, precision, and the row width of the row
+// passes (values a lane holds: 8 for n <= 256, 4 for n <= 128).
+const void* pick(int threads, int fp64, int vec) {
+  if (vec == 8) {
+    if (threads == 256) return fp64 ? (const void*)k_batched<256, double, 8> : (const void*)k_batched<256, float, 8>;
+    if (threads == 512) return fp64 ? (const void*)k_batched<512, double, 8> : (const void*)k_batched<512, float, 8>;
+  } else if (vec == 4) {
+    if (threads == 256) return fp64 ? (const void*)k_batched<256, double, 4> : (const void*)k_batched<256, float, 4>;
+    if (threads == 512) return fp64 ? (const void*)k_batched<512, double, 4> : (const void*)k_batched<512, float, 4>;
+  }
   return nullptr;
 }
 
@@ -831,19 +837,23 @@ size_t batched_dyn_smem(long long n_max, int fp64) {
   return (sizeof(bt::Smem) + 15) / 16 * 16 + (size_t)kBatchMaxBlock * ((n_max + 3) / 4 * 4) * (fp64 ? 8 : 4);
 }
 
-cudaError_t batched_configure(int threads, int fp64, long long n_max, int* per_sm) {
+cudaError_t batched_configure(int threads, int fp64, long long n_max, int vec, int* per_sm) {
   *per_sm = 0;
-  const void* f = bt::pick(threads, fp64);
+  const void* f = bt::pick(threads, fp64, vec);
   if (!f) return cudaErrorInvalidValue;
-  const size_t dyn = batched_dyn_smem(n_max, fp64);
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (n_max > 32LL * vec) return cudaSuccess;  // a row does not fit the row width: 0 CTAs
+  // the kernel's limit is a property of the function, shared by every bucket that
+  // launches it: set it for the widest rows the row width admits
+  const long long n_cap = std::min<long long>(kBatchMaxCols, 32LL * vec);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batched_dyn_smem(n_cap, fp64));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, threads, dyn);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, threads, batched_dyn_smem(n_max, fp64));
 }
 
-cudaError_t launch_batched(const BatchedArgs& a, int threads, int ctas, cudaStream_t s) {
-  const void* f = bt::pick(threads, a.fp64);
-  if (!f || ctas < 1) return cudaErrorInvalidValue;
+cudaError_t launch_batched(const BatchedArgs& a, int threads, int vec, int ctas, cudaStream_t s) {
+  const void* f = bt::pick(threads, a.fp64, vec);
+  if (!f || ctas < 1 || a.n_max > 32LL * vec) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.next, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   const size_t dyn = batched_dyn_smem(a.n_max, a.fp64);

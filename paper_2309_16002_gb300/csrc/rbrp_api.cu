@@ -959,11 +959,24 @@ rbrp_status rbrp_id(const void* X, int x_is_fp64, int64_t n, int64_t d, int64_t 
 
 namespace {
 
+// Per-shape buckets of a batch: problems with n > kBatchNarrow columns, then those with
+// n <= kBatchNarrow (the ones a row width of 4 values a lane can hold); each bucket is
+// its own persistent launch with its own schedule (CTA size, CTAs per SM, row width)
+// and slot size, the launches one after the other on the stream.
+constexpr long long kBatchNarrow = 128;
+constexpr int kBatchBuckets = 2;
 struct BatchPlan {
   long long m_max, n_max, kc_max, elems;
   int slots, fp64;
   size_t off_X, off_rows, off_cols, off_order, off_skel, off_W, off_next, slot, off_slots, total;
+  int nb;                                      // non-empty buckets
+  int bclass[kBatchBuckets];                   // their classes: 0 wide, 1 narrow
+  int bstart[kBatchBuckets], bcount[kBatchBuckets];  // their ranges in the processing order
+  long long bm[kBatchBuckets], bn[kBatchBuckets], bkc[kBatchBuckets], belems[kBatchBuckets];
+  size_t bslot[kBatchBuckets];
 };
+
+int batch_class(long long n) { return n > kBatchNarrow ? 0 : 1; }
 
 rbrp_status batch_plan(int32_t P, const int64_t* m, const int64_t* n, const rbrp_opts* o, BatchPlan* bp) {
   if (P < 0 || !o || !bp || (P > 0 && (!m || !n))) return RBRP_EINVAL;
@@ -982,7 +995,38 @@ rbrp_status batch_plan(int32_t P, const int64_t* m, const int64_t* n, const rbrp
     bp->elems += (long long)m[p] * n[p];
   }
   bp->fp64 = (o->precision == RBRP_FP64);
-  // one slot per CTA of the largest schedule (kBatchMaxCtasPerSm CTAs on every SM)
+  // the buckets, wide first
+  {
+    long long cm[kBatchBuckets] = {0, 0}, cn[kBatchBuckets] = {0, 0}, ckc[kBatchBuckets] = {0, 0},
+              ce[kBatchBuckets] = {0, 0};
+    int cnt[kBatchBuckets] = {0, 0};
+    for (int32_t p = 0; p < P; ++p) {
+      const int c = batch_class(n[p]);
+      long long kc = std::min<long long>(m[p], n[p]);
+      if (o->k_max > 0) kc = std::min<long long>(kc, o->k_max);
+      cm[c] = std::max<long long>(cm[c], m[p]);
+      cn[c] = std::max<long long>(cn[c], n[p]);
+      ckc[c] = std::max<long long>(ckc[c], kc);
+      ce[c] += (long long)m[p] * n[p];
+      ++cnt[c];
+    }
+    int start = 0;
+    for (int c = 0; c < kBatchBuckets; ++c) {
+      if (cnt[c] == 0) continue;
+      const int b = bp->nb++;
+      bp->bclass[b] = c;
+      bp->bstart[b] = start;
+      bp->bcount[b] = cnt[c];
+      bp->bm[b] = cm[c];
+      bp->bn[b] = cn[c];
+      bp->bkc[b] = ckc[c];
+      bp->belems[b] = ce[c];
+      bp->bslot[b] = batched_slot_bytes(cm[c], cn[c], ckc[c], o->block, bp->fp64);
+      start += cnt[c];
+    }
+  }
+  // one slot per CTA of the largest schedule (kBatchMaxCtasPerSm CTAs on every SM);
+  // a bucket of smaller problems fits more of its own slots in the same space
   bp->slots = std::max(1, std::min<int>(P, batched_sms() * kBatchMaxCtasPerSm));
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -1016,52 +1060,73 @@ struct TuneKey {
     return elems < o.elems;
   }
 };
+struct Sched {
+  int threads, per_sm, vec;
+};
 std::mutex g_tune_mu;
-std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;
+std::vector<std::pair<TuneKey, Sched>> g_tune_cache;
 
-bool tune_lookup(const TuneKey& k, int* threads, int* per_sm) {
+bool tune_lookup(const TuneKey& k, Sched* sc) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   for (auto& e : g_tune_cache)
     if (!(e.first < k) && !(k < e.first)) {
-      *threads = e.second.first;
-      *per_sm = e.second.second;
+      *sc = e.second;
       return true;
     }
   return false;
 }
 
-void tune_store(const TuneKey& k, int threads, int per_sm) {
+void tune_store(const TuneKey& k, const Sched& sc) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   for (auto& e : g_tune_cache)
     if (!(e.first < k) && !(k < e.first)) {
-      e.second = {threads, per_sm};
+      e.second = sc;
       return;
     }
-  g_tune_cache.push_back({k, {threads, per_sm}});
+  g_tune_cache.push_back({k, sc});
 }
 
 constexpr int kSchedThreads[] = {256, 512};
 
 }  // namespace
 
+struct BatchBucket {
+  BatchedArgs args;  // this bucket's queue (P, order, counter) and slot shape; tau set per run
+  TuneKey key;
+  int threads, per_sm, vec, ctas;
+  long long slots;   // slots of this bucket's size in the slot space
+};
+
 struct rbrp_batch_s {
   BatchPlan plan;
-  BatchedArgs args;  // tau set per run
-  TuneKey key;
-  int threads, per_sm, ctas;
+  int nb;
+  BatchBucket bk[kBatchBuckets];
 };
 
 namespace {
 
-// Makes (threads, per_sm) the handle's schedule if the kernel shape fits.
-rbrp_status apply_schedule(rbrp_batch_s* h, int threads, int per_sm) {
+// The narrowest row width that holds a row of the bucket.
+int default_vec(const BatchBucket& b) { return b.args.n_max <= 32LL * 4 ? 4 : 8; }
+
+// Makes (threads, per_sm, vec) bucket b's schedule if the kernel shape fits.
+rbrp_status apply_schedule(rbrp_batch_s* h, int b, int threads, int per_sm, int vec) {
+  if (b < 0 || b >= h->nb) return RBRP_EINVAL;
   if (per_sm < 1 || per_sm > kBatchMaxCtasPerSm) return RBRP_EINVAL;
+  BatchBucket& k = h->bk[b];
   int fit = 0;
-  CK(batched_configure(threads, h->plan.fp64, h->plan.n_max, &fit));
+  CK(batched_configure(threads, h->plan.fp64, k.args.n_max, vec, &fit));
   if (fit < per_sm) return RBRP_EINVAL;
-  h->threads = threads;
-  h->per_sm = per_sm;
-  h->ctas = std::max(1, std::min<int>(h->plan.slots, batched_sms() * per_sm));
+  k.threads = threads;
+  k.per_sm = per_sm;
+  k.vec = vec;
+  k.ctas = (int)std::max<long long>(1, std::min<long long>(k.slots, (long long)batched_sms() * per_sm));
+  return RBRP_OK;
+}
+
+rbrp_status run_bucket(rbrp_batch_s* h, int b, double tol, cudaStream_t s) {
+  BatchedArgs a = h->bk[b].args;
+  a.tau = tol;
+  CK(launch_batched(a, h->bk[b].threads, h->bk[b].vec, h->bk[b].ctas, s));
   return RBRP_OK;
 }
 
@@ -1102,9 +1167,13 @@ rbrp_status rbrp_batch_create(int32_t P, const void* const* X, const int64_t* m,
     cols[p] = n[p];
     order[p] = p;
   }
-  // largest problems first, so the last problems to start are short ones
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return rows[a] * cols[a] > rows[b] * cols[b]; });
+  // by bucket (wide, then narrow), largest problems first inside a bucket, so the
+  // last problems of a launch to start are short ones
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ca = batch_class(cols[a]), cb = batch_class(cols[b]);
+    if (ca != cb) return ca < cb;
+    return rows[a] * cols[a] > rows[b] * cols[b];
+  });
   CK(cudaMemcpyAsync(ws + bp.off_X, X, (size_t)P * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ws + bp.off_rows, rows.data(), (size_t)P * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ws + bp.off_cols, cols.data(), (size_t)P * 8, cudaMemcpyHostToDevice, s));
@@ -1116,7 +1185,7 @@ rbrp_status rbrp_batch_create(int32_t P, const void* const* X, const int64_t* m,
   rbrp_batch_s* h = new (std::nothrow) rbrp_batch_s();
   if (!h) return RBRP_ENOMEM;
   h->plan = bp;
-  BatchedArgs& a = h->args;
+  BatchedArgs a;
   a.P = P;
   a.X = (const void* const*)(ws + bp.off_X);
   a.rows = (const long long*)(ws + bp.off_rows);
@@ -1143,15 +1212,29 @@ rbrp_status rbrp_batch_create(int32_t P, const void* const* X, const int64_t* m,
   a.n_max = bp.n_max;
   a.kc_max = bp.kc_max;
   a.next = (unsigned int*)(ws + bp.off_next);
-  h->key = TuneKey{bp.fp64, o->block, (long long)P, bp.m_max, bp.n_max, bp.elems};
-  // schedule: the tuned one for this shape if any, else 256 threads, one CTA per SM
-  int th = 256, per = 1;
-  tune_lookup(h->key, &th, &per);
-  rs = apply_schedule(h, th, per);
-  if (rs != RBRP_OK) rs = apply_schedule(h, 256, 1);
-  if (rs != RBRP_OK) {
-    delete h;
-    return rs;
+  h->nb = bp.nb;
+  for (int b = 0; b < bp.nb; ++b) {
+    BatchBucket& k = h->bk[b];
+    k.args = a;
+    k.args.P = bp.bcount[b];
+    k.args.order = a.order + bp.bstart[b];
+    k.args.next = a.next + b;  // one work counter per bucket
+    k.args.m_max = bp.bm[b];
+    k.args.n_max = bp.bn[b];
+    k.args.kc_max = bp.bkc[b];
+    k.args.slot_bytes = bp.bslot[b];
+    k.slots = std::min<long long>(bp.bcount[b], (long long)((size_t)bp.slots * bp.slot / bp.bslot[b]));
+    k.key = TuneKey{bp.fp64, o->block, (long long)bp.bcount[b], bp.bm[b], bp.bn[b], bp.belems[b]};
+    // schedule: the tuned one for this bucket's shape if any, else 256 threads, one
+    // CTA per SM, the narrowest row width
+    Sched sc{256, 1, default_vec(k)};
+    tune_lookup(k.key, &sc);
+    rs = apply_schedule(h, b, sc.threads, sc.per_sm, sc.vec);
+    if (rs != RBRP_OK) rs = apply_schedule(h, b, 256, 1, default_vec(k));
+    if (rs != RBRP_OK) {
+      delete h;
+      return rs;
+    }
   }
   *out = h;
   return RBRP_OK;
@@ -1159,28 +1242,55 @@ rbrp_status rbrp_batch_create(int32_t P, const void* const* X, const int64_t* m,
 
 rbrp_status rbrp_batch_set_schedule(rbrp_batch h, int32_t threads, int32_t ctas_per_sm) {
   if (!h) return RBRP_EINVAL;
-  return apply_schedule(h, threads, ctas_per_sm);
+  for (int b = 0; b < h->nb; ++b) {
+    const rbrp_status rs = apply_schedule(h, b, threads, ctas_per_sm, default_vec(h->bk[b]));
+    if (rs != RBRP_OK) return rs;
+  }
+  return RBRP_OK;
 }
 
 rbrp_status rbrp_batch_get_schedule(rbrp_batch h, int32_t* threads, int32_t* ctas_per_sm, int32_t* ctas) {
   if (!h) return RBRP_EINVAL;
-  if (threads) *threads = h->threads;
-  if (ctas_per_sm) *ctas_per_sm = h->per_sm;
-  if (ctas) *ctas = h->ctas;
+  if (threads) *threads = h->bk[0].threads;
+  if (ctas_per_sm) *ctas_per_sm = h->bk[0].per_sm;
+  if (ctas) *ctas = h->bk[0].ctas;
   return RBRP_OK;
+}
+
+int32_t rbrp_batch_buckets(rbrp_batch h) { return h ? h->nb : 0; }
+
+rbrp_status rbrp_batch_get_bucket(rbrp_batch h, int32_t i, int32_t* problems, int64_t* n_max, int32_t* threads,
+                                  int32_t* ctas_per_sm, int32_t* vec, int32_t* ctas) {
+  if (!h || i < 0 || i >= h->nb) return RBRP_EINVAL;
+  const BatchBucket& k = h->bk[i];
+  if (problems) *problems = k.args.P;
+  if (n_max) *n_max = k.args.n_max;
+  if (threads) *threads = k.threads;
+  if (ctas_per_sm) *ctas_per_sm = k.per_sm;
+  if (vec) *vec = k.vec;
+  if (ctas) *ctas = k.ctas;
+  return RBRP_OK;
+}
+
+rbrp_status rbrp_batch_set_bucket_schedule(rbrp_batch h, int32_t i, int32_t threads, int32_t ctas_per_sm,
+                                           int32_t vec) {
+  if (!h) return RBRP_EINVAL;
+  return apply_schedule(h, i, threads, ctas_per_sm, vec);
 }
 
 rbrp_status rbrp_batch_run(rbrp_batch h, double tol, rbrp_stream_t stream) {
   if (!h) return RBRP_EINVAL;
   if (!(tol < 1.0)) return RBRP_EINVAL;
-  BatchedArgs a = h->args;
-  a.tau = tol;
-  CK(launch_batched(a, h->threads, h->ctas, (cudaStream_t)stream));
+  for (int b = 0; b < h->nb; ++b) {
+    const rbrp_status rs = run_bucket(h, b, tol, (cudaStream_t)stream);
+    if (rs != RBRP_OK) return rs;
+  }
   return RBRP_OK;
 }
 
 rbrp_status rbrp_batch_autotune(rbrp_batch h, double tol, int32_t reps, rbrp_stream_t stream, float* best_ms) {
   if (!h || reps < 1) return RBRP_EINVAL;
+  if (!(tol < 1.0)) return RBRP_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
@@ -1192,38 +1302,46 @@ rbrp_status rbrp_batch_autotune(rbrp_batch h, double tol, int32_t reps, rbrp_str
       return RBRP_ECUDA;
     }
   }
-  int best_t = h->threads, best_p = h->per_sm;
-  float best = -1.f;
   rbrp_status rs = RBRP_OK;
-  for (int th : kSchedThreads) {
-    for (int per = 1; per <= kBatchMaxCtasPerSm && rs == RBRP_OK; ++per) {
-      if (apply_schedule(h, th, per) != RBRP_OK) continue;  // shape does not fit
-      rs = rbrp_batch_run(h, tol, stream);                   // warm-up
-      cudaError_t e = cudaSuccess;
-      if (rs == RBRP_OK) e = cudaEventRecord(e0, s);
-      for (int r = 0; r < reps && rs == RBRP_OK && e == cudaSuccess; ++r) rs = rbrp_batch_run(h, tol, stream);
-      if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
-      if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        g_last_cuda = (int)e;
-        rs = RBRP_ECUDA;
-      }
-      if (rs == RBRP_OK && (best < 0.f || ms < best)) {
-        best = ms;
-        best_t = th;
-        best_p = per;
+  float total = 0.f;
+  // each bucket alone: every (CTA size, CTAs per SM, row width) that fits
+  for (int b = 0; b < h->nb && rs == RBRP_OK; ++b) {
+    BatchBucket& k = h->bk[b];
+    Sched best{k.threads, k.per_sm, k.vec};
+    float best_t = -1.f;
+    for (int th : kSchedThreads) {
+      for (int per = 1; per <= kBatchMaxCtasPerSm && rs == RBRP_OK; ++per) {
+        for (int vec : kBatchVecs) {
+          if (rs != RBRP_OK) break;
+          if (apply_schedule(h, b, th, per, vec) != RBRP_OK) continue;  // shape does not fit
+          rs = run_bucket(h, b, tol, s);                                 // warm-up
+          cudaError_t e = cudaSuccess;
+          if (rs == RBRP_OK) e = cudaEventRecord(e0, s);
+          for (int r = 0; r < reps && rs == RBRP_OK && e == cudaSuccess; ++r) rs = run_bucket(h, b, tol, s);
+          if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
+          if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (rs == RBRP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) {
+            g_last_cuda = (int)e;
+            rs = RBRP_ECUDA;
+          }
+          if (rs == RBRP_OK && (best_t < 0.f || ms < best_t)) {
+            best_t = ms;
+            best = Sched{th, per, vec};
+          }
+        }
       }
     }
+    if (rs != RBRP_OK) break;
+    rs = apply_schedule(h, b, best.threads, best.per_sm, best.vec);
+    if (rs == RBRP_OK) tune_store(k.key, best);
+    total += best_t / (float)reps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rs != RBRP_OK) return rs;
-  rs = apply_schedule(h, best_t, best_p);
-  if (rs != RBRP_OK) return rs;
-  tune_store(h->key, best_t, best_p);
-  if (best_ms) *best_ms = best / (float)reps;
+  if (best_ms) *best_ms = total;
   return RBRP_OK;
 }
 

@@ -443,12 +443,15 @@ struct BatchedArgs {
 size_t batched_slot_bytes(long long m_max, long long n_max, long long kc_max, int b, int fp64);
 int batched_sms();
 size_t batched_dyn_smem(long long n_max, int fp64);
-// Sets the kernel's shared-memory limit for (threads, precision, n_max) and
-// reports how many such CTAs fit on one SM (0: the shape cannot run).
-cudaError_t batched_configure(int threads, int fp64, long long n_max, int* per_sm);
+// Row widths of the batched kernel's row passes (values of a row a lane holds):
+// 8 (n <= 256) or 4 (n <= 128, half the registers and multiply-adds a row).
+constexpr int kBatchVecs[] = {8, 4};
+// Sets the kernel's shared-memory limit for (threads, precision, n_max, row width)
+// and reports how many such CTAs fit on one SM (0: the shape cannot run).
+cudaError_t batched_configure(int threads, int fp64, long long n_max, int vec, int* per_sm);
 // Zeroes the work counter and launches ctas CTAs of `threads` threads: two
 // stream operations and nothing else, so the call can be captured in a graph
 // (batched_configure must have run for this shape).
-cudaError_t launch_batched(const BatchedArgs& a, int threads, int ctas, cudaStream_t s);
+cudaError_t launch_batched(const BatchedArgs& a, int threads, int vec, int ctas, cudaStream_t s);
 
 }  // namespace rbrp

@@ -29,7 +29,7 @@ EXPORTS = ["rbrp_default_opts", "rbrp_workspace_size", "rbrp_id", "rbrp_host_wor
            "rbrp_status_string", "rbrp_last_cuda_error", "rbrp_profile_begin", "rbrp_profile_end",
            "rbrp_id_noalloc", "rbrp_batched_workspace_size", "rbrp_id_batched", "rbrp_batch_create",
            "rbrp_batch_run", "rbrp_batch_autotune", "rbrp_batch_set_schedule", "rbrp_batch_get_schedule",
-           "rbrp_batch_destroy", "rbrp_set_wait_limits", "rbrp_sketch_workspace_size", "rbrp_sketch_id",
+           "rbrp_batch_buckets", "rbrp_batch_get_bucket", "rbrp_batch_set_bucket_schedule", "rbrp_batch_destroy", "rbrp_set_wait_limits", "rbrp_sketch_workspace_size", "rbrp_sketch_id",
            "rbrp_set_loop_mode", "rbrp_shard_workspace_size", "rbrp_shard_create", "rbrp_shard_draw",
            "rbrp_shard_rows", "rbrp_shard_block", "rbrp_shard_l_rows", "rbrp_shard_w", "rbrp_shard_destroy"]
 
@@ -118,6 +118,12 @@ def load():
     P32 = ctypes.POINTER(ctypes.c_int32)
     L.rbrp_batch_get_schedule.argtypes = [vp, P32, P32, P32]
     L.rbrp_batch_get_schedule.restype = ctypes.c_int
+    L.rbrp_batch_buckets.argtypes = [vp]
+    L.rbrp_batch_buckets.restype = ctypes.c_int32
+    L.rbrp_batch_get_bucket.argtypes = [vp, ctypes.c_int32, P32, ctypes.POINTER(ctypes.c_int64), P32, P32, P32, P32]
+    L.rbrp_batch_get_bucket.restype = ctypes.c_int
+    L.rbrp_batch_set_bucket_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.rbrp_batch_set_bucket_schedule.restype = ctypes.c_int
     L.rbrp_batch_destroy.argtypes = [vp]
     L.rbrp_batch_destroy.restype = None
     L.rbrp_sketch_workspace_size.argtypes = [i64, i64, i64, i64, ctypes.POINTER(SketchOpts), ctypes.POINTER(sz)]
@@ -498,14 +504,33 @@ class Batch:
         return g
 
     def tune(self, tol, reps=2, stream=None):
-        """Time every schedule that fits, keep the fastest; returns the schedule and its ms per run."""
+        """Time every schedule that fits, bucket by bucket, keep the fastest; returns bucket 0's
+        schedule, the per-bucket schedules (buckets) and the ms per run summed over buckets."""
         best = ctypes.c_float(0.0)
         st = self._lib.rbrp_batch_autotune(self.h, float(tol), int(reps),
                                            ctypes.c_void_p(self._stream(stream).cuda_stream), ctypes.byref(best))
         _check(st, "rbrp_batch_autotune", allow_notconverged=False)
         out = self.schedule()
+        out["buckets"] = self.buckets()
         out["ms"] = float(best.value)
         return out
+
+    def buckets(self):
+        """Per-shape buckets: problems, largest n and schedule (threads, ctas_per_sm, vec, ctas) of each."""
+        out = []
+        for i in range(int(self._lib.rbrp_batch_buckets(self.h))):
+            pr, t, p, v, c = (ctypes.c_int32(0) for _ in range(5))
+            nm = ctypes.c_int64(0)
+            _check(self._lib.rbrp_batch_get_bucket(self.h, i, ctypes.byref(pr), ctypes.byref(nm), ctypes.byref(t),
+                                                   ctypes.byref(p), ctypes.byref(v), ctypes.byref(c)),
+                   "rbrp_batch_get_bucket", allow_notconverged=False)
+            out.append(dict(problems=pr.value, n_max=nm.value, threads=t.value, ctas_per_sm=p.value, vec=v.value,
+                            ctas=c.value))
+        return out
+
+    def set_bucket_schedule(self, i, threads, ctas_per_sm, vec):
+        _check(self._lib.rbrp_batch_set_bucket_schedule(self.h, int(i), int(threads), int(ctas_per_sm), int(vec)),
+               "rbrp_batch_set_bucket_schedule", allow_notconverged=False)
 
     def schedule(self):
         t, p, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)

@@ -196,6 +196,39 @@ def test_batch_schedules_graph_and_autotune_agree(G, precision):
     assert B2.schedule()["threads"] == info["threads"] and B2.schedule()["ctas_per_sm"] == info["ctas_per_sm"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_buckets_and_row_widths_agree(G, precision):
+    """The per-shape buckets (n > 128, then n <= 128) and every row width a bucket can take give
+    the one-shot results bit for bit; a row width narrower than a bucket's rows is refused."""
+    import torch
+    dt = np.float64 if precision == "fp64" else np.float32
+    Xs = [torch.from_numpy(np.ascontiguousarray(X)).to("cuda:0") for X in _problems(dt)]
+    ref = G.rbrp_id_batched(Xs, 1e-6, block=8, seed=9, precision=precision)
+    B = G.Batch(Xs, block=8, seed=9, precision=precision)
+    bk = B.buckets()
+    assert len(bk) == 2
+    assert sum(b["problems"] for b in bk) == len(Xs)
+    assert bk[0]["n_max"] > 128 and bk[1]["n_max"] <= 128
+    assert bk[0]["vec"] == 8 and bk[1]["vec"] == 4  # the narrowest width that holds the rows
+    with pytest.raises(G.RBRPError):
+        B.set_bucket_schedule(0, 256, 1, 4)  # the wide bucket's rows do not fit 4 values a lane
+    with pytest.raises(G.RBRPError):
+        B.set_bucket_schedule(2, 256, 1, 8)  # no such bucket
+    for vec in (8, 4):
+        for threads in (256, 512):
+            B.set_bucket_schedule(1, threads, 1, vec)
+            assert B.buckets()[1]["vec"] == vec and B.buckets()[1]["threads"] == threads
+            B.k_out.fill_(-1)
+            B.run(1e-6)
+            torch.cuda.synchronize()
+            for p, (o, r) in enumerate(zip(B.results(), ref)):
+                assert o["k"] == r["k"] and o["rel_err_sq"] == r["rel_err_sq"], (vec, threads, p)
+                assert torch.equal(o["S"], r["S"]) and torch.equal(o["W"], r["W"]), (vec, threads, p)
+    info = B.tune(1e-6, reps=1)
+    assert len(info["buckets"]) == 2 and info["ms"] > 0
+    assert info["buckets"][1]["vec"] in (4, 8) and info["buckets"][0]["vec"] == 8
+
+
 @pytest.mark.parametrize("sampler", ["random_exact", "greedy_exact", "greedy"])
 def test_batched_exact_sampler_and_tie_fallback(G, sampler):
     """The full FP64 ranking (forced, or reached when 2000 tied greedy keys overflow the
