@@ -477,9 +477,9 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
 // factorisation runs in one warp with no block-wide barrier.  Right-looking: lane l
 // holds columns l and l + 32 of the Schur complement (the Gram matrix minus the factor
 // so far) in registers.  Each step takes the trailing mass (a warp sum) and the pivot
-// (the largest remaining d_r > 0, ties to the smaller index: redux.sync max over the
-// FP32 bit patterns, which order like the values for d_r >= 0, then the lowest set
-// bit of a ballot of the maxima), and stops at the first step whose trailing mass
+// (the largest remaining d_r > 0, ties to the smaller index: a shuffle max over
+// 64-bit keys made of the FP32 bit pattern, which orders like the values for d_r >= 0,
+// and the complemented index), and stops at the first step whose trailing mass
 // fails the truncation test of Alg. 2; the pivot's owner publishes its column
 // c = S(:, p) through shared memory, every lane forms l_r = c_r / sqrt(d_p) for its
 // two candidates and applies the rank-1 update S(j, r) -= c_j c_r / d_p to its two
@@ -575,12 +575,20 @@ __global__ void __launch_bounds__(kPchol64Sum) k_pchol_f32_64(const float* __res
     ms = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, o);
+    // one 64-bit key per candidate, value bits above (63 - index): the largest key is the
+    // largest d_r, ties to the smaller index; five shuffle steps give value and index
     const unsigned b0 = (a0 && d0 > 0.f) ? __float_as_uint(d0) : 0u;
     const unsigned b1 = (a1 && d1 > 0.f) ? __float_as_uint(d1) : 0u;
-    mx = __reduce_max_sync(0xffffffffu, b1 > b0 ? b1 : b0);
-    const unsigned lo = __ballot_sync(0xffffffffu, mx != 0u && b0 == mx);  // candidates 0..31 at the maximum
-    const unsigned hi = __ballot_sync(0xffffffffu, mx != 0u && b1 == mx);  // candidates 32..63
-    p = lo ? (unsigned)(__ffs(lo) - 1) : (hi ? (unsigned)(31 + __ffs(hi)) : 0xffffffffu);
+    const unsigned long long k0 = ((unsigned long long)b0 << 32) | (unsigned)(63 - c0);
+    const unsigned long long k1 = ((unsigned long long)b1 << 32) | (unsigned)(63 - c1);
+    unsigned long long key = k1 > k0 ? k1 : k0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+      key = other > key ? other : key;
+    }
+    mx = (unsigned)(key >> 32);
+    p = mx ? (unsigned)(63 - (int)(key & 0xffffffffu)) : 0xffffffffu;
   };
   __syncwarp();
   reduce();

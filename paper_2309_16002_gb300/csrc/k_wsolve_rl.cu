@@ -16,7 +16,8 @@
 // whose first 64 columns (the next block) are issued first.  Each W block is
 // thus read by the tensor cores straight from shared memory once, instead of
 // being re-read for every block to its left; the B operand (rows of the
-// factors, K-major) streams from L2 in 128-column slices.  The products run
+// factors, K-major) streams from L2 in slices of up to 256 columns, hi and lo
+// halves in separate stages.  The products run
 // in the 3xTF32 form (hi*hi + hi*lo + lo*hi, about FP32 accuracy) with FP32
 // accumulators.  Panels right of the first one are separate launches, so the
 // W columns a panel reads back were written by an earlier launch.
@@ -40,7 +41,7 @@ namespace tc {
 constexpr int RM = 128;           // rows per tile (MMA M)
 constexpr int RB = 64;            // column block
 constexpr int RK = 32;            // K chunk: 128 bytes of FP32
-constexpr int RNS = 128;          // N slice of the products into the panel
+constexpr int RNS = 256;          // widest N slice of the products into the panel
 constexpr int RPW = 512;          // panel width = tensor-memory columns
 constexpr int RAS = 2;            // A-ring stages (in the space of the staged W block, see RCfg)
 constexpr int RBS = 5;            // B-ring stages
@@ -48,20 +49,25 @@ constexpr int kRThreads = 320;
 
 struct RCfg {
   static constexpr int A = RM * RK * 4;              // one half (hi or lo) of an A chunk: 16 KB
-  static constexpr int B = RNS * RK * 4;             // one half of a B chunk of 128 rows: 16 KB
-  static constexpr int B64 = RB * RK * 4;            // one half of a B chunk of 64 rows: 8 KB
+  static constexpr int B = RNS * RK * 4;             // one B stage: the hi or lo half of a chunk of <= 256 rows
   // The A ring (L chunks, W read back) is only used before the first W block of a
   // tile is staged, and the staged block only after the A chunks of the tile have
   // been consumed, so the two share 64 KB and the B ring gets five stages (160 KB
   // in flight covers the ~2 us a load from L2 takes under this traffic).
   static constexpr int F_OFF = 0;                    // the newest W block: [c0 hi][c0 lo][c1 hi][c1 lo]
   static constexpr int A_OFF = 0;                    // A ring: RAS x [hi][lo], aliasing F
-  static constexpr int B_OFF = 4 * A;                // B ring: RBS x [hi][lo]
-  static constexpr int BAR_OFF = B_OFF + RBS * 2 * B;
+  static constexpr int B_OFF = 4 * A;                // B ring: RBS stages, each a hi or a lo half
+  static constexpr int BAR_OFF = B_OFF + RBS * B;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
 static_assert(RCfg::SMEM <= 227 * 1024, "shared memory");
 static_assert(RAS * 2 * RCfg::A <= 4 * RCfg::A, "the A ring fits in the staged block's space");
+
+// Width of the next N slice of a product into [n0, n0 + rem) (rem a multiple of 64):
+// one tcgen05.mma of kind::tf32 holds the MMA issue for about the same time up to
+// N = 128 and N = 256 doubles the work per instruction, so slices are as wide as the
+// range allows.
+__host__ __device__ inline int slice_w(int rem) { return rem >= 256 ? 256 : (rem >= 128 ? 128 : 64); }
 
 // The panel [ps, pe) of a launch: blocks Jlo .. Jhi; wback: a later launch (a panel
 // to the left) reads this panel's W back, from the exact FP32 copy Wb.
@@ -72,6 +78,7 @@ struct RPanel {
 template <bool L64>
 __global__ void __launch_bounds__(kRThreads, 1)
     k_wsolve_rl(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmW,
+                const __grid_constant__ CUtensorMap tmG256h, const __grid_constant__ CUtensorMap tmG256l,
                 const __grid_constant__ CUtensorMap tmG128h, const __grid_constant__ CUtensorMap tmG128l,
                 const __grid_constant__ CUtensorMap tmG64h, const __grid_constant__ CUtensorMap tmG64l,
                 double* __restrict__ W64, long long ldw64, int w64_vec, float* __restrict__ Wb, long long ldwb,
@@ -152,16 +159,20 @@ __global__ void __launch_bounds__(kRThreads, 1)
         ++fa;
         return true;
       };
-      // B chunk: rows n0 .. of the factors (K-major), 128 or 64 of them, hi and lo
-      auto load_b = [&](bool wide, int x, int n0) {
-        const int s = (int)(gb % RBS);
-        if (!mbar_wait(b_empty(s), ((gb / RBS) & 1u) ^ 1u, abort, lim)) return false;
-        const uint32_t base = sb + C::B_OFF + s * 2 * C::B;
-        mbar_expect_tx(b_full(s), wide ? 2u * C::B : 2u * C::B64);
-        tma_load_2d_hint(base, wide ? &tmG128h : &tmG64h, b_full(s), x, n0, keep);
-        tma_load_2d_hint(base + C::B, wide ? &tmG128l : &tmG64l, b_full(s), x, n0, keep);
-        ++gb;
-        ++fb;
+      // B chunk: rows n0 .. n0 + w - 1 of the factors (K-major), its hi half into one
+      // stage and its lo half into the next
+      auto load_b = [&](int w, int x, int n0) {
+        for (int half = 0; half < 2; ++half) {
+          const int s = (int)(gb % RBS);
+          if (!mbar_wait(b_empty(s), ((gb / RBS) & 1u) ^ 1u, abort, lim)) return false;
+          const uint32_t base = sb + C::B_OFF + s * C::B;
+          const CUtensorMap* m = w == 256 ? (half ? &tmG256l : &tmG256h)
+                                          : (w == 128 ? (half ? &tmG128l : &tmG128h) : (half ? &tmG64l : &tmG64h));
+          mbar_expect_tx(b_full(s), (uint32_t)(w * RK * 4));
+          tma_load_2d_hint(base, m, b_full(s), x, n0, keep);
+          ++gb;
+          ++fb;
+        }
         return true;
       };
       uint32_t tp = 0;  // tiles of this CTA so far
@@ -177,12 +188,15 @@ __global__ void __launch_bounds__(kRThreads, 1)
           for (int kc = 0; kc < 2 && ok; ++kc) {
             const int x = J * RB + RK * kc;
             if (x >= k) break;
-            ok = load_a(&tmL, L64, x, y) && load_b(false, x, J * RB);
+            ok = load_a(&tmL, L64, x, y) && load_b(RB, x, J * RB);
           }
         // 2. D(:, panel) += W(:, pe ..) G(pe .., panel)
         for (int x = pe; x < k && ok; x += RK) {
           ok = load_a(&tmW, false, x, y);
-          for (int n0 = ps; n0 < pe && ok; n0 += RNS) ok = load_b(pe - n0 >= RNS, x, n0);
+          for (int n0 = ps, w = 0; n0 < pe && ok; n0 += w) {
+            w = slice_w(pe - n0);
+            ok = load_b(w, x, n0);
+          }
         }
         // 3. after W(:, J): the next block's 64 columns, then the rest of the panel
         for (int J = Jhi; J > Jlo && ok; --J) {
@@ -190,40 +204,52 @@ __global__ void __launch_bounds__(kRThreads, 1)
           for (int kc = 0; kc < 2 && ok; ++kc) {
             const int x = j0 + RK * kc;
             if (x >= k) break;
-            ok = load_b(false, x, j0 - RB);
+            ok = load_b(RB, x, j0 - RB);
           }
-          for (int n0 = ps; n0 < j0 - RB && ok; n0 += RNS)
+          for (int n0 = ps, w = 0; n0 < j0 - RB && ok; n0 += w) {
+            w = slice_w(j0 - RB - n0);
             for (int kc = 0; kc < 2 && ok; ++kc) {
               const int x = j0 + RK * kc;
               if (x >= k) break;
-              ok = load_b(j0 - RB - n0 >= RNS, x, n0);
+              ok = load_b(w, x, n0);
             }
+          }
         }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t id64 = idesc_tf32(RM, RB), id128 = idesc_tf32(RM, RNS);
       uint32_t ga = 0, gb = 0, nf = 0, it = 0;
       bool ok = true;
-      // 3xTF32 products of one K chunk (4 steps of 8): D += A_hi B_hi + A_hi B_lo + A_lo B_hi
-      auto mma3 = [&](uint32_t d, uint32_t a, uint32_t alo, uint32_t b, uint32_t blo, uint32_t id, bool first) {
-#pragma unroll
-        for (int kk = 0; kk < RK / 8; ++kk) {
-          mma_tf32(d, sdesc(a + kk * 32), sdesc(b + kk * 32), id, (first && kk == 0) ? 0u : 1u);
-          mma_tf32(d, sdesc(a + kk * 32), sdesc(blo + kk * 32), id, 1u);
-          mma_tf32(d, sdesc(alo + kk * 32), sdesc(b + kk * 32), id, 1u);
-        }
-      };
       auto wait_a = [&](int& s) {
         s = (int)(ga % RAS);
         const uint32_t ph = (ga / RAS) & 1u;
         return mbar_wait(a_full(s), ph, abort, lim) && mbar_wait(a_conv(s), ph, abort, lim);
       };
-      auto wait_b = [&](int& s) {
-        s = (int)(gb % RBS);
-        return mbar_wait(b_full(s), (gb / RBS) & 1u, abort, lim);
+      // 3xTF32 product of one K chunk (4 steps of 8) into D columns d .. d + w - 1:
+      // A_hi B_hi + A_lo B_hi from the B stage holding the hi half, then A_hi B_lo
+      // from the next stage (first: the first product into D, which overwrites it)
+      auto mma_chunk = [&](uint32_t d, uint32_t a, uint32_t alo, int w, bool first) {
+        const uint32_t id = idesc_tf32(RM, w);
+        for (int half = 0; half < 2; ++half) {
+          const int s = (int)(gb % RBS);
+          if (!mbar_wait(b_full(s), (gb / RBS) & 1u, abort, lim)) return false;
+          tc_after();
+          const uint32_t b = sb + C::B_OFF + s * C::B;
+#pragma unroll
+          for (int kk = 0; kk < RK / 8; ++kk) {
+            if (half == 0) {
+              mma_tf32(d, sdesc(a + kk * 32), sdesc(b + kk * 32), id, (first && kk == 0) ? 0u : 1u);
+              mma_tf32(d, sdesc(alo + kk * 32), sdesc(b + kk * 32), id, 1u);
+            } else {
+              mma_tf32(d, sdesc(a + kk * 32), sdesc(b + kk * 32), id, 1u);
+            }
+          }
+          mma_commit(b_empty(s));
+          ++gb;
+        }
+        return true;
       };
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         // the previous tile's accumulators have been read out
@@ -234,18 +260,19 @@ __global__ void __launch_bounds__(kRThreads, 1)
           for (int kc = 0; kc < 2; ++kc) {
             const int x = J * RB + RK * kc;
             if (x >= k) break;
-            int sa, sbb;
-            if (!wait_a(sa) || !wait_b(sbb)) {
+            int sa;
+            if (!wait_a(sa)) {
               ok = false;
               break;
             }
             tc_after();
-            const uint32_t a = sb + C::A_OFF + sa * 2 * C::A, b = sb + C::B_OFF + sbb * 2 * C::B;
-            mma3(tmem + (uint32_t)(J * RB - ps), a, a + C::A, b, b + C::B, id64, kc == 0);
+            const uint32_t a = sb + C::A_OFF + sa * 2 * C::A;
+            if (!mma_chunk(tmem + (uint32_t)(J * RB - ps), a, a + C::A, RB, kc == 0)) {
+              ok = false;
+              break;
+            }
             mma_commit(a_empty(sa));
-            mma_commit(b_empty(sbb));
             ++ga;
-            ++gb;
           }
         // 2. the W columns right of the panel
         for (int x = pe; x < k && ok; x += RK) {
@@ -254,18 +281,11 @@ __global__ void __launch_bounds__(kRThreads, 1)
             ok = false;
             break;
           }
+          tc_after();
           const uint32_t a = sb + C::A_OFF + sa * 2 * C::A;
-          for (int n0 = ps; n0 < pe; n0 += RNS) {
-            int sbb;
-            if (!wait_b(sbb)) {
-              ok = false;
-              break;
-            }
-            tc_after();
-            const uint32_t b = sb + C::B_OFF + sbb * 2 * C::B;
-            mma3(tmem + (uint32_t)(n0 - ps), a, a + C::A, b, b + C::B, pe - n0 >= RNS ? id128 : id64, false);
-            mma_commit(b_empty(sbb));
-            ++gb;
+          for (int n0 = ps, w = 0; n0 < pe && ok; n0 += w) {
+            w = slice_w(pe - n0);
+            ok = mma_chunk(tmem + (uint32_t)(n0 - ps), a, a + C::A, w, false);
           }
           mma_commit(a_empty(sa));
           ++ga;
@@ -282,39 +302,21 @@ __global__ void __launch_bounds__(kRThreads, 1)
           ++nf;
           tc_after();
           const uint32_t f = sb + C::F_OFF;
-          for (int kc = 0; kc < 2; ++kc) {
+          for (int kc = 0; kc < 2 && ok; ++kc) {
             const int x = j0 + RK * kc;
             if (x >= k) break;
-            int sbb;
-            if (!wait_b(sbb)) {
-              ok = false;
-              break;
-            }
-            tc_after();
-            const uint32_t b = sb + C::B_OFF + sbb * 2 * C::B;
             const uint32_t a = f + kc * 2 * C::A;
-            mma3(tmem + (uint32_t)(j0 - RB - ps), a, a + C::A, b, b + C::B, id64, false);
-            mma_commit(b_empty(sbb));
-            ++gb;
+            ok = mma_chunk(tmem + (uint32_t)(j0 - RB - ps), a, a + C::A, RB, false);
           }
           if (!ok) break;
           mma_commit(d_ready);  // D(:, J - 1) is complete
-          for (int n0 = ps; n0 < j0 - RB && ok; n0 += RNS) {
-            const bool wide = j0 - RB - n0 >= RNS;
-            for (int kc = 0; kc < 2; ++kc) {
+          for (int n0 = ps, w = 0; n0 < j0 - RB && ok; n0 += w) {
+            w = slice_w(j0 - RB - n0);
+            for (int kc = 0; kc < 2 && ok; ++kc) {
               const int x = j0 + RK * kc;
               if (x >= k) break;
-              int sbb;
-              if (!wait_b(sbb)) {
-                ok = false;
-                break;
-              }
-              tc_after();
-              const uint32_t b = sb + C::B_OFF + sbb * 2 * C::B;
               const uint32_t a = f + kc * 2 * C::A;
-              mma3(tmem + (uint32_t)(n0 - ps), a, a + C::A, b, b + C::B, wide ? id128 : id64, false);
-              mma_commit(b_empty(sbb));
-              ++gb;
+              ok = mma_chunk(tmem + (uint32_t)(n0 - ps), a, a + C::A, w, false);
             }
           }
           mma_commit(f_free);  // the staged W(:, J) is no longer read
@@ -516,15 +518,17 @@ cudaError_t wsolve_rl(const void* L, long long ldl, double* W64, long long ldw64
   L = (const char*)L + r0 * ldl * (L64 ? 8 : 4);
   W64 += r0 * ldw64;
   Wb += r0 * ldwb;
-  CUtensorMap mL, mW, mG128h, mG128l, mG64h, mG64l;
+  CUtensorMap mL, mW, mG256h, mG256l, mG128h, mG128l, mG64h, mG64l;
   if (L64) {
     if (!make_map(&mL, L, k, n, ldl * 8, 16, RM, true)) return cudaErrorInvalidValue;
   } else {
     if (!make_map(&mL, L, k, n, ldl * 4, RK, RM)) return cudaErrorInvalidValue;
   }
   if (!make_map(&mW, Wb, k, n, ldwb * 4, RK, RM)) return cudaErrorInvalidValue;
-  if (!make_map(&mG128h, Gh, k, k, ldt * 4, RK, RNS)) return cudaErrorInvalidValue;
-  if (!make_map(&mG128l, Gl, k, k, ldt * 4, RK, RNS)) return cudaErrorInvalidValue;
+  if (!make_map(&mG256h, Gh, k, k, ldt * 4, RK, 256)) return cudaErrorInvalidValue;
+  if (!make_map(&mG256l, Gl, k, k, ldt * 4, RK, 256)) return cudaErrorInvalidValue;
+  if (!make_map(&mG128h, Gh, k, k, ldt * 4, RK, 128)) return cudaErrorInvalidValue;
+  if (!make_map(&mG128l, Gl, k, k, ldt * 4, RK, 128)) return cudaErrorInvalidValue;
   if (!make_map(&mG64h, Gh, k, k, ldt * 4, RK, RB)) return cudaErrorInvalidValue;
   if (!make_map(&mG64l, Gl, k, k, ldt * 4, RK, RB)) return cudaErrorInvalidValue;
   const long long ntiles = (n + RM - 1) / RM;
@@ -539,8 +543,8 @@ cudaError_t wsolve_rl(const void* L, long long ldl, double* W64, long long ldw64
     pn.ps = pn.Jlo * RB;
     pn.pe = (int)((long long)(Jhi + 1) * RB < k ? (Jhi + 1) * RB : k);
     pn.wback = pn.Jlo > 0;
-    e = launch_pdl(k_wsolve_rl<L64>, dim3(grid), dim3(kRThreads), (size_t)C::SMEM, s, mL, mW, mG128h, mG128l, mG64h,
-                   mG64l, W64, ldw64, vec, Wb, ldwb, (int)n, (int)k, pn, st);
+    e = launch_pdl(k_wsolve_rl<L64>, dim3(grid), dim3(kRThreads), (size_t)C::SMEM, s, mL, mW, mG256h, mG256l,
+                   mG128h, mG128l, mG64h, mG64l, W64, ldw64, vec, Wb, ldwb, (int)n, (int)k, pn, st);
     if (e != cudaSuccess) return e;
     if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
     Jhi = pn.Jlo - 1;
