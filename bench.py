@@ -60,7 +60,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU baseline run (0: all rows)")
-    ap.add_argument("--ref-rows", type=int, default=20000, help="row sample per step of the reference arm")
+    ap.add_argument("--ref-rows", type=int, default=-1,
+                    help="row sample per step of the reference arm (-1: the whole workload when warm-up plus "
+                         "timed steps fit --ref-budget seconds, else the largest row sample that does)")
+    ap.add_argument("--ref-budget", type=float, default=300.0, help="seconds the reference arm may take in all")
     ap.add_argument("--workload", default="zipf_gmm",
                     choices=["zipf_gmm", "kernel_blocks", "gmm_fixed_rank", "spectral", "random_features"],
                     help="kernel_blocks: the batched workload (one rbrp_id_batched launch per step); "
@@ -280,12 +283,24 @@ def run_reference(a):
         return
     from paper_2309_16002_gb300 import workloads as WL
     X = make_input(a)
-    for _ in range(a.warmup):
-        cpu_oracle_leg(a, X, a.ref_rows)
+    rows = a.ref_rows
+    done = 0
+    if rows < 0:
+        # the first warm-up step on the whole workload; if warm-up plus timed steps would
+        # exceed the budget, the rest run on the largest row sample that fits (the oracle's
+        # O(n d k) work is linear in n)
+        t0 = time.perf_counter()
+        cpu_oracle_leg(a, X, 0)
+        t_full = time.perf_counter() - t0
+        done = 1
+        total = (a.warmup + a.steps) * t_full
+        rows = 0 if total <= a.ref_budget else max(1000, int(X.shape[0] * a.ref_budget / total))
+    for _ in range(max(0, a.warmup - done)):
+        cpu_oracle_leg(a, X, rows)
     vals = []
     info = None
     for _ in range(a.steps):
-        v, info = cpu_oracle_leg(a, X, a.ref_rows)
+        v, info = cpu_oracle_leg(a, X, rows)
         vals.append(v)
     ms = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps,

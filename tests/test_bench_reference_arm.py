@@ -36,6 +36,17 @@ def test_reference_arm_headline_workload_small():
     assert "1500 of 3000 rows" in j["cpu_baseline"]["sample"]
 
 
+def test_reference_arm_whole_workload_when_it_fits_the_budget():
+    """Default: the whole workload every step (no extrapolation) when warm-up plus timed steps fit
+    the time budget; past the budget, the largest row sample that fits."""
+    lines = _bench(["--steps", "2", "--warmup", "1", "--n", "3000", "--d", "100"])
+    j = _check_line(lines[0], "zipf_gmm_near_duplicates")
+    assert "the full 3000 x 100 workload" in j["cpu_baseline"]["sample"]
+    lines = _bench(["--steps", "2", "--warmup", "1", "--n", "3000", "--d", "100", "--ref-budget", "0.000001"])
+    j = _check_line(lines[0], "zipf_gmm_near_duplicates")
+    assert "of 3000 rows" in j["cpu_baseline"]["sample"]
+
+
 def test_reference_arm_batched_workload_small():
     lines = _bench(["--workload", "kernel_blocks", "--batch", "24", "--steps", "1", "--warmup", "0"])
     assert len(lines) == 1
