@@ -407,9 +407,12 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
 }
 
 // ------------------------------------------------------------------ persistent form
-// Plain TF32, b'_pad <= 64.  One CTA per SM walks 128-row tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; GEMM 1 of tile t+1 streams R from HBM through
-// ring 1 while GEMM 2 of tile t re-reads R (mostly from L2) through ring 3.
+// Plain TF32, b'_pad <= 64.  One CTA per SM walks tiles of prows <= 128 rows,
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; GEMM 1 of tile t+1 streams R from
+// HBM through ring 1 while GEMM 2 of tile t re-reads R (mostly from L2) through
+// ring 3.  The host picks prows (a multiple of 8) so that every CTA walks the same
+// number of tiles, up to one: with 128-row tiles, 10^5 rows on 152 SMs leave 22 CTAs
+// a sixth tile that the other 130 wait for (rows prows..127 of the MMA are unused).
 //
 // On sm_103a one tcgen05.mma of kind::tf32 (K = 8) occupies the SM's tensor
 // pipe for ~100 cycles up to N = 128 and reaches the full rate only at large N,
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
 // the R pieces of ring 3, warp 3 issues GEMM 2, warps 4-7 (one TMEM lane
 // quarter each, thread <-> row) are the epilogue, warp 8 stores finished R
 // pieces, warp 9 loads the Q'^T chunks.  D1 (Lhat) and D2 are double-buffered.
-constexpr int PROWS = 128;        // rows of R per tile
+constexpr int PROWS = 128;        // rows of R per tile at most (the MMA's M); prows <= PROWS are real
 constexpr int PNB = 128;          // columns per GEMM-2 chunk (MMA N)
 constexpr int PPC = PNB / NB2;    // 32-column epilogue pieces per chunk
 constexpr int PS1 = 4;            // ring-1 stages (R chunk + Q' chunk)
@@ -432,7 +435,7 @@ constexpr int kPThreads = 320;
 
 template <int BMAX>
 struct PCfg {
-  static constexpr int A1 = PROWS * BK1 * 4;          // 16 KB of R
+  static constexpr int A1 = PROWS * BK1 * 4;          // 16 KB of R (prows * 128 bytes filled)
   static constexpr int B1 = BMAX * BK1 * 4;           // Q' chunk
   static constexpr int ST1 = A1 + B1;
   static constexpr int R3 = PROWS * NB2 * 4;          // 16 KB of R
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmX,
                    const __grid_constant__ CUtensorMap tmQ,
                    const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
-                   long long d, const int* __restrict__ mark, double* __restrict__ dvec,
+                   long long d, int prows, const int* __restrict__ mark, double* __restrict__ dvec,
                    double* __restrict__ partials, State* st, int c0) {
   using C = PCfg<BMAX>;
   pdl_wait();
@@ -492,7 +495,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const int tno = (int)(st->t + 1);
   const int nK1 = (int)((d + BK1 - 1) / BK1);  // 32-column chunks of GEMM 1 (and epilogue pieces)
   const int nJ = (int)((d + PNB - 1) / PNB);   // GEMM-2 chunks
-  const long long ntiles = (n + PROWS - 1) / PROWS;
+  const long long ntiles = (n + prows - 1) / prows;
+  const uint32_t a1_bytes = (uint32_t)(prows * BK1 * 4), r3_bytes = (uint32_t)(prows * NB2 * 4);
   // Odd blocks walk the tiles from the last: a block then starts on the tiles the
   // previous block wrote last, which are still in L2 (the residual is larger
   // than L2, so a fixed order would always start on the least recent tiles).
@@ -555,9 +559,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(full1(s), (uint32_t)(C::A1 + C::B1));
+          mbar_expect_tx(full1(s), a1_bytes + (uint32_t)C::B1);
           const uint32_t base = sb + s * C::ST1;
-          tma_load_2d_hint(base, tmSrc, full1(s), kc * BK1, (int)(ptile(tile) * PROWS), keep);
+          tma_load_2d_hint(base, tmSrc, full1(s), kc * BK1, (int)(ptile(tile) * prows), keep);
           tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
         }
       }
@@ -606,8 +610,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
               ok = false;
               break;
             }
-            mbar_expect_tx(full3(s), (uint32_t)C::R3);
-            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, tmSrc, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS),
+            mbar_expect_tx(full3(s), r3_bytes);
+            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, tmSrc, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * prows),
                              drop);
           }
         }
@@ -677,8 +681,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     bool ok = true;
     double part = 0.0;  // this warp's rows over the CTA's tiles, in its tile order
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-      const long long row = ptile(tile) * PROWS + r;
-      const bool in = row < n;
+      const long long row = ptile(tile) * prows + r;
+      const bool in = r < prows && row < n;  // MMA rows prows..127 are don't-care
       const bool marked = last_chunk && in && (mark[row] == tno);
       // Lhat: TMEM -> registers -> L (GEMM 2 reads it from TMEM itself)
       const int dbuf = it & 1;
@@ -767,7 +771,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               ok = false;
               break;
             }
-            tma_store_2d_hint(&tmR, sb + C::OFF3 + s * C::R3, (PPC * j + pc) * NB2, (int)(ptile(tile) * PROWS), drop);
+            tma_store_2d_hint(&tmR, sb + C::OFF3 + s * C::R3, (PPC * j + pc) * NB2, (int)(ptile(tile) * prows), drop);
             tma_commit();
             if (g > 0) {
               tma_wait_read<1>();  // the previous piece's store has read its stage
@@ -808,6 +812,25 @@ __global__ void __launch_bounds__(kPThreads, 1)
   }
 }
 
+// Tile height and grid of the persistent form: the fewest rounds of 128-row tiles
+// over the SMs, then the smallest height (a multiple of 8, at least 32) that covers
+// n rows in that many rounds.
+struct PTiles {
+  int prows;
+  long long ntiles;
+  unsigned grid;
+};
+static PTiles ptiles(long long n, int sms) {
+  const long long rounds = std::max<long long>(1, ((n + PROWS - 1) / PROWS + sms - 1) / sms);
+  long long h = (n + sms * rounds - 1) / (sms * rounds);
+  h = std::min<long long>(PROWS, std::max<long long>(32, (h + 7) / 8 * 8));
+  PTiles t;
+  t.prows = (int)h;
+  t.ntiles = (n + h - 1) / h;
+  t.grid = (unsigned)std::min<long long>(t.ntiles, sms);
+  return t;
+}
+
 // SM count of the current device (asked once per device): the persistent grid, and
 // with it the number of partial sums the update leaves.
 int device_sms() {
@@ -838,16 +861,14 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
     if (dev < 64) attr_set.fetch_or(1ULL << dev);
   }
   CUtensorMap mR, mX, mQ, mQT;
-  if (!make_map(&mR, R, d, n, ldr * 4, 32, PROWS)) return cudaErrorInvalidValue;
-  if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, PROWS) : false) return cudaErrorInvalidValue;
+  const PTiles pt = ptiles(n, device_sms());
+  if (!make_map(&mR, R, d, n, ldr * 4, 32, pt.prows)) return cudaErrorInvalidValue;
+  if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, pt.prows) : false) return cudaErrorInvalidValue;
   if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
-  const int sms = device_sms();
-  const long long ntiles = (n + PROWS - 1) / PROWS;
-  const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT, L,
-                            ldl, n, d, mark, dvec, partials, const_cast<State*>(st), c0));
+  return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(pt.grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT,
+                            L, ldl, n, d, pt.prows, mark, dvec, partials, const_cast<State*>(st), c0));
 }
 
 // ------------------------------------------------------------------ host side
@@ -918,13 +939,9 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
 }  // namespace tc
 
 // Partial sums the update leaves for launch_finalize_block: 4 per CTA of the
-// persistent form (one CTA per SM, at most one per 128-row tile), or 2 per 64-row tile.
+// persistent form (one CTA per SM, at most one per tile), or 2 per 64-row tile.
 int update_tf32_parts(long long n, int bmax, int split) {
-  if (!split && bmax <= 64) {
-    const long long ntiles = (n + tc::PROWS - 1) / tc::PROWS;
-    const long long grid = std::min<long long>(ntiles, tc::device_sms());
-    return 4 * (int)grid;
-  }
+  if (!split && bmax <= 64) return 4 * (int)tc::ptiles(n, tc::device_sms()).grid;
   return 2 * (int)((n + tc::ROWS - 1) / tc::ROWS);
 }
 
