@@ -425,39 +425,46 @@ __global__ void __launch_bounds__(kThreads, Cfg<BMAX, SPLIT>::MIN_BLOCKS)
 // the R pieces of ring 3, warp 3 issues GEMM 2, warps 4-7 (one TMEM lane
 // quarter each, thread <-> row) are the epilogue, warp 8 stores finished R
 // pieces, warp 9 loads the Q'^T chunks.  D1 (Lhat) and D2 are double-buffered.
-constexpr int PROWS = 128;        // rows of R per tile at most (the MMA's M); prows <= PROWS are real
+constexpr int PROWS = 128;        // the MMA's M: rows prows .. 127 of a tile are don't-care
 constexpr int PNB = 128;          // columns per GEMM-2 chunk (MMA N)
 constexpr int PPC = PNB / NB2;    // 32-column epilogue pieces per chunk
-constexpr int PS1 = 4;            // ring-1 stages (R chunk + Q' chunk)
-constexpr int PS3 = 6;            // ring-3 R stages: load, epilogue, store
 constexpr int PSB = 1;            // Q'^T chunk stages: load, MMA (a chunk lasts ~8 kcycles)
 constexpr int kPThreads = 320;
+constexpr int kPTileRows = 128;   // TR of the form the dispatch launches
 
-template <int BMAX>
+// TR: the largest tile height (rows per stage); shorter stages give deeper rings in
+// the same shared memory.  Ring 1 holds R and Q' chunks, ring 3 the re-read R pieces.
+template <int BMAX, int TR>
 struct PCfg {
-  static constexpr int A1 = PROWS * BK1 * 4;          // 16 KB of R (prows * 128 bytes filled)
+  static_assert(TR == 128 || TR == 96 || TR == 64, "tile height");
+  static constexpr int PS1 = TR == 128 ? 4 : (TR == 96 ? 5 : 6);  // ring-1 stages
+  static constexpr int PS3 = TR == 128 ? 6 : (TR == 96 ? 7 : 12); // ring-3 stages: load, epilogue, store
+  static constexpr int A1 = TR * BK1 * 4;             // one R chunk (prows * 128 bytes filled)
   static constexpr int B1 = BMAX * BK1 * 4;           // Q' chunk
   static constexpr int ST1 = A1 + B1;
-  static constexpr int R3 = PROWS * NB2 * 4;          // 16 KB of R
+  static constexpr int R3 = TR * NB2 * 4;             // one R piece
   static constexpr int B2A = PNB * 128;               // one 32-wide K atom of a Q'^T chunk (16 KB)
   static constexpr int B2 = (BMAX / 32) * B2A;
   static constexpr int OFF3 = PS1 * ST1;
   static constexpr int OFFB = OFF3 + PS3 * R3;
   static constexpr int BAR_OFF = OFFB + PSB * B2;
-  static constexpr int SMEM = BAR_OFF + 512 + 1024;
+  static constexpr int BAR_BYTES = (8 * (2 * PS1 + 3 * PS3 + 2 * PSB) + 96 + 127) / 128 * 128;
+  static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
+  static_assert(ST1 % 1024 == 0 && A1 % 1024 == 0 && R3 % 1024 == 0, "swizzle atoms");
   static constexpr uint32_t D2COL = 2 * BMAX;          // D1 x2, then D2 x2 (PNB columns each)
   static constexpr uint32_t TMEM_COLS = (2 * BMAX + 2 * PNB <= 256) ? 256 : 512;
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-template <int BMAX>
+template <int BMAX, int TR>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmX,
                    const __grid_constant__ CUtensorMap tmQ,
                    const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
                    long long d, int prows, const int* __restrict__ mark, double* __restrict__ dvec,
                    double* __restrict__ partials, State* st, int c0) {
-  using C = PCfg<BMAX>;
+  using C = PCfg<BMAX, TR>;
+  constexpr int PS1 = C::PS1, PS3 = C::PS3;
   pdl_wait();
   if (st->done) return;
   // this launch applies columns c0 .. c0 + BMAX - 1 of Q' (a chunk of a wider block);
@@ -596,9 +603,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
       }
     }
   } else if (warp == 2) {
-    // ---------------- ring 3: R pieces of GEMM 2 (second read), for the epilogue
+    // ---------------- ring 3: R pieces of GEMM 2 (second read), for the epilogue; no cache
+    // hint (marking the re-read lines evict-first measured ~2 % slower)
     if (lane == 0) {
-      const uint64_t drop = l2_policy_evict_first();
       uint32_t g = 0;
       bool ok = true;
       for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -611,8 +618,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               break;
             }
             mbar_expect_tx(full3(s), r3_bytes);
-            tma_load_2d_hint(sb + C::OFF3 + s * C::R3, tmSrc, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * prows),
-                             drop);
+            tma_load_2d(sb + C::OFF3 + s * C::R3, tmSrc, full3(s), (PPC * j + pc) * NB2, (int)(ptile(tile) * prows));
           }
         }
       }
@@ -720,10 +726,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
           tmem_ld32(tmem + lane_base + C::D2COL + (uint32_t)(b2 * PNB + pc * NB2), u);
           tmem_wait_ld();
           uint8_t* rrow = smem + C::OFF3 + s * C::R3;
-          // all loads first, then the arithmetic, then all stores
+          // all loads first, then the arithmetic, then all stores; rows prows .. 127 lie
+          // past the piece (in the next stage when the stages hold fewer than 128 rows)
           float4 x[8];
 #pragma unroll
-          for (int ch = 0; ch < 8; ++ch) x[ch] = *(const float4*)(rrow + swz(r, ch));
+          for (int ch = 0; ch < 8; ++ch)
+            x[ch] = r < prows ? *(const float4*)(rrow + swz(r, ch)) : make_float4(0.f, 0.f, 0.f, 0.f);
           float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
           for (int ch = 0; ch < 8; ++ch) {
@@ -737,8 +745,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
             p2 = fmaf(x[ch].z, x[ch].z, p2);
             p3 = fmaf(x[ch].w, x[ch].w, p3);
           }
+          if (r < prows) {
 #pragma unroll
-          for (int ch = 0; ch < 8; ++ch) *(float4*)(rrow + swz(r, ch)) = x[ch];
+            for (int ch = 0; ch < 8; ++ch) *(float4*)(rrow + swz(r, ch)) = x[ch];
+          }
           nrm += (p0 + p1) + (p2 + p3);
           fence_async_smem();
           mbar_arrive(epi_done(s));
@@ -812,23 +822,32 @@ __global__ void __launch_bounds__(kPThreads, 1)
   }
 }
 
-// Tile height and grid of the persistent form: the fewest rounds of 128-row tiles
-// over the SMs, then the smallest height (a multiple of 8, at least 32) that covers
-// n rows in that many rounds.
+// Tile height and grid of the persistent form: for the fewest rounds of tr-row tiles
+// over the SMs and the next two round counts, the smallest height (a multiple of 8, at
+// least 32, at most tr) that covers n rows in that many rounds; of these, the one
+// whose busiest CTA walks the fewest rows.
 struct PTiles {
   int prows;
   long long ntiles;
   unsigned grid;
 };
-static PTiles ptiles(long long n, int sms) {
-  const long long rounds = std::max<long long>(1, ((n + PROWS - 1) / PROWS + sms - 1) / sms);
-  long long h = (n + sms * rounds - 1) / (sms * rounds);
-  h = std::min<long long>(PROWS, std::max<long long>(32, (h + 7) / 8 * 8));
-  PTiles t;
-  t.prows = (int)h;
-  t.ntiles = (n + h - 1) / h;
-  t.grid = (unsigned)std::min<long long>(t.ntiles, sms);
-  return t;
+static PTiles ptiles(long long n, int sms, int tr) {
+  const long long r0 = std::max<long long>(1, ((n + tr - 1) / tr + sms - 1) / sms);
+  PTiles best{tr, (n + tr - 1) / tr, 0};
+  long long best_rows = -1;
+  for (long long rounds = r0; rounds < r0 + 3; ++rounds) {
+    long long h = (n + sms * rounds - 1) / (sms * rounds);
+    h = std::min<long long>(tr, std::max<long long>(32, (h + 7) / 8 * 8));
+    const long long nt = (n + h - 1) / h;
+    const long long rows = (nt + sms - 1) / sms * h;  // rows of the busiest CTA
+    if (best_rows < 0 || rows < best_rows) {
+      best_rows = rows;
+      best.prows = (int)h;
+      best.ntiles = nt;
+    }
+  }
+  best.grid = (unsigned)std::min<long long>(best.ntiles, sms);
+  return best;
 }
 
 // SM count of the current device (asked once per device): the persistent grid, and
@@ -845,29 +864,29 @@ int device_sms() {
   return sms[dev];
 }
 
-template <int BMAX>
+template <int BMAX, int TR>
 cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long qrows,
                         long long ldp, const float* QpT, long long qtcols, long long ldpt, float* L, long long ldl,
                         const int* mark, double* dvec, double* partials, const State* st, int c0, cudaStream_t s,
                         const float* X0, long long ldx0) {
-  using C = PCfg<BMAX>;
+  using C = PCfg<BMAX, TR>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   if (dev >= 64 || !(attr_set.load() >> dev & 1ULL)) {
-    e = cudaFuncSetAttribute(k_update_tf32p<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    e = cudaFuncSetAttribute(k_update_tf32p<BMAX, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     if (dev < 64) attr_set.fetch_or(1ULL << dev);
   }
   CUtensorMap mR, mX, mQ, mQT;
-  const PTiles pt = ptiles(n, device_sms());
+  const PTiles pt = ptiles(n, device_sms(), TR);
   if (!make_map(&mR, R, d, n, ldr * 4, 32, pt.prows)) return cudaErrorInvalidValue;
   if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, pt.prows) : false) return cudaErrorInvalidValue;
   if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
-  return counted(launch_pdl(k_update_tf32p<BMAX>, dim3(pt.grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT,
+  return counted(launch_pdl(k_update_tf32p<BMAX, TR>, dim3(pt.grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT,
                             L, ldl, n, d, pt.prows, mark, dvec, partials, const_cast<State*>(st), c0));
 }
 
@@ -941,7 +960,7 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
 // Partial sums the update leaves for launch_finalize_block: 4 per CTA of the
 // persistent form (one CTA per SM, at most one per tile), or 2 per 64-row tile.
 int update_tf32_parts(long long n, int bmax, int split) {
-  if (!split && bmax <= 64) return 4 * (int)tc::ptiles(n, tc::device_sms()).grid;
+  if (!split && bmax <= 64) return 4 * (int)tc::ptiles(n, tc::device_sms(), tc::kPTileRows).grid;
   return 2 * (int)((n + tc::ROWS - 1) / tc::ROWS);
 }
 
@@ -971,10 +990,10 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
     return cudaErrorInvalidValue;
   }
   if (bmax <= 32)
-    return tc::launch_pcfg<32>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
+    return tc::launch_pcfg<32, tc::kPTileRows>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
                                s, X0, ldx0);
   if (bmax <= 64)
-    return tc::launch_pcfg<64>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
+    return tc::launch_pcfg<64, tc::kPTileRows>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
                                s, X0, ldx0);
   if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
 #undef RBRP_TC_ARGS
