@@ -28,10 +28,11 @@ sys.path.insert(0, ROOT)
 METRIC = "ID time-to-tol (ms) at 1e5×1e3, rel err ≤1e-4; % of HBM/TC roofline"
 # DRAM bytes (read + write) per launch of the persistent tensor-core update, per
 # row of R, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-# caches left as the preceding kernels leave them) of the 40000 x 1000 zipf_gmm
-# workload at b = 64 (profiles/k_update_tf32p_zipf_gmm_40000x1000.md), taken on
-# the kernel as it is now.
-UPD_TRAFFIC_PER_ROW = (194578176 + 132194304) / 40000
+# one pass, caches left as the preceding kernels leave them) of launches 7-9 of the
+# 100000 x 1000 zipf_gmm workload at b = 64
+# (profiles/k_update_tf32p_zipf_gmm_100000x1000.md), taken on the kernel as it is now:
+# reads 601.1 / 579.9 / 584.6 MB, writes 390.6 / 396.5 / 394.4 MB.
+UPD_TRAFFIC_PER_ROW = (601100800 + 579894784 + 584573952 + 390606336 + 396474624 + 394363136) / 3 / 100000
 UPD_TRAFFIC_D = 1000
 UPD_TRAFFIC_CURRENT = True
 FALLBACK_HBM = 6800.0
@@ -481,8 +482,10 @@ def run_ours(a):
                 "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
                 "peak_kind": peak_kind, "traffic": traffic,
                 "traffic_last_capture": captured,
-                "traffic_note": ("DRAM read+write bytes per launch from one ncu capture of the 40000 x 1000 "
-                                 "workload (L2 as the preceding kernels leave it), scaled by rows to this n"
+                "traffic_note": ("DRAM read+write bytes per launch from one ncu capture of three launches of "
+                                 "the 100000 x 1000 workload (L2 as the preceding kernels leave it), per row "
+                                 "times this n; above the algorithmic bytes because the GEMM-2 re-read of R "
+                                 "misses L2 for part of each tile"
                                  + ("" if UPD_TRAFFIC_CURRENT else "; taken on an earlier build of the kernel, "
                                     "so traffic is null until the next capture")
                                  if captured else None),
