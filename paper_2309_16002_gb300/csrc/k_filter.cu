@@ -477,13 +477,13 @@ __global__ void __launch_bounds__(kPcholF32Threads) k_pchol_f32(const float* __r
 // factorisation runs in one warp with no block-wide barrier.  Right-looking: lane l
 // holds columns l and l + 32 of the Schur complement (the Gram matrix minus the factor
 // so far) in registers.  Each step takes the trailing mass (a warp sum) and the pivot
-// (the largest remaining d_r > 0, ties to the smaller index: a shuffle max over
-// 64-bit keys made of the FP32 bit pattern, which orders like the values for d_r >= 0,
-// and the complemented index), and stops at the first step whose trailing mass
-// fails the truncation test of Alg. 2; the pivot's owner publishes its column
-// c = S(:, p) through shared memory, every lane forms l_r = c_r / sqrt(d_p) for its
-// two candidates and applies the rank-1 update S(j, r) -= c_j c_r / d_p to its two
-// columns.  The next step's reductions depend only on the downdated diagonal, so
+// (the largest remaining d_r > 0, ties to the smaller index: a warp max over the FP32
+// bit patterns, which order like the values for d_r >= 0, then a warp min over the
+// indices holding it), and stops at the first step whose trailing mass fails the
+// truncation test of Alg. 2; every lane reads c_r = S(r, p) for its two candidates
+// from its own columns (the matrix is symmetric up to rounding) and the lanes publish
+// the column c through shared memory together; each forms l_r = c_r / sqrt(d_p) and
+// applies the rank-1 update S(j, r) -= c_j c_r / d_p to its two columns.  The next step's reductions depend only on the downdated diagonal, so
 // they are issued before the 128 multiply-adds of the update and their latency
 // overlaps it.  The kernel writes the pivot-order factor Lc; Q'_V = Lc^{-1} V_perm
 // follows as a column-parallel substitution (k_trsm_rows_f32).
@@ -575,20 +575,14 @@ __global__ void __launch_bounds__(kPchol64Sum) k_pchol_f32_64(const float* __res
     ms = (a0 ? d0 : 0.f) + (a1 ? d1 : 0.f);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, o);
-    // one 64-bit key per candidate, value bits above (63 - index): the largest key is the
-    // largest d_r, ties to the smaller index; five shuffle steps give value and index
+    // the FP32 bit pattern orders like the value for d_r >= 0: the largest pattern over the
+    // warp, then the smallest index that holds it (two warp reductions)
     const unsigned b0 = (a0 && d0 > 0.f) ? __float_as_uint(d0) : 0u;
     const unsigned b1 = (a1 && d1 > 0.f) ? __float_as_uint(d1) : 0u;
-    const unsigned long long k0 = ((unsigned long long)b0 << 32) | (unsigned)(63 - c0);
-    const unsigned long long k1 = ((unsigned long long)b1 << 32) | (unsigned)(63 - c1);
-    unsigned long long key = k1 > k0 ? k1 : k0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
-      key = other > key ? other : key;
-    }
-    mx = (unsigned)(key >> 32);
-    p = mx ? (unsigned)(63 - (int)(key & 0xffffffffu)) : 0xffffffffu;
+    mx = __reduce_max_sync(0xffffffffu, b0 > b1 ? b0 : b1);
+    const unsigned cand = (mx != 0u && b0 == mx) ? (unsigned)c0 : ((mx != 0u && b1 == mx) ? (unsigned)c1 : 64u);
+    const unsigned pm = __reduce_min_sync(0xffffffffu, cand);
+    p = mx ? pm : 0xffffffffu;
   };
   __syncwarp();
   reduce();
@@ -597,17 +591,28 @@ __global__ void __launch_bounds__(kPchol64Sum) k_pchol_f32_64(const float* __res
     if (mx == 0u || !(ms >= tb * total && ms > 0.f)) break;  // the same on every lane; b' = i
     const float rinv = rsqrtf(__uint_as_float(mx));
     const float rdp = rinv * rinv;
-    if (lane == (int)(p & 31u)) {  // the pivot's owner publishes c = S(:, p)
-      if (p < 32u) {
-#pragma unroll
-        for (int j = 0; j < kPchol64; j += 4) *(float4*)(lv + j) = make_float4(col0[j], col0[j + 1], col0[j + 2], col0[j + 3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < kPchol64; j += 4) *(float4*)(lv + j) = make_float4(col1[j], col1[j + 1], col1[j + 2], col1[j + 3]);
-      }
+    // c_j = S(j, p): every lane reads its own two entries S(c0, p), S(c1, p) (the Schur
+    // complement is symmetric up to rounding) with a warp-uniform switch, and the lanes
+    // publish the column together for the rank-1 update
+    float cr0 = 0.f, cr1 = 0.f;
+    switch (p) {
+#define RBRP_PICK(k) \
+  case k:            \
+    cr0 = col0[k];   \
+    cr1 = col1[k];   \
+    break;
+#define RBRP_PICK8(k) RBRP_PICK(k) RBRP_PICK(k + 1) RBRP_PICK(k + 2) RBRP_PICK(k + 3) \
+                      RBRP_PICK(k + 4) RBRP_PICK(k + 5) RBRP_PICK(k + 6) RBRP_PICK(k + 7)
+      RBRP_PICK8(0) RBRP_PICK8(8) RBRP_PICK8(16) RBRP_PICK8(24)
+      RBRP_PICK8(32) RBRP_PICK8(40) RBRP_PICK8(48) RBRP_PICK8(56)
+#undef RBRP_PICK8
+#undef RBRP_PICK
+      default:
+        break;
     }
+    lv[c0] = cr0;
+    lv[c1] = cr1;
     __syncwarp();
-    const float cr0 = lv[c0], cr1 = lv[c1];
     const float l0 = cr0 * rinv, l1 = cr1 * rinv;
     if (a0) Lw[c0 * kPchol64LDF + i] = l0;
     if (a1) Lw[c1 * kPchol64LDF + i] = l1;
@@ -632,7 +637,7 @@ __global__ void __launch_bounds__(kPchol64Sum) k_pchol_f32_64(const float* __res
       col1[j + 2] = fmaf(-l4.z, f1, col1[j + 2]);
       col1[j + 3] = fmaf(-l4.w, f1, col1[j + 3]);
     }
-    __syncwarp();  // every lane has read lv before the next pivot's owner overwrites it
+    __syncwarp();  // every lane has read lv before the lanes write the next pivot's column
   }
   const int bp = steps;
   __syncwarp();
