@@ -429,41 +429,50 @@ constexpr int PROWS = 128;        // the MMA's M: rows prows .. 127 of a tile ar
 constexpr int PNB = 128;          // columns per GEMM-2 chunk (MMA N)
 constexpr int PPC = PNB / NB2;    // 32-column epilogue pieces per chunk
 constexpr int PSB = 1;            // Q'^T chunk stages: load, MMA (a chunk lasts ~8 kcycles)
-constexpr int kPThreads = 320;
 constexpr int kPTileRows = 128;   // TR of the form the dispatch launches
 
 // TR: the largest tile height (rows per stage); shorter stages give deeper rings in
 // the same shared memory.  Ring 1 holds R and Q' chunks, ring 3 the re-read R pieces.
-template <int BMAX, int TR>
+// SPLIT: the 3xTF32 form (hi*hi + hi*lo + lo*hi): ring 1 holds [R hi][Q' hi][R lo][Q' lo]
+// (four converter warps split R in place), the Q'^T stage its hi and lo halves, and
+// tensor memory Lhat's hi and lo halves (the epilogue writes them back as GEMM 2's A).
+template <int BMAX, int TR, bool SPLIT = false>
 struct PCfg {
   static_assert(TR == 128 || TR == 96 || TR == 64, "tile height");
-  static constexpr int PS1 = TR == 128 ? 4 : (TR == 96 ? 5 : 6);  // ring-1 stages
-  static constexpr int PS3 = TR == 128 ? 6 : (TR == 96 ? 7 : 12); // ring-3 stages: load, epilogue, store
+  static_assert(!SPLIT || TR == 128, "the split form uses 128-row stages");
+  static_assert(TR <= PROWS, "the MMA's M bounds the tile height");
+  static constexpr int NOP = SPLIT ? 2 : 1;           // hi (and lo) copies of an operand
+  static constexpr int PS1 = SPLIT ? 2 : (TR == 128 ? 4 : (TR == 96 ? 5 : 6));   // ring-1 stages
+  static constexpr int PS3 = SPLIT ? 3 : (TR == 128 ? 6 : (TR == 96 ? 7 : 12));  // ring-3 stages
+  static constexpr int THREADS = SPLIT ? 448 : 320;
   static constexpr int A1 = TR * BK1 * 4;             // one R chunk (prows * 128 bytes filled)
   static constexpr int B1 = BMAX * BK1 * 4;           // Q' chunk
-  static constexpr int ST1 = A1 + B1;
+  static constexpr int ST1 = NOP * (A1 + B1);
   static constexpr int R3 = TR * NB2 * 4;             // one R piece
   static constexpr int B2A = PNB * 128;               // one 32-wide K atom of a Q'^T chunk (16 KB)
-  static constexpr int B2 = (BMAX / 32) * B2A;
+  static constexpr int B2 = (BMAX / 32) * B2A;        // one half (hi or lo) of a Q'^T chunk
   static constexpr int OFF3 = PS1 * ST1;
   static constexpr int OFFB = OFF3 + PS3 * R3;
-  static constexpr int BAR_OFF = OFFB + PSB * B2;
-  static constexpr int BAR_BYTES = (8 * (2 * PS1 + 3 * PS3 + 2 * PSB) + 96 + 127) / 128 * 128;
+  static constexpr int BAR_OFF = OFFB + PSB * NOP * B2;
+  static constexpr int BAR_BYTES = (8 * (2 * PS1 + 3 * PS3 + 2 * PSB) + 104 + 8 * PS1 + 127) / 128 * 128;
   static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
   static_assert(ST1 % 1024 == 0 && A1 % 1024 == 0 && R3 % 1024 == 0, "swizzle atoms");
-  static constexpr uint32_t D2COL = 2 * BMAX;          // D1 x2, then D2 x2 (PNB columns each)
-  static constexpr uint32_t TMEM_COLS = (2 * BMAX + 2 * PNB <= 256) ? 256 : 512;
+  static constexpr uint32_t D1LO = 2 * BMAX;           // SPLIT: Lhat lo x2 after Lhat (hi) x2
+  static constexpr uint32_t D2COL = NOP * 2 * BMAX;    // then D2 x2 (PNB columns each)
+  static constexpr uint32_t TMEM_COLS = (D2COL + 2 * PNB <= 256) ? 256 : 512;
+  static_assert(D2COL + 2 * PNB <= 512, "tensor memory");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-template <int BMAX, int TR>
-__global__ void __launch_bounds__(kPThreads, 1)
+template <int BMAX, int TR, bool SPLIT>
+__global__ void __launch_bounds__(PCfg<BMAX, TR, SPLIT>::THREADS, 1)
     k_update_tf32p(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmX,
-                   const __grid_constant__ CUtensorMap tmQ,
-                   const __grid_constant__ CUtensorMap tmQT, float* __restrict__ L, long long ldl, long long n,
+                   const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmQlo,
+                   const __grid_constant__ CUtensorMap tmQT, const __grid_constant__ CUtensorMap tmQTlo,
+                   float* __restrict__ L, long long ldl, long long n,
                    long long d, int prows, const int* __restrict__ mark, double* __restrict__ dvec,
                    double* __restrict__ partials, State* st, int c0) {
-  using C = PCfg<BMAX, TR>;
+  using C = PCfg<BMAX, TR, SPLIT>;
   constexpr int PS1 = C::PS1, PS3 = C::PS3;
   pdl_wait();
   if (st->done) return;
@@ -494,6 +503,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
   auto d2_empty = [&](int b) { return x0 + 48u + 8u * b; };
   uint32_t* tmem_slot = (uint32_t*)(smem + (x0 + 64u - sb));
   const uint32_t drain1 = x0 + 72u, drain3 = x0 + 80u;  // abort path: MMA drains of GEMM 1 / GEMM 2
+  auto lhat_ready = [&](int b) { return x0 + 88u + 8u * b; };  // SPLIT: Lhat hi/lo written back
+  auto conv1 = [&](int s) { return x0 + 104u + 8u * s; };     // SPLIT: R lo of stage s written
+  static_assert(8 * (2 * PS1 + 3 * PS3 + 2 * PSB) + 104 + 8 * PS1 <= C::BAR_BYTES, "barrier area");
 
   __shared__ int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -537,6 +549,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     }
     mbar_init(drain1, 1);
     mbar_init(drain3, 1);
+    for (int b = 0; b < 2; ++b) mbar_init(lhat_ready(b), 128);
+    for (int s = 0; s < PS1; ++s) mbar_init(conv1(s), 128);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -566,10 +580,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(full1(s), a1_bytes + (uint32_t)C::B1);
+          mbar_expect_tx(full1(s), a1_bytes + (uint32_t)(C::NOP * C::B1));
           const uint32_t base = sb + s * C::ST1;
           tma_load_2d_hint(base, tmSrc, full1(s), kc * BK1, (int)(ptile(tile) * prows), keep);
           tma_load_2d(base + C::A1, &tmQ, full1(s), kc * BK1, 0);
+          if (SPLIT) tma_load_2d(base + 2 * C::A1 + C::B1, &tmQlo, full1(s), kc * BK1, 0);
         }
       }
       fills = g;
@@ -587,15 +602,22 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const uint32_t dt = tmem + (uint32_t)(buf * BMAX);
         for (int kc = 0; kc < nK1; ++kc, ++g) {
           const int s = (int)(g % PS1);
-          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort, lim)) {
+          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort, lim) ||
+              (SPLIT && !mbar_wait(conv1(s), (g / PS1) & 1u, abort, lim))) {
             ok = false;
             break;
           }
           tc_after();
           const uint32_t a = sb + s * C::ST1, b = a + C::A1;
+          const uint32_t alo = b + C::B1, blo = alo + C::A1;
 #pragma unroll
-          for (int kk = 0; kk < BK1 / 8; ++kk)
+          for (int kk = 0; kk < BK1 / 8; ++kk) {
             mma_tf32(dt, sdesc(a + kk * 32), sdesc(b + kk * 32), id1, (kc | kk) != 0 ? 1u : 0u);
+            if (SPLIT) {
+              mma_tf32(dt, sdesc(a + kk * 32), sdesc(blo + kk * 32), id1, 1u);
+              mma_tf32(dt, sdesc(alo + kk * 32), sdesc(b + kk * 32), id1, 1u);
+            }
+          }
           mma_commit(empty1(s));
         }
         if (!ok) break;
@@ -637,10 +659,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(fullb(s), (uint32_t)C::B2);
-          const uint32_t base = sb + C::OFFB + s * C::B2;
+          mbar_expect_tx(fullb(s), (uint32_t)(C::NOP * C::B2));
+          const uint32_t base = sb + C::OFFB + s * C::NOP * C::B2;
 #pragma unroll
-          for (int a = 0; a < BMAX / 32; ++a) tma_load_2d(base + a * C::B2A, &tmQT, fullb(s), a * 32, j * PNB);
+          for (int a = 0; a < BMAX / 32; ++a) {
+            tma_load_2d(base + a * C::B2A, &tmQT, fullb(s), a * 32, j * PNB);
+            if (SPLIT) tma_load_2d(base + C::B2 + a * C::B2A, &tmQTlo, fullb(s), a * 32, j * PNB);
+          }
         }
       }
       fills = g;
@@ -654,9 +679,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
       bool ok = true;
       for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int dbuf = it & 1;
-        if (!mbar_wait(d1_full(dbuf), (it >> 1) & 1u, abort, lim)) break;
+        // the plain form reads Lhat from the GEMM-1 accumulator; the split form waits for
+        // the epilogue's hi and lo halves
+        if (!mbar_wait(SPLIT ? lhat_ready(dbuf) : d1_full(dbuf), (it >> 1) & 1u, abort, lim)) break;
         tc_after();
         const uint32_t a1 = tmem + (uint32_t)(dbuf * BMAX);
+        const uint32_t a1lo = tmem + C::D1LO + (uint32_t)(dbuf * BMAX);
         for (int jj = 0; jj < nJ; ++jj, ++g) {
           const int s = (int)(g % PSB);
           const int buf = g & 1;
@@ -666,10 +694,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
           tc_after();
           const uint32_t dt = tmem + C::D2COL + (uint32_t)(buf * PNB);
-          const uint32_t b2 = sb + C::OFFB + s * C::B2;
+          const uint32_t b2 = sb + C::OFFB + s * C::NOP * C::B2;
           for (int q = 0; q < nk2; ++q) {
             const int a = q >> 2, kk = q & 3;
             mma_tf32_ta(dt, a1 + (uint32_t)(q * 8), sdesc(b2 + a * C::B2A + kk * 32), id2, q != 0 ? 1u : 0u);
+            if (SPLIT) {
+              mma_tf32_ta(dt, a1 + (uint32_t)(q * 8), sdesc(b2 + C::B2 + a * C::B2A + kk * 32), id2, 1u);
+              mma_tf32_ta(dt, a1lo + (uint32_t)(q * 8), sdesc(b2 + a * C::B2A + kk * 32), id2, 1u);
+            }
           }
           mma_commit(emptyb(s));
           mma_commit(d2_full(buf));
@@ -699,12 +731,32 @@ __global__ void __launch_bounds__(kPThreads, 1)
       if (BMAX > 32) tmem_ld32(tmem + lane_base + (uint32_t)(dbuf * BMAX) + 32u, *(uint32_t(*)[32])&v[32 % BMAX]);
       tmem_wait_ld();
       tc_before();
-      mbar_arrive(d1_empty(dbuf));
+      if (!SPLIT) mbar_arrive(d1_empty(dbuf));
       if (in) {
         float* lrow = L + row * ldl + kcol;
 #pragma unroll
         for (int jx = 0; jx < BMAX; ++jx)
           if (jx < bp) lrow[jx] = __uint_as_float(v[jx]);
+      }
+      if (SPLIT) {
+        // Lhat's TF32 hi (over the accumulator) and lo halves, GEMM 2's A operand
+#pragma unroll
+        for (int cb = 0; cb < BMAX / 32; ++cb) {
+          uint32_t h[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float x = __uint_as_float(v[32 * cb + j]);
+            const float hi = tf32_rn(x);
+            h[j] = __float_as_uint(hi);
+            v[32 * cb + j] = __float_as_uint(tf32_rn(x - hi));
+          }
+          tmem_st32(tmem + lane_base + (uint32_t)(dbuf * BMAX + 32 * cb), h);
+          tmem_st32(tmem + lane_base + C::D1LO + (uint32_t)(dbuf * BMAX + 32 * cb), *(uint32_t(*)[32])&v[32 * cb]);
+        }
+        tmem_wait_st();
+        tc_before();
+        mbar_arrive(lhat_ready(dbuf));
+        mbar_arrive(d1_empty(dbuf));
       }
       // GEMM 2 chunks, 32-column pieces: R -= Lhat Q', row norms, accepted rows zeroed
       float nrm = 0.f;  // FP32: the residual itself carries TF32 rounding
@@ -794,6 +846,34 @@ __global__ void __launch_bounds__(kPThreads, 1)
       if (g > 0) mbar_arrive(empty3((int)((g - 1) % PS3)));
       tma_wait_all0();
     }
+  } else if (SPLIT && warp >= 10) {
+    // ---------------- converters (split form): each ring-1 R chunk into its TF32 hi (in
+    // place) and lo halves, thread <-> row, 16-byte pieces in a bank-spread order
+    const int r = 32 * (warp - 10) + lane;
+    uint32_t g = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int kc = 0; kc < nK1; ++kc, ++g) {
+        const int s = (int)(g % PS1);
+        if (!mbar_wait(full1(s), (g / PS1) & 1u, abort, lim)) {
+          ok = false;
+          break;
+        }
+        uint8_t* a = smem + s * C::ST1 + (r >> 3) * 1024 + (r & 7) * 128;
+        uint8_t* alo = a + C::A1 + C::B1;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          const int cc = (ch ^ (r & 7)) * 16;
+          const float4 x = *(const float4*)(a + cc);
+          const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+          *(float4*)(a + cc) = h;
+          *(float4*)(alo + cc) =
+              make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
+        }
+        fence_async_smem();
+        mbar_arrive(conv1(s));
+      }
+    }
   }
 
   tc_before();
@@ -864,30 +944,39 @@ int device_sms() {
   return sms[dev];
 }
 
-template <int BMAX, int TR>
-cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, long long qrows,
-                        long long ldp, const float* QpT, long long qtcols, long long ldpt, float* L, long long ldl,
-                        const int* mark, double* dvec, double* partials, const State* st, int c0, cudaStream_t s,
-                        const float* X0, long long ldx0) {
-  using C = PCfg<BMAX, TR>;
+template <int BMAX, int TR, bool SPLIT>
+cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,
+                        long long qrows, long long ldp, const float* QpT, const float* QpT_lo, long long qtcols,
+                        long long ldpt, float* L, long long ldl, const int* mark, double* dvec, double* partials,
+                        const State* st, int c0, cudaStream_t s, const float* X0, long long ldx0) {
+  using C = PCfg<BMAX, TR, SPLIT>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static std::atomic<unsigned long long> attr_set{0};  // one bit per device
   if (dev >= 64 || !(attr_set.load() >> dev & 1ULL)) {
-    e = cudaFuncSetAttribute(k_update_tf32p<BMAX, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    e = cudaFuncSetAttribute(k_update_tf32p<BMAX, TR, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     if (dev < 64) attr_set.fetch_or(1ULL << dev);
   }
-  CUtensorMap mR, mX, mQ, mQT;
+  CUtensorMap mR, mX, mQ, mQT, mQlo, mQTlo;
   const PTiles pt = ptiles(n, device_sms(), TR);
   if (!make_map(&mR, R, d, n, ldr * 4, 32, pt.prows)) return cudaErrorInvalidValue;
   if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, pt.prows) : false) return cudaErrorInvalidValue;
   if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
   if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
-  return counted(launch_pdl(k_update_tf32p<BMAX, TR>, dim3(pt.grid), dim3(kPThreads), (size_t)C::SMEM, s, mR, mX, mQ, mQT,
-                            L, ldl, n, d, pt.prows, mark, dvec, partials, const_cast<State*>(st), c0));
+  if (SPLIT) {
+    if (!Qp_lo || !QpT_lo) return cudaErrorInvalidValue;
+    if (!make_map(&mQlo, Qp_lo, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
+    if (!make_map(&mQTlo, QpT_lo, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
+  } else {
+    mQlo = mQ;
+    mQTlo = mQT;
+  }
+  return counted(launch_pdl(k_update_tf32p<BMAX, TR, SPLIT>, dim3(pt.grid), dim3(C::THREADS), (size_t)C::SMEM, s, mR,
+                            mX, mQ, mQlo, mQT, mQTlo, L, ldl, n, d, pt.prows, mark, dvec, partials,
+                            const_cast<State*>(st), c0));
 }
 
 // ------------------------------------------------------------------ host side
@@ -960,7 +1049,7 @@ cudaError_t launch_cfg(float* R, long long ldr, long long n, long long d, const 
 // Partial sums the update leaves for launch_finalize_block: 4 per CTA of the
 // persistent form (one CTA per SM, at most one per tile), or 2 per 64-row tile.
 int update_tf32_parts(long long n, int bmax, int split) {
-  if (!split && bmax <= 64) return 4 * (int)tc::ptiles(n, tc::device_sms(), tc::kPTileRows).grid;
+  if (bmax <= 64) return 4 * (int)tc::ptiles(n, tc::device_sms(), split ? 128 : tc::kPTileRows).grid;
   return 2 * (int)((n + tc::ROWS - 1) / tc::ROWS);
 }
 
@@ -984,17 +1073,16 @@ cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d
   const long long qrows = ldpt - c0, qtcols = ldpt - c0;
 #define RBRP_TC_ARGS \
   R, ldr, n, d, Qc, Qlc, qrows, ldp, QTc, QTlc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0, s, X0, ldx0
+#define RBRP_TCP_ARGS \
+  R, ldr, n, d, Qc, Qlc, qrows, ldp, QTc, QTlc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0, s, X0, ldx0
   if (split) {
-    if (bmax <= 32) return tc::launch_cfg<32, true>(RBRP_TC_ARGS);
-    if (bmax <= 64) return tc::launch_cfg<64, true>(RBRP_TC_ARGS);
+    if (bmax <= 32) return tc::launch_pcfg<32, 128, true>(RBRP_TCP_ARGS);
+    if (bmax <= 64) return tc::launch_pcfg<64, 128, true>(RBRP_TCP_ARGS);
     return cudaErrorInvalidValue;
   }
-  if (bmax <= 32)
-    return tc::launch_pcfg<32, tc::kPTileRows>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
-                               s, X0, ldx0);
-  if (bmax <= 64)
-    return tc::launch_pcfg<64, tc::kPTileRows>(R, ldr, n, d, Qc, qrows, ldp, QTc, qtcols, ldpt, L, ldl, mark, dvec, partials, st, c0,
-                               s, X0, ldx0);
+  if (bmax <= 32) return tc::launch_pcfg<32, tc::kPTileRows, false>(RBRP_TCP_ARGS);
+  if (bmax <= 64) return tc::launch_pcfg<64, tc::kPTileRows, false>(RBRP_TCP_ARGS);
+#undef RBRP_TCP_ARGS
   if (bmax <= 128) return tc::launch_cfg<128, false>(RBRP_TC_ARGS);
 #undef RBRP_TC_ARGS
   return cudaErrorInvalidValue;
