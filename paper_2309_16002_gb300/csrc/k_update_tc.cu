@@ -442,14 +442,17 @@ struct PCfg {
   static_assert(!SPLIT || TR == 128, "the split form uses 128-row stages");
   static_assert(TR <= PROWS, "the MMA's M bounds the tile height");
   static constexpr int NOP = SPLIT ? 2 : 1;           // hi (and lo) copies of an operand
-  static constexpr int PS1 = SPLIT ? 2 : (TR == 128 ? 4 : (TR == 96 ? 5 : 6));   // ring-1 stages
+  static constexpr int PS1 = SPLIT ? 3 : (TR == 128 ? 4 : (TR == 96 ? 5 : 6));   // ring-1 stages
   static constexpr int PS3 = SPLIT ? 3 : (TR == 128 ? 6 : (TR == 96 ? 7 : 12));  // ring-3 stages
+  // GEMM-2 chunk width (MMA N): the split form's 64 leaves room for a third ring-1 stage
+  static constexpr int NB = SPLIT ? 64 : PNB;
+  static constexpr int PC = NB / NB2;                 // 32-column epilogue pieces per chunk
   static constexpr int THREADS = SPLIT ? 448 : 320;
   static constexpr int A1 = TR * BK1 * 4;             // one R chunk (prows * 128 bytes filled)
   static constexpr int B1 = BMAX * BK1 * 4;           // Q' chunk
   static constexpr int ST1 = NOP * (A1 + B1);
   static constexpr int R3 = TR * NB2 * 4;             // one R piece
-  static constexpr int B2A = PNB * 128;               // one 32-wide K atom of a Q'^T chunk (16 KB)
+  static constexpr int B2A = NB * 128;                // one 32-wide K atom of a Q'^T chunk
   static constexpr int B2 = (BMAX / 32) * B2A;        // one half (hi or lo) of a Q'^T chunk
   static constexpr int OFF3 = PS1 * ST1;
   static constexpr int OFFB = OFF3 + PS3 * R3;
@@ -458,9 +461,9 @@ struct PCfg {
   static constexpr int SMEM = BAR_OFF + BAR_BYTES + 1024;
   static_assert(ST1 % 1024 == 0 && A1 % 1024 == 0 && R3 % 1024 == 0, "swizzle atoms");
   static constexpr uint32_t D1LO = 2 * BMAX;           // SPLIT: Lhat lo x2 after Lhat (hi) x2
-  static constexpr uint32_t D2COL = NOP * 2 * BMAX;    // then D2 x2 (PNB columns each)
-  static constexpr uint32_t TMEM_COLS = (D2COL + 2 * PNB <= 256) ? 256 : 512;
-  static_assert(D2COL + 2 * PNB <= 512, "tensor memory");
+  static constexpr uint32_t D2COL = NOP * 2 * BMAX;    // then D2 x2 (NB columns each)
+  static constexpr uint32_t TMEM_COLS = (D2COL + 2 * NB <= 256) ? 256 : 512;
+  static_assert(D2COL + 2 * NB <= 512, "tensor memory");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -513,6 +516,7 @@ __global__ void __launch_bounds__(PCfg<BMAX, TR, SPLIT>::THREADS, 1)
   const int N1 = (bp + 15) / 16 * 16;
   const int tno = (int)(st->t + 1);
   const int nK1 = (int)((d + BK1 - 1) / BK1);  // 32-column chunks of GEMM 1 (and epilogue pieces)
+  constexpr int PNB = C::NB, PPC = C::PC;      // this form's GEMM-2 chunk width and pieces
   const int nJ = (int)((d + PNB - 1) / PNB);   // GEMM-2 chunks
   const long long ntiles = (n + prows - 1) / prows;
   const uint32_t a1_bytes = (uint32_t)(prows * BK1 * 4), r3_bytes = (uint32_t)(prows * NB2 * 4);
@@ -965,11 +969,11 @@ cudaError_t launch_pcfg(float* R, long long ldr, long long n, long long d, const
   if (X0 ? !make_map(&mX, X0, d, n, ldx0 * 4, 32, pt.prows) : false) return cudaErrorInvalidValue;
   if (!X0) mX = mR;
   if (!make_map(&mQ, Qp, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
-  if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
+  if (!make_map(&mQT, QpT, qtcols, d, ldpt * 4, 32, C::NB)) return cudaErrorInvalidValue;
   if (SPLIT) {
     if (!Qp_lo || !QpT_lo) return cudaErrorInvalidValue;
     if (!make_map(&mQlo, Qp_lo, d, qrows, ldp * 4, 32, BMAX)) return cudaErrorInvalidValue;
-    if (!make_map(&mQTlo, QpT_lo, qtcols, d, ldpt * 4, 32, PNB)) return cudaErrorInvalidValue;
+    if (!make_map(&mQTlo, QpT_lo, qtcols, d, ldpt * 4, 32, C::NB)) return cudaErrorInvalidValue;
   } else {
     mQlo = mQ;
     mQTlo = mQT;
