@@ -474,9 +474,10 @@ def run_ours(a):
                "profiled_pass_ms_per_step": prof_ms,
                "note": "update and W-solve times from the profiled pass (same steps, host-queued blocks, "
                        "an event pair around every update launch and W solve); other = timed ms - both"}
-    persistent = a.precision == "tf32" and a.block <= 64
+    # the persistent kernel runs plain TF32 at b <= 64 and every 3xTF32 block (64-column chunks)
+    persistent = (a.precision == "tf32" and a.block <= 64) or a.precision == "tf32x3"
     kname = ("k_update_tf32p" if persistent else "k_update_tf32") if a.precision.startswith("tf32") else "update_simt"
-    captured = UPD_TRAFFIC_PER_ROW * n if (persistent and d == UPD_TRAFFIC_D) else None
+    captured = UPD_TRAFFIC_PER_ROW * n if (a.precision == "tf32" and a.block <= 64 and d == UPD_TRAFFIC_D) else None
     traffic = captured if UPD_TRAFFIC_CURRENT else None
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": (upd_gbs / hbm) if upd_gbs else None,
