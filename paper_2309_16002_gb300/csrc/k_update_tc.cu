@@ -433,9 +433,10 @@ constexpr int kPTileRows = 128;   // TR of the form the dispatch launches
 
 // TR: the largest tile height (rows per stage); shorter stages give deeper rings in
 // the same shared memory.  Ring 1 holds R and Q' chunks, ring 3 the re-read R pieces.
-// SPLIT: the 3xTF32 form (hi*hi + hi*lo + lo*hi): ring 1 holds [R hi][Q' hi][R lo][Q' lo]
-// (four converter warps split R in place), the Q'^T stage its hi and lo halves, and
-// tensor memory Lhat's hi and lo halves (the epilogue writes them back as GEMM 2's A).
+// SPLIT: the 3xTF32 form (hi*hi + hi*lo + lo*hi): ring 1 holds [R][Q' hi][R lo][Q' lo]
+// (R as loaded serves as its hi half; four converter warps write R lo), the Q'^T stage
+// its hi and lo halves, and tensor memory Lhat's hi and lo halves (the epilogue writes
+// them back as GEMM 2's A).
 template <int BMAX, int TR, bool SPLIT = false>
 struct PCfg {
   static_assert(TR == 128 || TR == 96 || TR == 64, "tile height");
@@ -606,21 +607,28 @@ __global__ void __launch_bounds__(PCfg<BMAX, TR, SPLIT>::THREADS, 1)
         const uint32_t dt = tmem + (uint32_t)(buf * BMAX);
         for (int kc = 0; kc < nK1; ++kc, ++g) {
           const int s = (int)(g % PS1);
-          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort, lim) ||
-              (SPLIT && !mbar_wait(conv1(s), (g / PS1) & 1u, abort, lim))) {
+          if (!mbar_wait(full1(s), (g / PS1) & 1u, abort, lim)) {
             ok = false;
             break;
           }
           tc_after();
           const uint32_t a = sb + s * C::ST1, b = a + C::A1;
           const uint32_t alo = b + C::B1, blo = alo + C::A1;
+          // R hi is the chunk as loaded (the MMA reads FP32 as TF32, dropping the low 13 bits):
+          // hi*hi and hi*lo start at once, lo*hi once the converters have written R lo
 #pragma unroll
           for (int kk = 0; kk < BK1 / 8; ++kk) {
             mma_tf32(dt, sdesc(a + kk * 32), sdesc(b + kk * 32), id1, (kc | kk) != 0 ? 1u : 0u);
-            if (SPLIT) {
-              mma_tf32(dt, sdesc(a + kk * 32), sdesc(blo + kk * 32), id1, 1u);
-              mma_tf32(dt, sdesc(alo + kk * 32), sdesc(b + kk * 32), id1, 1u);
+            if (SPLIT) mma_tf32(dt, sdesc(a + kk * 32), sdesc(blo + kk * 32), id1, 1u);
+          }
+          if (SPLIT) {
+            if (!mbar_wait(conv1(s), (g / PS1) & 1u, abort, lim)) {
+              ok = false;
+              break;
             }
+            tc_after();
+#pragma unroll
+            for (int kk = 0; kk < BK1 / 8; ++kk) mma_tf32(dt, sdesc(alo + kk * 32), sdesc(b + kk * 32), id1, 1u);
           }
           mma_commit(empty1(s));
         }
@@ -851,8 +859,9 @@ __global__ void __launch_bounds__(PCfg<BMAX, TR, SPLIT>::THREADS, 1)
       tma_wait_all0();
     }
   } else if (SPLIT && warp >= 10) {
-    // ---------------- converters (split form): each ring-1 R chunk into its TF32 hi (in
-    // place) and lo halves, thread <-> row, 16-byte pieces in a bank-spread order
+    // ---------------- converters (split form): R lo = R - hi of each ring-1 R chunk, hi
+    // being R with its low 13 mantissa bits dropped (what the MMA reads from the FP32 chunk),
+    // rounded to TF32; thread <-> row, 16-byte pieces in a bank-spread order
     const int r = 32 * (warp - 10) + lane;
     uint32_t g = 0;
     bool ok = true;
@@ -869,10 +878,9 @@ __global__ void __launch_bounds__(PCfg<BMAX, TR, SPLIT>::THREADS, 1)
         for (int ch = 0; ch < 8; ++ch) {
           const int cc = (ch ^ (r & 7)) * 16;
           const float4 x = *(const float4*)(a + cc);
-          const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-          *(float4*)(a + cc) = h;
-          *(float4*)(alo + cc) =
-              make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
+          auto tr = [](float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); };
+          *(float4*)(alo + cc) = make_float4(tf32_rn(x.x - tr(x.x)), tf32_rn(x.y - tr(x.y)), tf32_rn(x.z - tr(x.z)),
+                                             tf32_rn(x.w - tr(x.w)));
         }
         fence_async_smem();
         mbar_arrive(conv1(s));
