@@ -59,7 +59,7 @@ typedef enum {
                    /* of the drawn rows and of Q, ONE projection pass against Q   */
                    /* with FP32 products, FP32 Gram matrix and FP32 pivoted       */
                    /* Cholesky filter, Q' = Lc^{-1} V_perm in FP32 (b <= 128; the */
-                   /* FP64 chain takes b <= 256, in 128-column chunks of Q').     */
+                   /* FP64 chain takes b <= 256, in 64-column chunks of Q').      */
   RBRP_FP32 = 2,   /* R in FP32, update on CUDA cores in FP32.  Default chain:    */
                    /* FP64 storage of V and Q, two projection passes (CGS2) with  */
                    /* FP32 products, FP64 Gram and filter, one FP64 CholQR pass   */

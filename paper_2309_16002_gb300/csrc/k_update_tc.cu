@@ -1066,8 +1066,10 @@ int update_tf32_parts(long long n, int bmax, int split) {
 }
 
 int update_tf32_chunk(int ldpt, int split) {
-  if (split) return ldpt < 64 ? ldpt : 64;
-  return ldpt <= 64 ? ldpt : 128;
+  // both forms run on the persistent kernel in chunks of up to 64 columns (a plain TF32
+  // launch of 128 columns on the 64-row kernel measured slower than two persistent passes)
+  (void)split;
+  return ldpt < 64 ? ldpt : 64;
 }
 
 cudaError_t launch_update_tf32(float* R, long long ldr, long long n, long long d, const float* Qp, const float* Qp_lo,

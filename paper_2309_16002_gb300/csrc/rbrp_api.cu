@@ -539,8 +539,7 @@ cudaError_t enqueue_chain(const Plan& p, const Bufs& u, const rbrp_opts* o, cuda
     const int split = (p.prec == RBRP_TF32X3);
     if (!(p.f32 && filter_f32_writes_factor((int)p.b)))  // else the Q' substitution wrote them
       LK(launch_qp_lowp(u.Qt, !p.f32, p.ldq, u.Qp, u.Qp_lo, p.ldp, u.QpT, u.QpT_lo, p.ldpt, d, (int)p.ldpt, st, s));
-    // blocks wider than one launch (3xTF32 above 64 columns, TF32 above 128) run as
-    // successive column chunks of Q'
+    // blocks wider than one launch (above 64 columns) run as successive column chunks of Q'
     const int cw = update_tf32_chunk((int)p.ldpt, split);
     LK(timed(g_prof.upd, s, [&] {
       cudaError_t ce = cudaSuccess;
