@@ -1,27 +1,38 @@
 // Fused residual update of RBRP on Blackwell tensor cores (sm_103a).
 //
-// Alg. 2's update step in the residual form: for every 128-row tile of R,
+// Alg. 2's update step in the residual form: for every tile of rows of R,
 //   Lhat = R_tile Q'^T            (GEMM 1, K = d, N = b'_pad)
-//   R_tile <- R_tile - Lhat Q'    (GEMM 2, K = b'_pad, N = d in 32-column chunks)
+//   R_tile <- R_tile - Lhat Q'    (GEMM 2, K = b'_pad, N = d in column chunks)
 //   d_i = ||R_i||^2, rows accepted in this block set to 0,
 //   Lhat written to L(:, k : k + b').
 // Operands are staged by TMA (128-byte swizzle) and multiplied by tcgen05.mma
-// kind::tf32 with FP32 accumulators in tensor memory.  Lhat goes TMEM ->
-// registers -> (global L, shared-memory A operand of GEMM 2).  The R tile is
-// read twice (GEMM 1 and the subtraction); the second read is served by L2.
+// kind::tf32 with FP32 accumulators in tensor memory.  The R tile is read twice
+// (GEMM 1 and the subtraction); the second read is mostly served by L2.
 //
-// SPLIT = true is the 3xTF32 form: every operand x is split into hi = x with
-// the low 13 mantissa bits cleared (exact in TF32) and lo = x - hi, and each
-// product is hi*hi + hi*lo + lo*hi.  That brings the contraction to ~FP32
-// accuracy, so the residual does not pick up the per-block floor that plain
-// TF32 leaves (relative energy ~u^2 with u = 2^-11).
+// Two kernels:
+//  - k_update_tf32p, the update itself: persistent (one CTA per SM walking tiles
+//    of up to 128 rows), b'_pad <= 64 columns of Q' a launch (wider blocks run as
+//    successive 64-column chunks), plain TF32 or the 3xTF32 split (SPLIT), with
+//    Lhat kept in tensor memory as GEMM 2's A operand.  Its roles and rings are
+//    described where it is defined.
+//  - k_update_tf32, non-persistent 64-row tiles: with G1 it computes only Lhat =
+//    X Q'^T for the downdate form of the update step (3xTF32), and it serves a
+//    direct plain-TF32 call with up to 128 columns.
 //
-// Roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 owns TMEM and
-// lane 0 issues the MMAs, warps 2-5 (128 threads, one row each) split the
-// GEMM-1 A operand (SPLIT), run the epilogues and issue the TMA stores.  The
-// row norms are summed in FP32 over each 32-column chunk and the chunk sums in
+// The 3xTF32 split: every operand x is taken as hi + lo with hi a TF32 value and
+// lo = x - hi rounded to TF32, and each product is hi*hi + hi*lo + lo*hi; that
+// brings the contraction to ~FP32 accuracy, so the residual does not pick up the
+// per-block floor that plain TF32 leaves (relative energy ~u^2 with u = 2^-11).
+// Q' and Lhat are split with hi rounded to nearest; in the persistent kernel the
+// R chunk as loaded is its own hi half (the MMA reads FP32 as TF32 by dropping the
+// low 13 mantissa bits) and lo is taken against that truncation.
+//
+// k_update_tf32's roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1
+// owns TMEM and lane 0 issues the MMAs, warps 2-5 (128 threads, one row each)
+// split the GEMM-1 A operand (SPLIT), run the epilogues and issue the TMA stores.
+// Row norms are summed in FP32 over each 32-column piece and the piece sums in
 // FP64 (per-element FP64 arithmetic would cost ~2 FMA/clock/SM on GB300).
-// Every mbarrier wait is bounded: after the limit the CTA records
+// Every mbarrier wait of both kernels is bounded: after the limit the CTA records
 // RBRP_ETIMEOUT in the State, stops issuing work, waits for the TMA copies and
 // MMAs it has issued (drain_ring / drain_mma), frees its TMEM and returns.
 #include <cuda.h>
