@@ -36,14 +36,16 @@ def _timed_out(G, Xd, tol, ws, **kw):
     return e.value.status
 
 
-def test_update_mbarrier_wait_gives_up_and_workspace_recovers(G):
-    """Persistent tensor-core update (TF32, b = 64): its first wait on a TMA load cannot be
-    met within one poll, so the CTA aborts, drains its own copies and MMAs, frees its tensor
-    memory and reports RBRP_ETIMEOUT; the next call on the same workspace is exact again."""
+@pytest.mark.parametrize("precision", ["tf32", "tf32x3"])
+def test_update_mbarrier_wait_gives_up_and_workspace_recovers(G, precision):
+    """Persistent tensor-core update (TF32 or its 3xTF32 split, b = 64): its first wait on a
+    TMA load (or, split, on the converter warps) cannot be met within one poll, so the CTA
+    aborts, drains its own copies and MMAs, frees its tensor memory and reports RBRP_ETIMEOUT;
+    the next call on the same workspace is exact again."""
     import torch
     X, _ = WL.spectral(n=6000, d=300, rate=0.93, seed=31, dtype=np.float32)
     Xd = torch.from_numpy(X).to("cuda:0")
-    kw = dict(block=64, seed=2, precision="tf32")
+    kw = dict(block=64, seed=2, precision=precision)
     ws = G.Workspace(*X.shape, G.make_opts(**kw), Xd.device)
     try:
         G.set_wait_limits(1, 0)
